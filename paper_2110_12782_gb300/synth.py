@@ -1,0 +1,200 @@
+"""Seeded synthetic graphs (the inputs of every test and benchmark).
+
+This module holds none of SketchNE's arithmetic: it only draws undirected,
+unweighted graphs with NumPy's PCG64 generator and returns them as symmetric
+CSR arrays (both directions of every edge stored, columns sorted within each
+row, no self-loops, no duplicate edges).  The oracle, the tests and the
+benchmark all take their graphs from here, so that both sides of every parity
+check see the same input.
+
+Graph families (stand-ins for the paper's datasets of Table 1):
+
+* ``sbm``: stochastic block model with equal blocks.  Every vertex pair is an
+  edge independently with probability ``p_in`` (same block) or ``p_out``;
+  drawn exactly in distribution as a binomial edge count per block pair
+  followed by a uniform choice of that many distinct pairs.
+* ``chung_lu``: power-law Chung-Lu graph.  Vertex weights
+  ``w_i ~ (i + i0)^(-1/(gamma-1))`` are scaled to the target mean degree and
+  capped at ``sqrt(sum w)``; ``sum(w)/2`` endpoint pairs are drawn i.i.d. with
+  probability proportional to ``w``; self-loops and repeats are dropped.
+  Vertex ids are therefore sorted by expected degree (id 0 is the largest hub).
+* ``complete_graph``, ``complete_bipartite_union``, ``from_edges``: small
+  graphs with closed-form spectra, used to pin the oracle.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Graph:
+    """Symmetric CSR: ``row_ptr`` int64 [n+1], ``col_idx`` int32 [nnz]."""
+
+    n: int
+    row_ptr: np.ndarray
+    col_idx: np.ndarray
+    name: str = ""
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+    def degrees(self) -> np.ndarray:
+        return np.diff(self.row_ptr).astype(np.int64)
+
+
+def _csr_from_undirected_pairs(n: int, i: np.ndarray, j: np.ndarray, name: str = "") -> Graph:
+    """Build a symmetric CSR from undirected pairs (self-loops and repeats removed)."""
+    i = np.asarray(i, dtype=np.int64)
+    j = np.asarray(j, dtype=np.int64)
+    keep = i != j
+    i, j = i[keep], j[keep]
+    lo = np.minimum(i, j)
+    hi = np.maximum(i, j)
+    key = np.unique(lo * n + hi)
+    lo = key // n
+    hi = key % n
+    src = np.concatenate([lo, hi])
+    dst = np.concatenate([hi, lo])
+    order = np.lexsort((dst, src))
+    src = src[order]
+    dst = dst[order]
+    counts = np.bincount(src, minlength=n)
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    return Graph(n=n, row_ptr=row_ptr, col_idx=dst.astype(np.int32), name=name)
+
+
+def from_edges(n: int, edges, name: str = "") -> Graph:
+    e = np.asarray(list(edges), dtype=np.int64).reshape(-1, 2)
+    return _csr_from_undirected_pairs(n, e[:, 0], e[:, 1], name=name)
+
+
+def complete_graph(n: int) -> Graph:
+    i, j = np.triu_indices(n, k=1)
+    return _csr_from_undirected_pairs(n, i, j, name=f"K{n}")
+
+
+def complete_bipartite_union(parts) -> Graph:
+    """Disjoint union of complete bipartite graphs K_{a,b}, one per (a, b) in ``parts``."""
+    src, dst = [], []
+    base = 0
+    for a, b in parts:
+        left = np.arange(base, base + a)
+        right = np.arange(base + a, base + a + b)
+        ii, jj = np.meshgrid(left, right, indexing="ij")
+        src.append(ii.ravel())
+        dst.append(jj.ravel())
+        base += a + b
+    return _csr_from_undirected_pairs(base, np.concatenate(src), np.concatenate(dst),
+                                      name="Kab-union")
+
+
+def _decode_triangle(idx: np.ndarray, m: int):
+    """Map a linear index over the pairs (i < j) of an m-set to (i, j)."""
+    idx = idx.astype(np.int64)
+    # row i starts at s(i) = i*(2m - i - 1)/2
+    b = 2 * m - 1
+    i = np.floor((b - np.sqrt(np.maximum(b * b - 8.0 * idx, 0.0))) / 2.0).astype(np.int64)
+    i = np.clip(i, 0, m - 2)
+
+    def start(r):
+        return r * (2 * m - r - 1) // 2
+
+    # correct floating-point rounding of the square root
+    for _ in range(3):
+        i = np.where(start(i) > idx, i - 1, i)
+        i = np.where(start(i + 1) <= idx, i + 1, i)
+    j = idx - start(i) + i + 1
+    return i, j
+
+
+def sbm(n: int, blocks: int, p_in: float, p_out: float, seed: int = 0) -> Graph:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    bounds = np.linspace(0, n, blocks + 1).round().astype(np.int64)
+    src, dst = [], []
+    for a in range(blocks):
+        for b in range(a, blocks):
+            na = bounds[a + 1] - bounds[a]
+            nb = bounds[b + 1] - bounds[b]
+            if a == b:
+                npairs = na * (na - 1) // 2
+                p = p_in
+            else:
+                npairs = na * nb
+                p = p_out
+            if npairs == 0 or p <= 0:
+                continue
+            cnt = int(rng.binomial(npairs, p))
+            if cnt == 0:
+                continue
+            pick = rng.choice(npairs, size=cnt, replace=False)
+            if a == b:
+                ii, jj = _decode_triangle(pick, int(na))
+            else:
+                ii, jj = pick // nb, pick % nb
+            src.append(ii + bounds[a])
+            dst.append(jj + bounds[b])
+    if not src:
+        return _csr_from_undirected_pairs(n, np.zeros(0), np.zeros(0), name="sbm")
+    return _csr_from_undirected_pairs(n, np.concatenate(src), np.concatenate(dst),
+                                      name=f"sbm(n={n},B={blocks},pin={p_in},pout={p_out},seed={seed})")
+
+
+def chung_lu(n: int, avg_degree: float, gamma: float, seed: int = 0, i0: float = 1.0,
+             chunk: int = 1 << 24) -> Graph:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    w = (np.arange(n, dtype=np.float64) + i0) ** (-1.0 / (gamma - 1.0))
+    w *= n * avg_degree / w.sum()
+    cap = np.sqrt(w.sum())
+    w = np.minimum(w, cap)
+    total = w.sum()
+    m = int(round(total / 2.0))
+    cdf = np.cumsum(w / total)
+    cdf[-1] = 1.0
+    keys = []
+    for c0 in range(0, m, chunk):
+        c = min(chunk, m - c0)
+        i = np.searchsorted(cdf, rng.random(c), side="right")
+        j = np.searchsorted(cdf, rng.random(c), side="right")
+        i = np.minimum(i, n - 1)
+        j = np.minimum(j, n - 1)
+        keep = i != j
+        i, j = i[keep], j[keep]
+        keys.append(np.unique(np.minimum(i, j).astype(np.int64) * n + np.maximum(i, j)))
+    key = np.unique(np.concatenate(keys)) if keys else np.zeros(0, np.int64)
+    return _csr_from_undirected_pairs(n, key // n, key % n,
+                                      name=f"chung_lu(n={n},avg={avg_degree},gamma={gamma},seed={seed})")
+
+
+def batched_mix(count: int = 64, n_lo: int = 2000, n_hi: int = 200000, deg_lo: float = 8.0,
+                deg_hi: float = 32.0, seed: int = 0):
+    """Uneven batch of graphs: graph g is seeded g; even g -> 8-block SBM with
+    p_in/p_out = 10, odd g -> Chung-Lu with gamma = 2.1."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ns = rng.integers(n_lo, n_hi + 1, size=count)
+    degs = rng.uniform(deg_lo, deg_hi, size=count)
+    graphs = []
+    for g in range(count):
+        n = int(ns[g])
+        avg = float(degs[g])
+        if g % 2 == 0:
+            blk = n / 8.0
+            p_out = avg / (17.0 * blk)
+            graphs.append(sbm(n, 8, 10.0 * p_out, p_out, seed=g))
+        else:
+            graphs.append(chung_lu(n, avg, 2.1, seed=g))
+    return graphs
+
+
+def named(config: str) -> Graph:
+    """The graph of a named workload."""
+    if config == "sbm4096":
+        return sbm(4096, 8, 0.01, 0.001, seed=0)
+    if config == "cl1m":
+        return chung_lu(1_000_000, 20.0, 2.1, seed=0)
+    if config == "cl10m":
+        return chung_lu(10_000_000, 30.0, 2.2, seed=0)
+    raise KeyError(config)

@@ -1,0 +1,332 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: published
+test vectors, closed forms, textbook spectra, exactness statements of the
+paper, library routines that reach the same result by another algorithm, and
+brute force on tiny inputs.  CPU only.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.stats
+
+from oracle import sketchne_oracle as o
+from paper_2110_12782_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _dense(g):
+    return o.adjacency(g.row_ptr, g.col_idx, g.n).toarray()
+
+
+# ---------------------------------------------------------------- random numbers
+def test_splitmix64_published_vectors():
+    want = [int(line, 16) for line in open(os.path.join(GOLDEN, "splitmix64_seed0.txt"))
+            if line.strip() and not line.startswith("#")]
+    got = [o.splitmix64_output(0, i) for i in range(1, len(want) + 1)]
+    assert got == want
+    # the vectorised form used for Omega agrees with the scalar one
+    key = o.stream_key(7, 1)
+    ctr = np.arange(100, dtype=np.uint64)
+    assert [int(x) for x in o.draw_np(key, ctr)] == [o.draw(key, int(c)) for c in range(100)]
+
+
+def test_lemire_bounded_definition_and_uniformity():
+    key = o.stream_key(3, 2)
+    n = 7
+    counts = np.zeros(n)
+    ctr = 0
+    for _ in range(14000):
+        x = o.draw(key, ctr)
+        v, ctr2 = o.bounded(key, ctr, n)
+        if ctr2 == ctr + 1:  # not rejected: the value is floor(x * n / 2^64)
+            assert v == (x * n) >> 64
+        ctr = ctr2
+        counts[v] += 1
+    chi2 = ((counts - counts.mean()) ** 2 / counts.mean()).sum()
+    assert scipy.stats.chi2.sf(chi2, n - 1) > 1e-4
+    # a bound just above 2^63 rejects about half of the draws
+    big = (1 << 63) + 1
+    ctr, rejected = 0, 0
+    for _ in range(400):
+        v, ctr2 = o.bounded(o.stream_key(1, 1), ctr, big)
+        rejected += ctr2 - ctr - 1
+        assert 0 <= v < big
+        ctr = ctr2
+    assert 100 < rejected < 800
+
+
+def test_sparse_sign_structure():
+    for n, cols, zeta in [(1000, 50, 8), (20, 30, 8), (5, 4, 8), (8, 3, 8), (100000, 40, 4)]:
+        S = o.gen_sparse_sign(n, cols, zeta, seed=11, stream=2)
+        z = min(n, zeta)
+        assert S.idx.shape == (cols, z)
+        for j in range(cols):
+            assert len(set(S.idx[j].tolist())) == z
+        assert S.idx.min() >= 0 and S.idx.max() < n
+        assert set(np.unique(S.sign).tolist()) <= {-1, 1}
+        assert np.array_equal(S.p, np.array(sorted(set(S.idx.ravel().tolist()))))
+        D = S.dense()
+        assert np.count_nonzero(D) == cols * z
+        assert np.allclose(np.abs(D[D != 0]), 1 / math.sqrt(z))
+    # deterministic, stream-dependent
+    a = o.gen_sparse_sign(1000, 20, 8, 5, 2)
+    b = o.gen_sparse_sign(1000, 20, 8, 5, 2)
+    c = o.gen_sparse_sign(1000, 20, 8, 5, 3)
+    assert np.array_equal(a.idx, b.idx) and np.array_equal(a.sign, b.sign)
+    assert not np.array_equal(a.idx, c.idx)
+
+
+def test_sparse_sign_uniform_rows_and_signs():
+    n = 50
+    S = o.gen_sparse_sign(n, 2000, 8, seed=1, stream=3)
+    counts = np.bincount(S.idx.ravel(), minlength=n)
+    chi2 = ((counts - counts.mean()) ** 2 / counts.mean()).sum()
+    assert scipy.stats.chi2.sf(chi2, n - 1) > 1e-4
+    plus = (S.sign == 1).sum()
+    assert abs(plus - S.sign.size / 2) < 4 * math.sqrt(S.sign.size / 4)
+
+
+def test_gaussian_omega_distribution_and_slicing():
+    G = o.gaussian_matrix(4000, 37, seed=2)
+    x = G.ravel()
+    assert scipy.stats.kstest(x, "norm").pvalue > 1e-4
+    assert abs(x.mean()) < 4 / math.sqrt(x.size)
+    assert abs(x.var() - 1) < 4 * math.sqrt(2 / x.size)
+    # rows are independent of how the matrix is chunked
+    part = o.gaussian_matrix(4000, 37, seed=2, row0=1234, rows=77)
+    assert np.array_equal(part, G[1234:1311])
+
+
+# ---------------------------------------------------------------- graph quantities
+def test_degrees_volume_star():
+    g = synth.from_edges(6, [(0, i) for i in range(1, 6)])
+    A = o.adjacency(g.row_ptr, g.col_idx, g.n)
+    assert np.array_equal(o.degrees(A), [5, 1, 1, 1, 1, 1])
+    assert o.volume(A) == 10
+
+
+def test_normalized_operator_textbook_spectra():
+    # K_n: D^-1/2 A D^-1/2 = (J - I)/(n-1): eigenvalues 1 (once), -1/(n-1)
+    n = 9
+    g = synth.complete_graph(n)
+    X = o.normalized_operator(o.adjacency(g.row_ptr, g.col_idx, n), 0.5).toarray()
+    ev = np.sort(np.linalg.eigvalsh(X))
+    assert np.allclose(ev, np.r_[np.full(n - 1, -1 / (n - 1)), 1.0], atol=1e-13)
+    # connected graph: top eigenvalue 1 with eigenvector D^1/2 1
+    g = synth.sbm(300, 3, 0.2, 0.05, seed=4)
+    A = o.adjacency(g.row_ptr, g.col_idx, g.n)
+    X = o.normalized_operator(A, 0.5).toarray()
+    ev, V = np.linalg.eigh(X)
+    assert abs(ev[-1] - 1) < 1e-12 and ev[0] >= -1 - 1e-12
+    u = np.sqrt(o.degrees(A))
+    u /= np.linalg.norm(u)
+    assert abs(abs(V[:, -1] @ u) - 1) < 1e-10
+
+
+# ---------------------------------------------------------------- Alg. 5
+def test_eigsvd_is_an_orthonormal_basis_of_range():
+    rng = np.random.default_rng(0)
+    Y = rng.standard_normal((500, 30)) @ np.diag(np.logspace(0, -3, 30))
+    Q, S, V = o.eigsvd(Y)
+    assert np.allclose(Q.T @ Q, np.eye(30), atol=1e-9)
+    U, sv, _ = np.linalg.svd(Y, full_matrices=False)
+    assert np.allclose(np.sort(S), np.sort(sv), rtol=1e-9)
+    assert np.allclose(Q @ Q.T, U @ U.T, atol=1e-9)
+
+
+def test_freigs_exact_on_bipartite_union():
+    # each K_{a,b} contributes eigenvalues +1 and -1 of D^-1/2 A D^-1/2, all
+    # other eigenvalues are 0; the 2c-dimensional eigenspace is found exactly.
+    # (k + s must not exceed rank(X) = 2c: eigSVD divides by the square roots
+    # of the Gram eigenvalues, which are 0 beyond the rank.)
+    parts = [(3, 5), (4, 4), (2, 7), (6, 3), (5, 5), (3, 9)]
+    g = synth.complete_bipartite_union(parts)
+    X = o.normalized_operator(o.adjacency(g.row_ptr, g.col_idx, g.n), 0.5)
+    k = 2 * len(parts)
+    U, lam = o.freigs(X, k, q=2, s=0, seed=1)
+    assert np.allclose(np.abs(lam), 1.0, atol=1e-10)
+    assert (lam > 0).sum() == len(parts)
+    assert np.allclose(X @ U, U * lam[None, :], atol=1e-9)
+    assert np.allclose(U.T @ U, np.eye(k), atol=1e-9)
+
+
+def test_freigs_matches_dense_eigh_on_leading_eigenvalues():
+    g = synth.sbm(600, 4, 0.08, 0.005, seed=3)
+    A = o.adjacency(g.row_ptr, g.col_idx, g.n)
+    for alpha in (0.5, 0.4):
+        X = o.normalized_operator(A, alpha)
+        ev = np.linalg.eigvalsh(X.toarray())
+        ev = ev[np.argsort(-np.abs(ev))]
+        U, lam = o.freigs(X, 16, q=30, s=16, seed=2)
+        # the four community eigenvalues are well separated from the bulk
+        assert np.allclose(lam[:4], ev[:4], rtol=1e-8)
+        assert np.all(np.abs(np.abs(lam) - np.abs(ev[:16])) < 0.05)
+
+
+def test_freigs_with_householder_qr_gives_same_eigenvalues():
+    # the span after each step does not depend on the orthonormal basis chosen
+    g = synth.sbm(400, 4, 0.1, 0.01, seed=5)
+    X = o.normalized_operator(o.adjacency(g.row_ptr, g.col_idx, g.n), 0.5)
+    k, s, q = 10, 6, 4
+    U, lam = o.freigs(X, k, q, s, seed=9)
+    Om = o.gaussian_matrix(g.n, k + s, 9)
+    Q, _ = np.linalg.qr(X @ Om)
+    for _ in range(q):
+        Q, _ = np.linalg.qr(X @ (X @ Q))
+    Sred = Q.T @ (X @ Q)
+    ev = np.linalg.eigvalsh(0.5 * (Sred + Sred.T))
+    ev = ev[np.argsort(-np.abs(ev))][:k]
+    assert np.allclose(lam, ev, rtol=1e-10, atol=1e-12)
+
+
+# ---------------------------------------------------------------- Eq. 1 / Eq. 2 / Eq. 11
+def test_netmf_matrix_closed_form_complete_graph():
+    for n, T, b in [(5, 10, 1.0), (12, 3, 2.0)]:
+        M = o.netmf_matrix_dense(_dense(synth.complete_graph(n)), T, b)
+        mu = -1.0 / (n - 1)
+        off = sum(1 - mu ** r for r in range(1, T + 1)) / (b * T)
+        diag = sum(1 + (n - 1) * mu ** r for r in range(1, T + 1)) / (b * T)
+        assert np.allclose(M[~np.eye(n, dtype=bool)], off, rtol=1e-13)
+        assert np.allclose(np.diag(M), diag, rtol=1e-13)
+    # n=5, T=10, b=1 puts every off-diagonal entry just above the threshold 1
+    M = o.netmf_matrix_dense(_dense(synth.complete_graph(5)), 10, 1.0)
+    assert 1.0 < M[0, 1] < 1.05 and o.trunc_log(M)[0, 1] > 0
+
+
+@pytest.mark.parametrize("alpha", [0.5, 0.4, 0.35])
+def test_eq11_equals_eq1_at_full_rank(alpha):
+    # with all n eigenpairs of D^-a A D^-a, L'R' of Eq. 11 is exactly Eq. 1's matrix
+    g = synth.sbm(60, 2, 0.4, 0.1, seed=1)
+    Ad = _dense(g)
+    A = o.adjacency(g.row_ptr, g.col_idx, g.n)
+    assert (o.degrees(A) > 0).all()
+    X = o.normalized_operator(A, alpha).toarray()
+    lam, U = np.linalg.eigh(X)
+    fac = o.netmf_factors(U, lam, o.degrees(A), o.volume(A), alpha, T=5, b=1.0)
+    M = o.netmf_matrix_dense(Ad, T=5, b=1.0)
+    assert np.allclose(fac.Lp @ fac.Rp, M, rtol=1e-9, atol=1e-9 * np.abs(M).max())
+    if alpha == 0.5:
+        M2 = o.netmf_eq2_dense(Ad, U, lam, T=5, b=1.0)
+        assert np.allclose(M2, M, rtol=1e-9, atol=1e-9 * np.abs(M).max())
+
+
+def test_top_eigenpair_contributes_exactly_one_over_b():
+    # alpha = 1/2: lambda_1 = 1, u_1 ~ D^1/2 1 give vol/(bT) d_i^-1/2 u_1i T u_1j d_j^-1/2 = 1/b
+    g = synth.sbm(200, 2, 0.2, 0.05, seed=2)
+    A = o.adjacency(g.row_ptr, g.col_idx, g.n)
+    deg = o.degrees(A)
+    u = np.sqrt(deg) / np.linalg.norm(np.sqrt(deg))
+    for b in (1.0, 3.0):
+        fac = o.netmf_factors(u[:, None], np.array([1.0]), deg, o.volume(A), 0.5, T=10, b=b)
+        assert np.allclose(fac.Lp @ fac.Rp, 1.0 / b, rtol=1e-12)
+
+
+def test_trunc_log_cases_and_lipschitz():
+    x = np.array([-3.0, 0.0, 0.5, 1.0, math.e, math.e ** 2])
+    assert np.allclose(o.trunc_log(x), [0, 0, 0, 0, 1, 2])
+    rng = np.random.default_rng(1)
+    a, b = rng.uniform(-2, 20, 10000), rng.uniform(-2, 20, 10000)
+    # trunc_log is 1-Lipschitz where both arguments are >= 1 or the log is flat
+    lhs = np.abs(o.trunc_log(a) - o.trunc_log(b))
+    assert np.all(lhs <= np.abs(np.maximum(a, 1) - np.maximum(b, 1)) + 1e-15)
+
+
+# ---------------------------------------------------------------- Alg. 4
+def _small_factors(n=300, k=24, seed=3, alpha=0.5):
+    g = synth.sbm(n, 3, 0.1, 0.01, seed=seed)
+    A = o.adjacency(g.row_ptr, g.col_idx, g.n)
+    X = o.normalized_operator(A, alpha)
+    U, lam = o.freigs(X, k, q=5, s=8, seed=seed)
+    return g, o.netmf_factors(U, lam, o.degrees(A), o.volume(A), alpha, 10, 1.0)
+
+
+def test_eq4_column_sampling_is_exact():
+    g, fac = _small_factors()
+    S = o.gen_sparse_sign(g.n, 40, 8, seed=4, stream=2)
+    Y = o.sketch_Y(fac.Lp, fac.Rp, S, row_block=64)
+    Yd = o.trunc_log(fac.Lp @ fac.Rp) @ S.dense()
+    assert np.linalg.norm(Y - Yd) <= 1e-12 * np.linalg.norm(Yd)
+    assert len(S.p) < g.n
+
+
+def test_z_core_is_exact():
+    g, fac = _small_factors()
+    O = o.gen_sparse_sign(g.n, 70, 8, seed=4, stream=3)
+    Z = o.sketch_Z(fac.Lp, fac.Rp, O)
+    Od = O.dense()
+    Zd = Od.T @ o.trunc_log(fac.Lp @ fac.Rp) @ Od
+    assert np.linalg.norm(Z - Zd) <= 1e-12 * np.linalg.norm(Zd)
+    assert np.allclose(Z, Z.T, rtol=0, atol=1e-12 * np.abs(Z).max())
+
+
+def test_single_pass_exact_for_identity_f():
+    # f = identity and rank(L'R') = k <= h: Alg. 4 recovers the SVD exactly
+    g, fac = _small_factors(k=12)
+    M = fac.Lp @ fac.Rp
+    d = 8
+    res = o.single_pass_svd(fac.Lp, fac.Rp, d, h=20, l=120, zeta=8, seed=6, f=o.identity)
+    U, sv, _ = np.linalg.svd(M)
+    assert np.allclose(res.sigma, sv[:d], rtol=1e-8)
+    gap_ok = [i for i in range(1, d + 1) if i == d or (sv[i - 1] - sv[i]) > 1e-3 * sv[0]]
+    dd = gap_ok[-1]
+    sines = o.principal_angle_sines(res.U[:, :dd], U[:, :dd])
+    assert sines.max() < 1e-6
+
+
+def test_single_pass_invariant_to_sign_scale_and_w_symmetric():
+    g, fac = _small_factors()
+    a = o.single_pass_svd(fac.Lp, fac.Rp, 8, 32, 150, 8, seed=2)
+    b = o.single_pass_svd(fac.Lp, fac.Rp, 8, 32, 150, 8, seed=2, sign_scale=1.0)
+    assert np.allclose(a.sigma, b.sigma, rtol=1e-10)
+    assert o.principal_angle_sines(a.U, b.U).max() < 1e-6  # sqrt(1-cos^2) floor ~1e-8
+    assert np.linalg.norm(a.W - a.W.T) <= 1e-12 * np.linalg.norm(a.W)
+
+
+def test_isolated_vertices_have_zero_rows():
+    g0 = synth.sbm(200, 2, 0.2, 0.02, seed=8)
+    # append 5 isolated vertices
+    n = g0.n + 5
+    row_ptr = np.concatenate([g0.row_ptr, np.full(5, g0.row_ptr[-1])])
+    p = o.Params(k=16, d=8, q=4, h=24, l=80)
+    r = o.embed(row_ptr, g0.col_idx, n, p)
+    assert np.all(r.sp.Y[g0.n:] == 0)
+    assert np.all(r.E[g0.n:] == 0)
+    assert np.all(r.U_k[g0.n:] == 0)
+
+
+def test_theorem1_bound_holds():
+    g = synth.sbm(400, 4, 0.08, 0.01, seed=12)
+    A = o.adjacency(g.row_ptr, g.col_idx, g.n)
+    deg = o.degrees(A)
+    assert (deg > 0).all()
+    for alpha in (0.5, 0.45):
+        X = o.normalized_operator(A, alpha)
+        k = 32
+        U, lam = o.freigs(X, k, q=10, s=16, seed=1)
+        fac = o.netmf_factors(U, lam, deg, o.volume(A), alpha, 10, 1.0)
+        lhs = np.linalg.norm(o.trunc_log(o.netmf_matrix_dense(A.toarray(), 10, 1.0))
+                             - o.trunc_log(fac.Lp @ fac.Rp))
+        ev = np.sort(np.abs(np.linalg.eigvalsh(X.toarray())))[::-1]
+        assert lhs <= o.theorem1_bound(ev, k, deg, o.volume(A), g.n, alpha, 10, 1.0)
+
+
+def test_embedding_dominant_subspace_matches_dense_svd():
+    # the four block directions of trunc_log(L'R') are separated from the rest
+    # by a wide gap; the single-pass sketch recovers them (randomized, so loose
+    # bounds), and its rank-d projection is close to the Eckart-Young optimum
+    g = synth.sbm(800, 4, 0.05, 0.005, seed=1)
+    p = o.Params(k=32, d=8, q=10, h=64, l=600)
+    r = o.embed(g.row_ptr, g.col_idx, g.n, p)
+    F = o.trunc_log(r.factors.Lp @ r.factors.Rp)
+    U, sv, _ = np.linalg.svd(F)
+    assert sv[3] > 2 * sv[4]
+    assert np.all(np.abs(r.sigma[:4] - sv[:4]) < 2e-2 * sv[:4])
+    assert o.principal_angle_sines(r.sp.U[:, :4], U[:, :4]).max() < 0.2
+    Ud = r.sp.U
+    resid = np.linalg.norm(F - Ud @ (Ud.T @ F))
+    optimum = math.sqrt(float(np.sum(sv[8:] ** 2)))
+    assert optimum <= resid <= 1.1 * optimum
