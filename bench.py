@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Benchmark of the SketchNE hot path (Alg. 6 lines 1-5) on GB300.
+
+One step = one full embedding of the workload graph: freigs (Alg. 5) with its
+CSR SpMM power iterations, the Eq. 11 factors, the sparse-sign single-pass SVD
+(Alg. 3, 4) with the fused trunc_log(M-hat) sketches Y and Z, the small QR /
+least-squares / SVD, and E = U_d Sigma_d^(1/2).
+
+Metric: M-hat entries evaluated by the sketches per second, n*v_S + v_O^2 per
+step (v_S, v_O = unique sparse-sign coordinates), over the whole step; the
+end-to-end embed time is ms_per_step.  Inputs resident in HBM for `value`;
+`e2e` repeats the measurement through sne_embed_host (graph in pinned host
+memory, copies inside the timed region, E and sigma read back every step).
+
+Default workload "cl1m": Chung-Lu power-law graph, n = 1,000,000, mean degree
+20, exponent 2.1, seed 0; T = 10, b = 1, k = 256, d = 128, zeta = 8,
+h = 2d + 16, l = d + 1000, q = 20, alpha = 0.5, plain FP32 path.
+
+--impl reference times the FP64 oracle (the CPU reference of this repo) on a
+bounded sample of the same workload on the host cores.
+
+Multi-GPU: one process per GPU (torchrun); the path does not shard, so every
+rank runs an independent replica (weak scaling) and `value` sums the ranks'
+work over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "trunc_log(M̂)·Ω entries/s and end-to-end embed time, mixed vs FP32 plain"
+UNIT = "entries/s"
+
+WORKLOADS = {
+    "cl1m": dict(kind="chung_lu", n=1_000_000, avg=20.0, gamma=2.1, d=128, k=256, T=10, q=20,
+                 label="Chung-Lu n=1M avg-degree 20 gamma 2.1, T=10 b=1 k=256 d=128 zeta=8 "
+                       "h=2d+16 l=d+1000 q=20 alpha=0.5, row block 8192"),
+    "sbm4096": dict(kind="sbm", n=4096, d=32, k=128, T=10, q=20,
+                    label="SBM n=4096 8 blocks p_in=0.01 p_out=0.001, T=10 b=1 k=128 d=32 zeta=8"),
+}
+
+
+def make_graph(w):
+    from paper_2110_12782_gb300 import synth
+    if w["kind"] == "chung_lu":
+        return synth.chung_lu(w["n"], w["avg"], w["gamma"], seed=0)
+    return synth.sbm(w["n"], 8, 0.01, 0.001, seed=0)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(gpu_index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks() -> tuple[dict, str]:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+# --------------------------------------------------------------------------- algorithmic work
+def algorithmic_work(cls: str, n: int, nnz: int, p, v_s: int, v_o: int) -> tuple[float, str, str]:
+    """Algorithmic bytes or flops of one step for a kernel class."""
+    K = p.k + p.s_eig
+    h, l, z, k, d = p.h, p.l, min(n, p.zeta), p.k, p.d
+    if cls == "spmm":
+        calls = 2 * p.q + 2
+        per = 8 * (n + 1) + 4 * nnz + 4 * n + 2 * 4 * n * K
+        return calls * per, "hbm", "GB/s"
+    if cls == "gram":
+        flops = (p.q + 2) * n * K * (K + 1) + 2 * n * K * K + n * k * (k + 1) + 2 * n * h * (h + 1)
+        return flops, "alu", "TFLOP/s"
+    if cls == "tall_gemm":
+        flops = (p.q + 2) * 2 * n * K * K + 2 * n * K * k + 2 * (h + l) * z * k * k \
+            + 2 * 2 * n * h * h + 2 * n * h * d
+        return flops, "alu", "TFLOP/s"
+    if cls in ("fused_sketch", "fused_sketch_tc"):
+        flops = 2 * k * (n * h * z + v_o * l * z)
+        return flops, ("tensor" if cls.endswith("_tc") else "alu"), "TFLOP/s"
+    return 0.0, "alu", "TFLOP/s"
+
+
+def alu_peak_tflops(sm_mhz: float) -> float:
+    """FP32 FFMA peak: 152 SMs x 128 FP32 lanes x 2 flops x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# --------------------------------------------------------------------------- oracle timing
+def oracle_sample_rate(g, p, U_k: np.ndarray, lam: np.ndarray, budget_s: float) -> dict:
+    """Eq. 4 in the FP64 oracle on a row sample; entries evaluated per second."""
+    from oracle import sketchne_oracle as o
+    A = o.adjacency(g.row_ptr, g.col_idx, g.n)
+    deg = o.degrees(A)
+    fac = o.netmf_factors(U_k, lam, deg, o.volume(A), p.alpha, p.T, p.b)
+    S = o.gen_sparse_sign(g.n, p.h, p.zeta, p.seed, o.STREAM_S)
+    v = len(S.p)
+    rows, done, spent = 512, 0, 0.0
+    rng = np.random.default_rng(0)
+    while spent < budget_s:
+        sel = np.sort(rng.choice(g.n, size=min(rows, g.n), replace=False))
+        t0 = time.perf_counter()
+        o.sketch_Y_rows(fac.Lp[sel], fac.Rp, S)
+        spent += time.perf_counter() - t0
+        done += len(sel)
+        rows = min(rows * 2, 16384)
+    return {"value": done * v / spent, "rows": done, "seconds": spent, "v": v}
+
+
+def cpu_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# --------------------------------------------------------------------------- reference arm
+def run_reference(args, rank: int) -> None:
+    if rank != 0:
+        return
+    from oracle import sketchne_oracle as o
+    w = WORKLOADS[args.workload]
+    g = make_graph(w)
+    p = o.Params(k=w["k"], d=w["d"], q=w["q"], T=w["T"]).resolved()
+    A = o.adjacency(g.row_ptr, g.col_idx, g.n)
+    # factors for the sampled sketch: freigs with a bounded number of power
+    # iterations (the sketch arithmetic timed below does not depend on q)
+    X = o.normalized_operator(A, p.alpha)
+    U, lam = o.freigs(X, p.k, min(p.q, 1), p.s_eig, p.seed)
+    budget = args.ref_step_seconds
+    for _ in range(args.warmup):
+        oracle_sample_rate(g, p, U, lam, budget * 0.2)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        r = oracle_sample_rate(g, p, U, lam, budget)
+        vals.append(r["value"])
+        secs.append(r["seconds"])
+    value = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": w["label"], "sample": "Eq. 4 rows of trunc_log(L'R'(:,p))S on "
+                   f"random row samples, ~{budget:.0f} s of CPU work per step",
+                   "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                         "sample": f"row samples of Eq. 4, {budget:.0f} s per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- our arm
+def run_ours(args, rank: int, world: int) -> None:
+    import torch
+    import torch.distributed as dist
+
+    from paper_2110_12782_gb300 import build
+    from paper_2110_12782_gb300 import sketchne as sk
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    build.build()
+    w = WORKLOADS[args.workload]
+    g = make_graph(w)
+    prec = {"fp32": sk.SNE_FP32, "bf16": sk.SNE_BF16, "fp16": sk.SNE_FP16}[args.precision]
+    orth = {"eigsvd": sk.SNE_ORTH_EIGSVD, "cholqr": sk.SNE_ORTH_CHOLQR}[args.orth]
+    p = sk.sne_params_init(w["d"], w["k"], q=w["q"], T=w["T"], precision=prec, orth=orth,
+                           row_block=8192)
+    G = sk.DeviceGraph.from_numpy(g.row_ptr, g.col_idx)
+    ws = sk.workspace(g.n, g.nnz, p, sk.SNE_WS_EMBED)
+    E = torch.empty(g.n, p.d, dtype=torch.float32, device="cuda")
+    sig = torch.empty(p.d, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+
+    def step():
+        sk.sne_embed(G, p, ws, E, sig)
+
+    for _ in range(args.warmup):
+        step()
+    sk.check_status(ws, "warm-up")
+    st = sk.sne_stats_read(ws)
+    entries = g.n * st.v_s + st.v_o * st.v_o
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- timed region: inputs resident in HBM, L2 flushed between steps
+    clocks = ClockSampler(local)
+    times = []
+    launches0 = sk.sne_kernel_launches()
+    for _ in range(args.steps):
+        flush.zero_()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    launches = sk.sne_kernel_launches() - launches0
+    clk = clocks.stop()
+    sk.check_status(ws, "timed steps")
+    total_ms = float(sum(times))
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps * entries / (total_ms / 1e3)
+
+    # ---- per-kernel-class times (events on the launching stream), same steps
+    sk.sne_profile_start()
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        step()
+    prof = sk.sne_profile_stop()
+    prof_total = sum(v[2] for v in prof.values())
+
+    # ---- end to end through the public host-buffer entry point
+    h_rp = torch.from_numpy(g.row_ptr).pin_memory()
+    h_ci = torch.from_numpy(g.col_idx).pin_memory()
+    h_E = torch.empty(g.n, p.d, dtype=torch.float32).pin_memory()
+    h_sig = torch.empty(p.d, dtype=torch.float64).pin_memory()
+    ws_h = sk.workspace(g.n, g.nnz, p, sk.SNE_WS_EMBED_HOST)
+    sk.sne_embed_host(h_rp, h_ci, None, g.n, p, ws_h, h_E, h_sig)
+    torch.cuda.synchronize()
+    e2e_t = []
+    for _ in range(args.steps):
+        flush.zero_()
+        barrier()
+        t0 = time.perf_counter()
+        sk.sne_embed_host(h_rp, h_ci, None, g.n, p, ws_h, h_E, h_sig)
+        torch.cuda.synchronize()
+        e2e_t.append(time.perf_counter() - t0)
+    sk.check_status(ws_h, "e2e steps")
+    e2e_total = float(sum(e2e_t))
+    if world > 1:
+        t = torch.tensor([e2e_total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    h2d = 8 * (g.n + 1) + 4 * g.nnz
+    d2h = 4 * g.n * p.d + 8 * p.d
+
+    # ---- roofline of the dominant kernel class
+    peaks, peak_kind = measured_peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][2])[0] if prof else None
+    roofline = None
+    if dom:
+        calls, nlaunch, ms = prof[dom]
+        work, bound, unit = algorithmic_work(dom, g.n, g.nnz, p, st.v_s, st.v_o)
+        per_step_ms = ms / args.steps
+        if work > 0:
+            if bound == "hbm":
+                achieved = work / (per_step_ms / 1e3) / 1e9
+                peak = float(peaks["hbm_gbs"])
+            elif bound == "tensor":
+                achieved = work / (per_step_ms / 1e3) / 1e12
+                peak = float(peaks["bf16_tflops"])
+            else:
+                achieved = work / (per_step_ms / 1e3) / 1e12
+                peak = alu_peak_tflops(float(peaks.get("sm_max_mhz", 2070.0)))
+            roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak,
+                        "unit": unit, "frac": achieved / peak, "traffic": None,
+                        "peak_source": f"{peak_kind}" if bound != "alu" else
+                        "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                        "share_of_step": ms / prof_total if prof_total else None}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        U = torch.empty(g.n, p.k, dtype=torch.float32, device="cuda")
+        lam = torch.empty(p.k, dtype=torch.float64, device="cuda")
+        ws_f = sk.workspace(g.n, g.nnz, p, sk.SNE_WS_FREIGS)
+        sk.sne_freigs(G, p, ws_f, U, lam)
+        from oracle import sketchne_oracle as o
+        op = o.Params(k=p.k, d=p.d, q=p.q, T=p.T, h=p.h, l=p.l).resolved()
+        r = oracle_sample_rate(g, op, U.cpu().double().numpy(), lam.cpu().numpy(), args.cpu_seconds)
+        cpu = {"value": r["value"], "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"Eq. 4 (trunc_log(L'R'(:,p))S, FP64) on {r['rows']} random rows, "
+                         f"{r['seconds']:.1f} s, factors from this run's freigs"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == sk.SNE_FP32 else args.precision,
+            "data": "synthetic",
+            "config": {"workload": w["label"], "n": g.n, "nnz": g.nnz, "v_S": st.v_s, "v_O": st.v_o,
+                       "entries_per_step": entries, "precision": args.precision, "orth": args.orth,
+                       "l2": "flushed between steps (256 MB write)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "e2e": {"value": world * args.steps * entries / e2e_total, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": 1e3 * e2e_total / args.steps},
+            "gpu_launches": int(launches),
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "kernel_ms_per_step": {k: v[2] / args.steps for k, v in sorted(prof.items(), key=lambda kv: -kv[1][2])},
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cl1m", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--orth", default="eigsvd", choices=["eigsvd", "cholqr"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=8.0)
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

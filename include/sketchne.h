@@ -1,0 +1,192 @@
+/*
+ * sketchne.h -- C ABI of libsketchne.so, the GB300 (sm_103a) hot path of
+ * SketchNE ("SketchNE: Embedding Billion-Scale Networks Accurately in One
+ * Hour", arXiv 2110.12782): the fast randomized eigendecomposition of the
+ * modified Laplacian D^-a A D^-a (Alg. 5), the factors L', R' of Eq. 11, and
+ * the sparse-sign randomized single-pass SVD of trunc_log(L'R') (Alg. 3, 4),
+ * giving the initial embedding E = U_d Sigma_d^(1/2) (Alg. 6 lines 1-5).
+ *
+ * Conventions for every entry point below:
+ *  - All array arguments are DEVICE pointers (memory of the current CUDA
+ *    device) unless the comment says "host".  The caller allocates and owns
+ *    every input, output and workspace; the library never allocates, frees or
+ *    keeps a pointer after the call returns.
+ *  - Dense matrices are row-major FP32 or FP64 with the leading dimension equal
+ *    to the column count stated for the argument.
+ *  - Every call is stream-ordered and asynchronous on `stream` (NULL = legacy
+ *    default stream); the host returns as soon as the work is enqueued.
+ *    Argument errors found on the host are returned immediately and enqueue
+ *    nothing.  Errors found on the device (NaN, a non-positive pivot, a bad
+ *    graph) are recorded in the workspace's status word and are read with
+ *    sne_status(), which synchronizes the stream.
+ *  - Return value: SNE_OK (0) or a negative SNE_ERR_* code.
+ *  - Calls that share a workspace must not overlap on the GPU.
+ */
+#ifndef SKETCHNE_H
+#define SKETCHNE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *sne_stream_t; /* the same type as cudaStream_t */
+
+enum {
+  SNE_OK = 0,
+  SNE_ERR_ARG = -1,       /* bad argument (NULL pointer, negative size, ...) */
+  SNE_ERR_GRAPH = -2,     /* CSR not valid: row_ptr not monotone, index out of range, asymmetric */
+  SNE_ERR_SIZE = -3,      /* inconsistent sizes: k+s > n, d > h, h > l, z > 64, ... */
+  SNE_ERR_WORKSPACE = -4, /* workspace NULL, too small or not 256-byte aligned */
+  SNE_ERR_CUDA = -5,      /* a CUDA launch or runtime call failed */
+  SNE_ERR_TIMEOUT = -6,   /* a bounded device-side wait ran out */
+  SNE_ERR_NUMERIC = -7    /* NaN/Inf or a non-positive pivot in a small solve */
+};
+
+enum { SNE_FP32 = 0, SNE_BF16 = 1, SNE_FP16 = 2 };          /* reconstruction GEMM precision */
+enum { SNE_F_TRUNC_LOG = 0, SNE_F_IDENTITY = 1 };          /* elementwise f of Problem 1 */
+enum { SNE_ORTH_EIGSVD = 0, SNE_ORTH_CHOLQR = 1 };         /* orthonormalization inside Alg. 5 */
+
+/* Undirected graph G = (V, E, A) in CSR (Sec. 2): both directions of every
+ * edge stored, no self-loops.  row_ptr int64 [n+1] (row_ptr[0] = 0,
+ * nondecreasing, row_ptr[n] = nnz), col_idx int32 [nnz] in [0, n),
+ * val FP32 [nnz] positive edge weights or NULL for an unweighted graph. */
+typedef struct sne_csr {
+  int64_t n;
+  int64_t nnz;
+  const int64_t *row_ptr;
+  const int32_t *col_idx;
+  const float *val;
+} sne_csr;
+
+/* Parameters (Table 2 and Alg. 4-6).
+ *  k      eigen rank (Alg. 5/6)                    q      power-iteration count (Alg. 5)
+ *  T      context window size (Eq. 1)              d      embedding dimension
+ *  h      sketch size of Y  (h = d + s1, Alg. 4)   l      sketch size of Z (l = d + s2, Alg. 4)
+ *  zeta   sparse-sign column density z (Alg. 3); the library uses z = min(n, zeta) <= 64
+ *  s_eig  oversampling of Alg. 5 (k + s_eig columns of Omega)
+ *  row_block  rows of L' per batch of Eq. 4 (0 = library's choice)
+ *  precision  SNE_FP32 | SNE_BF16 | SNE_FP16 for the L'R' reconstruction
+ *  f      SNE_F_TRUNC_LOG (NetMF) or SNE_F_IDENTITY (Problem 1 with f = id)
+ *  orth   SNE_ORTH_EIGSVD (Alg. 5 as printed) or SNE_ORTH_CHOLQR
+ *  alpha  exponent of the modified Laplacian D^-alpha A D^-alpha, in (0, 0.5]
+ *  b      number of negative samples (Eq. 1)       seed   seed of all random draws */
+typedef struct sne_params {
+  int32_t k, q, T, d, h, l, zeta, s_eig, row_block, precision, f, orth;
+  double alpha, b;
+  uint64_t seed;
+} sne_params;
+
+/* Counters filled by sne_stats() (host struct). */
+typedef struct sne_stats {
+  int32_t status;   /* device status word (SNE_OK or SNE_ERR_*) */
+  int32_t where;    /* id of the kernel that set the status (0 = none) */
+  int64_t v_s;      /* v of Alg. 4 line 3: unique rows of S */
+  int64_t v_o;      /* v of Alg. 4 line 6: unique rows of O */
+  double vol;       /* vol(G) */
+} sne_stats;
+
+/* Fills *p with the defaults: alpha = 0.5, q = 20, T = 10, b = 1, zeta = 8,
+ * s_eig = 16, h = 2d + 16, l = d + 1000 (s2 = 1000, Sec. 5.2), FP32, trunc_log,
+ * eigSVD, seed 0, and the given d and k. */
+int sne_params_init(sne_params *p, int32_t d, int32_t k);
+
+/* Static message for an SNE_* code (host). */
+const char *sne_error_string(int code);
+
+/* Workspace modes. */
+enum { SNE_WS_EMBED = 0, SNE_WS_FREIGS = 1, SNE_WS_SKETCH = 2, SNE_WS_EMBED_HOST = 3 };
+
+/* Bytes of device workspace needed by sne_embed (mode SNE_WS_EMBED),
+ * sne_freigs (SNE_WS_FREIGS) or sne_sketch_from_factors (SNE_WS_SKETCH) for a
+ * graph with n vertices and nnz stored entries.  Host-only. */
+int sne_workspace_bytes(int64_t n, int64_t nnz, const sne_params *p, int mode, size_t *bytes);
+
+/* Alg. 6 lines 1-5.  E: n x d FP32 (row i = embedding of vertex i), sigma: d
+ * FP64 singular values Sigma_d (descending).  Workspace from
+ * sne_workspace_bytes(..., SNE_WS_EMBED). */
+int sne_embed(const sne_csr *g, const sne_params *p, void *workspace, size_t ws_bytes,
+              float *E, double *sigma, sne_stream_t stream);
+
+/* sne_embed with the graph and the outputs in HOST memory.  g's row_ptr,
+ * col_idx and val point to host arrays (page-locked for the copies to be
+ * asynchronous); E_host (n x d FP32) and sigma_host (d FP64) are host arrays.
+ * The call copies the graph into the workspace, runs Alg. 6 lines 1-5 and
+ * copies E and sigma back, all on `stream`; the outputs are valid after the
+ * stream is synchronized.  Workspace: sne_workspace_bytes(..., SNE_WS_EMBED_HOST). */
+int sne_embed_host(const sne_csr *g_host, const sne_params *p, void *workspace, size_t ws_bytes,
+                   float *E_host, double *sigma_host, sne_stream_t stream);
+
+/* Alg. 5 on X = D^-alpha A D^-alpha: U: n x k FP32 (orthonormal columns),
+ * lambda: k FP64, ordered by |lambda| descending. */
+int sne_freigs(const sne_csr *g, const sne_params *p, void *workspace, size_t ws_bytes,
+               float *U, double *lambda, sne_stream_t stream);
+
+/* Alg. 6 lines 2-5 from given eigenpairs (U: n x k FP32, lambda: k FP64, on the
+ * device): Eq. 11 factors, Alg. 4 sketches and the embedding.  Outputs (each
+ * may be NULL): Y n x h FP32 (Alg. 4 line 4), Z l x l FP32 (line 7), E n x d
+ * FP32, sigma d FP64. */
+int sne_sketch_from_factors(const sne_csr *g, const sne_params *p, const float *U,
+                            const double *lambda, void *workspace, size_t ws_bytes, float *Y,
+                            float *Z, float *E, double *sigma, sne_stream_t stream);
+
+/* Alg. 3: sparse-sign matrix with `cols` columns over n rows, z = min(n, zeta)
+ * nonzeros per column.  idx: cols x z int32 rows (distinct within a column),
+ * sign: cols x z int8 (+1/-1); the value of an entry is sign / sqrt(z).  Bit
+ * for bit the SplitMix64 / Lemire draws of stream `stream_id` (2 = S, 3 = O). */
+int sne_sparse_sign(int64_t n, int32_t cols, int32_t zeta, uint64_t seed, int32_t stream_id,
+                    int32_t *idx, int8_t *sign, sne_stream_t stream);
+
+/* Omega = randn(n, cols) of Alg. 5 line 3 (Box-Muller on SplitMix64 draws of
+ * stream `stream_id`, 1 for Omega).  out: n x cols FP32. */
+int sne_gaussian(int64_t n, int32_t cols, uint64_t seed, int32_t stream_id, float *out,
+                 sne_stream_t stream);
+
+/* d_i = sum_j A_ij (FP32 [n]) and vol(G) = sum_i d_i (FP64 [1]) (Sec. 2). */
+int sne_degrees(const sne_csr *g, float *deg, double *vol, sne_stream_t stream);
+
+/* out_i = deg_i^beta, 0 where deg_i = 0 (FP32 [n]). */
+int sne_degree_power(const float *deg, int64_t n, double beta, float *out, sne_stream_t stream);
+
+/* One SpMM of Alg. 5: Y = D^-a A D^-a B, given dpow_i = d_i^-a.  B, Y: n x ncols
+ * FP32, distinct buffers. */
+int sne_spmm(const sne_csr *g, const float *dpow, const float *B, int32_t ncols, float *Y,
+             sne_stream_t stream);
+
+/* Checks the CSR on the device (monotone row_ptr, indices in range, symmetric
+ * pattern and weights) and records SNE_ERR_GRAPH in the workspace status word
+ * (any workspace of at least 256 bytes).  Read the result with sne_status(). */
+int sne_validate_csr(const sne_csr *g, void *workspace, size_t ws_bytes, sne_stream_t stream);
+
+/* Clears the status word of a workspace (stream-ordered). */
+int sne_status_reset(void *workspace, sne_stream_t stream);
+
+/* Synchronizes `stream` and returns the workspace's device status word. */
+int sne_status(const void *workspace, sne_stream_t stream);
+
+/* Synchronizes `stream` and copies the workspace counters into *out (host). */
+int sne_stats_read(const void *workspace, sne_stats *out, sne_stream_t stream);
+
+/* Kernel accounting (host only).  sne_kernel_launches returns the number of
+ * kernels this library has enqueued since it was loaded.  Between
+ * sne_profile_start and sne_profile_stop every launcher brackets its kernels
+ * with CUDA events on its stream; sne_profile_stop synchronizes those events
+ * and writes one sne_kernel_time per kernel class (at most max_entries,
+ * *count = number of classes seen). */
+typedef struct sne_kernel_time {
+  char name[24];       /* kernel class */
+  int64_t calls;       /* launcher calls */
+  int64_t launches;    /* kernels enqueued */
+  double total_ms;     /* summed event time */
+} sne_kernel_time;
+
+long long sne_kernel_launches(void);
+int sne_profile_start(void);
+int sne_profile_stop(sne_kernel_time *out, int max_entries, int *count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SKETCHNE_H */

@@ -1,0 +1,603 @@
+// C entry points of libsketchne.so: argument checks, the workspace layout, and
+// the stream-ordered sequence of kernels for Alg. 5 (freigs), Eq. 11 and
+// Alg. 4 (sparse-sign randomized single-pass SVD), i.e. Alg. 6 lines 1-5.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+
+#include "sne_internal.cuh"
+
+using namespace sne;
+
+namespace {
+
+// --------------------------------------------------------------------------
+// Sizes and workspace layout
+// --------------------------------------------------------------------------
+struct Dims {
+  int64_t n, nnz;
+  int k, K, h, l, z, d, nS, nO, Sm, Wab;
+};
+
+int make_dims(int64_t n, int64_t nnz, const sne_params *p, int mode, Dims *D) {
+  if (!p || n <= 0 || nnz < 0) return SNE_ERR_ARG;
+  if (mode == SNE_WS_EMBED_HOST) mode = SNE_WS_EMBED;
+  if (p->k <= 0 || p->d <= 0 || p->h <= 0 || p->l <= 0 || p->zeta <= 0 || p->T <= 0 ||
+      p->q < 0 || p->s_eig < 0 || !(p->b > 0) || !(p->alpha > 0) || p->alpha > 1.0)
+    return SNE_ERR_ARG;
+  if (p->precision != SNE_FP32 && p->precision != SNE_BF16 && p->precision != SNE_FP16)
+    return SNE_ERR_ARG;
+  if (p->f != SNE_F_TRUNC_LOG && p->f != SNE_F_IDENTITY) return SNE_ERR_ARG;
+  if (p->orth != SNE_ORTH_EIGSVD && p->orth != SNE_ORTH_CHOLQR) return SNE_ERR_ARG;
+  Dims d{};
+  d.n = n;
+  d.nnz = nnz;
+  d.k = p->k;
+  d.K = p->k + p->s_eig;
+  d.h = p->h;
+  d.l = p->l;
+  d.d = p->d;
+  d.z = (int)min64(n, p->zeta);
+  d.nS = d.h * d.z;
+  d.nO = d.l * d.z;
+  if (d.z > 64) return SNE_ERR_SIZE;
+  if (mode != SNE_WS_SKETCH && (d.K > n || d.K > 1024)) return SNE_ERR_SIZE;
+  if (mode != SNE_WS_FREIGS) {
+    if (d.d > d.h || d.h > d.l || d.h > n || d.h > 1024 || d.k > 1024) return SNE_ERR_SIZE;
+    if (d.nS > kUniqueMax || d.nO > kUniqueMax) return SNE_ERR_SIZE;
+  }
+  d.Sm = std::max(std::max(d.K, d.h), d.k);
+  d.Wab = (mode == SNE_WS_SKETCH) ? d.h : (mode == SNE_WS_FREIGS ? d.K : std::max(d.K, d.h));
+  *D = d;
+  return SNE_OK;
+}
+
+struct Bump {
+  char *base;
+  size_t off = 0;
+  template <class T>
+  T *take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    T *ptr = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return ptr;
+  }
+};
+
+struct Bufs {
+  Ctrl *ctrl;
+  float *deg, *dpow, *rsc, *acoef, *wgt;
+  float *A, *B, *C;  // tall buffers
+  float *partial;
+  double *m64[5];
+  void *eigscr;
+  float *m32[4];
+  double *w64, *lam;
+  float *w32;
+  int32_t *perm;
+  int32_t *idxS, *idxO, *uniqS, *uniqO, *posS, *posO;
+  int8_t *signS, *signO;
+  float *RpS, *RpO, *Yo, *Zf, *Gf;
+  double *G64, *Gp, *Tm, *Z64;
+  int64_t *h_rowptr;  // device staging of a host graph (SNE_WS_EMBED_HOST)
+  int32_t *h_col;
+  float *h_val, *h_E;
+  double *h_sigma;
+};
+
+size_t carve(const Dims &D, int mode, void *base, Bufs *b) {
+  Bump bp{static_cast<char *>(base)};
+  Bufs x{};
+  const bool host_mode = (mode == SNE_WS_EMBED_HOST);
+  if (host_mode) mode = SNE_WS_EMBED;
+  x.ctrl = bp.take<Ctrl>(1);
+  const int64_t n = D.n;
+  x.deg = bp.take<float>(n);
+  x.dpow = bp.take<float>(n);
+  x.rsc = bp.take<float>(n);
+  x.acoef = bp.take<float>(n);
+  x.wgt = bp.take<float>(n);
+  x.A = bp.take<float>((size_t)n * D.Wab);
+  x.B = bp.take<float>((size_t)n * D.Wab);
+  if (mode != SNE_WS_SKETCH) x.C = bp.take<float>((size_t)n * D.K);
+  size_t pf = 0;
+  if (mode != SNE_WS_SKETCH) pf = std::max(pf, gram_partial_floats(n, D.K, D.K));
+  if (mode != SNE_WS_FREIGS) {
+    pf = std::max(pf, gram_partial_floats(n, D.h, D.h));
+    pf = std::max(pf, gram_partial_floats(n, D.k, D.k));
+  }
+  x.partial = bp.take<float>(pf);
+  const size_t S2 = (size_t)D.Sm * D.Sm;
+  for (auto &m : x.m64) m = bp.take<double>(S2);
+  x.eigscr = bp.take<char>(std::max(eig_scratch_bytes(D.Sm), (S2 + 4 * (size_t)D.Sm) * 8 + 1024));
+  for (auto &m : x.m32) m = bp.take<float>(S2);
+  x.w64 = bp.take<double>(D.Sm);
+  x.lam = bp.take<double>(D.Sm);
+  x.w32 = bp.take<float>(D.Sm);
+  x.perm = bp.take<int32_t>(D.Sm);
+  if (mode != SNE_WS_FREIGS) {
+    x.idxS = bp.take<int32_t>(D.nS);
+    x.uniqS = bp.take<int32_t>(D.nS);
+    x.posS = bp.take<int32_t>(D.nS);
+    x.signS = bp.take<int8_t>(D.nS);
+    x.idxO = bp.take<int32_t>(D.nO);
+    x.uniqO = bp.take<int32_t>(D.nO);
+    x.posO = bp.take<int32_t>(D.nO);
+    x.signO = bp.take<int8_t>(D.nO);
+    x.RpS = bp.take<float>((size_t)D.nS * D.k);
+    x.RpO = bp.take<float>((size_t)D.nO * D.k);
+    const int64_t vmax = min64(n, D.nO);
+    x.Yo = bp.take<float>((size_t)vmax * D.l);
+    x.Zf = bp.take<float>((size_t)D.l * D.l);
+    x.Gf = bp.take<float>((size_t)D.l * D.h);
+    x.G64 = bp.take<double>((size_t)D.l * D.h);
+    x.Gp = bp.take<double>((size_t)D.h * D.l);
+    x.Tm = bp.take<double>((size_t)D.h * D.l);
+    x.Z64 = bp.take<double>((size_t)D.l * D.l);
+  }
+  if (host_mode) {
+    x.h_rowptr = bp.take<int64_t>(D.n + 1);
+    x.h_col = bp.take<int32_t>(D.nnz);
+    x.h_val = bp.take<float>(D.nnz);
+    x.h_E = bp.take<float>((size_t)D.n * D.d);
+    x.h_sigma = bp.take<double>(D.d);
+  }
+  if (b) *b = x;
+  return (bp.off + 255) & ~(size_t)255;
+}
+
+#define CK(call)                               \
+  do {                                         \
+    cudaError_t e__ = (call);                  \
+    if (e__ != cudaSuccess) return SNE_ERR_CUDA; \
+  } while (0)
+
+int check_graph(const sne_csr *g) {
+  if (!g || g->n <= 0 || g->nnz < 0 || !g->row_ptr || (g->nnz > 0 && !g->col_idx))
+    return SNE_ERR_ARG;
+  if (g->n > (int64_t)INT32_MAX - 1) return SNE_ERR_SIZE;
+  return SNE_OK;
+}
+
+int check_ws(void *ws, size_t bytes, size_t need) {
+  if (!ws || ((uintptr_t)ws % 256) != 0 || bytes < need) return SNE_ERR_WORKSPACE;
+  return SNE_OK;
+}
+
+// --------------------------------------------------------------------------
+// Small kernels local to the orchestration
+// --------------------------------------------------------------------------
+// out_i = mult * vol * deg_i^beta  (0 for isolated vertices)
+__global__ void rowscale_kernel(const float *deg, int64_t n, float beta, const double *vol,
+                                double mult, float *out) {
+  const float s = (float)(mult * (vol ? *vol : 1.0));
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float d = deg[i];
+    out[i] = d > 0.f ? s * powf(d, beta) : 0.f;
+  }
+}
+
+// eigSVD step: M[:, j] = V[:, j] / sqrt(w_j)
+__global__ void inv_sqrt_cols_kernel(const float *V, int n, int ldv, const float *w, float *M, int ldm,
+                                     Ctrl *ctrl) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n * n; q += gridDim.x * blockDim.x) {
+    const int r = q / n, c = q % n;
+    const float wc = w[c];
+    if (!(wc > 0.f)) {
+      if (r == 0) record_error(ctrl, SNE_ERR_NUMERIC, W_EIGSVD);
+      M[(int64_t)r * ldm + c] = 0.f;
+    } else {
+      M[(int64_t)r * ldm + c] = V[(int64_t)r * ldv + c] * rsqrtf(wc);
+    }
+  }
+}
+
+// out[a][j] = V[a][perm[j]] * colscale_j  (FP32), j < ncols; optional value outputs
+__global__ void select_cols_kernel(const double *V, int rows, int ldv, const int32_t *perm,
+                                   const double *w, int ncols, int scale_mode, float *out, int ldo,
+                                   double *vals_out, int vals_abs) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < rows * ncols; q += gridDim.x * blockDim.x) {
+    const int a = q / ncols, j = q % ncols;
+    const int src = perm[j];
+    double s = 1.0;
+    if (scale_mode == 1) s = sqrt(fabs(w[src]));
+    out[(int64_t)a * ldo + j] = (float)(V[(int64_t)a * ldv + src] * s);
+    if (a == 0 && vals_out) vals_out[j] = vals_abs ? fabs(w[src]) : w[src];
+  }
+}
+
+// K = G diag(lam) (FP32, k x k), G given in FP64
+__global__ void scale_cols_d2f_kernel(const double *G, int k, const double *lam, float *K) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < k * k; q += gridDim.x * blockDim.x) {
+    const int c = q % k;
+    K[q] = (float)(G[q] * lam[c]);
+  }
+}
+
+// I (k x k FP32)
+__global__ void eye_kernel(float *I, int k) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < k * k; q += gridDim.x * blockDim.x)
+    I[q] = (q / k == q % k) ? 1.f : 0.f;
+}
+
+// CfT[a][c] = lam_c * Csum[c][a]   i.e. (diag(lam) Csum)^T
+__global__ void core_transpose_kernel(const float *Csum, int k, const double *lam, float *CfT) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < k * k; q += gridDim.x * blockDim.x) {
+    const int a = q / k, c = q % k;
+    CfT[q] = (float)lam[c] * Csum[(int64_t)c * k + a];
+  }
+}
+
+inline unsigned grid_for(int64_t work, int per = 256, int cap = 152 * 8) {
+  int64_t b = (work + per - 1) / per;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (unsigned)b;
+}
+
+// --------------------------------------------------------------------------
+// Pipeline pieces
+// --------------------------------------------------------------------------
+// Q (n x w) = orth(Y) with eigSVD (frPCA: B = Y^T Y = V diag(w) V^T,
+// Q = Y V diag(w)^-1/2) or Cholesky QR (B = R^T R, Q = Y R^-1).  The small
+// factorization runs in FP64 when `fp64` (sketch QR), else in FP32 (the
+// orthonormalizations inside the power iteration of Alg. 5).
+int orth_tall(const Dims &D, const Bufs &b, int method, bool fp64, const float *Y, int64_t ldy, int w,
+              float *Q, int64_t ldq, cudaStream_t st) {
+  CK(launch_gram(Y, ldy, w, Y, ldy, w, D.n, nullptr, true, b.partial, b.m64[0], w, st));
+  if (method == SNE_ORTH_EIGSVD) {
+    CK(launch_d2f(b.m64[0], w, w, w, b.m32[0], w, st));
+    CK(launch_sym_eig<float>(b.m32[0], w, w, b.w32, b.m32[1], w, b.eigscr, b.ctrl, st));
+    { ProfScope ps_(K_MISC, st); inv_sqrt_cols_kernel<<<grid_for((int64_t)w * w), 256, 0, st>>>(b.m32[1], w, w, b.w32, b.m32[2],
+                                                                   w, b.ctrl); }
+    CK(cudaGetLastError());
+  } else if (fp64) {
+    CK(launch_chol_inverse<double>(b.m64[0], w, w, b.m64[1], w, b.m64[2], b.ctrl, st));
+    CK(launch_d2f(b.m64[1], w, w, w, b.m32[2], w, st));
+  } else {
+    CK(launch_d2f(b.m64[0], w, w, w, b.m32[0], w, st));
+    CK(launch_chol_inverse<float>(b.m32[0], w, w, b.m32[2], w, b.m32[1], b.ctrl, st));
+  }
+  CK(launch_tall_gemm(Y, ldy, nullptr, D.n, w, b.m32[2], w, w, nullptr, Q, ldq, st));
+  return SNE_OK;
+}
+
+// Alg. 5.  Leaves U_k (n x k, ld k) in `U` and lambda (k) in `lam`.
+int run_freigs(const sne_csr &g, const sne_params &p, const Dims &D, const Bufs &b, float *U,
+               double *lam, cudaStream_t st) {
+  const int K = D.K;
+  const int64_t ld = D.Wab;
+  float *Q = b.A, *T1 = b.B, *T2 = b.C;
+  CK(launch_degree_power(b.deg, D.n, -p.alpha, b.dpow, 1.0f, st));
+  CK(launch_gaussian(D.n, K, p.seed, 1, T1, ld, st));              // Omega
+  CK(launch_spmm(g, b.dpow, T1, ld, K, T2, K, st));                // Y = X Omega
+  int rc = orth_tall(D, b, p.orth, false, T2, K, K, Q, ld, st);    // Q = eigSVD(Y)
+  if (rc) return rc;
+  for (int it = 0; it < p.q; ++it) {
+    CK(launch_spmm(g, b.dpow, Q, ld, K, T1, ld, st));              // X Q
+    CK(launch_spmm(g, b.dpow, T1, ld, K, T2, K, st));              // X X Q
+    rc = orth_tall(D, b, p.orth, false, T2, K, K, Q, ld, st);      // Q = eigSVD(X X Q)
+    if (rc) return rc;
+  }
+  // one more FP32 Cholesky-QR pass over the final basis (a no-op in exact
+  // arithmetic) so that Q is orthonormal to working precision before the
+  // Rayleigh-Ritz step assumes Q^T Q = I
+  CK(cudaMemcpy2DAsync(T2, K * sizeof(float), Q, ld * sizeof(float), K * sizeof(float), D.n,
+                       cudaMemcpyDeviceToDevice, st));
+  rc = orth_tall(D, b, SNE_ORTH_CHOLQR, false, T2, K, K, Q, ld, st);
+  if (rc) return rc;
+  // Rayleigh-Ritz: S = Q^T X Q (FP64), eig(S), U = Q U_hat, top k by |lambda|
+  CK(launch_spmm(g, b.dpow, Q, ld, K, T1, ld, st));
+  CK(launch_gram(Q, ld, K, T1, ld, K, D.n, nullptr, false, b.partial, b.m64[0], K, st));
+  CK(launch_symmetrize(b.m64[0], K, K, st));
+  CK(launch_sym_eig<double>(b.m64[0], K, K, b.w64, b.m64[1], K, b.eigscr, b.ctrl, st));
+  CK(launch_eig_order<double>(b.w64, K, true, b.perm, st));
+  { ProfScope ps_(K_MISC, st); select_cols_kernel<<<grid_for((int64_t)K * D.k), 256, 0, st>>>(b.m64[1], K, K, b.perm, b.w64, D.k,
+                                                                 0, b.m32[0], D.k, lam, 0); }
+  CK(cudaGetLastError());
+  CK(launch_tall_gemm(Q, ld, nullptr, D.n, K, b.m32[0], D.k, D.k, nullptr, U, D.k, st));
+  return SNE_OK;
+}
+
+// Eq. 11 + Alg. 4 from U_k (ld k), lambda.  Optional outputs Y, Z, E, sigma.
+int run_sketch(const sne_csr &g, const sne_params &p, const Dims &D, const Bufs &b, const float *U,
+               const double *lam, float *Yout, float *Zout, float *E, double *sigma,
+               cudaStream_t st) {
+  const int k = D.k, h = D.h, l = D.l, z = D.z;
+  const float sv = 1.0f / sqrtf((float)z);
+  // --- Eq. 11 factors
+  CK(launch_degree_power(b.deg, D.n, -1.0 + p.alpha, b.acoef, 1.0f, st));      // a = d^(-1+alpha)
+  CK(launch_degree_power(b.deg, D.n, -1.0 + 2.0 * p.alpha, b.wgt, 1.0f, st));  // d^(-1+2alpha)
+  { ProfScope ps_(K_MISC, st); rowscale_kernel<<<grid_for(D.n), 256, 0, st>>>(b.deg, D.n, (float)(-1.0 + p.alpha), &b.ctrl->vol,
+                                                 1.0 / (p.b * p.T), b.rsc); }    // vol/(bT) a
+  CK(cudaGetLastError());
+  CK(launch_gram(U, k, k, U, k, k, D.n, b.wgt, true, b.partial, b.m64[0], k, st));  // U^T D U
+  { ProfScope ps_(K_MISC, st); scale_cols_d2f_kernel<<<grid_for((int64_t)k * k), 256, 0, st>>>(b.m64[0], k, lam, b.m32[0]); }  // K
+  { ProfScope ps_(K_MISC, st); eye_kernel<<<grid_for((int64_t)k * k), 256, 0, st>>>(b.m32[1], k); }                            // I
+  CK(cudaGetLastError());
+  // Horner: Csum = I + K (I + K (... (I))) = sum_{r=1..T} K^(r-1)
+  float *cur = b.m32[1], *nxt = b.m32[2];
+  for (int r = 1; r < p.T; ++r) {
+    { ProfScope ps_(K_MISC, st); eye_kernel<<<grid_for((int64_t)k * k), 256, 0, st>>>(nxt, k); }
+    CK(cudaGetLastError());
+    CK(launch_small_gemm<float>(false, false, k, k, k, 1.0f, b.m32[0], k, cur, k, 1.0f, nxt, k, st));
+    std::swap(cur, nxt);
+  }
+  { ProfScope ps_(K_MISC, st); core_transpose_kernel<<<grid_for((int64_t)k * k), 256, 0, st>>>(cur, k, lam, b.m32[3]); }  // C^T
+  CK(cudaGetLastError());
+  // --- Alg. 3: S (stream 2) and O (stream 3); unique coordinates
+  CK(launch_sparse_sign(D.n, h, z, p.seed, 2, b.idxS, b.signS, b.ctrl, st));
+  CK(launch_sparse_sign(D.n, l, z, p.seed, 3, b.idxO, b.signO, b.ctrl, st));
+  CK(launch_unique(b.idxS, D.nS, b.uniqS, &b.ctrl->v_s, b.posS, b.ctrl, W_UNIQUE, st));
+  CK(launch_unique(b.idxO, D.nO, b.uniqO, &b.ctrl->v_o, b.posO, b.ctrl, W_UNIQUE, st));
+  // R'(:, idx)^T = a_idx U(idx, :) C^T
+  CK(launch_tall_gemm(U, k, b.idxS, D.nS, k, b.m32[3], k, k, b.acoef, b.RpS, k, st));
+  CK(launch_tall_gemm(U, k, b.idxO, D.nO, k, b.m32[3], k, k, b.acoef, b.RpO, k, st));
+  // --- Alg. 4 line 4: Y = f(L' R'(:, p)) S(p, :)
+  float *Y = Yout ? Yout : b.A;
+  CK(launch_fused_sketch_f32(U, k, nullptr, nullptr, D.n, k, b.rsc, b.RpS, b.signS, h, z, sv, p.f, Y,
+                             h, st));
+  // --- Alg. 4 line 7: Z = O(p,:)^T f(L'(p,:) R'(:,p)) O(p,:)
+  const int64_t vmax = min64(D.n, D.nO);
+  CK(launch_fused_sketch_f32(U, k, b.uniqO, &b.ctrl->v_o, vmax, k, b.rsc, b.RpO, b.signO, l, z, sv,
+                             p.f, b.Yo, l, st));
+  float *Z = Zout ? Zout : b.Zf;
+  CK(launch_signed_gather_sum(b.Yo, l, l, b.posO, b.signO, l, z, sv, Z, l, st));
+  if (!E && !sigma) return SNE_OK;
+  // --- Alg. 4 line 5: Q = orth(Y) by Cholesky QR, twice
+  int rc = orth_tall(D, b, SNE_ORTH_CHOLQR, true, Y, h, h, b.B, h, st);  // Q1
+  if (rc) return rc;
+  rc = orth_tall(D, b, SNE_ORTH_CHOLQR, true, b.B, h, h, b.A, h, st);    // Q
+  if (rc) return rc;
+  float *Q = b.A;
+  // --- Alg. 4 line 8: W = (O^T Q)^+ Z (Q^T O)^+ via the normal equations (FP64)
+  CK(launch_signed_gather_sum(Q, h, h, b.idxO, b.signO, l, z, sv, b.Gf, h, st));  // G = O^T Q
+  CK(launch_f2d(b.Gf, l, h, h, b.G64, h, st));
+  CK(launch_f2d(Z, l, l, l, b.Z64, l, st));
+  CK(launch_small_gemm<double>(true, false, h, h, l, 1.0, b.G64, h, b.G64, h, 0.0, b.m64[0], h, st));
+  CK(launch_chol_inverse<double>(b.m64[0], h, h, b.m64[1], h, b.m64[2], b.ctrl, st));  // R^-1, G^T G = R^T R
+  CK(launch_small_gemm<double>(false, true, h, h, h, 1.0, b.m64[1], h, b.m64[1], h, 0.0, b.m64[2], h,
+                               st));                                               // (G^T G)^-1
+  CK(launch_small_gemm<double>(false, true, h, l, h, 1.0, b.m64[2], h, b.G64, h, 0.0, b.Gp, l, st));
+  CK(launch_small_gemm<double>(false, false, h, l, l, 1.0, b.Gp, l, b.Z64, l, 0.0, b.Tm, l, st));
+  CK(launch_small_gemm<double>(false, true, h, h, l, 1.0, b.Tm, l, b.Gp, l, 0.0, b.m64[3], h, st));
+  // --- Alg. 4 line 9: svd(W).  W is symmetric (Z is), so its singular values
+  // are |eigenvalues| and its left singular vectors are eigenvectors (Lemma 1).
+  CK(launch_symmetrize(b.m64[3], h, h, st));
+  CK(launch_sym_eig<double>(b.m64[3], h, h, b.w64, b.m64[4], h, b.eigscr, b.ctrl, st));
+  CK(launch_eig_order<double>(b.w64, h, true, b.perm, st));
+  // E = Q U_hat(:, 1:d) Sigma_d^(1/2)  (Alg. 4 line 10, Alg. 6 line 5)
+  { ProfScope ps_(K_MISC, st); select_cols_kernel<<<grid_for((int64_t)h * D.d), 256, 0, st>>>(b.m64[4], h, h, b.perm, b.w64, D.d,
+                                                                 1, b.m32[0], D.d, sigma, 1); }
+  CK(cudaGetLastError());
+  if (E) CK(launch_tall_gemm(Q, h, nullptr, D.n, h, b.m32[0], D.d, D.d, nullptr, E, D.d, st));
+  return SNE_OK;
+}
+
+}  // namespace
+
+// ==========================================================================
+// extern "C" entry points
+// ==========================================================================
+extern "C" {
+
+int sne_params_init(sne_params *p, int32_t d, int32_t k) {
+  if (!p || d <= 0 || k <= 0) return SNE_ERR_ARG;
+  std::memset(p, 0, sizeof(*p));
+  p->k = k;
+  p->q = 20;
+  p->T = 10;
+  p->d = d;
+  p->h = 2 * d + 16;
+  p->l = d + 1000;
+  p->zeta = 8;
+  p->s_eig = 16;
+  p->row_block = 0;
+  p->precision = SNE_FP32;
+  p->f = SNE_F_TRUNC_LOG;
+  p->orth = SNE_ORTH_EIGSVD;
+  p->alpha = 0.5;
+  p->b = 1.0;
+  p->seed = 0;
+  return SNE_OK;
+}
+
+const char *sne_error_string(int code) {
+  switch (code) {
+    case SNE_OK: return "ok";
+    case SNE_ERR_ARG: return "invalid argument";
+    case SNE_ERR_GRAPH: return "invalid graph (CSR not monotone, out of range or asymmetric)";
+    case SNE_ERR_SIZE: return "inconsistent or unsupported sizes";
+    case SNE_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
+    case SNE_ERR_CUDA: return "CUDA error";
+    case SNE_ERR_TIMEOUT: return "bounded device wait timed out";
+    case SNE_ERR_NUMERIC: return "numerical failure (NaN/Inf or non-positive pivot)";
+    default: return "unknown error";
+  }
+}
+
+int sne_workspace_bytes(int64_t n, int64_t nnz, const sne_params *p, int mode, size_t *bytes) {
+  if (!bytes || mode < SNE_WS_EMBED || mode > SNE_WS_EMBED_HOST) return SNE_ERR_ARG;
+  Dims D;
+  int rc = make_dims(n, nnz, p, mode, &D);
+  if (rc) return rc;
+  *bytes = carve(D, mode, nullptr, nullptr);
+  return SNE_OK;
+}
+
+int sne_status_reset(void *ws, sne_stream_t stream) {
+  if (!ws) return SNE_ERR_WORKSPACE;
+  return cudaMemsetAsync(ws, 0, sizeof(Ctrl), (cudaStream_t)stream) == cudaSuccess ? SNE_OK
+                                                                                 : SNE_ERR_CUDA;
+}
+
+int sne_status(const void *ws, sne_stream_t stream) {
+  if (!ws) return SNE_ERR_WORKSPACE;
+  int32_t st = 0;
+  if (cudaMemcpyAsync(&st, ws, sizeof(int32_t), cudaMemcpyDeviceToHost, (cudaStream_t)stream) !=
+      cudaSuccess)
+    return SNE_ERR_CUDA;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return SNE_ERR_CUDA;
+  return st;
+}
+
+int sne_stats_read(const void *ws, sne_stats *out, sne_stream_t stream) {
+  if (!ws || !out) return SNE_ERR_ARG;
+  Ctrl c;
+  if (cudaMemcpyAsync(&c, ws, sizeof(Ctrl), cudaMemcpyDeviceToHost, (cudaStream_t)stream) !=
+      cudaSuccess)
+    return SNE_ERR_CUDA;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return SNE_ERR_CUDA;
+  out->status = c.status;
+  out->where = c.where;
+  out->v_s = c.v_s;
+  out->v_o = c.v_o;
+  out->vol = c.vol;
+  return SNE_OK;
+}
+
+int sne_sparse_sign(int64_t n, int32_t cols, int32_t zeta, uint64_t seed, int32_t stream_id,
+                    int32_t *idx, int8_t *sign, sne_stream_t stream) {
+  if (n <= 0 || cols < 0 || zeta <= 0 || !idx || !sign || n > (int64_t)INT32_MAX - 1)
+    return SNE_ERR_ARG;
+  const int z = (int)min64(n, zeta);
+  if (z > 64) return SNE_ERR_SIZE;
+  return launch_sparse_sign(n, cols, z, seed, stream_id, idx, sign, nullptr, (cudaStream_t)stream) ==
+                 cudaSuccess
+             ? SNE_OK
+             : SNE_ERR_CUDA;
+}
+
+int sne_gaussian(int64_t n, int32_t cols, uint64_t seed, int32_t stream_id, float *out,
+                 sne_stream_t stream) {
+  if (n < 0 || cols < 0 || (!out && n * cols > 0)) return SNE_ERR_ARG;
+  return launch_gaussian(n, cols, seed, stream_id, out, cols, (cudaStream_t)stream) == cudaSuccess
+             ? SNE_OK
+             : SNE_ERR_CUDA;
+}
+
+int sne_degrees(const sne_csr *g, float *deg, double *vol, sne_stream_t stream) {
+  int rc = check_graph(g);
+  if (rc) return rc;
+  if (!deg || !vol) return SNE_ERR_ARG;
+  return launch_degrees(*g, deg, vol, (cudaStream_t)stream) == cudaSuccess ? SNE_OK : SNE_ERR_CUDA;
+}
+
+int sne_degree_power(const float *deg, int64_t n, double beta, float *out, sne_stream_t stream) {
+  if (n < 0 || (n > 0 && (!deg || !out))) return SNE_ERR_ARG;
+  return launch_degree_power(deg, n, beta, out, 1.0f, (cudaStream_t)stream) == cudaSuccess
+             ? SNE_OK
+             : SNE_ERR_CUDA;
+}
+
+int sne_spmm(const sne_csr *g, const float *dpow, const float *B, int32_t ncols, float *Y,
+             sne_stream_t stream) {
+  int rc = check_graph(g);
+  if (rc) return rc;
+  if (!dpow || !B || !Y || ncols <= 0 || B == Y) return SNE_ERR_ARG;
+  return launch_spmm(*g, dpow, B, ncols, ncols, Y, ncols, (cudaStream_t)stream) == cudaSuccess
+             ? SNE_OK
+             : SNE_ERR_CUDA;
+}
+
+int sne_validate_csr(const sne_csr *g, void *ws, size_t ws_bytes, sne_stream_t stream) {
+  int rc = check_graph(g);
+  if (rc) return rc;
+  rc = check_ws(ws, ws_bytes, sizeof(Ctrl));
+  if (rc) return rc;
+  return launch_validate(*g, reinterpret_cast<Ctrl *>(ws), (cudaStream_t)stream) == cudaSuccess
+             ? SNE_OK
+             : SNE_ERR_CUDA;
+}
+
+int sne_freigs(const sne_csr *g, const sne_params *p, void *ws, size_t ws_bytes, float *U,
+               double *lambda, sne_stream_t stream) {
+  int rc = check_graph(g);
+  if (rc) return rc;
+  Dims D;
+  rc = make_dims(g->n, g->nnz, p, SNE_WS_FREIGS, &D);
+  if (rc) return rc;
+  Bufs b;
+  rc = check_ws(ws, ws_bytes, carve(D, SNE_WS_FREIGS, nullptr, nullptr));
+  if (rc) return rc;
+  if (!U || !lambda) return SNE_ERR_ARG;
+  carve(D, SNE_WS_FREIGS, ws, &b);
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaMemsetAsync(b.ctrl, 0, sizeof(Ctrl), st));
+  CK(launch_degrees(*g, b.deg, &b.ctrl->vol, st));
+  return run_freigs(*g, *p, D, b, U, lambda, st);
+}
+
+int sne_sketch_from_factors(const sne_csr *g, const sne_params *p, const float *U,
+                            const double *lambda, void *ws, size_t ws_bytes, float *Y, float *Z,
+                            float *E, double *sigma, sne_stream_t stream) {
+  int rc = check_graph(g);
+  if (rc) return rc;
+  Dims D;
+  rc = make_dims(g->n, g->nnz, p, SNE_WS_SKETCH, &D);
+  if (rc) return rc;
+  rc = check_ws(ws, ws_bytes, carve(D, SNE_WS_SKETCH, nullptr, nullptr));
+  if (rc) return rc;
+  if (!U || !lambda) return SNE_ERR_ARG;
+  if (p->precision != SNE_FP32) return SNE_ERR_ARG;  // mixed precision: see sketch_tc.cu
+  Bufs b;
+  carve(D, SNE_WS_SKETCH, ws, &b);
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaMemsetAsync(b.ctrl, 0, sizeof(Ctrl), st));
+  CK(launch_degrees(*g, b.deg, &b.ctrl->vol, st));
+  return run_sketch(*g, *p, D, b, U, lambda, Y, Z, E, sigma, st);
+}
+
+int sne_embed(const sne_csr *g, const sne_params *p, void *ws, size_t ws_bytes, float *E,
+              double *sigma, sne_stream_t stream) {
+  int rc = check_graph(g);
+  if (rc) return rc;
+  Dims D;
+  rc = make_dims(g->n, g->nnz, p, SNE_WS_EMBED, &D);
+  if (rc) return rc;
+  rc = check_ws(ws, ws_bytes, carve(D, SNE_WS_EMBED, nullptr, nullptr));
+  if (rc) return rc;
+  if (!E || !sigma) return SNE_ERR_ARG;
+  if (p->precision != SNE_FP32) return SNE_ERR_ARG;
+  Bufs b;
+  carve(D, SNE_WS_EMBED, ws, &b);
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaMemsetAsync(b.ctrl, 0, sizeof(Ctrl), st));
+  CK(launch_degrees(*g, b.deg, &b.ctrl->vol, st));
+  // U_k goes to the third tall buffer, lambda to the FP64 scratch tail
+  float *Uk = b.C;
+  double *lam = b.lam;
+  rc = run_freigs(*g, *p, D, b, Uk, lam, st);
+  if (rc) return rc;
+  return run_sketch(*g, *p, D, b, Uk, lam, nullptr, nullptr, E, sigma, st);
+}
+
+int sne_embed_host(const sne_csr *g, const sne_params *p, void *ws, size_t ws_bytes, float *E_host,
+                   double *sigma_host, sne_stream_t stream) {
+  int rc = check_graph(g);
+  if (rc) return rc;
+  Dims D;
+  rc = make_dims(g->n, g->nnz, p, SNE_WS_EMBED_HOST, &D);
+  if (rc) return rc;
+  rc = check_ws(ws, ws_bytes, carve(D, SNE_WS_EMBED_HOST, nullptr, nullptr));
+  if (rc) return rc;
+  if (!E_host || !sigma_host) return SNE_ERR_ARG;
+  Bufs b;
+  carve(D, SNE_WS_EMBED_HOST, ws, &b);
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(b.h_rowptr, g->row_ptr, (D.n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  if (D.nnz > 0)
+    CK(cudaMemcpyAsync(b.h_col, g->col_idx, D.nnz * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  if (g->val && D.nnz > 0)
+    CK(cudaMemcpyAsync(b.h_val, g->val, D.nnz * sizeof(float), cudaMemcpyHostToDevice, st));
+  sne_csr dg{g->n, g->nnz, b.h_rowptr, b.h_col, g->val ? b.h_val : nullptr};
+  rc = sne_embed(&dg, p, ws, ws_bytes, b.h_E, b.h_sigma, stream);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(E_host, b.h_E, (size_t)D.n * D.d * sizeof(float), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(sigma_host, b.h_sigma, D.d * sizeof(double), cudaMemcpyDeviceToHost, st));
+  return SNE_OK;
+}
+
+}  // extern "C"

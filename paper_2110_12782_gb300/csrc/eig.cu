@@ -1,0 +1,454 @@
+// Small symmetric eigensolver and Cholesky factorization for the Gram and
+// reduced matrices of Alg. 4 and Alg. 5 (sizes up to a few hundred).
+//
+// FP32 eigendecomposition: cyclic Jacobi with the round-robin ("circle")
+// ordering.  A round pairs all indices into m/2 disjoint pairs (m = n rounded
+// up to even); the m/2 rotations are computed from the current matrix and
+// applied at once as independent 2x2 blocks J_i^T A_(i,j) J_j, with the
+// symmetric matrix packed (lower triangle) in shared memory of one CTA.  A
+// sweep is m-1 rounds; sweeps stop when every off-diagonal element is below
+// eps * sqrt(|a_pp a_qq|).  Each round's rotations are recorded; a second,
+// multi-CTA kernel accumulates V = J_1 J_2 ... row block by row block.
+//
+// FP64 eigendecomposition (Rayleigh-Ritz, svd(W)): the FP32 result refined in
+// FP64 by the iteration of Ogita and Aishima ("Iterative refinement for
+// symmetric eigenvalue decomposition", Japan J. Indust. Appl. Math. 35, 2018):
+// R = I - X^T X, S = X^T A X, lambda_i = s_ii / (1 - r_ii),
+// delta = 2 (|S - diag(lambda)| + |A| |R|), E_ij = (s_ij + lambda_j r_ij) /
+// (lambda_j - lambda_i) when |lambda_i - lambda_j| > delta, else r_ij / 2,
+// X <- X + X E; two iterations.
+#include <cfloat>
+#include <cmath>
+
+#include "sne_internal.cuh"
+
+namespace sne {
+
+constexpr int kJacobiMaxN = 320;
+constexpr int kJacobiMaxSweeps = 30;
+
+struct Rot {
+  int p, q;
+  float c, s;
+};
+
+__device__ __forceinline__ int packed_lower(int a, int b) {  // a >= b
+  return a * (a + 1) / 2 + b;
+}
+__device__ __forceinline__ int packed_any(int a, int b) {
+  return a >= b ? packed_lower(a, b) : packed_lower(b, a);
+}
+
+// circle method: pair t of round r among m players (m even)
+__device__ __forceinline__ void rr_pair(int m, int r, int t, int *p, int *q) {
+  int a, b;
+  if (t == 0) {
+    a = 0;
+    b = 1 + (r % (m - 1));
+  } else {
+    a = 1 + ((r + t) % (m - 1));
+    b = 1 + ((r + m - 1 - t) % (m - 1));
+  }
+  *p = min(a, b);
+  *q = max(a, b);
+}
+
+size_t jacobi_rot_capacity(int n) {
+  const int m = n + (n & 1);
+  return (size_t)kJacobiMaxSweeps * (m - 1) * (m / 2);
+}
+
+__global__ void __launch_bounds__(1024) jacobi_kernel(const float *__restrict__ A, int n, int lda,
+                                                      float *__restrict__ w, Rot *__restrict__ rot,
+                                                      int *__restrict__ nrounds, Ctrl *ctrl) {
+  extern __shared__ __align__(16) float jsm[];
+  const int m = n + (n & 1);
+  const int P = m / 2;
+  float *Ap = jsm;                                   // n(n+1)/2
+  float *rc = Ap + n * (n + 1) / 2;                  // P
+  float *rs = rc + P;                                // P
+  int *rp = reinterpret_cast<int *>(rs + P);         // P
+  int *rq = rp + P;                                  // P
+  __shared__ unsigned int off_bits;
+  __shared__ float offmax_final;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < n * (n + 1) / 2; e += nt) {
+    const int a = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+    int aa = a;
+    while (aa * (aa + 1) / 2 > e) --aa;
+    while ((aa + 1) * (aa + 2) / 2 <= e) ++aa;
+    const int b = e - aa * (aa + 1) / 2;
+    Ap[e] = A[(int64_t)aa * lda + b];
+  }
+  __syncthreads();
+  const float tol = 2.0f * FLT_EPSILON;
+  const int nblocks = P * (P + 1) / 2;
+  int round = 0;
+  int sweep = 0;
+  for (; sweep < kJacobiMaxSweeps; ++sweep) {
+    if (tid == 0) off_bits = 0u;
+    __syncthreads();
+    for (int r = 0; r < m - 1; ++r) {
+      for (int t = tid; t < P; t += nt) {
+        int p, q;
+        rr_pair(m, r, t, &p, &q);
+        float c = 1.0f, s = 0.0f;
+        if (q < n) {
+          const float apq = Ap[packed_lower(q, p)];
+          const float app = Ap[packed_lower(p, p)], aqq = Ap[packed_lower(q, q)];
+          const float scale = sqrtf(fabsf(app * aqq));
+          const float rel = (apq == 0.0f) ? 0.0f : (scale > 0.0f ? fabsf(apq) / scale : FLT_MAX);
+          atomicMax(&off_bits, __float_as_uint(rel));
+          if (rel > tol) {
+            const float tau = (aqq - app) / (2.0f * apq);
+            const float tt = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
+            c = rsqrtf(1.0f + tt * tt);
+            s = tt * c;
+          }
+        }
+        rc[t] = c;
+        rs[t] = s;
+        rp[t] = p;
+        rq[t] = q;
+        rot[(int64_t)round * P + t] = Rot{p, q, c, s};
+      }
+      __syncthreads();
+      for (int bi = tid; bi < nblocks; bi += nt) {
+        int j = (int)((sqrtf(8.0f * bi + 1.0f) - 1.0f) * 0.5f);
+        while (j * (j + 1) / 2 > bi) --j;
+        while ((j + 1) * (j + 2) / 2 <= bi) ++j;
+        const int i = bi - j * (j + 1) / 2;  // i <= j
+        const float c1 = rc[i], s1 = rs[i], c2 = rc[j], s2 = rs[j];
+        if (s1 == 0.0f && s2 == 0.0f) continue;
+        const int p1 = rp[i], q1 = rq[i], p2 = rp[j], q2 = rq[j];
+        if (i == j) {
+          if (q1 >= n) continue;
+          const float app = Ap[packed_lower(p1, p1)], aqq = Ap[packed_lower(q1, q1)];
+          const float apq = Ap[packed_lower(q1, p1)];
+          const float t_ = s1 / c1;
+          Ap[packed_lower(p1, p1)] = app - t_ * apq;
+          Ap[packed_lower(q1, q1)] = aqq + t_ * apq;
+          Ap[packed_lower(q1, p1)] = 0.0f;
+          continue;
+        }
+        // block rows (p1, q1), columns (p2, q2): B' = J1^T B J2
+        const bool v1q = q1 < n, v2q = q2 < n;
+        const float b00 = Ap[packed_any(p1, p2)];
+        const float b01 = v2q ? Ap[packed_any(p1, q2)] : 0.0f;
+        const float b10 = v1q ? Ap[packed_any(q1, p2)] : 0.0f;
+        const float b11 = (v1q && v2q) ? Ap[packed_any(q1, q2)] : 0.0f;
+        const float x1 = c1 * b00 - s1 * b10, x2 = c1 * b01 - s1 * b11;
+        const float x3 = s1 * b00 + c1 * b10, x4 = s1 * b01 + c1 * b11;
+        Ap[packed_any(p1, p2)] = x1 * c2 - x2 * s2;
+        if (v2q) Ap[packed_any(p1, q2)] = x1 * s2 + x2 * c2;
+        if (v1q) Ap[packed_any(q1, p2)] = x3 * c2 - x4 * s2;
+        if (v1q && v2q) Ap[packed_any(q1, q2)] = x3 * s2 + x4 * c2;
+      }
+      __syncthreads();
+      ++round;
+    }
+    const float om = __uint_as_float(off_bits);  // read by all before anyone resets it
+    __syncthreads();
+    if (om <= tol) {
+      ++sweep;
+      break;
+    }
+  }
+  if (tid == 0) {
+    offmax_final = __uint_as_float(off_bits);
+    *nrounds = round;
+  }
+  __syncthreads();
+  if (offmax_final > 1e-4f && tid == 0) record_error(ctrl, SNE_ERR_NUMERIC, W_EIG);
+  for (int i = tid; i < n; i += nt) w[i] = Ap[packed_lower(i, i)];
+}
+
+// V = J_1 J_2 ... J_R (row block per CTA, rows held in shared memory)
+constexpr int kVRows = 16;
+__global__ void __launch_bounds__(256) jacobi_vectors_kernel(const Rot *__restrict__ rot,
+                                                             const int *__restrict__ nrounds, int n,
+                                                             float *__restrict__ V, int ldv) {
+  extern __shared__ __align__(16) float vs[];  // kVRows x (n + 1)
+  const int ld = n + 1;
+  const int r0 = blockIdx.x * kVRows;
+  const int rows = min(kVRows, n - r0);
+  const int tid = threadIdx.x;
+  for (int e = tid; e < kVRows * ld; e += blockDim.x) {
+    const int rr = e / ld, cc = e % ld;
+    vs[e] = (rr < rows && r0 + rr == cc) ? 1.0f : 0.0f;
+  }
+  __syncthreads();
+  const int m = n + (n & 1);
+  const int P = m / 2;
+  const int R = *nrounds;
+  for (int r = 0; r < R; ++r) {
+    const Rot *rr = rot + (int64_t)r * P;
+    for (int it = tid; it < rows * P; it += blockDim.x) {
+      const int row = it / P, t = it % P;
+      const Rot g = rr[t];
+      if (g.s == 0.0f || g.q >= n) continue;
+      float *v = vs + row * ld;
+      const float vp = v[g.p], vq = v[g.q];
+      v[g.p] = g.c * vp - g.s * vq;
+      v[g.q] = g.s * vp + g.c * vq;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < rows * n; e += blockDim.x) {
+    const int rr = e / n, cc = e % n;
+    V[(int64_t)(r0 + rr) * ldv + cc] = vs[rr * ld + cc];
+  }
+}
+
+cudaError_t launch_jacobi_f32(const float *A, int32_t n, int32_t lda, float *w, float *V, int32_t ldv,
+                              void *rot_scratch, int *nrounds, Ctrl *ctrl, cudaStream_t st) {
+  const int m = n + (n & 1);
+  const size_t smem = ((size_t)n * (n + 1) / 2 + 2 * (m / 2)) * sizeof(float) + 2 * (m / 2) * sizeof(int);
+  cudaError_t e = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  {
+    ProfScope ps_(K_EIG, st);
+    jacobi_kernel<<<1, 1024, smem, st>>>(A, n, lda, w, reinterpret_cast<Rot *>(rot_scratch), nrounds,
+                                         ctrl);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t vsm = (size_t)kVRows * (n + 1) * sizeof(float);
+  e = cudaFuncSetAttribute(jacobi_vectors_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)vsm);
+  if (e != cudaSuccess) return e;
+  {
+    ProfScope ps_(K_EIG, st);
+    jacobi_vectors_kernel<<<(n + kVRows - 1) / kVRows, 256, vsm, st>>>(
+        reinterpret_cast<const Rot *>(rot_scratch), nrounds, n, V, ldv);
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Ogita-Aishima refinement step (FP64), single CTA:
+// given T1 = X^T X and S = X^T A X, writes lambda and E (over T1).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) oa_update_kernel(double *T1, const double *S, const double *A,
+                                                         int lda, int n, double *lam) {
+  __shared__ double red[3][32];
+  __shared__ double sdelta;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < n; i += nt) lam[i] = S[(int64_t)i * n + i] / T1[(int64_t)i * n + i];
+  __syncthreads();
+  double so = 0.0, sa = 0.0, sr = 0.0;
+  for (int64_t q = tid; q < (int64_t)n * n; q += nt) {
+    const int i = (int)(q / n), j = (int)(q % n);
+    const double s = S[q] - (i == j ? lam[i] : 0.0);
+    const double r = (i == j ? 1.0 : 0.0) - T1[q];
+    so += s * s;
+    const double av = A[(int64_t)i * lda + j];
+    sa += av * av;
+    sr += r * r;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    so += __shfl_xor_sync(0xffffffffu, so, o);
+    sa += __shfl_xor_sync(0xffffffffu, sa, o);
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+  }
+  if ((tid & 31) == 0) {
+    red[0][tid >> 5] = so;
+    red[1][tid >> 5] = sa;
+    red[2][tid >> 5] = sr;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0, b = 0, c = 0;
+    for (int wv = 0; wv < (nt >> 5); ++wv) {
+      a += red[0][wv];
+      b += red[1][wv];
+      c += red[2][wv];
+    }
+    sdelta = 2.0 * (sqrt(a) + sqrt(b) * sqrt(c));
+  }
+  __syncthreads();
+  const double delta = sdelta;
+  for (int64_t q = tid; q < (int64_t)n * n; q += nt) {
+    const int i = (int)(q / n), j = (int)(q % n);
+    const double r = (i == j ? 1.0 : 0.0) - T1[q];
+    const double gap = lam[j] - lam[i];
+    double e;
+    if (i != j && fabs(gap) > delta) e = (S[q] + lam[j] * r) / gap;
+    else e = 0.5 * r;
+    T1[q] = e;
+  }
+}
+
+__global__ void add_inplace_kernel(double *X, const double *Y, int64_t count) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < count;
+       q += (int64_t)gridDim.x * blockDim.x)
+    X[q] += Y[q];
+}
+
+// ---------------------------------------------------------------------------
+// Cholesky A = R^T R and R^-1 in shared memory (packed upper triangle).
+// Row i of the packed upper triangle starts at i*n - i*(i-1)/2.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int packed_upper(int n, int i, int j) {  // j >= i
+  return i * n - i * (i - 1) / 2 + (j - i);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) chol_inv_packed_kernel(const T *__restrict__ A, int n, int lda,
+                                                               T *__restrict__ Rinv, int ldi,
+                                                               Ctrl *ctrl) {
+  extern __shared__ __align__(16) unsigned char csm[];
+  T *U = reinterpret_cast<T *>(csm);       // n(n+1)/2
+  T *tmp = U + n * (n + 1) / 2;            // n
+  __shared__ T piv;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = 0; i < n; ++i)
+    for (int j = i + tid; j < n; j += nt) U[packed_upper(n, i, j)] = A[(int64_t)i * lda + j];
+  __syncthreads();
+  // right-looking Cholesky
+  for (int j = 0; j < n; ++j) {
+    if (tid == 0) {
+      T d = U[packed_upper(n, j, j)];
+      if (!(d > T(0)) || !isfinite((double)d)) {
+        record_error(ctrl, SNE_ERR_NUMERIC, W_CHOL);
+        d = T(1);
+      }
+      d = sqrt(d);
+      U[packed_upper(n, j, j)] = d;
+      piv = T(1) / d;
+    }
+    __syncthreads();
+    const T inv = piv;
+    for (int c = j + 1 + tid; c < n; c += nt) U[packed_upper(n, j, c)] *= inv;
+    __syncthreads();
+    const int mm = n - j - 1;
+    const int cnt = mm * (mm + 1) / 2;
+    for (int e = tid; e < cnt; e += nt) {
+      // e enumerates (r, c) with j < r <= c < n, row-major over r
+      int r = (int)((2 * mm + 1 - sqrtf((float)((2 * mm + 1) * (2 * mm + 1) - 8 * e))) * 0.5f);
+      while (r > 0 && r * (2 * mm - r + 1) / 2 > e) --r;
+      while ((r + 1) * (2 * mm - r) / 2 <= e) ++r;
+      const int c = e - r * (2 * mm - r + 1) / 2 + r;
+      const int rr = j + 1 + r, cc = j + 1 + c;
+      U[packed_upper(n, rr, cc)] -= U[packed_upper(n, j, rr)] * U[packed_upper(n, j, cc)];
+    }
+    __syncthreads();
+  }
+  // in-place inverse of the upper triangular factor, column by column
+  for (int j = 0; j < n; ++j) {
+    for (int k = tid; k < j; k += nt) tmp[k] = U[packed_upper(n, k, j)];
+    __syncthreads();
+    const T xjj = T(1) / U[packed_upper(n, j, j)];
+    for (int i = tid; i < j; i += nt) {
+      T s = 0;
+      for (int k = i; k < j; ++k) s += U[packed_upper(n, i, k)] * tmp[k];
+      U[packed_upper(n, i, j)] = -xjj * s;
+    }
+    __syncthreads();
+    if (tid == 0) U[packed_upper(n, j, j)] = xjj;
+    __syncthreads();
+  }
+  for (int64_t q = tid; q < (int64_t)n * n; q += nt) {
+    const int i = (int)(q / n), j = (int)(q % n);
+    Rinv[(int64_t)i * ldi + j] = (j >= i) ? U[packed_upper(n, i, j)] : T(0);
+  }
+}
+
+template <typename T>
+bool chol_inv_fits(int n) {
+  return ((size_t)n * (n + 1) / 2 + n) * sizeof(T) <= 200 * 1024;
+}
+
+template <typename T>
+cudaError_t launch_chol_inverse(const T *A, int32_t n, int32_t lda, T *Rinv, int32_t ldi, T *scratch,
+                                Ctrl *ctrl, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (chol_inv_fits<T>(n)) {
+    const size_t smem = ((size_t)n * (n + 1) / 2 + n) * sizeof(T);
+    cudaError_t e = cudaFuncSetAttribute(chol_inv_packed_kernel<T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    ProfScope ps_(K_CHOL, st);
+    chol_inv_packed_kernel<T><<<1, 1024, smem, st>>>(A, n, lda, Rinv, ldi, ctrl);
+    return cudaGetLastError();
+  }
+  // global-memory path: factor a copy, then invert
+  cudaError_t e = cudaMemcpy2DAsync(scratch, n * sizeof(T), A, lda * sizeof(T), n * sizeof(T), n,
+                                    cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return e;
+  e = launch_cholesky_upper<T>(scratch, n, n, ctrl, st);
+  if (e != cudaSuccess) return e;
+  return launch_triu_inverse<T>(scratch, n, n, Rinv, ldi, ctrl, st);
+}
+template cudaError_t launch_chol_inverse<float>(const float *, int32_t, int32_t, float *, int32_t,
+                                                float *, Ctrl *, cudaStream_t);
+template cudaError_t launch_chol_inverse<double>(const double *, int32_t, int32_t, double *, int32_t,
+                                                 double *, Ctrl *, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Public eigensolver entry (replaces the tridiagonal QR for n <= 320)
+// scratch layout (bytes): see eig_scratch_bytes.
+// ---------------------------------------------------------------------------
+size_t eig_scratch_bytes(int n) {
+  const size_t n2 = (size_t)n * n;
+  return 256 + jacobi_rot_capacity(n) * sizeof(Rot) + 2 * n2 * sizeof(float) + n * sizeof(float) +
+         3 * n2 * sizeof(double) + 1024;
+}
+
+cudaError_t launch_sym_eig_fast(float *A, int32_t n, int32_t lda, float *w, float *V, int32_t ldv,
+                                void *scratch, Ctrl *ctrl, cudaStream_t st) {
+  char *base = static_cast<char *>(scratch);
+  int *nrounds = reinterpret_cast<int *>(base);
+  void *rot = base + 256;
+  return launch_jacobi_f32(A, n, lda, w, V, ldv, rot, nrounds, ctrl, st);
+}
+
+cudaError_t launch_sym_eig_fast(double *A, int32_t n, int32_t lda, double *w, double *V, int32_t ldv,
+                                void *scratch, Ctrl *ctrl, cudaStream_t st) {
+  char *base = static_cast<char *>(scratch);
+  int *nrounds = reinterpret_cast<int *>(base);
+  Rot *rot = reinterpret_cast<Rot *>(base + 256);
+  float *A32 = reinterpret_cast<float *>(rot + jacobi_rot_capacity(n));
+  float *V32 = A32 + (size_t)n * n;
+  float *w32 = V32 + (size_t)n * n;
+  double *T1 = reinterpret_cast<double *>(
+      (reinterpret_cast<uintptr_t>(w32 + n) + 255) & ~(uintptr_t)255);
+  double *T2 = T1 + (size_t)n * n;
+  double *T3 = T2 + (size_t)n * n;
+  if (ldv != n) return cudaErrorInvalidValue;
+  cudaError_t e = launch_d2f(A, n, n, lda, A32, n, st);
+  if (e != cudaSuccess) return e;
+  e = launch_jacobi_f32(A32, n, n, w32, V32, n, rot, nrounds, ctrl, st);
+  if (e != cudaSuccess) return e;
+  // X = V (FP64), A copied compact into T3's neighbour: use T3 for S
+  e = launch_f2d(V32, n, n, n, V, ldv, st);
+  if (e != cudaSuccess) return e;
+  double *Ac = T3;  // S
+  for (int it = 0; it < 2; ++it) {
+    e = launch_small_gemm<double>(true, false, n, n, n, 1.0, V, ldv, V, ldv, 0.0, T1, n, st);  // X^T X
+    if (e != cudaSuccess) return e;
+    e = launch_small_gemm<double>(false, false, n, n, n, 1.0, A, lda, V, ldv, 0.0, T2, n, st);  // A X
+    if (e != cudaSuccess) return e;
+    e = launch_small_gemm<double>(true, false, n, n, n, 1.0, V, ldv, T2, n, 0.0, Ac, n, st);  // S
+    if (e != cudaSuccess) return e;
+    {
+      ProfScope ps_(K_EIG, st);
+      oa_update_kernel<<<1, 1024, 0, st>>>(T1, Ac, A, lda, n, w);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = launch_small_gemm<double>(false, false, n, n, n, 1.0, V, ldv, T1, n, 0.0, T2, n, st);  // X E
+    if (e != cudaSuccess) return e;
+    {
+      ProfScope ps_(K_EIG, st);
+      add_inplace_kernel<<<(unsigned)min64(1024, ((int64_t)n * n + 255) / 256), 256, 0, st>>>(
+          V, T2, (int64_t)n * n);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace sne

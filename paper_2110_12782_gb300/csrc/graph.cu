@@ -1,0 +1,262 @@
+// Graph kernels: degrees and vol(G) (Sec. 2), the implicit SpMM with the
+// modified Laplacian X = D^-a A D^-a (Alg. 5, Sec. 4.4 "Parallelization"),
+// and CSR validation.
+#include "sne_internal.cuh"
+
+namespace sne {
+
+__global__ void degrees_kernel(int64_t n, const int64_t *__restrict__ row_ptr,
+                               const float *__restrict__ val, float *__restrict__ deg,
+                               double *__restrict__ vol) {
+  double local = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int64_t b = row_ptr[i], e = row_ptr[i + 1];
+    float d;
+    if (val == nullptr) {
+      d = (float)(e - b);
+    } else {
+      double acc = 0.0;  // exact order-independent enough: per-row FP64 sum
+      for (int64_t p = b; p < e; ++p) acc += (double)val[p];
+      d = (float)acc;
+    }
+    deg[i] = d;
+    local += (double)d;
+  }
+  for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+  __shared__ double ws[32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = local;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) atomicAdd(vol, v);
+  }
+}
+
+cudaError_t launch_degrees(const sne_csr &g, float *deg, double *vol, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(vol, 0, sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  if (g.n <= 0) return cudaSuccess;
+  int64_t blocks = (g.n + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  ProfScope ps_(K_MISC, st);
+  degrees_kernel<<<(unsigned)blocks, 256, 0, st>>>(g.n, g.row_ptr, g.val, deg, vol);
+  return cudaGetLastError();
+}
+
+__global__ void degree_power_kernel(const float *__restrict__ deg, int64_t n, float beta, float scale,
+                                    float *__restrict__ out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const float d = deg[i];
+    out[i] = d > 0.0f ? scale * powf(d, beta) : 0.0f;
+  }
+}
+
+cudaError_t launch_degree_power(const float *deg, int64_t n, double beta, float *out, float scale,
+                                cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  ProfScope ps_(K_MISC, st);
+  degree_power_kernel<<<(unsigned)blocks, 256, 0, st>>>(deg, n, (float)beta, scale, out);
+  return cudaGetLastError();
+}
+
+// Y[i, :] = s_i * sum_{p in row i} w_p s_{col_p} B[col_p, :],  s = d^-a.
+// One warp per row; each lane owns VPL float4 column groups of the row; the
+// row's (col, weight) pairs are fetched 32 at a time and broadcast by shuffle.
+template <int VPL>
+__global__ void __launch_bounds__(256) spmm_vec4_kernel(
+    int64_t n, const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+    const float *__restrict__ val, const float *__restrict__ dpow, const float *__restrict__ B,
+    int64_t ldb, int32_t nvec, float *__restrict__ Y, int64_t ldy) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= n) return;
+  float4 acc[VPL];
+#pragma unroll
+  for (int v = 0; v < VPL; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int64_t beg = row_ptr[row], end = row_ptr[row + 1];
+  for (int64_t p0 = beg; p0 < end; p0 += 32) {
+    const int64_t p = p0 + lane;
+    int32_t c = 0;
+    float w = 0.f;
+    if (p < end) {
+      c = col[p];
+      w = dpow[c] * (val ? val[p] : 1.0f);
+    }
+    const int cnt = (int)min64(32, end - p0);
+    int t = 0;
+    for (; t + 2 <= cnt; t += 2) {
+      const int32_t c0 = __shfl_sync(0xffffffffu, c, t);
+      const int32_t c1 = __shfl_sync(0xffffffffu, c, t + 1);
+      const float w0 = __shfl_sync(0xffffffffu, w, t);
+      const float w1 = __shfl_sync(0xffffffffu, w, t + 1);
+      const float4 *r0 = reinterpret_cast<const float4 *>(B + (int64_t)c0 * ldb);
+      const float4 *r1 = reinterpret_cast<const float4 *>(B + (int64_t)c1 * ldb);
+#pragma unroll
+      for (int v = 0; v < VPL; ++v) {
+        const int q = lane + 32 * v;
+        if (q < nvec) {
+          const float4 x0 = __ldg(r0 + q);
+          const float4 x1 = __ldg(r1 + q);
+          acc[v].x += w0 * x0.x + w1 * x1.x;
+          acc[v].y += w0 * x0.y + w1 * x1.y;
+          acc[v].z += w0 * x0.z + w1 * x1.z;
+          acc[v].w += w0 * x0.w + w1 * x1.w;
+        }
+      }
+    }
+    for (; t < cnt; ++t) {
+      const int32_t c0 = __shfl_sync(0xffffffffu, c, t);
+      const float w0 = __shfl_sync(0xffffffffu, w, t);
+      const float4 *r0 = reinterpret_cast<const float4 *>(B + (int64_t)c0 * ldb);
+#pragma unroll
+      for (int v = 0; v < VPL; ++v) {
+        const int q = lane + 32 * v;
+        if (q < nvec) {
+          const float4 x0 = __ldg(r0 + q);
+          acc[v].x += w0 * x0.x;
+          acc[v].y += w0 * x0.y;
+          acc[v].z += w0 * x0.z;
+          acc[v].w += w0 * x0.w;
+        }
+      }
+    }
+  }
+  const float si = dpow[row];
+  float4 *yr = reinterpret_cast<float4 *>(Y + row * ldy);
+#pragma unroll
+  for (int v = 0; v < VPL; ++v) {
+    const int q = lane + 32 * v;
+    if (q < nvec) yr[q] = make_float4(si * acc[v].x, si * acc[v].y, si * acc[v].z, si * acc[v].w);
+  }
+}
+
+// Scalar fallback for widths that are not a multiple of 4 (or unaligned).
+__global__ void __launch_bounds__(256) spmm_scalar_kernel(
+    int64_t n, const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+    const float *__restrict__ val, const float *__restrict__ dpow, const float *__restrict__ B,
+    int64_t ldb, int32_t ncols, float *__restrict__ Y, int64_t ldy) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= n) return;
+  const int64_t beg = row_ptr[row], end = row_ptr[row + 1];
+  const float si = dpow[row];
+  for (int c0 = 0; c0 < ncols; c0 += 32 * 8) {
+    float acc[8];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) acc[v] = 0.f;
+    for (int64_t p = beg; p < end; ++p) {
+      const int32_t c = col[p];
+      const float w = dpow[c] * (val ? val[p] : 1.0f);
+      const float *br = B + (int64_t)c * ldb;
+#pragma unroll
+      for (int v = 0; v < 8; ++v) {
+        const int q = c0 + lane + 32 * v;
+        if (q < ncols) acc[v] += w * br[q];
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      const int q = c0 + lane + 32 * v;
+      if (q < ncols) Y[row * ldy + q] = si * acc[v];
+    }
+  }
+}
+
+cudaError_t launch_spmm(const sne_csr &g, const float *dpow, const float *B, int64_t ldb,
+                        int32_t ncols, float *Y, int64_t ldy, cudaStream_t st) {
+  if (g.n <= 0 || ncols <= 0) return cudaSuccess;
+  ProfScope ps_(K_SPMM, st);
+  const unsigned blocks = (unsigned)((g.n + 7) / 8);
+  const bool vec = (ncols % 4 == 0) && (ldb % 4 == 0) && (ldy % 4 == 0) &&
+                   ((uintptr_t)B % 16 == 0) && ((uintptr_t)Y % 16 == 0);
+  const int nvec = ncols / 4;
+  if (vec && nvec <= 32 * 12) {
+    const int vpl = (nvec + 31) / 32;
+#define SNE_SPMM_CASE(V)                                                                     \
+  case V:                                                                                    \
+    spmm_vec4_kernel<V><<<blocks, 256, 0, st>>>(g.n, g.row_ptr, g.col_idx, g.val, dpow, B, ldb, \
+                                                nvec, Y, ldy);                               \
+    break;
+    switch (vpl) {
+      SNE_SPMM_CASE(1)
+      SNE_SPMM_CASE(2)
+      SNE_SPMM_CASE(3)
+      SNE_SPMM_CASE(4)
+      SNE_SPMM_CASE(5)
+      SNE_SPMM_CASE(6)
+      SNE_SPMM_CASE(7)
+      SNE_SPMM_CASE(8)
+      SNE_SPMM_CASE(9)
+      SNE_SPMM_CASE(10)
+      SNE_SPMM_CASE(11)
+      SNE_SPMM_CASE(12)
+      default:
+        break;
+    }
+#undef SNE_SPMM_CASE
+  } else {
+    spmm_scalar_kernel<<<blocks, 256, 0, st>>>(g.n, g.row_ptr, g.col_idx, g.val, dpow, B, ldb, ncols,
+                                               Y, ldy);
+  }
+  return cudaGetLastError();
+}
+
+// CSR validation: row_ptr[0] = 0, nondecreasing, row_ptr[n] = nnz; columns in
+// range, strictly increasing within a row, no self-loop; every (i, j, w) has
+// its mirror (j, i, w).
+__global__ void validate_kernel(int64_t n, int64_t nnz, const int64_t *__restrict__ row_ptr,
+                                const int32_t *__restrict__ col, const float *__restrict__ val,
+                                Ctrl *ctrl) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int64_t b = row_ptr[i], e = row_ptr[i + 1];
+    bool bad = (b > e) || (b < 0) || (e > nnz) || (i == 0 && b != 0) || (i == n - 1 && e != nnz);
+    if (!bad) {
+      for (int64_t p = b; p < e; ++p) {
+        const int32_t j = col[p];
+        if (j < 0 || j >= n || j == i || (p > b && col[p - 1] >= j)) {
+          bad = true;
+          break;
+        }
+        // mirror (j, i): binary search in row j
+        int64_t lo = row_ptr[j], hi = row_ptr[j + 1] - 1;
+        if (lo < 0 || hi >= nnz) {
+          bad = true;
+          break;
+        }
+        bool found = false;
+        while (lo <= hi) {
+          const int64_t mid = (lo + hi) >> 1;
+          const int32_t cm = col[mid];
+          if (cm == i) {
+            found = (val == nullptr) || (val[mid] == val[p]);
+            break;
+          }
+          if (cm < i) lo = mid + 1;
+          else hi = mid - 1;
+        }
+        if (!found) {
+          bad = true;
+          break;
+        }
+      }
+    }
+    if (bad) record_error(ctrl, SNE_ERR_GRAPH, W_VALIDATE);
+  }
+}
+
+cudaError_t launch_validate(const sne_csr &g, Ctrl *ctrl, cudaStream_t st) {
+  if (g.n <= 0) return cudaSuccess;
+  int64_t blocks = (g.n + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  ProfScope ps_(K_MISC, st);
+  validate_kernel<<<(unsigned)blocks, 256, 0, st>>>(g.n, g.nnz, g.row_ptr, g.col_idx, g.val, ctrl);
+  return cudaGetLastError();
+}
+
+}  // namespace sne

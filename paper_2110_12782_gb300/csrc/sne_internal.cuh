@@ -1,0 +1,171 @@
+// Internal declarations shared by the translation units of libsketchne.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sketchne.h"
+
+namespace sne {
+
+__host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
+
+// ---------------------------------------------------------------------------
+// Device control block: first 256 bytes of every workspace.
+// ---------------------------------------------------------------------------
+struct Ctrl {
+  int32_t status;  // first error code recorded on the device (0 = none)
+  int32_t where;   // id of the kernel that recorded it
+  int32_t v_s;     // unique rows of S (Alg. 4 line 3)
+  int32_t v_o;     // unique rows of O (Alg. 4 line 6)
+  double vol;      // vol(G)
+  int32_t pad[58];
+};
+static_assert(sizeof(Ctrl) == 256, "control block is 256 bytes");
+
+enum Where : int32_t {
+  W_NONE = 0,
+  W_VALIDATE = 1,
+  W_CHOL = 2,
+  W_EIG = 3,
+  W_TRIINV = 4,
+  W_EIGSVD = 5,
+  W_NAN = 6,
+  W_SPARSE_SIGN = 7,
+  W_UNIQUE = 8,
+};
+
+__device__ __forceinline__ void record_error(Ctrl *c, int32_t code, int32_t where) {
+  if (c == nullptr) return;
+  if (atomicCAS(&c->status, 0, code) == 0) c->where = where;
+}
+
+// ---------------------------------------------------------------------------
+// Launch accounting / profiling (prof.cu).  A ProfScope covers the `nk`
+// kernels one launcher enqueues on `st`.
+// ---------------------------------------------------------------------------
+enum KClass : int {
+  K_SPMM = 0, K_GRAM, K_TALL_GEMM, K_SMALL_GEMM, K_EIG, K_CHOL, K_TRIINV, K_FUSED, K_GATHER, K_RNG,
+  K_UNIQUE, K_MISC, K_FUSED_TC, K_GRAM_TC, K_TALL_TC, K_COUNT
+};
+class ProfScope {
+ public:
+  ProfScope(int cls, cudaStream_t st, int nk = 1);
+  ~ProfScope();
+  ProfScope(const ProfScope &) = delete;
+  ProfScope &operator=(const ProfScope &) = delete;
+
+ private:
+  int cls_, nk_;
+  cudaStream_t st_;
+  cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
+
+// ---------------------------------------------------------------------------
+// Counter-based random numbers: SplitMix64 (Steele, Lea, Flood 2014) read as a
+// counter-based generator.  Output i (1-based) of SplitMix64 started at state s
+// is mix64(s + i * GOLDEN).  stream_key(seed, stream) is output stream+1 of
+// SplitMix64(seed); draw(key, ctr) is output ctr+1 of SplitMix64(key).
+// ---------------------------------------------------------------------------
+constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;
+
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ uint64_t stream_key(uint64_t seed, uint32_t stream) {
+  return mix64(seed + kGolden * (uint64_t)(stream + 1));
+}
+__host__ __device__ __forceinline__ uint64_t draw(uint64_t key, uint64_t ctr) {
+  return mix64(key + kGolden * (ctr + 1));
+}
+
+// ---------------------------------------------------------------------------
+// Launchers (host functions; every one enqueues on `st` and returns a
+// cudaError_t from cudaGetLastError()).
+// ---------------------------------------------------------------------------
+// rng.cu
+cudaError_t launch_gaussian(int64_t n, int32_t cols, uint64_t seed, int32_t stream_id, float *out,
+                            int64_t ld, cudaStream_t st);
+cudaError_t launch_sparse_sign(int64_t n, int32_t cols, int32_t z, uint64_t seed, int32_t stream_id,
+                               int32_t *idx, int8_t *sign, Ctrl *ctrl, cudaStream_t st);
+// Sorts `count` row indices, writes the unique ones to uniq (ascending), their
+// number to *nuniq (device), and for every input its position in uniq to pos.
+constexpr int kUniqueMax = 32768;
+cudaError_t launch_unique(const int32_t *keys, int32_t count, int32_t *uniq, int32_t *nuniq,
+                          int32_t *pos, Ctrl *ctrl, int32_t where, cudaStream_t st);
+
+// graph.cu
+cudaError_t launch_degrees(const sne_csr &g, float *deg, double *vol, cudaStream_t st);
+cudaError_t launch_degree_power(const float *deg, int64_t n, double beta, float *out, float scale,
+                                cudaStream_t st);
+cudaError_t launch_spmm(const sne_csr &g, const float *dpow, const float *B, int64_t ldb,
+                        int32_t ncols, float *Y, int64_t ldy, cudaStream_t st);
+cudaError_t launch_validate(const sne_csr &g, Ctrl *ctrl, cudaStream_t st);
+
+// dense.cu
+// C (Ka x Kb, FP64, ldc) = sum_i w_i A[i, :]^T B[i, :]  over i < n; w may be NULL.
+// `partial` is FP32 scratch of gram_partial_floats(n, Ka, Kb) floats.
+size_t gram_partial_floats(int64_t n, int32_t Ka, int32_t Kb);
+cudaError_t launch_gram(const float *A, int64_t lda, int32_t Ka, const float *B, int64_t ldb,
+                        int32_t Kb, int64_t n, const float *w, bool symmetric, float *partial,
+                        double *C, int32_t ldc, cudaStream_t st);
+// C[i, :] = rs_i * sum_a A[r(i), a] M[a, :]   (r(i) = ridx[i] or i; rs = 1 if NULL)
+cudaError_t launch_tall_gemm(const float *A, int64_t lda, const int32_t *ridx, int64_t n, int32_t Ka,
+                             const float *M, int32_t ldm, int32_t Kc, const float *rs, float *C,
+                             int64_t ldc, cudaStream_t st);
+// Small dense GEMM (multi-CTA): C = alpha * op(A) op(B) + beta * C, row-major.
+template <typename T>
+cudaError_t launch_small_gemm(bool ta, bool tb, int32_t M, int32_t N, int32_t K, T alpha,
+                              const T *A, int32_t lda, const T *B, int32_t ldb, T beta, T *C,
+                              int32_t ldc, cudaStream_t st);
+// Single-CTA small factorizations (n <= 1024), matrices in global memory.
+template <typename T>
+cudaError_t launch_cholesky_upper(T *A, int32_t n, int32_t lda, Ctrl *ctrl, cudaStream_t st);
+template <typename T>
+cudaError_t launch_triu_inverse(const T *R, int32_t n, int32_t ldr, T *Rinv, int32_t ldi,
+                                Ctrl *ctrl, cudaStream_t st);
+// Symmetric eigendecomposition: A (n x n) = V diag(w) V^T, w unordered.
+// V is returned row-major n x n (column j = eigenvector j), ldv = n.  A may be
+// overwritten.  scratch: eig_scratch_bytes(n) bytes, 256-byte aligned.
+size_t eig_scratch_bytes(int n);
+template <typename T>
+cudaError_t launch_sym_eig(T *A, int32_t n, int32_t lda, T *w, T *V, int32_t ldv, void *scratch,
+                           Ctrl *ctrl, cudaStream_t st);
+cudaError_t launch_sym_eig_fast(float *A, int32_t n, int32_t lda, float *w, float *V, int32_t ldv,
+                                void *scratch, Ctrl *ctrl, cudaStream_t st);
+cudaError_t launch_sym_eig_fast(double *A, int32_t n, int32_t lda, double *w, double *V,
+                                int32_t ldv, void *scratch, Ctrl *ctrl, cudaStream_t st);
+constexpr int kFastEigMaxN = 320;
+// Rinv = R^-1 where A = R^T R (Cholesky); scratch: n*n T (used only for n too
+// large for shared memory).
+template <typename T>
+cudaError_t launch_chol_inverse(const T *A, int32_t n, int32_t lda, T *Rinv, int32_t ldi, T *scratch,
+                                Ctrl *ctrl, cudaStream_t st);
+// Orders eigenpairs: perm[j] = index of the j-th largest (|w| if by_abs else w).
+template <typename T>
+cudaError_t launch_eig_order(const T *w, int32_t n, bool by_abs, int32_t *perm, cudaStream_t st);
+// Elementwise helpers.
+cudaError_t launch_d2f(const double *src, int32_t rows, int32_t cols, int32_t lds, float *dst,
+                       int32_t ldd, cudaStream_t st);
+cudaError_t launch_f2d(const float *src, int32_t rows, int32_t cols, int32_t lds, double *dst,
+                       int32_t ldd, cudaStream_t st);
+cudaError_t launch_symmetrize(double *A, int32_t n, int32_t lda, cudaStream_t st);
+cudaError_t launch_check_finite_f(const float *x, int64_t count, Ctrl *ctrl, int32_t where,
+                                  cudaStream_t st);
+
+// sketch.cu
+// out[i, c] = sv * sum_{t<z} sign[c*z+t] * f(rs[r(i)] * <A[r(i), :], B[c*z+t, :]>)
+cudaError_t launch_fused_sketch_f32(const float *A, int64_t lda, const int32_t *ridx,
+                                    const int32_t *nrows_dev, int64_t nrows, int32_t k,
+                                    const float *rs, const float *B, const int8_t *sign,
+                                    int32_t cols_out, int32_t z, float sv, int32_t f, float *out,
+                                    int64_t ldo, cudaStream_t st);
+// out[c, :] = sv * sum_t sign[c*z+t] * In[idx[c*z+t], :]
+cudaError_t launch_signed_gather_sum(const float *In, int64_t ldi, int32_t width, const int32_t *idx,
+                                     const int8_t *sign, int32_t cols, int32_t z, float sv,
+                                     float *out, int64_t ldo, cudaStream_t st);
+
+}  // namespace sne

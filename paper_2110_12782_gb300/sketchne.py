@@ -1,0 +1,304 @@
+"""ctypes binding of libsketchne.so (declared in include/sketchne.h).
+
+Argument marshalling only: every function here has the name of the C entry
+point it calls, checks that the tensors it is given live on the GPU with the
+expected dtype and layout, passes their device pointers and the current torch
+stream, and raises ``SketchNEError`` on a nonzero return code.  PyTorch is used
+for device memory and streams; no arithmetic of the method happens here.
+
+The library must have been built (``paper_2110_12782_gb300.build.build()``);
+importing a function fails loudly otherwise -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsketchne.so")
+
+SNE_OK = 0
+SNE_ERR_ARG = -1
+SNE_ERR_GRAPH = -2
+SNE_ERR_SIZE = -3
+SNE_ERR_WORKSPACE = -4
+SNE_ERR_CUDA = -5
+SNE_ERR_TIMEOUT = -6
+SNE_ERR_NUMERIC = -7
+
+SNE_FP32, SNE_BF16, SNE_FP16 = 0, 1, 2
+SNE_F_TRUNC_LOG, SNE_F_IDENTITY = 0, 1
+SNE_ORTH_EIGSVD, SNE_ORTH_CHOLQR = 0, 1
+SNE_WS_EMBED, SNE_WS_FREIGS, SNE_WS_SKETCH, SNE_WS_EMBED_HOST = 0, 1, 2, 3
+
+EXPORTS = [
+    "sne_params_init", "sne_error_string", "sne_workspace_bytes", "sne_embed", "sne_freigs",
+    "sne_sketch_from_factors", "sne_sparse_sign", "sne_gaussian", "sne_degrees",
+    "sne_degree_power", "sne_spmm", "sne_validate_csr", "sne_status_reset", "sne_status",
+    "sne_stats_read", "sne_embed_host", "sne_kernel_launches", "sne_profile_start",
+    "sne_profile_stop",
+]
+
+
+class SketchNEError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {sne_error_string(code)} ({code})")
+
+
+class sne_csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("row_ptr", ctypes.c_void_p),
+                ("col_idx", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class sne_params(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int32) for f in
+                ("k", "q", "T", "d", "h", "l", "zeta", "s_eig", "row_block", "precision", "f",
+                 "orth")] + [("alpha", ctypes.c_double), ("b", ctypes.c_double),
+                             ("seed", ctypes.c_uint64)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class sne_stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("where", ctypes.c_int32), ("v_s", ctypes.c_int64),
+                ("v_o", ctypes.c_int64), ("vol", ctypes.c_double)]
+
+
+class sne_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("calls", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("total_ms", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "paper_2110_12782_gb300.build.build() (requires nvcc)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, u64, dbl = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
+                                  ctypes.c_double)
+        P = ctypes.POINTER
+        sig = {
+            "sne_params_init": [P(sne_params), i32, i32],
+            "sne_error_string": [ctypes.c_int],
+            "sne_workspace_bytes": [i64, i64, P(sne_params), ctypes.c_int, P(ctypes.c_size_t)],
+            "sne_embed": [P(sne_csr), P(sne_params), vp, ctypes.c_size_t, vp, vp, vp],
+            "sne_freigs": [P(sne_csr), P(sne_params), vp, ctypes.c_size_t, vp, vp, vp],
+            "sne_sketch_from_factors": [P(sne_csr), P(sne_params), vp, vp, vp, ctypes.c_size_t, vp,
+                                        vp, vp, vp, vp],
+            "sne_sparse_sign": [i64, i32, i32, u64, i32, vp, vp, vp],
+            "sne_gaussian": [i64, i32, u64, i32, vp, vp],
+            "sne_degrees": [P(sne_csr), vp, vp, vp],
+            "sne_degree_power": [vp, i64, dbl, vp, vp],
+            "sne_spmm": [P(sne_csr), vp, vp, i32, vp, vp],
+            "sne_validate_csr": [P(sne_csr), vp, ctypes.c_size_t, vp],
+            "sne_status_reset": [vp, vp],
+            "sne_status": [vp, vp],
+            "sne_stats_read": [vp, P(sne_stats), vp],
+            "sne_embed_host": [P(sne_csr), P(sne_params), vp, ctypes.c_size_t, vp, vp, vp],
+            "sne_kernel_launches": [],
+            "sne_profile_start": [],
+            "sne_profile_stop": [P(sne_kernel_time), ctypes.c_int, P(ctypes.c_int)],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = {"sne_error_string": ctypes.c_char_p,
+                          "sne_kernel_launches": ctypes.c_longlong}.get(name, ctypes.c_int)
+        _lib = L
+    return _lib
+
+
+# ----------------------------------------------------------------------------- helpers
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _ptr(t, dtype=None, name="tensor", allow_none=False) -> int | None:
+    if t is None:
+        if allow_none:
+            return None
+        raise ValueError(f"{name} is required")
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != SNE_OK:
+        raise SketchNEError(rc, where)
+
+
+class DeviceGraph:
+    """A symmetric CSR graph held in device tensors, with its sne_csr struct."""
+
+    def __init__(self, row_ptr: torch.Tensor, col_idx: torch.Tensor, val: torch.Tensor | None = None):
+        self.row_ptr = row_ptr
+        self.col_idx = col_idx
+        self.val = val
+        self.n = row_ptr.numel() - 1
+        self.nnz = col_idx.numel()
+        self.csr = sne_csr(self.n, self.nnz, _ptr(row_ptr, torch.int64, "row_ptr"),
+                           _ptr(col_idx, torch.int32, "col_idx") if self.nnz else None,
+                           _ptr(val, torch.float32, "val", allow_none=True))
+
+    @classmethod
+    def from_numpy(cls, row_ptr, col_idx, val=None, device="cuda"):
+        rp = torch.as_tensor(row_ptr, dtype=torch.int64).to(device)
+        ci = torch.as_tensor(col_idx, dtype=torch.int32).to(device)
+        v = None if val is None else torch.as_tensor(val, dtype=torch.float32).to(device)
+        return cls(rp, ci, v)
+
+
+# ----------------------------------------------------------------------------- entry points
+def sne_params_init(d: int, k: int, **overrides) -> sne_params:
+    p = sne_params()
+    _check(lib().sne_params_init(ctypes.byref(p), d, k), "sne_params_init")
+    for key, v in overrides.items():
+        if not hasattr(p, key):
+            raise KeyError(key)
+        setattr(p, key, v)
+    return p
+
+
+def sne_error_string(code: int) -> str:
+    return lib().sne_error_string(code).decode()
+
+
+def sne_workspace_bytes(n: int, nnz: int, p: sne_params, mode: int = SNE_WS_EMBED) -> int:
+    out = ctypes.c_size_t(0)
+    _check(lib().sne_workspace_bytes(n, nnz, ctypes.byref(p), mode, ctypes.byref(out)),
+           "sne_workspace_bytes")
+    return out.value
+
+
+def workspace(n: int, nnz: int, p: sne_params, mode: int = SNE_WS_EMBED, device="cuda") -> torch.Tensor:
+    """A device byte tensor large enough for the given mode (256-byte aligned)."""
+    nbytes = sne_workspace_bytes(n, nnz, p, mode)
+    t = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+    off = (-t.data_ptr()) % 256
+    return t[off:off + nbytes]
+
+
+def sne_embed(g: DeviceGraph, p: sne_params, ws: torch.Tensor, E: torch.Tensor, sigma: torch.Tensor,
+              stream=None) -> None:
+    _check(lib().sne_embed(ctypes.byref(g.csr), ctypes.byref(p), _ptr(ws, torch.uint8, "workspace"),
+                           ws.numel(), _ptr(E, torch.float32, "E"), _ptr(sigma, torch.float64, "sigma"),
+                           _stream(stream)), "sne_embed")
+
+
+def sne_freigs(g: DeviceGraph, p: sne_params, ws: torch.Tensor, U: torch.Tensor, lam: torch.Tensor,
+               stream=None) -> None:
+    _check(lib().sne_freigs(ctypes.byref(g.csr), ctypes.byref(p), _ptr(ws, torch.uint8, "workspace"),
+                            ws.numel(), _ptr(U, torch.float32, "U"), _ptr(lam, torch.float64, "lambda"),
+                            _stream(stream)), "sne_freigs")
+
+
+def sne_sketch_from_factors(g: DeviceGraph, p: sne_params, U: torch.Tensor, lam: torch.Tensor,
+                            ws: torch.Tensor, Y=None, Z=None, E=None, sigma=None, stream=None) -> None:
+    _check(lib().sne_sketch_from_factors(
+        ctypes.byref(g.csr), ctypes.byref(p), _ptr(U, torch.float32, "U"),
+        _ptr(lam, torch.float64, "lambda"), _ptr(ws, torch.uint8, "workspace"), ws.numel(),
+        _ptr(Y, torch.float32, "Y", True), _ptr(Z, torch.float32, "Z", True),
+        _ptr(E, torch.float32, "E", True), _ptr(sigma, torch.float64, "sigma", True),
+        _stream(stream)), "sne_sketch_from_factors")
+
+
+def sne_sparse_sign(n: int, cols: int, zeta: int, seed: int, stream_id: int, idx: torch.Tensor,
+                    sign: torch.Tensor, stream=None) -> None:
+    _check(lib().sne_sparse_sign(n, cols, zeta, seed, stream_id, _ptr(idx, torch.int32, "idx"),
+                                 _ptr(sign, torch.int8, "sign"), _stream(stream)), "sne_sparse_sign")
+
+
+def sne_gaussian(n: int, cols: int, seed: int, stream_id: int, out: torch.Tensor, stream=None) -> None:
+    _check(lib().sne_gaussian(n, cols, seed, stream_id, _ptr(out, torch.float32, "out"),
+                              _stream(stream)), "sne_gaussian")
+
+
+def sne_degrees(g: DeviceGraph, deg: torch.Tensor, vol: torch.Tensor, stream=None) -> None:
+    _check(lib().sne_degrees(ctypes.byref(g.csr), _ptr(deg, torch.float32, "deg"),
+                             _ptr(vol, torch.float64, "vol"), _stream(stream)), "sne_degrees")
+
+
+def sne_degree_power(deg: torch.Tensor, beta: float, out: torch.Tensor, stream=None) -> None:
+    _check(lib().sne_degree_power(_ptr(deg, torch.float32, "deg"), deg.numel(), beta,
+                                  _ptr(out, torch.float32, "out"), _stream(stream)),
+           "sne_degree_power")
+
+
+def sne_spmm(g: DeviceGraph, dpow: torch.Tensor, B: torch.Tensor, Y: torch.Tensor, stream=None) -> None:
+    _check(lib().sne_spmm(ctypes.byref(g.csr), _ptr(dpow, torch.float32, "dpow"),
+                          _ptr(B, torch.float32, "B"), B.shape[1], _ptr(Y, torch.float32, "Y"),
+                          _stream(stream)), "sne_spmm")
+
+
+def sne_validate_csr(g: DeviceGraph, ws: torch.Tensor, stream=None) -> None:
+    _check(lib().sne_validate_csr(ctypes.byref(g.csr), _ptr(ws, torch.uint8, "workspace"), ws.numel(),
+                                  _stream(stream)), "sne_validate_csr")
+
+
+def sne_status_reset(ws: torch.Tensor, stream=None) -> None:
+    _check(lib().sne_status_reset(_ptr(ws, torch.uint8, "workspace"), _stream(stream)),
+           "sne_status_reset")
+
+
+def sne_status(ws: torch.Tensor, stream=None) -> int:
+    return lib().sne_status(_ptr(ws, torch.uint8, "workspace"), _stream(stream))
+
+
+def sne_stats_read(ws: torch.Tensor, stream=None) -> sne_stats:
+    out = sne_stats()
+    _check(lib().sne_stats_read(_ptr(ws, torch.uint8, "workspace"), ctypes.byref(out), _stream(stream)),
+           "sne_stats_read")
+    return out
+
+
+def check_status(ws: torch.Tensor, where: str = "device", stream=None) -> None:
+    """Raises if the workspace's device status word records an error."""
+    _check(sne_status(ws, stream), where)
+
+
+def sne_embed_host(row_ptr, col_idx, val, n: int, p: sne_params, ws: torch.Tensor, E_host: torch.Tensor,
+                   sigma_host: torch.Tensor, stream=None) -> None:
+    """sne_embed from host arrays (torch CPU tensors, pinned for asynchronous copies)."""
+    for t, nm in ((row_ptr, "row_ptr"), (col_idx, "col_idx"), (E_host, "E"), (sigma_host, "sigma")):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{nm} must be a contiguous host tensor")
+    g = sne_csr(n, col_idx.numel(), row_ptr.data_ptr(), col_idx.data_ptr(),
+                None if val is None else val.data_ptr())
+    _check(lib().sne_embed_host(ctypes.byref(g), ctypes.byref(p), _ptr(ws, torch.uint8, "workspace"),
+                                ws.numel(), E_host.data_ptr(), sigma_host.data_ptr(), _stream(stream)),
+           "sne_embed_host")
+
+
+def sne_kernel_launches() -> int:
+    return int(lib().sne_kernel_launches())
+
+
+def sne_profile_start() -> None:
+    _check(lib().sne_profile_start(), "sne_profile_start")
+
+
+def sne_profile_stop() -> dict:
+    """Per kernel class: {name: (calls, launches, total_ms)}."""
+    arr = (sne_kernel_time * 32)()
+    cnt = ctypes.c_int(0)
+    _check(lib().sne_profile_stop(arr, 32, ctypes.byref(cnt)), "sne_profile_stop")
+    return {arr[i].name.decode(): (arr[i].calls, arr[i].launches, arr[i].total_ms)
+            for i in range(cnt.value)}

@@ -14,9 +14,11 @@ Graph families (stand-ins for the paper's datasets of Table 1):
   drawn exactly in distribution as a binomial edge count per block pair
   followed by a uniform choice of that many distinct pairs.
 * ``chung_lu``: power-law Chung-Lu graph.  Vertex weights
-  ``w_i ~ (i + i0)^(-1/(gamma-1))`` are scaled to the target mean degree and
-  capped at ``sqrt(sum w)``; ``sum(w)/2`` endpoint pairs are drawn i.i.d. with
-  probability proportional to ``w``; self-loops and repeats are dropped.
+  ``w_i ~ (i + i0)^(-1/(gamma-1))`` are scaled so that their sum is
+  ``n * avg_degree`` after capping every weight at ``sqrt(n * avg_degree)``;
+  endpoint pairs are drawn i.i.d. with probability proportional to ``w``,
+  self-loops and repeats are dropped, and drawing continues until
+  ``n * avg_degree / 2`` distinct edges exist (realized mean degree = target).
   Vertex ids are therefore sorted by expected degree (id 0 is the largest hub).
 * ``complete_graph``, ``complete_bipartite_union``, ``from_edges``: small
   graphs with closed-form spectra, used to pin the oracle.
@@ -51,16 +53,18 @@ def _csr_from_undirected_pairs(n: int, i: np.ndarray, j: np.ndarray, name: str =
     j = np.asarray(j, dtype=np.int64)
     keep = i != j
     i, j = i[keep], j[keep]
-    lo = np.minimum(i, j)
-    hi = np.maximum(i, j)
-    key = np.unique(lo * n + hi)
+    key = np.unique(np.minimum(i, j) * n + np.maximum(i, j))
+    return _csr_from_unique_keys(n, key, name)
+
+
+def _csr_from_unique_keys(n: int, key: np.ndarray, name: str = "") -> Graph:
+    """CSR from sorted unique keys lo*n + hi (lo < hi) of undirected edges."""
     lo = key // n
-    hi = key % n
-    src = np.concatenate([lo, hi])
-    dst = np.concatenate([hi, lo])
-    order = np.lexsort((dst, src))
-    src = src[order]
-    dst = dst[order]
+    hi = key - lo * n
+    both = np.concatenate([key, hi * n + lo])
+    both.sort()
+    src = both // n
+    dst = both - src * n
     counts = np.bincount(src, minlength=n)
     row_ptr = np.zeros(n + 1, dtype=np.int64)
     np.cumsum(counts, out=row_ptr[1:])
@@ -146,27 +150,35 @@ def sbm(n: int, blocks: int, p_in: float, p_out: float, seed: int = 0) -> Graph:
 def chung_lu(n: int, avg_degree: float, gamma: float, seed: int = 0, i0: float = 1.0,
              chunk: int = 1 << 24) -> Graph:
     rng = np.random.Generator(np.random.PCG64(seed))
-    w = (np.arange(n, dtype=np.float64) + i0) ** (-1.0 / (gamma - 1.0))
-    w *= n * avg_degree / w.sum()
-    cap = np.sqrt(w.sum())
-    w = np.minimum(w, cap)
-    total = w.sum()
-    m = int(round(total / 2.0))
-    cdf = np.cumsum(w / total)
+    base = (np.arange(n, dtype=np.float64) + i0) ** (-1.0 / (gamma - 1.0))
+    target = n * avg_degree
+    # scale so that sum(min(s * base, sqrt(sum))) = n * avg_degree (the cap keeps p_ij <= 1)
+    cap = np.sqrt(target)
+    lo_s, hi_s = 0.0, target / base.sum() * 1e3
+    for _ in range(100):
+        mid = 0.5 * (lo_s + hi_s)
+        if np.minimum(base * mid, cap).sum() < target:
+            lo_s = mid
+        else:
+            hi_s = mid
+    w = np.minimum(base * hi_s, cap)
+    cdf = np.cumsum(w / w.sum())
     cdf[-1] = 1.0
-    keys = []
-    for c0 in range(0, m, chunk):
-        c = min(chunk, m - c0)
-        i = np.searchsorted(cdf, rng.random(c), side="right")
-        j = np.searchsorted(cdf, rng.random(c), side="right")
-        i = np.minimum(i, n - 1)
-        j = np.minimum(j, n - 1)
-        keep = i != j
-        i, j = i[keep], j[keep]
-        keys.append(np.unique(np.minimum(i, j).astype(np.int64) * n + np.maximum(i, j)))
-    key = np.unique(np.concatenate(keys)) if keys else np.zeros(0, np.int64)
-    return _csr_from_undirected_pairs(n, key // n, key % n,
-                                      name=f"chung_lu(n={n},avg={avg_degree},gamma={gamma},seed={seed})")
+    want = int(round(target / 2.0))  # distinct undirected edges
+    key = np.zeros(0, dtype=np.int64)
+    draw = want
+    while key.size < want:
+        parts = []
+        for c0 in range(0, draw, chunk):
+            c = min(chunk, draw - c0)
+            a = np.minimum(np.searchsorted(cdf, rng.random(c), side="right"), n - 1)
+            b = np.minimum(np.searchsorted(cdf, rng.random(c), side="right"), n - 1)
+            keep = a != b
+            a, b = a[keep], b[keep]
+            parts.append(np.minimum(a, b).astype(np.int64) * n + np.maximum(a, b))
+        key = np.unique(np.concatenate([key, *parts]))
+        draw = int((want - key.size) * 1.3) + 1024
+    return _csr_from_unique_keys(n, key, name=f"chung_lu(n={n},avg={avg_degree},gamma={gamma},seed={seed})")
 
 
 def batched_mix(count: int = 64, n_lo: int = 2000, n_hi: int = 200000, deg_lo: float = 8.0,
