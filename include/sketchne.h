@@ -169,6 +169,26 @@ int sne_status(const void *workspace, sne_stream_t stream);
 /* Synchronizes `stream` and copies the workspace counters into *out (host). */
 int sne_stats_read(const void *workspace, sne_stats *out, sne_stream_t stream);
 
+/* Allocation-free sne_freigs, for callers that cannot allocate device memory:
+ * for example a plug-in running inside a host framework whose allocator owns
+ * all device memory and forbids raw cudaMalloc, or a caller that may not
+ * allocate (or wait for an allocator) in the middle of a latency-bound step.
+ * The paper has no counterpart; this is an interface convenience.
+ * The workspace is a static 32 MiB device array compiled into this library
+ * (every GPU that loads the library holds it until the process exits).  A
+ * graph whose freigs workspace (sne_workspace_bytes(..., SNE_WS_FREIGS)) is
+ * larger than 32 MiB is rejected with SNE_ERR_SIZE before any work is
+ * enqueued.  The call allocates nothing: the first call on a device looks up
+ * the array's device address once (cudaGetSymbolAddress) and caches it; make
+ * that first call before any stream capture.  Every call shares the array, so
+ * calls that overlap on the GPU (other streams, other host threads) race: the
+ * caller must serialize them.  The call clears the status word it uses, runs
+ * Alg. 5 exactly as sne_freigs does, and, if `status` (a DEVICE int32) is not
+ * NULL, copies the device status word (SNE_OK or SNE_ERR_*) into it.
+ * U: n x k FP32 and lambda: k FP64 as in sne_freigs. */
+int sne_freigs_static(const sne_csr *g, const sne_params *p, float *U, double *lambda,
+                      int32_t *status, sne_stream_t stream);
+
 /* Kernel accounting (host only).  sne_kernel_launches returns the number of
  * kernels this library has enqueued since it was loaded.  Between
  * sne_profile_start and sne_profile_stop every launcher brackets its kernels

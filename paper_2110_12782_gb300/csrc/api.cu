@@ -5,6 +5,7 @@
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "sne_internal.cuh"
 
@@ -601,3 +602,60 @@ int sne_embed_host(const sne_csr *g, const sne_params *p, void *ws, size_t ws_by
 }
 
 }  // extern "C"
+
+// ==========================================================================
+// Allocation-free variant of sne_freigs.  Its workspace is a static device
+// array of this library (one per device the library is used on), so the
+// caller passes only inputs and outputs.
+// ==========================================================================
+namespace {
+
+constexpr size_t kStaticWorkspaceBytes = (size_t)32 << 20;  // 32 MiB
+__device__ __align__(256) unsigned char g_static_workspace[kStaticWorkspaceBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void *g_static_ptr[kMaxDevices] = {nullptr};
+
+// Device address of g_static_workspace on the current device.  The host name
+// of a __device__ array is only a stand-in, so the address is looked up once
+// per device with cudaGetSymbolAddress and cached.
+int static_workspace_ptr(void **out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SNE_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (g_static_ptr[dev] == nullptr) {
+    void *ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_static_workspace) != cudaSuccess || ptr == nullptr)
+      return SNE_ERR_CUDA;
+    g_static_ptr[dev] = ptr;
+  }
+  *out = g_static_ptr[dev];
+  return SNE_OK;
+}
+
+}  // namespace
+
+extern "C" int sne_freigs_static(const sne_csr *g, const sne_params *p, float *U, double *lambda,
+                                 int32_t *status, sne_stream_t stream) {
+  int rc = check_graph(g);
+  if (rc) return rc;
+  Dims D;
+  rc = make_dims(g->n, g->nnz, p, SNE_WS_FREIGS, &D);
+  if (rc) return rc;
+  if (!U || !lambda) return SNE_ERR_ARG;
+  if (carve(D, SNE_WS_FREIGS, nullptr, nullptr) > kStaticWorkspaceBytes) return SNE_ERR_SIZE;
+  void *ws = nullptr;
+  rc = static_workspace_ptr(&ws);
+  if (rc) return rc;
+  Bufs b;
+  carve(D, SNE_WS_FREIGS, ws, &b);
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaMemsetAsync(b.ctrl, 0, sizeof(Ctrl), st));  // the array keeps the previous call's status
+  CK(launch_degrees(*g, b.deg, &b.ctrl->vol, st));
+  rc = run_freigs(*g, *p, D, b, U, lambda, st);
+  if (rc) return rc;
+  if (status)
+    CK(cudaMemcpyAsync(status, &b.ctrl->status, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+  return SNE_OK;
+}

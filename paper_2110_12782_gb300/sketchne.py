@@ -38,7 +38,7 @@ EXPORTS = [
     "sne_sketch_from_factors", "sne_sparse_sign", "sne_gaussian", "sne_degrees",
     "sne_degree_power", "sne_spmm", "sne_validate_csr", "sne_status_reset", "sne_status",
     "sne_stats_read", "sne_embed_host", "sne_kernel_launches", "sne_profile_start",
-    "sne_profile_stop",
+    "sne_profile_stop", "sne_freigs_static",
 ]
 
 
@@ -107,6 +107,7 @@ def lib() -> ctypes.CDLL:
             "sne_kernel_launches": [],
             "sne_profile_start": [],
             "sne_profile_stop": [P(sne_kernel_time), ctypes.c_int, P(ctypes.c_int)],
+            "sne_freigs_static": [P(sne_csr), P(sne_params), vp, vp, vp, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -302,3 +303,12 @@ def sne_profile_stop() -> dict:
     _check(lib().sne_profile_stop(arr, 32, ctypes.byref(cnt)), "sne_profile_stop")
     return {arr[i].name.decode(): (arr[i].calls, arr[i].launches, arr[i].total_ms)
             for i in range(cnt.value)}
+
+
+def sne_freigs_static(g: DeviceGraph, p: sne_params, U: torch.Tensor, lam: torch.Tensor,
+                      status: torch.Tensor | None = None, stream=None) -> None:
+    """Alg. 5 with the library's static device workspace (no allocation)."""
+    _check(lib().sne_freigs_static(ctypes.byref(g.csr), ctypes.byref(p), _ptr(U, torch.float32, "U"),
+                                   _ptr(lam, torch.float64, "lambda"),
+                                   _ptr(status, torch.int32, "status", True), _stream(stream)),
+           "sne_freigs_static")

@@ -1,0 +1,65 @@
+"""sne_freigs_static: the allocation-free entry point.
+
+Some callers cannot allocate device memory (a plug-in inside a host framework
+whose allocator owns the GPU, or a step that may not wait on an allocator).
+sne_freigs_static runs Alg. 5 with a static 32 MiB workspace inside the
+library instead of a caller-provided one.  These tests call it through the C
+ABI twice in a row and compare each result with sne_freigs on the same graph,
+and check that a graph needing more than the static workspace is rejected.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2110_12782_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sk():
+    from paper_2110_12782_gb300 import build
+    build.build()
+    from paper_2110_12782_gb300 import sketchne
+    sketchne.lib()
+    return sketchne
+
+
+def test_static_freigs_matches_workspace_freigs_twice(sk):
+    g = synth.named("sbm4096")
+    G = sk.DeviceGraph.from_numpy(g.row_ptr, g.col_idx)
+    p = sk.sne_params_init(32, 128, q=8)
+    k = p.k
+    ws = sk.workspace(g.n, g.nnz, p, sk.SNE_WS_FREIGS)
+    U_ref = torch.empty(g.n, k, dtype=torch.float32, device="cuda")
+    lam_ref = torch.empty(k, dtype=torch.float64, device="cuda")
+    sk.sne_freigs(G, p, ws, U_ref, lam_ref)
+    assert sk.sne_status(ws) == 0
+    U_ref = U_ref.cpu().numpy().astype(np.float64)
+    lam_ref = lam_ref.cpu().numpy()
+    for _ in range(2):
+        U = torch.full((g.n, k), float("nan"), dtype=torch.float32, device="cuda")
+        lam = torch.full((k,), float("nan"), dtype=torch.float64, device="cuda")
+        status = torch.full((1,), 12345, dtype=torch.int32, device="cuda")
+        sk.sne_freigs_static(G, p, U, lam, status)
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0
+        U = U.cpu().numpy().astype(np.float64)
+        lam = lam.cpu().numpy()
+        # same kernels, same inputs: equal within the parity tolerances
+        assert np.allclose(lam, lam_ref, rtol=0, atol=1e-6)
+        assert np.abs(np.abs(U) - np.abs(U_ref)).max() < 1e-4
+
+
+def test_static_freigs_rejects_graphs_beyond_the_static_workspace(sk):
+    n = 200_000
+    p = sk.sne_params_init(32, 128)
+    assert sk.sne_workspace_bytes(n, 10 * n, p, sk.SNE_WS_FREIGS) > (32 << 20)
+    rp = torch.zeros(n + 1, dtype=torch.int64, device="cuda")
+    ci = torch.zeros(1, dtype=torch.int32, device="cuda")
+    G = sk.DeviceGraph(rp, ci[:0])
+    U = torch.empty(n, p.k, dtype=torch.float32, device="cuda")
+    lam = torch.empty(p.k, dtype=torch.float64, device="cuda")
+    with pytest.raises(sk.SketchNEError) as e:
+        sk.sne_freigs_static(G, p, U, lam)
+    assert e.value.code == sk.SNE_ERR_SIZE
