@@ -19,6 +19,8 @@ namespace {
 struct Dims {
   int64_t n, nnz;
   int k, K, h, l, z, d, nS, nO, Sm, Wab;
+  bool half;  // mixed-precision reconstruction (BF16 / FP16)
+  int kpad;   // k rounded up to a multiple of 64 for the tensor-core operands
 };
 
 int make_dims(int64_t n, int64_t nnz, const sne_params *p, int mode, Dims *D) {
@@ -49,6 +51,12 @@ int make_dims(int64_t n, int64_t nnz, const sne_params *p, int mode, Dims *D) {
     if (d.nS > kUniqueMax || d.nO > kUniqueMax) return SNE_ERR_SIZE;
   }
   d.Sm = std::max(std::max(d.K, d.h), d.k);
+  d.half = p->precision != SNE_FP32;
+  d.kpad = (d.k + 63) / 64 * 64;
+  if (d.half && mode != SNE_WS_FREIGS) {
+    if (!(d.z == 1 || d.z == 2 || d.z == 4 || d.z == 8 || d.z == 16 || d.z == 32)) return SNE_ERR_SIZE;
+    if (d.kpad > 384) return SNE_ERR_SIZE;
+  }
   d.Wab = (mode == SNE_WS_SKETCH) ? d.h : (mode == SNE_WS_FREIGS ? d.K : std::max(d.K, d.h));
   *D = d;
   return SNE_OK;
@@ -81,6 +89,8 @@ struct Bufs {
   int8_t *signS, *signO;
   float *RpS, *RpO, *Yo, *Zf, *Gf;
   double *G64, *Gp, *Tm, *Z64;
+  void *Ah, *AhO, *BhS, *BhO;  // half operands of the tensor-core sketch
+  float *rowfA, *rowfO, *colfS, *colfO;
   int64_t *h_rowptr;  // device staging of a host graph (SNE_WS_EMBED_HOST)
   int32_t *h_col;
   float *h_val, *h_E;
@@ -136,6 +146,16 @@ size_t carve(const Dims &D, int mode, void *base, Bufs *b) {
     x.Gp = bp.take<double>((size_t)D.h * D.l);
     x.Tm = bp.take<double>((size_t)D.h * D.l);
     x.Z64 = bp.take<double>((size_t)D.l * D.l);
+    if (D.half) {
+      x.Ah = bp.take<uint16_t>((size_t)n * D.kpad);
+      x.AhO = bp.take<uint16_t>((size_t)vmax * D.kpad);
+      x.BhS = bp.take<uint16_t>((size_t)D.nS * D.kpad);
+      x.BhO = bp.take<uint16_t>((size_t)D.nO * D.kpad);
+      x.rowfA = bp.take<float>(n);
+      x.rowfO = bp.take<float>(vmax);
+      x.colfS = bp.take<float>(D.nS);
+      x.colfO = bp.take<float>(D.nO);
+    }
   }
   if (host_mode) {
     x.h_rowptr = bp.take<int64_t>(D.n + 1);
@@ -337,13 +357,29 @@ int run_sketch(const sne_csr &g, const sne_params &p, const Dims &D, const Bufs 
   CK(launch_tall_gemm(U, k, b.idxS, D.nS, k, b.m32[3], k, k, b.acoef, b.RpS, k, st));
   CK(launch_tall_gemm(U, k, b.idxO, D.nO, k, b.m32[3], k, k, b.acoef, b.RpO, k, st));
   // --- Alg. 4 line 4: Y = f(L' R'(:, p)) S(p, :)
+  // --- Alg. 4 line 7: Y' = f(L'(p,:) R'(:,p)) O(p,:) on the rows p = p_O
   float *Y = Yout ? Yout : b.A;
-  CK(launch_fused_sketch_f32(U, k, nullptr, nullptr, D.n, k, b.rsc, b.RpS, b.signS, h, z, sv, p.f, Y,
-                             h, st));
-  // --- Alg. 4 line 7: Z = O(p,:)^T f(L'(p,:) R'(:,p)) O(p,:)
   const int64_t vmax = min64(D.n, D.nO);
-  CK(launch_fused_sketch_f32(U, k, b.uniqO, &b.ctrl->v_o, vmax, k, b.rsc, b.RpO, b.signO, l, z, sv,
-                             p.f, b.Yo, l, st));
+  if (!D.half) {
+    CK(launch_fused_sketch_f32(U, k, nullptr, nullptr, D.n, k, b.rsc, b.RpS, b.signS, h, z, sv, p.f,
+                               Y, h, st));
+    CK(launch_fused_sketch_f32(U, k, b.uniqO, &b.ctrl->v_o, vmax, k, b.rsc, b.RpO, b.signO, l, z,
+                               sv, p.f, b.Yo, l, st));
+  } else {
+    const bool fp16 = p.precision == SNE_FP16;
+    CK(launch_to_half_rows(fp16, U, k, nullptr, nullptr, D.n, k, D.kpad, b.rsc, b.Ah, b.rowfA, st));
+    CK(launch_to_half_rows(fp16, U, k, b.uniqO, &b.ctrl->v_o, vmax, k, D.kpad, b.rsc, b.AhO,
+                           b.rowfO, st));
+    CK(launch_to_half_rows(fp16, b.RpS, k, nullptr, nullptr, D.nS, k, D.kpad, nullptr, b.BhS,
+                           b.colfS, st));
+    CK(launch_to_half_rows(fp16, b.RpO, k, nullptr, nullptr, D.nO, k, D.kpad, nullptr, b.BhO,
+                           b.colfO, st));
+    CK(launch_fused_sketch_tc(fp16, b.Ah, D.n, nullptr, D.kpad, b.BhS, D.nS, h, z, b.rowfA, b.colfS,
+                              b.signS, sv, p.f, Y, h, b.ctrl, st));
+    CK(launch_fused_sketch_tc(fp16, b.AhO, vmax, &b.ctrl->v_o, D.kpad, b.BhO, D.nO, l, z, b.rowfO,
+                              b.colfO, b.signO, sv, p.f, b.Yo, l, b.ctrl, st));
+  }
+  // --- Z = O(p,:)^T Y'  (Alg. 4 line 7)
   float *Z = Zout ? Zout : b.Zf;
   CK(launch_signed_gather_sum(b.Yo, l, l, b.posO, b.signO, l, z, sv, Z, l, st));
   if (!E && !sigma) return SNE_OK;
@@ -542,7 +578,6 @@ int sne_sketch_from_factors(const sne_csr *g, const sne_params *p, const float *
   rc = check_ws(ws, ws_bytes, carve(D, SNE_WS_SKETCH, nullptr, nullptr));
   if (rc) return rc;
   if (!U || !lambda) return SNE_ERR_ARG;
-  if (p->precision != SNE_FP32) return SNE_ERR_ARG;  // mixed precision: see sketch_tc.cu
   Bufs b;
   carve(D, SNE_WS_SKETCH, ws, &b);
   cudaStream_t st = (cudaStream_t)stream;
@@ -561,7 +596,6 @@ int sne_embed(const sne_csr *g, const sne_params *p, void *ws, size_t ws_bytes, 
   rc = check_ws(ws, ws_bytes, carve(D, SNE_WS_EMBED, nullptr, nullptr));
   if (rc) return rc;
   if (!E || !sigma) return SNE_ERR_ARG;
-  if (p->precision != SNE_FP32) return SNE_ERR_ARG;
   Bufs b;
   carve(D, SNE_WS_EMBED, ws, &b);
   cudaStream_t st = (cudaStream_t)stream;

@@ -1,0 +1,475 @@
+// Mixed-precision fused reconstruct + f + sparse-sign sketch (Eq. 4 and the
+// Z core of Alg. 4) on the fifth-generation tensor cores of sm_103a.
+//
+// The reconstruction L' R'(:, p) runs as a BF16 or FP16 GEMM with FP32
+// accumulation.  Per-row and per-column scaling keeps both operands in
+// [-1, 1]: A_hat[i, :] = U[i, :] / max|U[i, :]| with row factor
+// rowf_i = max|U[i, :]| * vol/(bT) * d_i^(-1+alpha), and
+// B_hat[e, :] = R'(:, idx_e)^T / colf_e with colf_e = max|R'(:, idx_e)|, so
+// that x_ie = rowf_i * colf_e * <A_hat_i, B_hat_e> is formed in FP32 before f.
+//
+// One CTA owns a tile of 128 rows and walks over all evaluated columns in
+// tiles of 256:
+//   warp 0   TMA producer: the 128 x k A tile once, then 256 x 64 B k-blocks
+//            through a ring of shared-memory stages (128-byte swizzle);
+//   warp 1   allocates 512 TMEM columns (two 128 x 256 FP32 accumulators)
+//            and issues tcgen05.mma (M 128, N 256, K 16) from one thread;
+//   warps 2-5  epilogue: tcgen05.ld of the accumulator rows, x = scale * acc,
+//            f(x), sign, and the z-column segmented sums in registers, then
+//            the Y (or Y') row segment is stored.
+// Double-buffered accumulators let the epilogue of tile j overlap the MMAs
+// of tile j+1.  Every mbarrier wait is bounded (about 2 s of %globaltimer);
+// on timeout the CTA records SNE_ERR_TIMEOUT, stops issuing work, waits for
+// its in-flight MMAs and copies, frees TMEM and returns.
+#include <cuda.h>
+
+#include "sne_internal.cuh"
+
+namespace sne {
+
+namespace tc {
+
+constexpr int BM = 128;
+constexpr int BN = 256;
+constexpr int BK = 64;                        // elements per k-block (128 bytes)
+constexpr int kABlockBytes = BM * BK * 2;     // 16 KB
+constexpr int kBStageBytes = BN * BK * 2;     // 32 KB
+constexpr int kThreads = 192;
+constexpr unsigned long long kTimeoutNs = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; false on timeout or when another role aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          Ctrl *ctrl) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (gtimer() - t0 > kTimeoutNs) {
+      *abort_flag = 1;
+      record_error(ctrl, SNE_ERR_TIMEOUT, W_TC);
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, uint64_t *bar, int x,
+                                            int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+      "%4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(tm), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
+  d |= (uint64_t)1 << 46;             // descriptor version
+  d |= (uint64_t)2 << 61;             // 128-byte swizzle
+  return d;
+}
+__device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.u32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int F>
+__device__ __forceinline__ float fx(float x) {
+  if (F == SNE_F_TRUNC_LOG) return x > 1.0f ? __logf(x) : 0.0f;
+  return x;
+}
+
+}  // namespace tc
+
+template <int F, int Z>
+__global__ void __launch_bounds__(tc::kThreads, 1) fused_sketch_tc_kernel(
+    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+    int64_t nrows_max, const int32_t *__restrict__ nrows_dev, int kblocks, int stages,
+    int ncols_eval, int cols_out, const float *__restrict__ rowf, const float *__restrict__ colf,
+    const int8_t *__restrict__ sign, float sv, uint32_t idesc, float *__restrict__ out, int64_t ldo,
+    Ctrl *ctrl) {
+  using namespace tc;
+  extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
+  unsigned char *sA = smem;
+  unsigned char *sB = sA + (size_t)kblocks * kABlockBytes;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(sB + (size_t)stages * kBStageBytes);
+  uint64_t *a_full = bars;
+  uint64_t *full = bars + 1;
+  uint64_t *empty = full + stages;
+  uint64_t *tfull = empty + stages;   // 2
+  uint64_t *tempty = tfull + 2;       // 2
+  uint64_t *done = tempty + 2;        // 1
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+  int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t nrows = nrows_dev ? (int64_t)(*nrows_dev) : nrows_max;
+  const int64_t row0 = (int64_t)blockIdx.x * BM;
+  if (row0 >= nrows) return;  // uniform for the CTA
+  const int ntiles = (ncols_eval + BN - 1) / BN;
+
+  if (threadIdx.x == 0) {
+    mbar_init(a_full, 1);
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 128);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  volatile int *abortv = abort_flag;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer
+      mbar_expect_tx(a_full, (uint32_t)(kblocks * kABlockBytes));
+      for (int kb = 0; kb < kblocks; ++kb)
+        tma_load_2d(sA + (size_t)kb * kABlockBytes, &tmA, a_full, kb * BK, (int)row0);
+      int it = 0;
+      int issued = 0;
+      bool ok = true;
+      for (int j = 0; j < ntiles && ok; ++j) {
+        for (int kb = 0; kb < kblocks; ++kb, ++it) {
+          const int s = it % stages;
+          const uint32_t ph = (uint32_t)((it / stages) & 1);
+          if (!mbar_wait(&empty[s], ph ^ 1u, abortv, ctrl)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&full[s], (uint32_t)kBStageBytes);
+          tma_load_2d(sB + (size_t)s * kBStageBytes, &tmB, &full[s], kb * BK, j * BN);
+          ++issued;
+        }
+      }
+      if (!ok) {
+        // let the copies already issued land before the CTA exits
+        (void)mbar_wait(a_full, 0, abortv, ctrl);
+        const int first = issued > stages ? issued - stages : 0;
+        for (int q = first; q < issued; ++q) {
+          const uint64_t t0 = gtimer();
+          while (!mbar_try_wait(&full[q % stages], (uint32_t)((q / stages) & 1)) &&
+                 gtimer() - t0 < kTimeoutNs) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      bool ok = mbar_wait(a_full, 0, abortv, ctrl);
+      int it = 0;
+      for (int j = 0; j < ntiles && ok; ++j) {
+        const int buf = j & 1;
+        const uint32_t use = (uint32_t)(j >> 1);
+        if (!mbar_wait(&tempty[buf], (use & 1u) ^ 1u, abortv, ctrl)) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t dt = tmem + (uint32_t)(buf * BN);
+        for (int kb = 0; kb < kblocks; ++kb, ++it) {
+          const int s = it % stages;
+          if (!mbar_wait(&full[s], (uint32_t)((it / stages) & 1), abortv, ctrl)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t a0 = smem_u32(sA + (size_t)kb * kABlockBytes);
+          const uint32_t b0 = smem_u32(sB + (size_t)s * kBStageBytes);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk)
+            mma_f16(dt, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), idesc, (kb | kk) ? 1u : 0u);
+          mma_commit(&empty[s]);
+        }
+        if (!ok) break;
+        mma_commit(&tfull[buf]);
+      }
+      // wait for every MMA issued by this thread before TMEM is released
+      mma_commit(done);
+      const uint64_t t0 = gtimer();
+      while (!mbar_try_wait(done, 0) && gtimer() - t0 < kTimeoutNs) {
+      }
+    }
+  } else {
+    // ---------------- epilogue warps 2..5
+    const int ew = warp & 3;  // TMEM lane quarter this warp may access
+    const int64_t row = row0 + 32 * ew + lane;
+    const bool row_ok = row < nrows;
+    const float rf = row_ok ? rowf[row] : 0.0f;
+    constexpr int G = 32 / Z;  // output columns per 32-column chunk
+    for (int j = 0; j < ntiles; ++j) {
+      const int buf = j & 1;
+      const uint32_t use = (uint32_t)(j >> 1);
+      if (!mbar_wait(&tfull[buf], use & 1u, abortv, ctrl)) break;
+      fence_after();
+#pragma unroll 1
+      for (int c = 0; c < BN / 32; ++c) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * ew) << 16) + (uint32_t)(buf * BN + c * 32), v);
+        const int e0 = j * BN + c * 32;
+        if (e0 >= ncols_eval) continue;
+        float acc[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) acc[g] = 0.0f;
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+          const int e = e0 + t;
+          const float cf = e < ncols_eval ? __ldg(colf + e) : 0.0f;
+          const float sg = e < ncols_eval ? (float)__ldg(sign + e) : 0.0f;
+          acc[t / Z] = fmaf(sg, tc::fx<F>(rf * cf * v[t]), acc[t / Z]);
+        }
+        if (row_ok) {
+          const int oc0 = e0 / Z;
+#pragma unroll
+          for (int g = 0; g < G; ++g)
+            if (oc0 + g < cols_out) out[row * ldo + oc0 + g] = sv * acc[g];
+        }
+      }
+      fence_before();
+      mbar_arrive(&tempty[buf]);
+    }
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+// ---------------------------------------------------------------------------
+// Row-normalized half-precision copies of the GEMM operands
+// ---------------------------------------------------------------------------
+template <typename H>
+__device__ __forceinline__ H to_h(float x);
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_h<__nv_bfloat16>(float x) {
+  return __float2bfloat16_rn(x);
+}
+template <>
+__device__ __forceinline__ __half to_h<__half>(float x) {
+  return __float2half_rn(x);
+}
+
+// dst[r, :kpad] = src[s(r), :k] / max|src[s(r), :k]| (zero padded); scale[r] =
+// max|src[s(r), :]| * extra[s(r)].  Rows r >= *nrows_dev (when given) are zero.
+template <typename H>
+__global__ void __launch_bounds__(256) to_half_rows_kernel(
+    const float *__restrict__ src, int64_t lds, const int32_t *__restrict__ ridx,
+    const int32_t *__restrict__ nrows_dev, int64_t nrows_max, int k, int kpad,
+    const float *__restrict__ extra, H *__restrict__ dst, float *__restrict__ scale) {
+  const int lane = threadIdx.x & 31;
+  const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (r >= nrows_max) return;
+  const int64_t nrows = nrows_dev ? (int64_t)(*nrows_dev) : nrows_max;
+  H *d = dst + r * kpad;
+  if (r >= nrows) {
+    for (int c = lane; c < kpad; c += 32) d[c] = to_h<H>(0.0f);
+    if (lane == 0) scale[r] = 0.0f;
+    return;
+  }
+  const int64_t s = ridx ? (int64_t)ridx[r] : r;
+  const float *x = src + s * lds;
+  float m = 0.0f;
+  for (int c = lane; c < k; c += 32) m = fmaxf(m, fabsf(x[c]));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  const float inv = m > 0.0f ? 1.0f / m : 0.0f;
+  for (int c = lane; c < kpad; c += 32) d[c] = to_h<H>(c < k ? x[c] * inv : 0.0f);
+  if (lane == 0) scale[r] = m * (extra ? extra[s] : 1.0f);
+}
+
+cudaError_t launch_to_half_rows(bool fp16, const float *src, int64_t lds, const int32_t *ridx,
+                                const int32_t *nrows_dev, int64_t nrows_max, int k, int kpad,
+                                const float *extra, void *dst, float *scale, cudaStream_t st) {
+  if (nrows_max <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((nrows_max + 7) / 8);
+  ProfScope ps_(K_MISC, st);
+  if (fp16)
+    to_half_rows_kernel<__half><<<blocks, 256, 0, st>>>(src, lds, ridx, nrows_dev, nrows_max, k, kpad,
+                                                        extra, static_cast<__half *>(dst), scale);
+  else
+    to_half_rows_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(
+        src, lds, ridx, nrows_dev, nrows_max, k, kpad, extra, static_cast<__nv_bfloat16 *>(dst),
+        scale);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Tensor maps (driver entry point looked up through the runtime)
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+static bool make_map(CUtensorMap *tm, bool fp16, const void *ptr, int64_t rows, int kpad,
+                     int box_rows) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t gdim[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
+  cuuint64_t gstride[1] = {(cuuint64_t)kpad * 2};
+  cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(tm, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                   const_cast<void *>(ptr), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+size_t fused_tc_smem_bytes(int kpad, int *stages_out) {
+  const int kblocks = kpad / tc::BK;
+  int stages = 4;
+  while (stages > 2 && (size_t)kblocks * tc::kABlockBytes + (size_t)stages * tc::kBStageBytes >
+                           200 * 1024)
+    --stages;
+  if (stages_out) *stages_out = stages;
+  return 1024 + (size_t)kblocks * tc::kABlockBytes + (size_t)stages * tc::kBStageBytes + 256;
+}
+
+cudaError_t launch_fused_sketch_tc(bool fp16, const void *Ahat, int64_t nrows_max,
+                                   const int32_t *nrows_dev, int kpad, const void *Bhat,
+                                   int ncols_eval, int cols_out, int z, const float *rowf,
+                                   const float *colf, const int8_t *sign, float sv, int f, float *out,
+                                   int64_t ldo, Ctrl *ctrl, cudaStream_t st) {
+  if (nrows_max <= 0 || cols_out <= 0) return cudaSuccess;
+  if (kpad % tc::BK != 0 || kpad <= 0) return cudaErrorInvalidValue;
+  if (!(z == 1 || z == 2 || z == 4 || z == 8 || z == 16 || z == 32)) return cudaErrorInvalidValue;
+  if (((uintptr_t)Ahat % 16) || ((uintptr_t)Bhat % 16)) return cudaErrorInvalidValue;
+  int stages = 0;
+  const size_t smem = fused_tc_smem_bytes(kpad, &stages);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  CUtensorMap tmA, tmB;
+  if (!make_map(&tmA, fp16, Ahat, nrows_max, kpad, tc::BM)) return cudaErrorInvalidValue;
+  if (!make_map(&tmB, fp16, Bhat, ncols_eval, kpad, tc::BN)) return cudaErrorInvalidValue;
+  // instruction descriptor: D F32, A/B F16 (0) or BF16 (1), K-major, N = 256, M = 128
+  const uint32_t fmt = fp16 ? 0u : 1u;
+  const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(tc::BN >> 3) << 17) |
+                         ((uint32_t)(tc::BM >> 4) << 24);
+  const unsigned grid = (unsigned)((nrows_max + tc::BM - 1) / tc::BM);
+  const int kblocks = kpad / tc::BK;
+#define SNE_TC_LAUNCH(FV, ZV)                                                                     \
+  do {                                                                                            \
+    auto kern = fused_sketch_tc_kernel<FV, ZV>;                                                   \
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
+                                         (int)smem);                                              \
+    if (e != cudaSuccess) return e;                                                               \
+    ProfScope ps_(K_FUSED_TC, st);                                                                \
+    kern<<<grid, tc::kThreads, smem, st>>>(tmA, tmB, nrows_max, nrows_dev, kblocks, stages,       \
+                                           ncols_eval, cols_out, rowf, colf, sign, sv, idesc, out, \
+                                           ldo, ctrl);                                            \
+  } while (0)
+#define SNE_TC_Z(FV)             \
+  switch (z) {                   \
+    case 1: SNE_TC_LAUNCH(FV, 1); break;  \
+    case 2: SNE_TC_LAUNCH(FV, 2); break;  \
+    case 4: SNE_TC_LAUNCH(FV, 4); break;  \
+    case 8: SNE_TC_LAUNCH(FV, 8); break;  \
+    case 16: SNE_TC_LAUNCH(FV, 16); break; \
+    default: SNE_TC_LAUNCH(FV, 32); break; \
+  }
+  if (f == SNE_F_TRUNC_LOG) {
+    SNE_TC_Z(SNE_F_TRUNC_LOG)
+  } else {
+    SNE_TC_Z(SNE_F_IDENTITY)
+  }
+#undef SNE_TC_Z
+#undef SNE_TC_LAUNCH
+  return cudaGetLastError();
+}
+
+}  // namespace sne

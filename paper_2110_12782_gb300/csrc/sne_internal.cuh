@@ -1,6 +1,8 @@
 // Internal declarations shared by the translation units of libsketchne.so.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -34,6 +36,7 @@ enum Where : int32_t {
   W_NAN = 6,
   W_SPARSE_SIGN = 7,
   W_UNIQUE = 8,
+  W_TC = 9,
 };
 
 __device__ __forceinline__ void record_error(Ctrl *c, int32_t code, int32_t where) {
@@ -163,6 +166,17 @@ cudaError_t launch_fused_sketch_f32(const float *A, int64_t lda, const int32_t *
                                     const float *rs, const float *B, const int8_t *sign,
                                     int32_t cols_out, int32_t z, float sv, int32_t f, float *out,
                                     int64_t ldo, cudaStream_t st);
+// sketch_tc.cu: mixed-precision fused sketch (BF16 or FP16 operands, FP32
+// accumulation on tcgen05).  Operands are row-normalized half copies made by
+// launch_to_half_rows; kpad is k rounded up to a multiple of 64.
+cudaError_t launch_to_half_rows(bool fp16, const float *src, int64_t lds, const int32_t *ridx,
+                                const int32_t *nrows_dev, int64_t nrows_max, int k, int kpad,
+                                const float *extra, void *dst, float *scale, cudaStream_t st);
+cudaError_t launch_fused_sketch_tc(bool fp16, const void *Ahat, int64_t nrows_max,
+                                   const int32_t *nrows_dev, int kpad, const void *Bhat,
+                                   int ncols_eval, int cols_out, int z, const float *rowf,
+                                   const float *colf, const int8_t *sign, float sv, int f, float *out,
+                                   int64_t ldo, Ctrl *ctrl, cudaStream_t st);
 // out[c, :] = sv * sum_t sign[c*z+t] * In[idx[c*z+t], :]
 cudaError_t launch_signed_gather_sum(const float *In, int64_t ldi, int32_t width, const int32_t *idx,
                                      const int8_t *sign, int32_t cols, int32_t z, float sv,
