@@ -82,6 +82,7 @@ struct Bufs {
   double *m64[5];
   void *eigscr;
   float *m32[4];
+  float *mT;  // transposed small factor for the tensor-core tall product
   double *w64, *lam;
   float *w32;
   int32_t *perm;
@@ -123,6 +124,7 @@ size_t carve(const Dims &D, int mode, void *base, Bufs *b) {
   for (auto &m : x.m64) m = bp.take<double>(S2);
   x.eigscr = bp.take<char>(std::max(eig_scratch_bytes(D.Sm), (S2 + 4 * (size_t)D.Sm) * 8 + 1024));
   for (auto &m : x.m32) m = bp.take<float>(S2);
+  x.mT = bp.take<float>(S2);
   x.w64 = bp.take<double>(D.Sm);
   x.lam = bp.take<double>(D.Sm);
   x.w32 = bp.take<float>(D.Sm);
@@ -267,7 +269,7 @@ inline unsigned grid_for(int64_t work, int per = 256, int cap = 152 * 8) {
 // orthonormalizations inside the power iteration of Alg. 5).
 int orth_tall(const Dims &D, const Bufs &b, int method, bool fp64, const float *Y, int64_t ldy, int w,
               float *Q, int64_t ldq, cudaStream_t st) {
-  CK(launch_gram(Y, ldy, w, Y, ldy, w, D.n, nullptr, true, b.partial, b.m64[0], w, st));
+  CK(launch_gram(Y, ldy, w, Y, ldy, w, D.n, nullptr, true, b.partial, b.m64[0], w, st, b.ctrl));
   if (method == SNE_ORTH_EIGSVD) {
     CK(launch_d2f(b.m64[0], w, w, w, b.m32[0], w, st));
     CK(launch_sym_eig<float>(b.m32[0], w, w, b.w32, b.m32[1], w, b.eigscr, b.ctrl, st));
@@ -281,7 +283,7 @@ int orth_tall(const Dims &D, const Bufs &b, int method, bool fp64, const float *
     CK(launch_d2f(b.m64[0], w, w, w, b.m32[0], w, st));
     CK(launch_chol_inverse<float>(b.m32[0], w, w, b.m32[2], w, b.m32[1], b.ctrl, st));
   }
-  CK(launch_tall_gemm(Y, ldy, nullptr, D.n, w, b.m32[2], w, w, nullptr, Q, ldq, st));
+  CK(launch_tall_gemm_auto(Y, ldy, D.n, w, b.m32[2], w, w, Q, ldq, b.mT, b.ctrl, st));
   return SNE_OK;
 }
 
@@ -311,14 +313,14 @@ int run_freigs(const sne_csr &g, const sne_params &p, const Dims &D, const Bufs 
   if (rc) return rc;
   // Rayleigh-Ritz: S = Q^T X Q (FP64), eig(S), U = Q U_hat, top k by |lambda|
   CK(launch_spmm(g, b.dpow, Q, ld, K, T1, ld, st));
-  CK(launch_gram(Q, ld, K, T1, ld, K, D.n, nullptr, false, b.partial, b.m64[0], K, st));
+  CK(launch_gram(Q, ld, K, T1, ld, K, D.n, nullptr, false, b.partial, b.m64[0], K, st, b.ctrl));
   CK(launch_symmetrize(b.m64[0], K, K, st));
   CK(launch_sym_eig<double>(b.m64[0], K, K, b.w64, b.m64[1], K, b.eigscr, b.ctrl, st));
   CK(launch_eig_order<double>(b.w64, K, true, b.perm, st));
   { ProfScope ps_(K_MISC, st); select_cols_kernel<<<grid_for((int64_t)K * D.k), 256, 0, st>>>(b.m64[1], K, K, b.perm, b.w64, D.k,
                                                                  0, b.m32[0], D.k, lam, 0); }
   CK(cudaGetLastError());
-  CK(launch_tall_gemm(Q, ld, nullptr, D.n, K, b.m32[0], D.k, D.k, nullptr, U, D.k, st));
+  CK(launch_tall_gemm_auto(Q, ld, D.n, K, b.m32[0], D.k, D.k, U, D.k, b.mT, b.ctrl, st));
   return SNE_OK;
 }
 
@@ -334,7 +336,7 @@ int run_sketch(const sne_csr &g, const sne_params &p, const Dims &D, const Bufs 
   { ProfScope ps_(K_MISC, st); rowscale_kernel<<<grid_for(D.n), 256, 0, st>>>(b.deg, D.n, (float)(-1.0 + p.alpha), &b.ctrl->vol,
                                                  1.0 / (p.b * p.T), b.rsc); }    // vol/(bT) a
   CK(cudaGetLastError());
-  CK(launch_gram(U, k, k, U, k, k, D.n, b.wgt, true, b.partial, b.m64[0], k, st));  // U^T D U
+  CK(launch_gram(U, k, k, U, k, k, D.n, b.wgt, true, b.partial, b.m64[0], k, st, b.ctrl));  // U^T D U
   { ProfScope ps_(K_MISC, st); scale_cols_d2f_kernel<<<grid_for((int64_t)k * k), 256, 0, st>>>(b.m64[0], k, lam, b.m32[0]); }  // K
   { ProfScope ps_(K_MISC, st); eye_kernel<<<grid_for((int64_t)k * k), 256, 0, st>>>(b.m32[1], k); }                            // I
   CK(cudaGetLastError());
@@ -409,7 +411,7 @@ int run_sketch(const sne_csr &g, const sne_params &p, const Dims &D, const Bufs 
   { ProfScope ps_(K_MISC, st); select_cols_kernel<<<grid_for((int64_t)h * D.d), 256, 0, st>>>(b.m64[4], h, h, b.perm, b.w64, D.d,
                                                                  1, b.m32[0], D.d, sigma, 1); }
   CK(cudaGetLastError());
-  if (E) CK(launch_tall_gemm(Q, h, nullptr, D.n, h, b.m32[0], D.d, D.d, nullptr, E, D.d, st));
+  if (E) CK(launch_tall_gemm_auto(Q, h, D.n, h, b.m32[0], D.d, D.d, E, D.d, b.mT, b.ctrl, st));
   return SNE_OK;
 }
 

@@ -4,6 +4,7 @@
 // inverse, symmetric eigendecomposition by Householder tridiagonalization and
 // implicit shifted QR).
 #include <cfloat>
+#include <cstdlib>
 #include <cmath>
 
 #include "sne_internal.cuh"
@@ -31,13 +32,24 @@ static void gram_grid(int64_t n, int Ka, int Kb, bool symmetric, int *tiles, int
   *chunks = want;
 }
 
+bool tc_gemm_enabled() {
+  static int enabled = -1;
+  if (enabled < 0) {
+    const char *v = getenv("SNE_SIMT_GEMM");
+    enabled = (v && v[0] == '1') ? 0 : 1;
+  }
+  return enabled == 1;
+}
+
 size_t gram_partial_floats(int64_t n, int32_t Ka, int32_t Kb) {
+  const size_t tcf = gram_tc_partial_floats(n, Ka, Kb);
   int tiles, chunks;
   gram_grid(n, Ka, Kb, false, &tiles, &chunks);
   int tiles_s, chunks_s;
   gram_grid(n, Ka, Kb, Ka == Kb, &tiles_s, &chunks_s);
   if (chunks_s > chunks) chunks = chunks_s;
-  return (size_t)chunks * (size_t)Ka * (size_t)Kb;
+  const size_t simt = (size_t)chunks * (size_t)Ka * (size_t)Kb;
+  return simt > tcf ? simt : tcf;
 }
 
 __global__ void __launch_bounds__(kGThreads) gram_partial_kernel(
@@ -134,10 +146,22 @@ __global__ void gram_reduce_kernel(const float *__restrict__ partial, int32_t Ka
   }
 }
 
+cudaError_t launch_gram_reduce(const float *partial, int Ka, int Kb, int chunks, double *C, int ldc,
+                               cudaStream_t st) {
+  const int64_t total = (int64_t)Ka * Kb;
+  ProfScope ps_(K_GRAM_TC, st);
+  gram_reduce_kernel<<<(unsigned)min64(1024, (total + 255) / 256), 256, 0, st>>>(
+      partial, Ka, Kb, chunks, 0, C, ldc);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gram(const float *A, int64_t lda, int32_t Ka, const float *B, int64_t ldb,
                         int32_t Kb, int64_t n, const float *w, bool symmetric, float *partial,
-                        double *C, int32_t ldc, cudaStream_t st) {
+                        double *C, int32_t ldc, cudaStream_t st, Ctrl *ctrl) {
   if (symmetric && (A != B || Ka != Kb || lda != ldb)) return cudaErrorInvalidValue;
+  if (tc_gemm_enabled() && tc_gemm_supported(Kb) && lda % 4 == 0 && ldb % 4 == 0 &&
+      (uintptr_t)A % 16 == 0 && (uintptr_t)B % 16 == 0 && n >= 256)
+    return launch_gram_tc(A, lda, Ka, B, ldb, Kb, n, w, partial, C, ldc, ctrl, st);
   int tiles, chunks;
   gram_grid(n, Ka, Kb, symmetric, &tiles, &chunks);
   const int64_t rpc = (n + chunks - 1) / chunks;
@@ -220,6 +244,30 @@ __global__ void __launch_bounds__(256) tall_gemm_kernel(
       if (c < Kc) C[row * ldc + c] = s * acc[i][j];
     }
   }
+}
+
+__global__ void transpose_kernel(const float *M, int rows, int cols, int ldm, float *Mt) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < rows * cols; q += gridDim.x * blockDim.x) {
+    const int r = q / cols, c = q % cols;
+    Mt[(int64_t)c * rows + r] = M[(int64_t)r * ldm + c];
+  }
+}
+
+cudaError_t launch_tall_gemm_auto(const float *A, int64_t lda, int64_t n, int32_t Ka, const float *M,
+                                  int32_t ldm, int32_t Kc, float *C, int64_t ldc, float *Mt,
+                                  Ctrl *ctrl, cudaStream_t st) {
+  if (tc_gemm_enabled() && tc_gemm_supported(Kc) && Mt && lda % 4 == 0 && ldc % 4 == 0 &&
+      Ka % 4 == 0 && (uintptr_t)A % 16 == 0 && n >= 256) {
+    {
+      ProfScope ps_(K_MISC, st);
+      transpose_kernel<<<(unsigned)min64(1024, ((int64_t)Ka * Kc + 255) / 256), 256, 0, st>>>(
+          M, Ka, Kc, ldm, Mt);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_tall_gemm_tc(A, lda, n, Ka, Mt, Kc, C, ldc, ctrl, st);
+  }
+  return launch_tall_gemm(A, lda, nullptr, n, Ka, M, ldm, Kc, nullptr, C, ldc, st);
 }
 
 cudaError_t launch_tall_gemm(const float *A, int64_t lda, const int32_t *ridx, int64_t n, int32_t Ka,

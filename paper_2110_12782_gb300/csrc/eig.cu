@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const float *__restrict__ 
   }
   __syncthreads();
   const float tol = 2.0f * FLT_EPSILON;
-  const int nblocks = P * (P + 1) / 2;
+  const int warp_id = tid >> 5, lane_id = tid & 31, nwarps = nt >> 5;
   int round = 0;
   int sweep = 0;
   for (; sweep < kJacobiMaxSweeps; ++sweep) {
@@ -113,36 +113,37 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const float *__restrict__ 
         rot[(int64_t)round * P + t] = Rot{p, q, c, s};
       }
       __syncthreads();
-      for (int bi = tid; bi < nblocks; bi += nt) {
-        int j = (int)((sqrtf(8.0f * bi + 1.0f) - 1.0f) * 0.5f);
-        while (j * (j + 1) / 2 > bi) --j;
-        while ((j + 1) * (j + 2) / 2 <= bi) ++j;
-        const int i = bi - j * (j + 1) / 2;  // i <= j
-        const float c1 = rc[i], s1 = rs[i], c2 = rc[j], s2 = rs[j];
-        if (s1 == 0.0f && s2 == 0.0f) continue;
-        const int p1 = rp[i], q1 = rq[i], p2 = rp[j], q2 = rq[j];
-        if (i == j) {
-          if (q1 >= n) continue;
-          const float app = Ap[packed_lower(p1, p1)], aqq = Ap[packed_lower(q1, q1)];
-          const float apq = Ap[packed_lower(q1, p1)];
-          const float t_ = s1 / c1;
-          Ap[packed_lower(p1, p1)] = app - t_ * apq;
-          Ap[packed_lower(q1, q1)] = aqq + t_ * apq;
-          Ap[packed_lower(q1, p1)] = 0.0f;
-          continue;
+      // 2x2 blocks (i, j), i <= j: warp per block row i, lanes over j
+      for (int i = warp_id; i < P; i += nwarps) {
+        const float c1 = rc[i], s1 = rs[i];
+        const int p1 = rp[i], q1 = rq[i];
+        for (int j = i + lane_id; j < P; j += 32) {
+          const float c2 = rc[j], s2 = rs[j];
+          if (s1 == 0.0f && s2 == 0.0f) continue;
+          const int p2 = rp[j], q2 = rq[j];
+          if (i == j) {
+            if (q1 >= n) continue;
+            const float app = Ap[packed_lower(p1, p1)], aqq = Ap[packed_lower(q1, q1)];
+            const float apq = Ap[packed_lower(q1, p1)];
+            const float t_ = s1 / c1;
+            Ap[packed_lower(p1, p1)] = app - t_ * apq;
+            Ap[packed_lower(q1, q1)] = aqq + t_ * apq;
+            Ap[packed_lower(q1, p1)] = 0.0f;
+            continue;
+          }
+          // block rows (p1, q1), columns (p2, q2): B' = J1^T B J2
+          const bool v1q = q1 < n, v2q = q2 < n;
+          const float b00 = Ap[packed_any(p1, p2)];
+          const float b01 = v2q ? Ap[packed_any(p1, q2)] : 0.0f;
+          const float b10 = v1q ? Ap[packed_any(q1, p2)] : 0.0f;
+          const float b11 = (v1q && v2q) ? Ap[packed_any(q1, q2)] : 0.0f;
+          const float x1 = c1 * b00 - s1 * b10, x2 = c1 * b01 - s1 * b11;
+          const float x3 = s1 * b00 + c1 * b10, x4 = s1 * b01 + c1 * b11;
+          Ap[packed_any(p1, p2)] = x1 * c2 - x2 * s2;
+          if (v2q) Ap[packed_any(p1, q2)] = x1 * s2 + x2 * c2;
+          if (v1q) Ap[packed_any(q1, p2)] = x3 * c2 - x4 * s2;
+          if (v1q && v2q) Ap[packed_any(q1, q2)] = x3 * s2 + x4 * c2;
         }
-        // block rows (p1, q1), columns (p2, q2): B' = J1^T B J2
-        const bool v1q = q1 < n, v2q = q2 < n;
-        const float b00 = Ap[packed_any(p1, p2)];
-        const float b01 = v2q ? Ap[packed_any(p1, q2)] : 0.0f;
-        const float b10 = v1q ? Ap[packed_any(q1, p2)] : 0.0f;
-        const float b11 = (v1q && v2q) ? Ap[packed_any(q1, q2)] : 0.0f;
-        const float x1 = c1 * b00 - s1 * b10, x2 = c1 * b01 - s1 * b11;
-        const float x3 = s1 * b00 + c1 * b10, x4 = s1 * b01 + c1 * b11;
-        Ap[packed_any(p1, p2)] = x1 * c2 - x2 * s2;
-        if (v2q) Ap[packed_any(p1, q2)] = x1 * s2 + x2 * c2;
-        if (v1q) Ap[packed_any(q1, p2)] = x3 * c2 - x4 * s2;
-        if (v1q && v2q) Ap[packed_any(q1, q2)] = x3 * s2 + x4 * c2;
       }
       __syncthreads();
       ++round;
@@ -322,16 +323,12 @@ __global__ void __launch_bounds__(1024) chol_inv_packed_kernel(const T *__restri
     const T inv = piv;
     for (int c = j + 1 + tid; c < n; c += nt) U[packed_upper(n, j, c)] *= inv;
     __syncthreads();
-    const int mm = n - j - 1;
-    const int cnt = mm * (mm + 1) / 2;
-    for (int e = tid; e < cnt; e += nt) {
-      // e enumerates (r, c) with j < r <= c < n, row-major over r
-      int r = (int)((2 * mm + 1 - sqrtf((float)((2 * mm + 1) * (2 * mm + 1) - 8 * e))) * 0.5f);
-      while (r > 0 && r * (2 * mm - r + 1) / 2 > e) --r;
-      while ((r + 1) * (2 * mm - r) / 2 <= e) ++r;
-      const int c = e - r * (2 * mm - r + 1) / 2 + r;
-      const int rr = j + 1 + r, cc = j + 1 + c;
-      U[packed_upper(n, rr, cc)] -= U[packed_upper(n, j, rr)] * U[packed_upper(n, j, cc)];
+    // trailing update U(r, c) -= U(j, r) U(j, c), j < r <= c: warp per row r
+    for (int rr = j + 1 + (tid >> 5); rr < n; rr += (nt >> 5)) {
+      const T ujr = U[packed_upper(n, j, rr)];
+      T *urow = U + packed_upper(n, rr, rr) - rr;  // urow[c] = U(rr, c) for c >= rr
+      const T *ujrow = U + packed_upper(n, j, j) - j;
+      for (int cc = rr + (tid & 31); cc < n; cc += 32) urow[cc] -= ujr * ujrow[cc];
     }
     __syncthreads();
   }

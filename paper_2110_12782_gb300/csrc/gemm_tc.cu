@@ -1,0 +1,585 @@
+// FP32-accurate tall-skinny products on tcgen05 (kind::tf32, three passes):
+//   TALL  C[i, :] = A[i, :] M            (A n x K row-major, M K x Kc; the
+//                                          operand B is M^T, K-major)
+//   GRAM  P[c]    = sum_{i in chunk c} w_i A[i, :]^T B[i, :]
+//                                        (both operands MN-major, read straight
+//                                          from the row-major tall matrices)
+// used for the eigSVD / Cholesky-QR orthonormalizations and the Rayleigh-Ritz
+// product of Alg. 5, the sketch QR of Alg. 4 and E = Q U_hat.
+//
+// Each operand x is split in shared memory into hi = rna_tf32(x) and
+// lo = x - hi (exact), and the accumulator takes A_hi B_hi + A_hi B_lo +
+// A_lo B_hi, so the product carries about 2^-21 relative error per term
+// (the FP32 result up to the dropped A_lo B_lo term).  The split is done
+// elementwise on the swizzled tiles by the four epilogue warps between the TMA
+// load and the MMA of every stage.
+//
+// The tall product uses gemm_tf32x3_kernel<false>; the Gram uses
+// gram_tf32x3_kernel below, which transposes its tiles in shared memory.
+//
+// One CTA computes a 128-row output tile over all Npad <= 288 output columns
+// (TMEM holds the 128 x Npad FP32 accumulator; the columns are issued as MMAs
+// of N = 256 and N = Npad - 256).  Warp 0: TMA; warp 1: TMEM and MMA issue;
+// warps 2-5: operand split, then the epilogue (tcgen05.ld, store).
+#include <cuda.h>
+
+#include "sne_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace sne {
+
+namespace gt {
+constexpr int BM = 128;        // output rows per CTA (MMA M)
+constexpr int BK = 32;         // FP32 elements per k-block (128 bytes)
+constexpr int kMaxN = 288;     // padded output columns per CTA
+constexpr int kThreads = 192;
+constexpr int kABytes = BM * BK * 4;  // 16 KB
+}  // namespace gt
+
+template <bool MN>
+__global__ void __launch_bounds__(gt::kThreads, 1) gemm_tf32x3_kernel(
+    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+    const __grid_constant__ CUtensorMap tmB2, int npad,
+    int nkb, int64_t rows_per_chunk, int64_t nrows_total, const float *__restrict__ w, int mrows,
+    int ncols, float *__restrict__ out, int64_t ldo, int64_t chunk_stride, Ctrl *ctrl) {
+  using namespace tc;
+  extern __shared__ __align__(1024) unsigned char g_smem_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(g_smem_raw) + 1023) & ~(uintptr_t)1023);
+  const int bbytes = npad * gt::BK * 4;                       // B region of a stage
+  const int stage_bytes = 2 * gt::kABytes + 2 * bbytes;        // hi + lo of A and B
+  const int stages = 2;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)stages * stage_bytes);
+  uint64_t *full = bars;            // [stages] TMA landed
+  uint64_t *split = full + stages;  // [stages] hi/lo ready for the MMA
+  uint64_t *empty = split + stages; // [stages] MMA done with the stage
+  uint64_t *done = empty + stages;  // accumulator complete
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+  int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // tile coordinates
+  const int64_t m0 = (int64_t)blockIdx.x * gt::BM;          // TALL: row i0; GRAM: column a0
+  const int64_t r0 = MN ? (int64_t)blockIdx.y * rows_per_chunk : 0;
+  int kblocks = nkb;
+  if (MN) {
+    const int64_t r1 = min64(nrows_total, r0 + rows_per_chunk);
+    kblocks = r1 > r0 ? (int)((r1 - r0 + gt::BK - 1) / gt::BK) : 0;
+  }
+  const int n1 = npad > 256 ? 256 : npad;  // first MMA column block
+  const int n2 = npad - n1;                // second (0, 32 ... 32)
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&split[s], 128);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  volatile int *abortv = abort_flag;
+
+  auto stage_ptr = [&](int s) { return smem + (size_t)s * stage_bytes; };
+  // stage layout: A_hi | A_lo | B_hi | B_lo
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      bool ok = true;
+      for (int kb = 0; kb < kblocks; ++kb) {
+        const int s = kb % stages;
+        if (!mbar_wait(&empty[s], (uint32_t)(((kb / stages) & 1) ^ 1), abortv, ctrl)) {
+          ok = false;
+          break;
+        }
+        unsigned char *st = stage_ptr(s);
+        mbar_expect_tx(&full[s], (uint32_t)(gt::kABytes + bbytes));
+        if (!MN) {
+          // K-major: A box {32 k, 128 rows}; B boxes {32 k, n1 rows} and {32 k, n2 rows}
+          tma_load_2d(st, &tmA, &full[s], kb * gt::BK, (int)m0);
+          tma_load_2d(st + 2 * gt::kABytes, &tmB, &full[s], kb * gt::BK, 0);
+          if (n2 > 0) tma_load_2d(st + 2 * gt::kABytes + n1 * 128, &tmB2, &full[s], kb * gt::BK, n1);
+        } else {
+          // MN-major: boxes {32 columns, 32 rows}; A: 4 boxes, B: npad/32 boxes, 4 KB apart
+          const int y = (int)(r0 + (int64_t)kb * gt::BK);
+          for (int m = 0; m < gt::BM / 32; ++m)
+            tma_load_2d(st + m * 4096, &tmA, &full[s], (int)m0 + 32 * m, y);
+          for (int t = 0; t < npad / 32; ++t)
+            tma_load_2d(st + 2 * gt::kABytes + t * 4096, &tmB, &full[s], 32 * t, y);
+        }
+        ++issued;
+      }
+      if (!ok) {
+        const int first = issued > stages ? issued - stages : 0;
+        for (int q = first; q < issued; ++q) {
+          const uint64_t t0 = gtimer();
+          while (!mbar_try_wait(&full[q % stages], (uint32_t)((q / stages) & 1)) &&
+                 gtimer() - t0 < kTimeoutNs) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // instruction descriptors: D F32, A/B TF32 (2), major bits, N, M = 128
+      const uint32_t major = MN ? ((1u << 15) | (1u << 16)) : 0u;
+      const uint32_t base = (1u << 4) | (2u << 7) | (2u << 10) | major | ((uint32_t)(gt::BM >> 4) << 24);
+      const uint32_t id1 = base | ((uint32_t)(n1 >> 3) << 17);
+      const uint32_t id2 = base | ((uint32_t)((n2 > 0 ? n2 : 16) >> 3) << 17);
+      bool ok = true;
+      for (int kb = 0; kb < kblocks; ++kb) {
+        const int s = kb % stages;
+        if (!mbar_wait(&split[s], (uint32_t)((kb / stages) & 1), abortv, ctrl)) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t ahi = smem_u32(stage_ptr(s));
+        const uint32_t alo = ahi + gt::kABytes;
+        const uint32_t bhi = ahi + 2 * gt::kABytes;
+        const uint32_t blo = bhi + bbytes;
+#pragma unroll
+        for (int kk = 0; kk < gt::BK / 8; ++kk) {
+          const uint32_t acc = (kb | kk) ? 1u : 0u;
+          uint64_t da_hi, da_lo, db1_hi, db1_lo, db2_hi, db2_lo;
+          if (!MN) {
+            da_hi = sdesc2(ahi + kk * 32, 16, 1024);
+            da_lo = sdesc2(alo + kk * 32, 16, 1024);
+            db1_hi = sdesc2(bhi + kk * 32, 16, 1024);
+            db1_lo = sdesc2(blo + kk * 32, 16, 1024);
+            db2_hi = sdesc2(bhi + n1 * 128 + kk * 32, 16, 1024);
+            db2_lo = sdesc2(blo + n1 * 128 + kk * 32, 16, 1024);
+          } else {
+            da_hi = sdesc2(ahi + kk * 1024, 4096, 1024);
+            da_lo = sdesc2(alo + kk * 1024, 4096, 1024);
+            db1_hi = sdesc2(bhi + kk * 1024, 4096, 1024);
+            db1_lo = sdesc2(blo + kk * 1024, 4096, 1024);
+            db2_hi = sdesc2(bhi + (n1 / 32) * 4096 + kk * 1024, 4096, 1024);
+            db2_lo = sdesc2(blo + (n1 / 32) * 4096 + kk * 1024, 4096, 1024);
+          }
+          mma_tf32(tmem, da_hi, db1_hi, id1, acc);
+          mma_tf32(tmem, da_hi, db1_lo, id1, 1u);
+          mma_tf32(tmem, da_lo, db1_hi, id1, 1u);
+          if (n2 > 0) {
+            mma_tf32(tmem + n1, da_hi, db2_hi, id2, acc);
+            mma_tf32(tmem + n1, da_hi, db2_lo, id2, 1u);
+            mma_tf32(tmem + n1, da_lo, db2_hi, id2, 1u);
+          }
+        }
+        mma_commit(&empty[s]);
+      }
+      (void)ok;
+      mma_commit(done);
+    }
+  } else {
+    // ---------------- warps 2..5: operand split, then epilogue
+    const int t = threadIdx.x - 64;  // 0..127
+    bool ok = true;
+    for (int kb = 0; kb < kblocks; ++kb) {
+      const int s = kb % stages;
+      if (!mbar_wait(&full[s], (uint32_t)((kb / stages) & 1), abortv, ctrl)) {
+        ok = false;
+        break;
+      }
+      unsigned char *st = stage_ptr(s);
+      float4 *ahi = reinterpret_cast<float4 *>(st);
+      float4 *alo = reinterpret_cast<float4 *>(st + gt::kABytes);
+      const int nA4 = gt::kABytes / 16;
+      for (int q = t; q < nA4; q += 128) {
+        float4 x = ahi[q];
+        if (MN && w) {
+          // row (K index) of this 16-byte chunk inside its 32 x 32 box
+          const int64_t i = r0 + (int64_t)kb * gt::BK + ((q % 256) / 8);
+          const float wi = i < nrows_total ? w[i] : 0.0f;
+          x.x *= wi;
+          x.y *= wi;
+          x.z *= wi;
+          x.w *= wi;
+        }
+        const float4 h = make_float4(tf32_rna(x.x), tf32_rna(x.y), tf32_rna(x.z), tf32_rna(x.w));
+        ahi[q] = h;
+        alo[q] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+      }
+      float4 *bhi = reinterpret_cast<float4 *>(st + 2 * gt::kABytes);
+      float4 *blo = reinterpret_cast<float4 *>(st + 2 * gt::kABytes + bbytes);
+      const int nB4 = bbytes / 16;
+      for (int q = t; q < nB4; q += 128) {
+        const float4 x = bhi[q];
+        const float4 h = make_float4(tf32_rna(x.x), tf32_rna(x.y), tf32_rna(x.z), tf32_rna(x.w));
+        bhi[q] = h;
+        blo[q] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(&split[s]);
+    }
+    // epilogue: the accumulator row of this thread
+    if (ok && kblocks > 0 && mbar_wait(done, 0, abortv, ctrl)) {
+      fence_after();
+      const int ew = warp & 3;
+      const int64_t r = m0 + 32 * ew + lane;  // output row (TALL) or column a (GRAM)
+      float *orow = out + (MN ? (int64_t)blockIdx.y * chunk_stride : 0) + r * ldo;
+      const bool rok = r < mrows;
+      for (int c = 0; c < npad; c += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * ew) << 16) + (uint32_t)c, v);
+        if (rok) {
+#pragma unroll
+          for (int q = 0; q < 32; ++q)
+            if (c + q < ncols) orow[c + q] = v[q];
+        }
+      }
+    } else if (MN && kblocks == 0) {
+      // empty chunk: its partial sums are zero
+      const int ew = warp & 3;
+      const int64_t r = m0 + 32 * ew + lane;
+      if (r < mrows) {
+        float *orow = out + (int64_t)blockIdx.y * chunk_stride + r * ldo;
+        for (int c = 0; c < ncols; ++c) orow[c] = 0.0f;
+      }
+    }
+  }
+  // release TMEM once every MMA has completed
+  if (warp == 1 && lane == 0) {
+    const uint64_t t0 = gtimer();
+    while (!mbar_try_wait(done, 0) && gtimer() - t0 < kTimeoutNs) {
+    }
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+// ---------------------------------------------------------------------------
+// Gram kernel: the row-major tall matrices arrive from TMA as 32 x 32 boxes in
+// which the contiguous direction is the output index (a or b) and the rows are
+// the reduction index i.  The split warps transpose every box into the
+// K-major 128-byte-swizzled layout (row = a or b, 32 consecutive i per
+// 128-byte row, 16-byte chunk c of row r stored at chunk c ^ (r % 8)) while
+// forming hi and lo, so the MMA reads K-major operands.
+// smem: raw[2] (TMA) | hi/lo (one set, released by the MMA of the k-block)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(gt::kThreads, 1) gram_tf32x3_kernel(
+    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int npad,
+    int64_t rows_per_chunk, int64_t nrows_total, const float *__restrict__ w, int mrows, int ncols,
+    float *__restrict__ out, int64_t ldo, int64_t chunk_stride, Ctrl *ctrl) {
+  using namespace tc;
+  extern __shared__ __align__(1024) unsigned char gg_smem_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(gg_smem_raw) + 1023) & ~(uintptr_t)1023);
+  const int bbytes = npad * gt::BK * 4;
+  const int raw_bytes = gt::kABytes + bbytes;
+  unsigned char *raw0 = smem;
+  unsigned char *hilo = smem + 2 * (size_t)raw_bytes;  // A_hi | A_lo | B_hi | B_lo
+  uint64_t *bars = reinterpret_cast<uint64_t *>(hilo + 2 * (size_t)raw_bytes);
+  uint64_t *full = bars;          // [2]
+  uint64_t *rawfree = full + 2;   // [2]
+  uint64_t *ready = rawfree + 2;  // hi/lo written
+  uint64_t *hfree = ready + 1;    // MMA done with hi/lo
+  uint64_t *done = hfree + 1;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+  int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * gt::BM;  // first output row a of the tile
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_chunk;
+  const int64_t r1 = min64(nrows_total, r0 + rows_per_chunk);
+  const int kblocks = r1 > r0 ? (int)((r1 - r0 + gt::BK - 1) / gt::BK) : 0;
+  const int n1 = npad > 256 ? 256 : npad;
+  const int n2 = npad - n1;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&rawfree[s], 128);
+    }
+    mbar_init(ready, 128);
+    mbar_init(hfree, 1);
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  volatile int *abortv = abort_flag;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int kb = 0; kb < kblocks; ++kb) {
+        const int s = kb & 1;
+        if (!mbar_wait(&rawfree[s], (uint32_t)(((kb >> 1) & 1) ^ 1), abortv, ctrl)) break;
+        unsigned char *rb = raw0 + (size_t)s * raw_bytes;
+        mbar_expect_tx(&full[s], (uint32_t)raw_bytes);
+        const int y = (int)(r0 + (int64_t)kb * gt::BK);
+        for (int m = 0; m < gt::BM / 32; ++m)
+          tma_load_2d(rb + m * 4096, &tmA, &full[s], (int)m0 + 32 * m, y);
+        for (int t = 0; t < npad / 32; ++t)
+          tma_load_2d(rb + gt::kABytes + t * 4096, &tmB, &full[s], 32 * t, y);
+        ++issued;
+      }
+      const int first = issued > 2 ? issued - 2 : 0;
+      for (int q = first; q < issued; ++q) {  // copies in flight land before exit
+        const uint64_t t0 = gtimer();
+        while (!mbar_try_wait(&full[q & 1], (uint32_t)((q >> 1) & 1)) && gtimer() - t0 < kTimeoutNs) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t base = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(gt::BM >> 4) << 24);
+      const uint32_t id1 = base | ((uint32_t)(n1 >> 3) << 17);
+      const uint32_t id2 = base | ((uint32_t)((n2 > 0 ? n2 : 16) >> 3) << 17);
+      const uint32_t ahi = smem_u32(hilo);
+      const uint32_t alo = ahi + gt::kABytes;
+      const uint32_t bhi = ahi + 2 * gt::kABytes;
+      const uint32_t blo = bhi + bbytes;
+      for (int kb = 0; kb < kblocks; ++kb) {
+        if (!mbar_wait(ready, (uint32_t)(kb & 1), abortv, ctrl)) break;
+        fence_after();
+#pragma unroll
+        for (int kk = 0; kk < gt::BK / 8; ++kk) {
+          const uint32_t acc = (kb | kk) ? 1u : 0u;
+          const uint64_t da_hi = sdesc2(ahi + kk * 32, 16, 1024);
+          const uint64_t da_lo = sdesc2(alo + kk * 32, 16, 1024);
+          mma_tf32(tmem, da_hi, sdesc2(bhi + kk * 32, 16, 1024), id1, acc);
+          mma_tf32(tmem, da_hi, sdesc2(blo + kk * 32, 16, 1024), id1, 1u);
+          mma_tf32(tmem, da_lo, sdesc2(bhi + kk * 32, 16, 1024), id1, 1u);
+          if (n2 > 0) {
+            mma_tf32(tmem + n1, da_hi, sdesc2(bhi + n1 * 128 + kk * 32, 16, 1024), id2, acc);
+            mma_tf32(tmem + n1, da_hi, sdesc2(blo + n1 * 128 + kk * 32, 16, 1024), id2, 1u);
+            mma_tf32(tmem + n1, da_lo, sdesc2(bhi + n1 * 128 + kk * 32, 16, 1024), id2, 1u);
+          }
+        }
+        mma_commit(hfree);
+      }
+      mma_commit(done);
+    }
+  } else {
+    const int t = threadIdx.x - 64;
+    bool ok = true;
+    float *hiA = reinterpret_cast<float *>(hilo);
+    float *loA = hiA + gt::kABytes / 4;
+    float *hiB = loA + gt::kABytes / 4;
+    float *loB = hiB + bbytes / 4;
+    for (int kb = 0; kb < kblocks; ++kb) {
+      const int s = kb & 1;
+      if (!mbar_wait(&full[s], (uint32_t)((kb >> 1) & 1), abortv, ctrl)) {
+        ok = false;
+        break;
+      }
+      if (kb > 0 && !mbar_wait(hfree, (uint32_t)((kb - 1) & 1), abortv, ctrl)) {
+        ok = false;
+        break;
+      }
+      const float4 *rb = reinterpret_cast<const float4 *>(raw0 + (size_t)s * raw_bytes);
+      const int64_t ibase = r0 + (int64_t)kb * gt::BK;
+      // A: 4 boxes; chunk q -> box m = q / 256, row i = (q % 256) / 8, physical chunk c = q % 8
+      for (int q = t; q < gt::kABytes / 16; q += 128) {
+        const int m = q >> 8, i = (q & 255) >> 3, c = q & 7;
+        const int a4 = c ^ (i & 7);
+        float4 x = rb[q];
+        if (w) {
+          const int64_t gi = ibase + i;
+          const float wi = gi < nrows_total ? w[gi] : 0.0f;
+          x.x *= wi;
+          x.y *= wi;
+          x.z *= wi;
+          x.w *= wi;
+        }
+        const float xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int A = 32 * m + 4 * a4 + j;  // K-major row
+          const int off = A * 32 + ((((i >> 2) ^ (A & 7))) << 2) + (i & 3);
+          const float h = tf32_rna(xv[j]);
+          hiA[off] = h;
+          loA[off] = xv[j] - h;
+        }
+      }
+      const float4 *rbB = rb + gt::kABytes / 16;
+      for (int q = t; q < bbytes / 16; q += 128) {
+        const int m = q >> 8, i = (q & 255) >> 3, c = q & 7;
+        const int a4 = c ^ (i & 7);
+        const float4 x = rbB[q];
+        const float xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int Bq = 32 * m + 4 * a4 + j;
+          const int off = Bq * 32 + ((((i >> 2) ^ (Bq & 7))) << 2) + (i & 3);
+          const float h = tf32_rna(xv[j]);
+          hiB[off] = h;
+          loB[off] = xv[j] - h;
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(&rawfree[s]);
+      mbar_arrive(ready);
+    }
+    const int ew = warp & 3;
+    const int64_t r = m0 + 32 * ew + lane;
+    const bool rok = r < mrows;
+    float *orow = out + (int64_t)blockIdx.y * chunk_stride + r * ldo;
+    if (ok && kblocks > 0 && mbar_wait(done, 0, abortv, ctrl)) {
+      fence_after();
+      for (int c = 0; c < npad; c += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * ew) << 16) + (uint32_t)c, v);
+        if (rok) {
+#pragma unroll
+          for (int q = 0; q < 32; ++q)
+            if (c + q < ncols) orow[c + q] = v[q];
+        }
+      }
+    } else if (kblocks == 0 && rok) {
+      for (int c = 0; c < ncols; ++c) orow[c] = 0.0f;
+    }
+  }
+  if (warp == 1 && lane == 0) {
+    const uint64_t t0 = gtimer();
+    while (!mbar_try_wait(done, 0) && gtimer() - t0 < kTimeoutNs) {
+    }
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn2)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn2 encode_fn2() {
+  static EncodeTiledFn2 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn2>(p);
+  }
+  return fn;
+}
+
+// 2-D FP32 tensor map over rows x cols (leading dimension ld floats),
+// box {bx columns, by rows}, 128-byte swizzle.
+static bool map_f32(CUtensorMap *tm, const float *ptr, int64_t rows, int64_t cols, int64_t ld, int bx,
+                    int by) {
+  EncodeTiledFn2 enc = encode_fn2();
+  if (!enc) return false;
+  if ((uintptr_t)ptr % 16 || (ld * 4) % 16) return false;
+  cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t gstride[1] = {(cuuint64_t)ld * 4};
+  cuuint32_t box[2] = {(cuuint32_t)bx, (cuuint32_t)by};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(ptr), gdim, gstride, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static size_t gemm_tc_smem(int npad) {
+  const size_t stage = 2 * (size_t)gt::kABytes + 2 * (size_t)npad * gt::BK * 4;
+  return 1024 + 2 * stage + 256;
+}
+
+bool tc_gemm_supported(int ncols) {
+  const int npad = (ncols + 31) / 32 * 32;
+  return npad <= gt::kMaxN && gemm_tc_smem(npad) <= 227 * 1024;
+}
+
+// C[i, :Kc] = A[i, :K] M  with Mt = M^T (Kc x K, row-major, ld K).
+cudaError_t launch_tall_gemm_tc(const float *A, int64_t lda, int64_t n, int K, const float *Mt, int Kc,
+                                float *C, int64_t ldc, Ctrl *ctrl, cudaStream_t st) {
+  if (n <= 0 || Kc <= 0) return cudaSuccess;
+  const int npad = (Kc + 31) / 32 * 32;
+  if (!tc_gemm_supported(Kc)) return cudaErrorInvalidValue;
+  CUtensorMap tmA, tmB, tmB2;
+  const int n1 = npad > 256 ? 256 : npad;
+  const int n2 = npad - n1;
+  if (!map_f32(&tmA, A, n, K, lda, gt::BK, gt::BM)) return cudaErrorInvalidValue;
+  // B = M^T: rows [0, n1) in one box, rows [n1, npad) in a second box of n2 rows
+  if (!map_f32(&tmB, Mt, Kc, K, K, gt::BK, n1)) return cudaErrorInvalidValue;
+  if (!map_f32(&tmB2, Mt, Kc, K, K, gt::BK, n2 > 0 ? n2 : 32)) return cudaErrorInvalidValue;
+  const size_t smem = gemm_tc_smem(npad);
+  auto kern = gemm_tf32x3_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int nkb = (K + gt::BK - 1) / gt::BK;
+  ProfScope ps_(K_TALL_TC, st);
+  kern<<<(unsigned)((n + gt::BM - 1) / gt::BM), gt::kThreads, smem, st>>>(
+      tmA, tmB, tmB2, npad, nkb, 0, n, nullptr, (int)min64(n, (int64_t)INT32_MAX), Kc, C, ldc, 0, ctrl);
+  return cudaGetLastError();
+}
+
+size_t gram_tc_partial_floats(int64_t n, int Ka, int Kb) {
+  const int mtiles = (Ka + gt::BM - 1) / gt::BM;
+  int chunks = (152 * 2 + mtiles - 1) / mtiles;
+  const int64_t maxc = (n + 4 * gt::BK - 1) / (4 * gt::BK);
+  if (chunks > maxc) chunks = (int)maxc;
+  if (chunks < 1) chunks = 1;
+  return (size_t)chunks * Ka * Kb;
+}
+
+// partial[c][a][b] = sum_{i in chunk c} w_i A[i, a] B[i, b]; C = sum_c partial (FP64).
+
+cudaError_t launch_gram_tc(const float *A, int64_t lda, int Ka, const float *B, int64_t ldb, int Kb,
+                           int64_t n, const float *w, float *partial, double *C, int ldc, Ctrl *ctrl,
+                           cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int npad = (Kb + 31) / 32 * 32;
+  if (!tc_gemm_supported(Kb)) return cudaErrorInvalidValue;
+  const int mtiles = (Ka + gt::BM - 1) / gt::BM;
+  int chunks = (152 * 2 + mtiles - 1) / mtiles;
+  const int64_t maxc = (n + 4 * gt::BK - 1) / (4 * gt::BK);
+  if (chunks > maxc) chunks = (int)maxc;
+  if (chunks < 1) chunks = 1;
+  // rows per chunk: a multiple of the 32-row k-block so chunks never overlap
+  int64_t rpc = (n + chunks - 1) / chunks;
+  rpc = (rpc + gt::BK - 1) / gt::BK * gt::BK;
+  CUtensorMap tmA, tmB;
+  if (!map_f32(&tmA, A, n, Ka, lda, 32, gt::BK)) return cudaErrorInvalidValue;
+  if (!map_f32(&tmB, B, n, Kb, ldb, 32, gt::BK)) return cudaErrorInvalidValue;
+  const size_t smem = gemm_tc_smem(npad);  // raw[2] + one hi/lo set: same total
+  auto kern = gram_tf32x3_kernel;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  {
+    ProfScope ps_(K_GRAM_TC, st);
+    kern<<<dim3((unsigned)mtiles, (unsigned)chunks), gt::kThreads, smem, st>>>(
+        tmA, tmB, npad, rpc, n, w, Ka, Kb, partial, Kb, (int64_t)Ka * Kb, ctrl);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_gram_reduce(partial, Ka, Kb, chunks, C, ldc, st);
+}
+
+}  // namespace sne

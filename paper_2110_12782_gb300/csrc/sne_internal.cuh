@@ -114,7 +114,24 @@ cudaError_t launch_validate(const sne_csr &g, Ctrl *ctrl, cudaStream_t st);
 size_t gram_partial_floats(int64_t n, int32_t Ka, int32_t Kb);
 cudaError_t launch_gram(const float *A, int64_t lda, int32_t Ka, const float *B, int64_t ldb,
                         int32_t Kb, int64_t n, const float *w, bool symmetric, float *partial,
-                        double *C, int32_t ldc, cudaStream_t st);
+                        double *C, int32_t ldc, cudaStream_t st, Ctrl *ctrl = nullptr);
+// gemm_tc.cu: FP32-accurate (3 x TF32) tensor-core versions, used when
+// tc_gemm_supported(columns) and the operands are 16-byte aligned.
+bool tc_gemm_supported(int ncols);
+bool tc_gemm_enabled();
+size_t gram_tc_partial_floats(int64_t n, int Ka, int Kb);
+cudaError_t launch_gram_tc(const float *A, int64_t lda, int Ka, const float *B, int64_t ldb, int Kb,
+                           int64_t n, const float *w, float *partial, double *C, int ldc, Ctrl *ctrl,
+                           cudaStream_t st);
+cudaError_t launch_gram_reduce(const float *partial, int Ka, int Kb, int chunks, double *C, int ldc,
+                               cudaStream_t st);
+cudaError_t launch_tall_gemm_tc(const float *A, int64_t lda, int64_t n, int K, const float *Mt, int Kc,
+                                float *C, int64_t ldc, Ctrl *ctrl, cudaStream_t st);
+// C = A M through the tensor-core path when possible (Mt: Ka x Kc scratch for M^T),
+// else the SIMT tall_gemm.
+cudaError_t launch_tall_gemm_auto(const float *A, int64_t lda, int64_t n, int32_t Ka, const float *M,
+                                  int32_t ldm, int32_t Kc, float *C, int64_t ldc, float *Mt,
+                                  Ctrl *ctrl, cudaStream_t st);
 // C[i, :] = rs_i * sum_a A[r(i), a] M[a, :]   (r(i) = ridx[i] or i; rs = 1 if NULL)
 cudaError_t launch_tall_gemm(const float *A, int64_t lda, const int32_t *ridx, int64_t n, int32_t Ka,
                              const float *M, int32_t ldm, int32_t Kc, const float *rs, float *C,
