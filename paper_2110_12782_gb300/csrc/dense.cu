@@ -129,14 +129,14 @@ __global__ void __launch_bounds__(kGThreads) gram_partial_kernel(
 }
 
 __global__ void gram_reduce_kernel(const float *__restrict__ partial, int32_t Ka, int32_t Kb,
-                                   int32_t chunks, int symmetric, double *__restrict__ C,
+                                   int32_t chunks, int sym_tile, double *__restrict__ C,
                                    int32_t ldc) {
   const int64_t total = (int64_t)Ka * Kb;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     int a = (int)(e / Kb), b = (int)(e % Kb);
     int sa = a, sb = b;
-    if (symmetric && (a / kGT) > (b / kGT)) {
+    if (sym_tile > 0 && (a / sym_tile) > (b / sym_tile)) {
       sa = b;
       sb = a;
     }
@@ -146,12 +146,12 @@ __global__ void gram_reduce_kernel(const float *__restrict__ partial, int32_t Ka
   }
 }
 
-cudaError_t launch_gram_reduce(const float *partial, int Ka, int Kb, int chunks, double *C, int ldc,
-                               cudaStream_t st) {
+cudaError_t launch_gram_reduce(const float *partial, int Ka, int Kb, int chunks, int sym_tile,
+                               double *C, int ldc, cudaStream_t st) {
   const int64_t total = (int64_t)Ka * Kb;
   ProfScope ps_(K_GRAM_TC, st);
   gram_reduce_kernel<<<(unsigned)min64(1024, (total + 255) / 256), 256, 0, st>>>(
-      partial, Ka, Kb, chunks, 0, C, ldc);
+      partial, Ka, Kb, chunks, sym_tile, C, ldc);
   return cudaGetLastError();
 }
 
@@ -161,7 +161,8 @@ cudaError_t launch_gram(const float *A, int64_t lda, int32_t Ka, const float *B,
   if (symmetric && (A != B || Ka != Kb || lda != ldb)) return cudaErrorInvalidValue;
   if (tc_gemm_enabled() && tc_gemm_supported(Kb) && lda % 4 == 0 && ldb % 4 == 0 &&
       (uintptr_t)A % 16 == 0 && (uintptr_t)B % 16 == 0 && n >= 256)
-    return launch_gram_tc(A, lda, Ka, B, ldb, Kb, n, w, partial, C, ldc, ctrl, st);
+    return launch_gram_tc(A, lda, Ka, B, ldb, Kb, n, w, symmetric && A == B && Ka == Kb, partial, C,
+                          ldc, ctrl, st);
   int tiles, chunks;
   gram_grid(n, Ka, Kb, symmetric, &tiles, &chunks);
   const int64_t rpc = (n + chunks - 1) / chunks;
@@ -172,7 +173,7 @@ cudaError_t launch_gram(const float *A, int64_t lda, int32_t Ka, const float *B,
   if (e != cudaSuccess) return e;
   const int64_t total = (int64_t)Ka * Kb;
   gram_reduce_kernel<<<(unsigned)min64(1024, (total + 255) / 256), 256, 0, st>>>(
-      partial, Ka, Kb, chunks, symmetric ? 1 : 0, C, ldc);
+      partial, Ka, Kb, chunks, symmetric ? kGT : 0, C, ldc);
   return cudaGetLastError();
 }
 

@@ -273,18 +273,22 @@ __global__ void __launch_bounds__(gt::kThreads, 1) gemm_tf32x3_kernel(
 // smem: raw[2] (TMA) | hi/lo (one set, released by the MMA of the k-block)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(gt::kThreads, 1) gram_tf32x3_kernel(
-    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int npad,
+    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int npad_max,
     int64_t rows_per_chunk, int64_t nrows_total, const float *__restrict__ w, int mrows, int ncols,
-    float *__restrict__ out, int64_t ldo, int64_t chunk_stride, Ctrl *ctrl) {
+    float *__restrict__ out, int64_t ldo, int64_t chunk_stride, int symmetric, Ctrl *ctrl) {
   using namespace tc;
   extern __shared__ __align__(1024) unsigned char gg_smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(gg_smem_raw) + 1023) & ~(uintptr_t)1023);
+  // symmetric Gram: tile a0 needs only the columns b >= a0 (the reduce mirrors)
+  const int b0 = symmetric ? (int)((int64_t)blockIdx.x * gt::BM) : 0;
+  const int npad = ((ncols - b0) + 31) / 32 * 32;
   const int bbytes = npad * gt::BK * 4;
   const int raw_bytes = gt::kABytes + bbytes;
+  const int raw_max = gt::kABytes + npad_max * gt::BK * 4;
   unsigned char *raw0 = smem;
-  unsigned char *hilo = smem + 2 * (size_t)raw_bytes;  // A_hi | A_lo | B_hi | B_lo
-  uint64_t *bars = reinterpret_cast<uint64_t *>(hilo + 2 * (size_t)raw_bytes);
+  unsigned char *hilo = smem + 2 * (size_t)raw_max;  // A_hi | A_lo | B_hi | B_lo
+  uint64_t *bars = reinterpret_cast<uint64_t *>(hilo + 2 * (size_t)raw_max);
   uint64_t *full = bars;          // [2]
   uint64_t *rawfree = full + 2;   // [2]
   uint64_t *ready = rawfree + 2;  // hi/lo written
@@ -331,13 +335,13 @@ __global__ void __launch_bounds__(gt::kThreads, 1) gram_tf32x3_kernel(
       for (int kb = 0; kb < kblocks; ++kb) {
         const int s = kb & 1;
         if (!mbar_wait(&rawfree[s], (uint32_t)(((kb >> 1) & 1) ^ 1), abortv, ctrl)) break;
-        unsigned char *rb = raw0 + (size_t)s * raw_bytes;
+        unsigned char *rb = raw0 + (size_t)s * raw_max;
         mbar_expect_tx(&full[s], (uint32_t)raw_bytes);
         const int y = (int)(r0 + (int64_t)kb * gt::BK);
         for (int m = 0; m < gt::BM / 32; ++m)
           tma_load_2d(rb + m * 4096, &tmA, &full[s], (int)m0 + 32 * m, y);
         for (int t = 0; t < npad / 32; ++t)
-          tma_load_2d(rb + gt::kABytes + t * 4096, &tmB, &full[s], 32 * t, y);
+          tma_load_2d(rb + gt::kABytes + t * 4096, &tmB, &full[s], b0 + 32 * t, y);
         ++issued;
       }
       const int first = issued > 2 ? issued - 2 : 0;
@@ -394,7 +398,7 @@ __global__ void __launch_bounds__(gt::kThreads, 1) gram_tf32x3_kernel(
         ok = false;
         break;
       }
-      const float4 *rb = reinterpret_cast<const float4 *>(raw0 + (size_t)s * raw_bytes);
+      const float4 *rb = reinterpret_cast<const float4 *>(raw0 + (size_t)s * raw_max);
       const int64_t ibase = r0 + (int64_t)kb * gt::BK;
       // A: 4 boxes; chunk q -> box m = q / 256, row i = (q % 256) / 8, physical chunk c = q % 8
       for (int q = t; q < gt::kABytes / 16; q += 128) {
@@ -441,7 +445,7 @@ __global__ void __launch_bounds__(gt::kThreads, 1) gram_tf32x3_kernel(
     const int ew = warp & 3;
     const int64_t r = m0 + 32 * ew + lane;
     const bool rok = r < mrows;
-    float *orow = out + (int64_t)blockIdx.y * chunk_stride + r * ldo;
+    float *orow = out + (int64_t)blockIdx.y * chunk_stride + r * ldo + b0;
     if (ok && kblocks > 0 && mbar_wait(done, 0, abortv, ctrl)) {
       fence_after();
       for (int c = 0; c < npad; c += 32) {
@@ -450,11 +454,11 @@ __global__ void __launch_bounds__(gt::kThreads, 1) gram_tf32x3_kernel(
         if (rok) {
 #pragma unroll
           for (int q = 0; q < 32; ++q)
-            if (c + q < ncols) orow[c + q] = v[q];
+            if (b0 + c + q < ncols) orow[c + q] = v[q];
         }
       }
     } else if (kblocks == 0 && rok) {
-      for (int c = 0; c < ncols; ++c) orow[c] = 0.0f;
+      for (int c = 0; b0 + c < ncols; ++c) orow[c] = 0.0f;
     }
   }
   if (warp == 1 && lane == 0) {
@@ -552,8 +556,8 @@ size_t gram_tc_partial_floats(int64_t n, int Ka, int Kb) {
 // partial[c][a][b] = sum_{i in chunk c} w_i A[i, a] B[i, b]; C = sum_c partial (FP64).
 
 cudaError_t launch_gram_tc(const float *A, int64_t lda, int Ka, const float *B, int64_t ldb, int Kb,
-                           int64_t n, const float *w, float *partial, double *C, int ldc, Ctrl *ctrl,
-                           cudaStream_t st) {
+                           int64_t n, const float *w, bool symmetric, float *partial, double *C,
+                           int ldc, Ctrl *ctrl, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int npad = (Kb + 31) / 32 * 32;
   if (!tc_gemm_supported(Kb)) return cudaErrorInvalidValue;
@@ -575,11 +579,11 @@ cudaError_t launch_gram_tc(const float *A, int64_t lda, int Ka, const float *B, 
   {
     ProfScope ps_(K_GRAM_TC, st);
     kern<<<dim3((unsigned)mtiles, (unsigned)chunks), gt::kThreads, smem, st>>>(
-        tmA, tmB, npad, rpc, n, w, Ka, Kb, partial, Kb, (int64_t)Ka * Kb, ctrl);
+        tmA, tmB, npad, rpc, n, w, Ka, Kb, partial, Kb, (int64_t)Ka * Kb, symmetric ? 1 : 0, ctrl);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return launch_gram_reduce(partial, Ka, Kb, chunks, C, ldc, st);
+  return launch_gram_reduce(partial, Ka, Kb, chunks, symmetric ? gt::BM : 0, C, ldc, st);
 }
 
 }  // namespace sne

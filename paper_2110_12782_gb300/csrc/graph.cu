@@ -170,6 +170,7 @@ __global__ void __launch_bounds__(256) spmm_scalar_kernel(
 cudaError_t launch_spmm(const sne_csr &g, const float *dpow, const float *B, int64_t ldb,
                         int32_t ncols, float *Y, int64_t ldy, cudaStream_t st) {
   if (g.n <= 0 || ncols <= 0) return cudaSuccess;
+
   ProfScope ps_(K_SPMM, st);
   const unsigned blocks = (unsigned)((g.n + 7) / 8);
   const bool vec = (ncols % 4 == 0) && (ldb % 4 == 0) && (ldy % 4 == 0) &&

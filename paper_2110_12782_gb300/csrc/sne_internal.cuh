@@ -121,10 +121,12 @@ bool tc_gemm_supported(int ncols);
 bool tc_gemm_enabled();
 size_t gram_tc_partial_floats(int64_t n, int Ka, int Kb);
 cudaError_t launch_gram_tc(const float *A, int64_t lda, int Ka, const float *B, int64_t ldb, int Kb,
-                           int64_t n, const float *w, float *partial, double *C, int ldc, Ctrl *ctrl,
-                           cudaStream_t st);
-cudaError_t launch_gram_reduce(const float *partial, int Ka, int Kb, int chunks, double *C, int ldc,
-                               cudaStream_t st);
+                           int64_t n, const float *w, bool symmetric, float *partial, double *C,
+                           int ldc, Ctrl *ctrl, cudaStream_t st);
+// C = sum over chunks of partial[c] (FP64); with sym_tile > 0 the entries
+// (a, b) with a / sym_tile > b / sym_tile are read from (b, a).
+cudaError_t launch_gram_reduce(const float *partial, int Ka, int Kb, int chunks, int sym_tile,
+                               double *C, int ldc, cudaStream_t st);
 cudaError_t launch_tall_gemm_tc(const float *A, int64_t lda, int64_t n, int K, const float *Mt, int Kc,
                                 float *C, int64_t ldc, Ctrl *ctrl, cudaStream_t st);
 // C = A M through the tensor-core path when possible (Mt: Ka x Kc scratch for M^T),
