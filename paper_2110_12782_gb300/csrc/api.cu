@@ -155,8 +155,8 @@ size_t carve(const Dims &D, int mode, void *base, Bufs *b) {
       x.BhO = bp.take<uint16_t>((size_t)D.nO * D.kpad);
       x.rowfA = bp.take<float>(n);
       x.rowfO = bp.take<float>(vmax);
-      x.colfS = bp.take<float>(D.nS);
-      x.colfO = bp.take<float>(D.nO);
+      x.colfS = bp.take<float>(D.nS + 256);
+      x.colfO = bp.take<float>(D.nO + 256);
     }
   }
   if (host_mode) {
@@ -369,13 +369,17 @@ int run_sketch(const sne_csr &g, const sne_params &p, const Dims &D, const Bufs 
                                sv, p.f, b.Yo, l, st));
   } else {
     const bool fp16 = p.precision == SNE_FP16;
-    CK(launch_to_half_rows(fp16, U, k, nullptr, nullptr, D.n, k, D.kpad, b.rsc, b.Ah, b.rowfA, st));
-    CK(launch_to_half_rows(fp16, U, k, b.uniqO, &b.ctrl->v_o, vmax, k, D.kpad, b.rsc, b.AhO,
-                           b.rowfO, st));
-    CK(launch_to_half_rows(fp16, b.RpS, k, nullptr, nullptr, D.nS, k, D.kpad, nullptr, b.BhS,
-                           b.colfS, st));
-    CK(launch_to_half_rows(fp16, b.RpO, k, nullptr, nullptr, D.nO, k, D.kpad, nullptr, b.BhO,
-                           b.colfO, st));
+    CK(launch_to_half_rows(fp16, U, k, nullptr, nullptr, D.n, k, D.kpad, b.rsc, nullptr, b.Ah,
+                           b.rowfA, st));
+    CK(launch_to_half_rows(fp16, U, k, b.uniqO, &b.ctrl->v_o, vmax, k, D.kpad, b.rsc, nullptr,
+                           b.AhO, b.rowfO, st));
+    // column factors carry the sparse signs; zero padding up to the 256-column tile
+    CK(cudaMemsetAsync(b.colfS, 0, (size_t)(D.nS + 256) * sizeof(float), st));
+    CK(cudaMemsetAsync(b.colfO, 0, (size_t)(D.nO + 256) * sizeof(float), st));
+    CK(launch_to_half_rows(fp16, b.RpS, k, nullptr, nullptr, D.nS, k, D.kpad, nullptr, b.signS,
+                           b.BhS, b.colfS, st));
+    CK(launch_to_half_rows(fp16, b.RpO, k, nullptr, nullptr, D.nO, k, D.kpad, nullptr, b.signO,
+                           b.BhO, b.colfO, st));
     CK(launch_fused_sketch_tc(fp16, b.Ah, D.n, nullptr, D.kpad, b.BhS, D.nS, h, z, b.rowfA, b.colfS,
                               b.signS, sv, p.f, Y, h, b.ctrl, st));
     CK(launch_fused_sketch_tc(fp16, b.AhO, vmax, &b.ctrl->v_o, D.kpad, b.BhO, D.nO, l, z, b.rowfO,

@@ -31,12 +31,11 @@ namespace sne {
 // PTX helpers: tc_ptx.cuh
 
 template <int F, int Z>
-__global__ void __launch_bounds__(tc::kThreads, 1) fused_sketch_tc_kernel(
+__global__ void __launch_bounds__(tc::kThreadsSketch, 1) fused_sketch_tc_kernel(
     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
     int64_t nrows_max, const int32_t *__restrict__ nrows_dev, int kblocks, int stages,
     int ncols_eval, int cols_out, const float *__restrict__ rowf, const float *__restrict__ colf,
-    const int8_t *__restrict__ sign, float sv, uint32_t idesc, float *__restrict__ out, int64_t ldo,
-    Ctrl *ctrl) {
+    float out_scale, uint32_t idesc, float *__restrict__ out, int64_t ldo, Ctrl *ctrl) {
   using namespace tc;
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>(
@@ -67,7 +66,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) fused_sketch_tc_kernel(
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 128);
+      mbar_init(&tempty[b], 256);
     }
     mbar_init(done, 1);
     *abort_flag = 0;
@@ -158,38 +157,57 @@ __global__ void __launch_bounds__(tc::kThreads, 1) fused_sketch_tc_kernel(
       }
     }
   } else {
-    // ---------------- epilogue warps 2..5
-    const int ew = warp & 3;  // TMEM lane quarter this warp may access
+    // ---------------- epilogue warps 2..9: warp w reads TMEM lane quarter
+    // w % 4 (rows 32(w%4) .. +32) and half (w - 2) / 4 of the 256 columns
+    const int ew = warp & 3;
+    const int half = (warp - 2) >> 2;
     const int64_t row = row0 + 32 * ew + lane;
     const bool row_ok = row < nrows;
     const float rf = row_ok ? rowf[row] : 0.0f;
-    constexpr int G = 32 / Z;  // output columns per 32-column chunk
+    constexpr int G = 32 / Z;        // output columns per 32-column chunk
     for (int j = 0; j < ntiles; ++j) {
       const int buf = j & 1;
       const uint32_t use = (uint32_t)(j >> 1);
       if (!mbar_wait(&tfull[buf], use & 1u, abortv, ctrl)) break;
       fence_after();
+      const int ebase = j * BN + half * 128;
 #pragma unroll 1
-      for (int c = 0; c < BN / 32; ++c) {
+      for (int c = 0; c < 4; ++c) {
         float v[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * ew) << 16) + (uint32_t)(buf * BN + c * 32), v);
-        const int e0 = j * BN + c * 32;
-        if (e0 >= ncols_eval) continue;
+        tmem_ld32(tmem + ((uint32_t)(32 * ew) << 16) + (uint32_t)(buf * BN + half * 128 + c * 32), v);
+        const float4 *cf4 = reinterpret_cast<const float4 *>(colf + ebase + c * 32);
         float acc[G];
 #pragma unroll
         for (int g = 0; g < G; ++g) acc[g] = 0.0f;
 #pragma unroll
-        for (int t = 0; t < 32; ++t) {
-          const int e = e0 + t;
-          const float cf = e < ncols_eval ? __ldg(colf + e) : 0.0f;
-          const float sg = e < ncols_eval ? (float)__ldg(sign + e) : 0.0f;
-          acc[t / Z] = fmaf(sg, tc::fx<F>(rf * cf * v[t]), acc[t / Z]);
-        }
-        if (row_ok) {
-          const int oc0 = e0 / Z;
+        for (int q = 0; q < 8; ++q) {
+          const float4 cf = __ldg(cf4 + q);
+          const float cfv[4] = {cf.x, cf.y, cf.z, cf.w};
 #pragma unroll
-          for (int g = 0; g < G; ++g)
-            if (oc0 + g < cols_out) out[row * ldo + oc0 + g] = sv * acc[g];
+          for (int u = 0; u < 4; ++u) {
+            const int t = 4 * q + u;
+            const float x = rf * fabsf(cfv[u]) * v[t];
+            const float l = tc::fx2<F>(x);
+            // trunc_log is >= 0, so the sign of cf can be copied onto it
+            if (F == SNE_F_TRUNC_LOG) acc[t / Z] += copysignf(l, cfv[u]);
+            else acc[t / Z] += (cfv[u] < 0.0f) ? -l : l;
+          }
+        }
+        // G consecutive outputs of this row: columns (ebase + 32 c) / Z ..
+        const int oc0 = (ebase + 32 * c) / Z;
+        if (row_ok && oc0 < cols_out) {
+          float *o = out + row * ldo + oc0;
+          if (G % 4 == 0 && oc0 + G <= cols_out && ((reinterpret_cast<uintptr_t>(o) & 15) == 0)) {
+#pragma unroll
+            for (int g = 0; g < G; g += 4)
+              *reinterpret_cast<float4 *>(o + g) =
+                  make_float4(out_scale * acc[g], out_scale * acc[g + 1], out_scale * acc[g + 2],
+                              out_scale * acc[g + 3]);
+          } else {
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+              if (oc0 + g < cols_out) o[g] = out_scale * acc[g];
+          }
         }
       }
       fence_before();
@@ -223,7 +241,8 @@ template <typename H>
 __global__ void __launch_bounds__(256) to_half_rows_kernel(
     const float *__restrict__ src, int64_t lds, const int32_t *__restrict__ ridx,
     const int32_t *__restrict__ nrows_dev, int64_t nrows_max, int k, int kpad,
-    const float *__restrict__ extra, H *__restrict__ dst, float *__restrict__ scale) {
+    const float *__restrict__ extra, const int8_t *__restrict__ sgn, H *__restrict__ dst,
+    float *__restrict__ scale) {
   const int lane = threadIdx.x & 31;
   const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   if (r >= nrows_max) return;
@@ -241,21 +260,25 @@ __global__ void __launch_bounds__(256) to_half_rows_kernel(
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   const float inv = m > 0.0f ? 1.0f / m : 0.0f;
   for (int c = lane; c < kpad; c += 32) d[c] = to_h<H>(c < k ? x[c] * inv : 0.0f);
-  if (lane == 0) scale[r] = m * (extra ? extra[s] : 1.0f);
+  if (lane == 0) {
+    const float sc = m * (extra ? extra[s] : 1.0f);
+    scale[r] = (sgn && sgn[r] < 0) ? -sc : sc;
+  }
 }
 
 cudaError_t launch_to_half_rows(bool fp16, const float *src, int64_t lds, const int32_t *ridx,
                                 const int32_t *nrows_dev, int64_t nrows_max, int k, int kpad,
-                                const float *extra, void *dst, float *scale, cudaStream_t st) {
+                                const float *extra, const int8_t *sgn, void *dst, float *scale,
+                                cudaStream_t st) {
   if (nrows_max <= 0) return cudaSuccess;
   const unsigned blocks = (unsigned)((nrows_max + 7) / 8);
   ProfScope ps_(K_MISC, st);
   if (fp16)
     to_half_rows_kernel<__half><<<blocks, 256, 0, st>>>(src, lds, ridx, nrows_dev, nrows_max, k, kpad,
-                                                        extra, static_cast<__half *>(dst), scale);
+                                                        extra, sgn, static_cast<__half *>(dst), scale);
   else
     to_half_rows_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(
-        src, lds, ridx, nrows_dev, nrows_max, k, kpad, extra, static_cast<__nv_bfloat16 *>(dst),
+        src, lds, ridx, nrows_dev, nrows_max, k, kpad, extra, sgn, static_cast<__nv_bfloat16 *>(dst),
         scale);
   return cudaGetLastError();
 }
@@ -327,6 +350,9 @@ cudaError_t launch_fused_sketch_tc(bool fp16, const void *Ahat, int64_t nrows_ma
                          ((uint32_t)(tc::BM >> 4) << 24);
   const unsigned grid = (unsigned)((nrows_max + tc::BM - 1) / tc::BM);
   const int kblocks = kpad / tc::BK;
+  // f = trunc_log: the kernel sums signed log2 values; ln 2 joins sv here
+  const float out_scale = (f == SNE_F_TRUNC_LOG) ? sv * 0.69314718055994530942f : sv;
+  (void)sign;
 #define SNE_TC_LAUNCH(FV, ZV)                                                                     \
   do {                                                                                            \
     auto kern = fused_sketch_tc_kernel<FV, ZV>;                                                   \
@@ -334,9 +360,9 @@ cudaError_t launch_fused_sketch_tc(bool fp16, const void *Ahat, int64_t nrows_ma
                                          (int)smem);                                              \
     if (e != cudaSuccess) return e;                                                               \
     ProfScope ps_(K_FUSED_TC, st);                                                                \
-    kern<<<grid, tc::kThreads, smem, st>>>(tmA, tmB, nrows_max, nrows_dev, kblocks, stages,       \
-                                           ncols_eval, cols_out, rowf, colf, sign, sv, idesc, out, \
-                                           ldo, ctrl);                                            \
+    kern<<<grid, tc::kThreadsSketch, smem, st>>>(tmA, tmB, nrows_max, nrows_dev, kblocks, stages, \
+                                                 ncols_eval, cols_out, rowf, colf, out_scale,     \
+                                                 idesc, out, ldo, ctrl);                          \
   } while (0)
 #define SNE_TC_Z(FV)             \
   switch (z) {                   \

@@ -187,10 +187,13 @@ cudaError_t launch_fused_sketch_f32(const float *A, int64_t lda, const int32_t *
                                     int64_t ldo, cudaStream_t st);
 // sketch_tc.cu: mixed-precision fused sketch (BF16 or FP16 operands, FP32
 // accumulation on tcgen05).  Operands are row-normalized half copies made by
-// launch_to_half_rows; kpad is k rounded up to a multiple of 64.
+// launch_to_half_rows; kpad is k rounded up to a multiple of 64; colf holds
+// sign_e * colf_e and is readable (zero padded) up to a multiple of 256.
+// scale[r] = max|src row| * extra[s(r)], negated where sgn[r] < 0 (sgn may be NULL).
 cudaError_t launch_to_half_rows(bool fp16, const float *src, int64_t lds, const int32_t *ridx,
                                 const int32_t *nrows_dev, int64_t nrows_max, int k, int kpad,
-                                const float *extra, void *dst, float *scale, cudaStream_t st);
+                                const float *extra, const int8_t *sgn, void *dst, float *scale,
+                                cudaStream_t st);
 cudaError_t launch_fused_sketch_tc(bool fp16, const void *Ahat, int64_t nrows_max,
                                    const int32_t *nrows_dev, int kpad, const void *Bhat,
                                    int ncols_eval, int cols_out, int z, const float *rowf,

@@ -15,6 +15,7 @@ constexpr int BK = 64;                        // elements per k-block (128 bytes
 constexpr int kABlockBytes = BM * BK * 2;     // 16 KB
 constexpr int kBStageBytes = BN * BK * 2;     // 32 KB
 constexpr int kThreads = 192;
+constexpr int kThreadsSketch = 320;  // TMA warp, MMA warp, 8 epilogue warps
 constexpr unsigned long long kTimeoutNs = 2000000000ull;
 
 // Shared-memory descriptor with explicit byte offsets (128-byte swizzle).
@@ -142,6 +143,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// f in log2 units (the caller multiplies the sums by ln 2)
+template <int F>
+__device__ __forceinline__ float fx2(float x) {
+  if (F == SNE_F_TRUNC_LOG) return x > 1.0f ? __log2f(x) : 0.0f;
+  return x;
 }
 
 template <int F>
