@@ -189,6 +189,48 @@ int sne_stats_read(const void *workspace, sne_stats *out, sne_stream_t stream);
 int sne_freigs_static(const sne_csr *g, const sne_params *p, float *U, double *lambda,
                       int32_t *status, sne_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Dense building blocks of Alg. 5 and Alg. 4, callable one by one.  Same
+ * conventions as above: device pointers, row-major, stream-ordered; a
+ * workspace of the stated size (256-byte aligned) whose first bytes hold the
+ * device status word (read with sne_status).
+ * ------------------------------------------------------------------------ */
+
+/* Gram matrix of tall row-major FP32 matrices:
+ *   C (ka x kb, FP64, row stride ldc) = sum_{i<n} w_i A[i, :]^T B[i, :]
+ * A: n x ka (row stride lda), B: n x kb (ldb), w: n FP32 or NULL (all ones).
+ * This is B = Y^T Y of eigSVD (Alg. 5), the Cholesky-QR Gram of Alg. 4's
+ * orth(Y), S = Q^T (X Q) of the Rayleigh-Ritz step and U_k^T D^(-1+2 alpha)
+ * U_k of Eq. 11.  accurate = 0: products FP32-accurate (3 x TF32 on the
+ * tensor cores, or FP32 FMA), summed in FP32 over row blocks and in FP64
+ * across blocks (relative error ~1e-6).  accurate = 1: FP32 FMA over groups of
+ * 8 rows, the group sums added exactly into double-float pairs (relative
+ * error ~1e-9), the form Eq. 11's core uses.  A == B with ka == kb and lda ==
+ * ldb computes only the upper block triangle and mirrors it.
+ * Errors: SNE_ERR_ARG (bad sizes or NULL), SNE_ERR_WORKSPACE. */
+int sne_gram_workspace_bytes(int64_t n, int32_t ka, int32_t kb, size_t *bytes);
+int sne_gram(int64_t n, int32_t ka, int32_t kb, const float *A, int64_t lda, const float *B,
+             int64_t ldb, const float *w, double *C, int32_t ldc, int32_t accurate,
+             void *workspace, size_t ws_bytes, sne_stream_t stream);
+
+/* Tall-times-small product C (n x kc, row stride ldc) = A (n x ka, lda) M
+ * (ka x kc, ldm), all FP32, FP32-accurate: Q = Y V Delta^-1/2 of eigSVD,
+ * Q = Y R^-1 of Cholesky QR, U_k = Q U_hat of Alg. 5 and U_d = Q U_hat(:, 1:d)
+ * of Alg. 4.  Errors as sne_gram. */
+int sne_tall_gemm_workspace_bytes(int32_t ka, int32_t kc, size_t *bytes);
+int sne_tall_gemm(int64_t n, int32_t ka, int32_t kc, const float *A, int64_t lda, const float *M,
+                  int32_t ldm, float *C, int64_t ldc, void *workspace, size_t ws_bytes,
+                  sne_stream_t stream);
+
+/* Eigendecomposition of a symmetric FP64 matrix S (n x n, lds; n <= 1024) as
+ * in the Rayleigh-Ritz step of Alg. 5: lambda (n) ordered by |lambda|
+ * descending, V (n x n, ldv) with column j the eigenvector of lambda[j].  S is
+ * not modified.  A failure to converge sets SNE_ERR_NUMERIC in the status
+ * word.  Errors as sne_gram. */
+int sne_sym_eig_workspace_bytes(int32_t n, size_t *bytes);
+int sne_sym_eig(int32_t n, const double *S, int32_t lds, double *lambda, double *V, int32_t ldv,
+                void *workspace, size_t ws_bytes, sne_stream_t stream);
+
 /* Kernel accounting (host only).  sne_kernel_launches returns the number of
  * kernels this library has enqueued since it was loaded.  Between
  * sne_profile_start and sne_profile_stop every launcher brackets its kernels

@@ -76,7 +76,7 @@ struct Bump {
 
 struct Bufs {
   Ctrl *ctrl;
-  float *deg, *dpow, *rsc, *acoef, *wgt;
+  float *deg, *dpow, *rsc, *rsc_lo, *wgt;
   float *A, *B, *C;  // tall buffers
   float *partial;
   double *m64[5];
@@ -108,7 +108,7 @@ size_t carve(const Dims &D, int mode, void *base, Bufs *b) {
   x.deg = bp.take<float>(n);
   x.dpow = bp.take<float>(n);
   x.rsc = bp.take<float>(n);
-  x.acoef = bp.take<float>(n);
+  x.rsc_lo = bp.take<float>(n);
   x.wgt = bp.take<float>(n);
   x.A = bp.take<float>((size_t)n * D.Wab);
   x.B = bp.take<float>((size_t)n * D.Wab);
@@ -192,13 +192,19 @@ int check_ws(void *ws, size_t bytes, size_t need) {
 // Small kernels local to the orchestration
 // --------------------------------------------------------------------------
 // out_i = mult * vol * deg_i^beta  (0 for isolated vertices)
-__global__ void rowscale_kernel(const float *deg, int64_t n, float beta, const double *vol,
-                                double mult, float *out) {
-  const float s = (float)(mult * (vol ? *vol : 1.0));
+// out_i + out_lo_i = mult * vol * deg_i^beta evaluated in FP64 and split into
+// two FP32 parts: one rounding shared by all rows (of the scalar, or of the
+// power of a common degree) would shift every entry of L'R' alike
+__global__ void rowscale_kernel(const float *deg, int64_t n, double beta, const double *vol,
+                                double mult, float *out, float *out_lo) {
+  const double s = mult * (vol ? *vol : 1.0);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const float d = deg[i];
-    out[i] = d > 0.f ? s * powf(d, beta) : 0.f;
+    const double x = d > 0.f ? s * pow((double)d, beta) : 0.0;
+    const float hi = (float)x;
+    out[i] = hi;
+    if (out_lo) out_lo[i] = (float)(x - (double)hi);
   }
 }
 
@@ -231,25 +237,30 @@ __global__ void select_cols_kernel(const double *V, int rows, int ldv, const int
   }
 }
 
-// K = G diag(lam) (FP32, k x k), G given in FP64
-__global__ void scale_cols_d2f_kernel(const double *G, int k, const double *lam, float *K) {
+// K = G diag(lam) (FP64, k x k)
+__global__ void scale_cols_kernel(const double *G, int k, const double *lam, double *K) {
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < k * k; q += gridDim.x * blockDim.x) {
     const int c = q % k;
-    K[q] = (float)(G[q] * lam[c]);
+    K[q] = G[q] * lam[c];
   }
 }
 
-// I (k x k FP32)
-__global__ void eye_kernel(float *I, int k) {
+// I (k x k FP64)
+__global__ void eye_kernel(double *I, int k) {
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < k * k; q += gridDim.x * blockDim.x)
-    I[q] = (q / k == q % k) ? 1.f : 0.f;
+    I[q] = (q / k == q % k) ? 1.0 : 0.0;
 }
 
-// CfT[a][c] = lam_c * Csum[c][a]   i.e. (diag(lam) Csum)^T
-__global__ void core_transpose_kernel(const float *Csum, int k, const double *lam, float *CfT) {
+// CfT + CfT_lo = (diag(lam) Csum)^T, i.e. [a][c] = lam_c Csum[c][a], as an
+// FP32 pair
+__global__ void core_transpose_kernel(const double *Csum, int k, const double *lam, float *CfT,
+                                      float *CfT_lo) {
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < k * k; q += gridDim.x * blockDim.x) {
     const int a = q / k, c = q % k;
-    CfT[q] = (float)lam[c] * Csum[(int64_t)c * k + a];
+    const double v = lam[c] * Csum[(int64_t)c * k + a];
+    const float hi = (float)v;
+    CfT[q] = hi;
+    CfT_lo[q] = (float)(v - (double)hi);
   }
 }
 
@@ -331,24 +342,26 @@ int run_sketch(const sne_csr &g, const sne_params &p, const Dims &D, const Bufs 
   const int k = D.k, h = D.h, l = D.l, z = D.z;
   const float sv = 1.0f / sqrtf((float)z);
   // --- Eq. 11 factors
-  CK(launch_degree_power(b.deg, D.n, -1.0 + p.alpha, b.acoef, 1.0f, st));      // a = d^(-1+alpha)
   CK(launch_degree_power(b.deg, D.n, -1.0 + 2.0 * p.alpha, b.wgt, 1.0f, st));  // d^(-1+2alpha)
-  { ProfScope ps_(K_MISC, st); rowscale_kernel<<<grid_for(D.n), 256, 0, st>>>(b.deg, D.n, (float)(-1.0 + p.alpha), &b.ctrl->vol,
-                                                 1.0 / (p.b * p.T), b.rsc); }    // vol/(bT) a
+  { ProfScope ps_(K_MISC, st); rowscale_kernel<<<grid_for(D.n), 256, 0, st>>>(b.deg, D.n, -1.0 + p.alpha, &b.ctrl->vol,
+                                                 1.0 / (p.b * p.T), b.rsc, b.rsc_lo); }    // vol/(bT) a
   CK(cudaGetLastError());
-  CK(launch_gram(U, k, k, U, k, k, D.n, b.wgt, true, b.partial, b.m64[0], k, st, b.ctrl));  // U^T D U
-  { ProfScope ps_(K_MISC, st); scale_cols_d2f_kernel<<<grid_for((int64_t)k * k), 256, 0, st>>>(b.m64[0], k, lam, b.m32[0]); }  // K
-  { ProfScope ps_(K_MISC, st); eye_kernel<<<grid_for((int64_t)k * k), 256, 0, st>>>(b.m32[1], k); }                            // I
+  // G = U^T D^(-1+2 alpha) U in FP64 accuracy: most entries of L'R' lie just
+  // above the trunc_log threshold, where an error in the core C shifts every
+  // one of them, and the Horner sum multiplies the error of G by up to T^2/2
+  CK(launch_gram_accurate(U, k, k, U, k, k, D.n, b.wgt, true, b.partial, b.m64[0], k, st));
+  { ProfScope ps_(K_MISC, st); scale_cols_kernel<<<grid_for((int64_t)k * k), 256, 0, st>>>(b.m64[0], k, lam, b.m64[1]); }  // K
+  { ProfScope ps_(K_MISC, st); eye_kernel<<<grid_for((int64_t)k * k), 256, 0, st>>>(b.m64[2], k); }                        // I
   CK(cudaGetLastError());
-  // Horner: Csum = I + K (I + K (... (I))) = sum_{r=1..T} K^(r-1)
-  float *cur = b.m32[1], *nxt = b.m32[2];
+  // Horner in FP64: Csum = I + K (I + K (... (I))) = sum_{r=1..T} K^(r-1)
+  double *cur = b.m64[2], *nxt = b.m64[3];
   for (int r = 1; r < p.T; ++r) {
     { ProfScope ps_(K_MISC, st); eye_kernel<<<grid_for((int64_t)k * k), 256, 0, st>>>(nxt, k); }
     CK(cudaGetLastError());
-    CK(launch_small_gemm<float>(false, false, k, k, k, 1.0f, b.m32[0], k, cur, k, 1.0f, nxt, k, st));
+    CK(launch_small_gemm<double>(false, false, k, k, k, 1.0, b.m64[1], k, cur, k, 1.0, nxt, k, st));
     std::swap(cur, nxt);
   }
-  { ProfScope ps_(K_MISC, st); core_transpose_kernel<<<grid_for((int64_t)k * k), 256, 0, st>>>(cur, k, lam, b.m32[3]); }  // C^T
+  { ProfScope ps_(K_MISC, st); core_transpose_kernel<<<grid_for((int64_t)k * k), 256, 0, st>>>(cur, k, lam, b.m32[3], b.m32[2]); }  // C^T
   CK(cudaGetLastError());
   // --- Alg. 3: S (stream 2) and O (stream 3); unique coordinates
   CK(launch_sparse_sign(D.n, h, z, p.seed, 2, b.idxS, b.signS, b.ctrl, st));
@@ -356,16 +369,16 @@ int run_sketch(const sne_csr &g, const sne_params &p, const Dims &D, const Bufs 
   CK(launch_unique(b.idxS, D.nS, b.uniqS, &b.ctrl->v_s, b.posS, b.ctrl, W_UNIQUE, st));
   CK(launch_unique(b.idxO, D.nO, b.uniqO, &b.ctrl->v_o, b.posO, b.ctrl, W_UNIQUE, st));
   // R'(:, idx)^T = a_idx U(idx, :) C^T
-  CK(launch_tall_gemm(U, k, b.idxS, D.nS, k, b.m32[3], k, k, b.acoef, b.RpS, k, st));
-  CK(launch_tall_gemm(U, k, b.idxO, D.nO, k, b.m32[3], k, k, b.acoef, b.RpO, k, st));
+  CK(launch_rprime_rows(U, k, b.idxS, D.nS, b.m32[3], b.m32[2], b.deg, -1.0 + p.alpha, b.RpS, st));
+  CK(launch_rprime_rows(U, k, b.idxO, D.nO, b.m32[3], b.m32[2], b.deg, -1.0 + p.alpha, b.RpO, st));
   // --- Alg. 4 line 4: Y = f(L' R'(:, p)) S(p, :)
   // --- Alg. 4 line 7: Y' = f(L'(p,:) R'(:,p)) O(p,:) on the rows p = p_O
   float *Y = Yout ? Yout : b.A;
   const int64_t vmax = min64(D.n, D.nO);
   if (!D.half) {
-    CK(launch_fused_sketch_f32(U, k, nullptr, nullptr, D.n, k, b.rsc, b.RpS, b.signS, h, z, sv, p.f,
+    CK(launch_fused_sketch_f32(U, k, nullptr, nullptr, D.n, k, b.rsc, b.rsc_lo, b.RpS, b.signS, h, z, sv, p.f,
                                Y, h, st));
-    CK(launch_fused_sketch_f32(U, k, b.uniqO, &b.ctrl->v_o, vmax, k, b.rsc, b.RpO, b.signO, l, z,
+    CK(launch_fused_sketch_f32(U, k, b.uniqO, &b.ctrl->v_o, vmax, k, b.rsc, b.rsc_lo, b.RpO, b.signO, l, z,
                                sv, p.f, b.Yo, l, st));
   } else {
     const bool fp16 = p.precision == SNE_FP16;
@@ -389,15 +402,23 @@ int run_sketch(const sne_csr &g, const sne_params &p, const Dims &D, const Bufs 
   float *Z = Zout ? Zout : b.Zf;
   CK(launch_signed_gather_sum(b.Yo, l, l, b.posO, b.signO, l, z, sv, Z, l, st));
   if (!E && !sigma) return SNE_OK;
-  // --- Alg. 4 line 5: Q = orth(Y) by Cholesky QR, twice
-  int rc = orth_tall(D, b, SNE_ORTH_CHOLQR, true, Y, h, h, b.B, h, st);  // Q1
+  // O^T Y (FP64), taken before Y's buffer is reused for Q
+  CK(launch_signed_gather_sum64(Y, h, h, b.idxO, b.signO, l, z, (double)sv, b.Tm, h, st));
+  // --- Alg. 4 line 5: Q = orth(Y) = Y R^-1 by Cholesky QR, twice (R = R2 R1)
+  int rc = orth_tall(D, b, SNE_ORTH_CHOLQR, true, Y, h, h, b.B, h, st);  // Q1 = Y R1^-1
   if (rc) return rc;
-  rc = orth_tall(D, b, SNE_ORTH_CHOLQR, true, b.B, h, h, b.A, h, st);    // Q
+  CK(cudaMemcpyAsync(b.m64[3], b.m64[1], (size_t)h * h * sizeof(double), cudaMemcpyDeviceToDevice,
+                     st));                                                  // R1^-1
+  rc = orth_tall(D, b, SNE_ORTH_CHOLQR, true, b.B, h, h, b.A, h, st);    // Q = Q1 R2^-1
   if (rc) return rc;
   float *Q = b.A;
-  // --- Alg. 4 line 8: W = (O^T Q)^+ Z (Q^T O)^+ via the normal equations (FP64)
-  CK(launch_signed_gather_sum(Q, h, h, b.idxO, b.signO, l, z, sv, b.Gf, h, st));  // G = O^T Q
-  CK(launch_f2d(b.Gf, l, h, h, b.G64, h, st));
+  CK(launch_small_gemm<double>(false, false, h, h, h, 1.0, b.m64[3], h, b.m64[1], h, 0.0, b.m64[4],
+                               h, st));                                     // R^-1 = R1^-1 R2^-1
+  // --- Alg. 4 line 8: W = (O^T Q)^+ Z (Q^T O)^+ via the normal equations (FP64).
+  // G = O^T Q is formed as (O^T Y) R^-1 in FP64: the solves magnify errors in
+  // G by cond(G) (several thousand on large power-law graphs), so G must not
+  // carry the FP32 rounding of Q
+  CK(launch_small_gemm<double>(false, false, l, h, h, 1.0, b.Tm, h, b.m64[4], h, 0.0, b.G64, h, st));
   CK(launch_f2d(Z, l, l, l, b.Z64, l, st));
   CK(launch_small_gemm<double>(true, false, h, h, l, 1.0, b.G64, h, b.G64, h, 0.0, b.m64[0], h, st));
   CK(launch_chol_inverse<double>(b.m64[0], h, h, b.m64[1], h, b.m64[2], b.ctrl, st));  // R^-1, G^T G = R^T R

@@ -48,7 +48,8 @@ size_t gram_partial_floats(int64_t n, int32_t Ka, int32_t Kb) {
   int tiles_s, chunks_s;
   gram_grid(n, Ka, Kb, Ka == Kb, &tiles_s, &chunks_s);
   if (chunks_s > chunks) chunks = chunks_s;
-  const size_t simt = (size_t)chunks * (size_t)Ka * (size_t)Kb;
+  // FP64 partials of the double-float Gram take two floats per entry
+  const size_t simt = 2 * (size_t)chunks * (size_t)Ka * (size_t)Kb;
   return simt > tcf ? simt : tcf;
 }
 
@@ -79,12 +80,15 @@ __global__ void __launch_bounds__(kGThreads) gram_partial_kernel(
   const int64_t r1 = min64(n, r0 + rows_per_chunk);
   const int tid = threadIdx.x;
   const int ty = tid >> 3, tx = tid & 7;
-  float acc[8][8];
+  // two-level sum: acc takes 256 rows at a time and is then added into tot,
+  // so no FP32 chain grows longer than 256 + rows/256 terms
+  float acc[8][8], tot[8][8];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    for (int j = 0; j < 8; ++j) acc[i][j] = tot[i][j] = 0.f;
 
+  int blk = 0;
   for (int64_t rs = r0; rs < r1; rs += kGR) {
     // load 32 rows x 64 columns of A and B (one column per thread)
 #pragma unroll 4
@@ -114,7 +118,21 @@ __global__ void __launch_bounds__(kGThreads) gram_partial_kernel(
         for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
     }
     __syncthreads();
+    if (++blk == 256 / kGR) {
+      blk = 0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          tot[i][j] += acc[i][j];
+          acc[i][j] = 0.f;
+        }
+    }
   }
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) tot[i][j] += acc[i][j];
   float *P = partial + (size_t)blockIdx.y * Ka * Kb;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
@@ -123,7 +141,7 @@ __global__ void __launch_bounds__(kGThreads) gram_partial_kernel(
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int b = b0 + tx * 8 + j;
-      if (b < Kb) P[(size_t)a * Kb + b] = acc[i][j];
+      if (b < Kb) P[(size_t)a * Kb + b] = tot[i][j];
     }
   }
 }
@@ -152,6 +170,183 @@ cudaError_t launch_gram_reduce(const float *partial, int Ka, int Kb, int chunks,
   ProfScope ps_(K_GRAM_TC, st);
   gram_reduce_kernel<<<(unsigned)min64(1024, (total + 255) / 256), 256, 0, st>>>(
       partial, Ka, Kb, chunks, sym_tile, C, ldc);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// FP64-accurate Gram.  Every output is accumulated over groups of 16 rows
+// with FP32 FMA; each group sum is then added into a double-float pair
+// (hi, lo) with Knuth's TwoSum, which is exact, so the rounding error does not
+// grow with n: the group sums carry a relative error of a few units of 2^-24
+// of a group, and the pair keeps about 48 bits of the total.  64 x 64
+// output tile per CTA, 128 threads with 4 x 8 outputs each; one FP64 partial
+// per row chunk.
+// ---------------------------------------------------------------------------
+constexpr int kDThreads = 128;
+
+__device__ __forceinline__ void two_sum_into(float &hi, float &lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  const float ap = s - bp;
+  lo += (hi - ap) + (x - bp);
+  hi = s;
+}
+
+__global__ void __launch_bounds__(kDThreads) gram_df_partial_kernel(
+    const float *__restrict__ A, int64_t lda, int32_t Ka, const float *__restrict__ B, int64_t ldb,
+    int32_t Kb, int64_t n, const float *__restrict__ w, int symmetric, int32_t tiles_a,
+    int64_t rows_per_chunk, double *__restrict__ partial) {
+  __shared__ __align__(16) float As[kGR][kGT];
+  __shared__ __align__(16) float Bs[kGR][kGT];
+  int ta, tb;
+  int t = blockIdx.x;
+  if (symmetric) {
+    ta = 0;
+    int rowlen = tiles_a;
+    while (t >= rowlen) {
+      t -= rowlen;
+      ++ta;
+      --rowlen;
+    }
+    tb = ta + t;
+  } else {
+    ta = t / ((Kb + kGT - 1) / kGT);
+    tb = t % ((Kb + kGT - 1) / kGT);
+  }
+  const int a0 = ta * kGT, b0 = tb * kGT;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_chunk;
+  const int64_t r1 = min64(n, r0 + rows_per_chunk);
+  const int tid = threadIdx.x;
+  const int ty = tid >> 3, tx = tid & 7;  // 16 x 8 threads: rows ty*4.., cols tx*8..
+  float hi[4][8], lo[4][8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) hi[i][j] = lo[i][j] = 0.f;
+  // a stage is 32 rows x 64 columns of A and of B = 1024 float4, 8 per thread;
+  // float4 q of the stage: matrix q / 512, row (q / 16) % 32, column 4 (q % 16)
+  const bool vec = (lda % 4 == 0) && (ldb % 4 == 0) && ((uintptr_t)A % 16 == 0) &&
+                   ((uintptr_t)B % 16 == 0);
+  float4 pre[8];
+  auto fetch = [&](int64_t rs) {
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int q = tid + kDThreads * m;
+      const bool isA = q < 512;
+      const int r = (q >> 4) & 31, c = 4 * (q & 15);
+      const int64_t row = rs + r;
+      const int cbase = (isA ? a0 : b0) + c;
+      const int K = isA ? Ka : Kb;
+      const float *src = isA ? A + row * lda : B + row * ldb;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (row < r1) {
+        if (vec && cbase + 3 < K) {
+          v = __ldg(reinterpret_cast<const float4 *>(src + cbase));
+        } else {
+          if (cbase < K) v.x = src[cbase];
+          if (cbase + 1 < K) v.y = src[cbase + 1];
+          if (cbase + 2 < K) v.z = src[cbase + 2];
+          if (cbase + 3 < K) v.w = src[cbase + 3];
+        }
+        if (isA && w) {
+          const float wr = w[row];
+          v.x *= wr;
+          v.y *= wr;
+          v.z *= wr;
+          v.w *= wr;
+        }
+      }
+      pre[m] = v;
+    }
+  };
+  if (r0 < r1) fetch(r0);
+  for (int64_t rs = r0; rs < r1; rs += kGR) {
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int q = tid + kDThreads * m;
+      const int r = (q >> 4) & 31, c = 4 * (q & 15);
+      *reinterpret_cast<float4 *>(q < 512 ? &As[r][c] : &Bs[r][c]) = pre[m];
+    }
+    __syncthreads();
+    if (rs + kGR < r1) fetch(rs + kGR);  // in flight while this stage is summed
+#pragma unroll
+    for (int g = 0; g < kGR; g += 16) {
+      float acc[4][8];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+#pragma unroll
+      for (int r = g; r < g + 16; ++r) {
+        const float4 av = *reinterpret_cast<const float4 *>(&As[r][ty * 4]);
+        const float4 b_lo = *reinterpret_cast<const float4 *>(&Bs[r][tx * 8]);
+        const float4 b_hi = *reinterpret_cast<const float4 *>(&Bs[r][tx * 8 + 4]);
+        const float a4[4] = {av.x, av.y, av.z, av.w};
+        const float b8[8] = {b_lo.x, b_lo.y, b_lo.z, b_lo.w, b_hi.x, b_hi.y, b_hi.z, b_hi.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a4[i], b8[j], acc[i][j]);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) two_sum_into(hi[i][j], lo[i][j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  double *P = partial + (size_t)blockIdx.y * Ka * Kb;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int a = a0 + ty * 4 + i;
+    if (a >= Ka) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int b = b0 + tx * 8 + j;
+      if (b < Kb) P[(size_t)a * Kb + b] = (double)hi[i][j] + (double)lo[i][j];
+    }
+  }
+}
+
+__global__ void gram_reduce64_kernel(const double *__restrict__ partial, int32_t Ka, int32_t Kb,
+                                     int32_t chunks, int sym_tile, double *__restrict__ C,
+                                     int32_t ldc) {
+  const int64_t total = (int64_t)Ka * Kb;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int a = (int)(e / Kb), b = (int)(e % Kb);
+    int sa = a, sb = b;
+    if (sym_tile > 0 && (a / sym_tile) > (b / sym_tile)) {
+      sa = b;
+      sb = a;
+    }
+    double s = 0.0;
+    for (int c = 0; c < chunks; ++c) s += partial[(size_t)c * Ka * Kb + (size_t)sa * Kb + sb];
+    C[(int64_t)a * ldc + b] = s;
+  }
+}
+
+cudaError_t launch_gram_accurate(const float *A, int64_t lda, int32_t Ka, const float *B,
+                                 int64_t ldb, int32_t Kb, int64_t n, const float *w,
+                                 bool symmetric, float *partial, double *C, int32_t ldc,
+                                 cudaStream_t st) {
+  if (symmetric && (A != B || Ka != Kb || lda != ldb)) return cudaErrorInvalidValue;
+  if (n <= 0 || Ka <= 0 || Kb <= 0) return cudaErrorInvalidValue;
+  int tiles, chunks;
+  gram_grid(n, Ka, Kb, symmetric, &tiles, &chunks);
+  int64_t rpc = (n + chunks - 1) / chunks;
+  rpc = (rpc + kGR - 1) / kGR * kGR;
+  double *p64 = reinterpret_cast<double *>(partial);
+  {
+    ProfScope ps_(K_GRAM, st, 2);
+    gram_df_partial_kernel<<<dim3(tiles, chunks), kDThreads, 0, st>>>(
+        A, lda, Ka, B, ldb, Kb, n, w, symmetric ? 1 : 0, ceil_div(Ka, kGT), rpc, p64);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t total = (int64_t)Ka * Kb;
+    gram_reduce64_kernel<<<(unsigned)min64(1024, (total + 255) / 256), 256, 0, st>>>(
+        p64, Ka, Kb, chunks, symmetric ? kGT : 0, C, ldc);
+  }
   return cudaGetLastError();
 }
 
@@ -288,7 +483,9 @@ template <typename T>
 __global__ void __launch_bounds__(256) small_gemm_kernel(int ta, int tb, int M, int N, int K,
                                                          T alpha, const T *__restrict__ A, int lda,
                                                          const T *__restrict__ B, int ldb, T beta,
-                                                         T *__restrict__ C, int ldc) {
+                                                         T *__restrict__ C, int ldc,
+                                                         const int *__restrict__ skip) {
+  if (skip && *skip) return;
   __shared__ T As[32][33];
   __shared__ T Bs[32][33];
   const int tid = threadIdx.x;
@@ -336,20 +533,20 @@ __global__ void __launch_bounds__(256) small_gemm_kernel(int ta, int tb, int M, 
 template <typename T>
 cudaError_t launch_small_gemm(bool ta, bool tb, int32_t M, int32_t N, int32_t K, T alpha,
                               const T *A, int32_t lda, const T *B, int32_t ldb, T beta, T *C,
-                              int32_t ldc, cudaStream_t st) {
+                              int32_t ldc, cudaStream_t st, const int *skip) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   dim3 grid((unsigned)ceil_div(N, 32), (unsigned)ceil_div(M, 32));
   ProfScope ps_(K_SMALL_GEMM, st);
   small_gemm_kernel<T><<<grid, 256, 0, st>>>(ta ? 1 : 0, tb ? 1 : 0, M, N, K, alpha, A, lda, B, ldb,
-                                             beta, C, ldc);
+                                             beta, C, ldc, skip);
   return cudaGetLastError();
 }
 template cudaError_t launch_small_gemm<float>(bool, bool, int32_t, int32_t, int32_t, float,
                                               const float *, int32_t, const float *, int32_t, float,
-                                              float *, int32_t, cudaStream_t);
+                                              float *, int32_t, cudaStream_t, const int *);
 template cudaError_t launch_small_gemm<double>(bool, bool, int32_t, int32_t, int32_t, double,
                                                const double *, int32_t, const double *, int32_t,
-                                               double, double *, int32_t, cudaStream_t);
+                                               double, double *, int32_t, cudaStream_t, const int *);
 
 // ---------------------------------------------------------------------------
 // Cholesky A = R^T R (R upper triangular, written over A, zeros below).

@@ -7,16 +7,17 @@
 // applied at once as independent 2x2 blocks J_i^T A_(i,j) J_j, with the
 // symmetric matrix packed (lower triangle) in shared memory of one CTA.  A
 // sweep is m-1 rounds; sweeps stop when every off-diagonal element is below
-// eps * sqrt(|a_pp a_qq|).  Each round's rotations are recorded; a second,
+// 2 eps * max(sqrt(|a_pp a_qq|), |A|_F / (2 sqrt(n))).  Each round's rotations are recorded; a second,
 // multi-CTA kernel accumulates V = J_1 J_2 ... row block by row block.
 //
 // FP64 eigendecomposition (Rayleigh-Ritz, svd(W)): the FP32 result refined in
 // FP64 by the iteration of Ogita and Aishima ("Iterative refinement for
 // symmetric eigenvalue decomposition", Japan J. Indust. Appl. Math. 35, 2018):
 // R = I - X^T X, S = X^T A X, lambda_i = s_ii / (1 - r_ii),
-// delta = 2 (|S - diag(lambda)| + |A| |R|), E_ij = (s_ij + lambda_j r_ij) /
-// (lambda_j - lambda_i) when |lambda_i - lambda_j| > delta, else r_ij / 2,
-// X <- X + X E; two iterations.
+// delta = 2 (|S - diag(lambda)| + |A| |R|) (Frobenius norms, floored at
+// 1e-4 max |lambda|), E_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i) when
+// |lambda_i - lambda_j| > delta, else r_ij / 2, X <- X + X E; at most six
+// iterations, the rest skipped on the device once max |E| < 1e-14.
 #include <cfloat>
 #include <cmath>
 
@@ -26,6 +27,7 @@ namespace sne {
 
 constexpr int kJacobiMaxN = 320;
 constexpr int kJacobiMaxSweeps = 30;
+constexpr int kRefineSteps = 6;
 
 struct Rot {
   int p, q;
@@ -71,6 +73,7 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const float *__restrict__ 
   int *rq = rp + P;                                  // P
   __shared__ unsigned int off_bits;
   __shared__ float offmax_final;
+  __shared__ float fro_sq;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int e = tid; e < n * (n + 1) / 2; e += nt) {
     const int a = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
@@ -80,8 +83,27 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const float *__restrict__ 
     const int b = e - aa * (aa + 1) / 2;
     Ap[e] = A[(int64_t)aa * lda + b];
   }
+  if (tid == 0) fro_sq = 0.0f;
+  __syncthreads();
+  {
+    float part = 0.0f;
+    for (int e = tid; e < n * (n + 1) / 2; e += nt) {
+      const int a = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+      int aa = a;
+      while (aa * (aa + 1) / 2 > e) --aa;
+      while ((aa + 1) * (aa + 2) / 2 <= e) ++aa;
+      const float v = Ap[e];
+      part += (e - aa * (aa + 1) / 2 == aa) ? v * v : 2.0f * v * v;
+    }
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((tid & 31) == 0) atomicAdd(&fro_sq, part);
+  }
   __syncthreads();
   const float tol = 2.0f * FLT_EPSILON;
+  // a pair is rotated while |a_pq| exceeds tol * sqrt(|a_pp a_qq|) (relative
+  // accuracy for graded matrices) and also eps * rms(lambda) = eps |A|_F /
+  // sqrt(n): below that the element is FP32 rounding noise
+  const float denom_floor = 0.5f * sqrtf(fro_sq / (float)n);
   const int warp_id = tid >> 5, lane_id = tid & 31, nwarps = nt >> 5;
   int round = 0;
   int sweep = 0;
@@ -96,7 +118,7 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const float *__restrict__ 
         if (q < n) {
           const float apq = Ap[packed_lower(q, p)];
           const float app = Ap[packed_lower(p, p)], aqq = Ap[packed_lower(q, q)];
-          const float scale = sqrtf(fabsf(app * aqq));
+          const float scale = fmaxf(sqrtf(fabsf(app * aqq)), denom_floor);
           const float rel = (apq == 0.0f) ? 0.0f : (scale > 0.0f ? fabsf(apq) / scale : FLT_MAX);
           atomicMax(&off_bits, __float_as_uint(rel));
           if (rel > tol) {
@@ -232,11 +254,18 @@ cudaError_t launch_jacobi_f32(const float *A, int32_t n, int32_t lda, float *w, 
 // given T1 = X^T X and S = X^T A X, writes lambda and E (over T1).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) oa_update_kernel(double *T1, const double *S, const double *A,
-                                                         int lda, int n, double *lam) {
-  __shared__ double red[3][32];
+                                                         int lda, int n, double *lam, int *done) {
+  __shared__ double red[4][32];
   __shared__ double sdelta;
+  __shared__ unsigned long long emax_bits;
+  if (*done) return;
   const int tid = threadIdx.x, nt = blockDim.x;
-  for (int i = tid; i < n; i += nt) lam[i] = S[(int64_t)i * n + i] / T1[(int64_t)i * n + i];
+  if (tid == 0) emax_bits = 0ull;
+  double lmax = 0.0;
+  for (int i = tid; i < n; i += nt) {
+    lam[i] = S[(int64_t)i * n + i] / T1[(int64_t)i * n + i];
+    lmax = fmax(lmax, fabs(lam[i]));
+  }
   __syncthreads();
   double so = 0.0, sa = 0.0, sr = 0.0;
   for (int64_t q = tid; q < (int64_t)n * n; q += nt) {
@@ -252,24 +281,33 @@ __global__ void __launch_bounds__(1024) oa_update_kernel(double *T1, const doubl
     so += __shfl_xor_sync(0xffffffffu, so, o);
     sa += __shfl_xor_sync(0xffffffffu, sa, o);
     sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
   }
   if ((tid & 31) == 0) {
     red[0][tid >> 5] = so;
     red[1][tid >> 5] = sa;
     red[2][tid >> 5] = sr;
+    red[3][tid >> 5] = lmax;
   }
   __syncthreads();
   if (tid == 0) {
-    double a = 0, b = 0, c = 0;
+    double a = 0, b = 0, c = 0, lm = 0;
     for (int wv = 0; wv < (nt >> 5); ++wv) {
       a += red[0][wv];
       b += red[1][wv];
       c += red[2][wv];
+      lm = fmax(lm, red[3][wv]);
     }
-    sdelta = 2.0 * (sqrt(a) + sqrt(b) * sqrt(c));
+    // pairs closer than 1e-4 max|lambda| are treated as one cluster (only
+    // re-orthogonalized).  The FP32 start mixes such a pair by an angle of up
+    // to eps_32 |A| / gap, too large for the first-order correction to
+    // converge; left unresolved, the pair's residual stays at the FP32
+    // rounding level and its eigenvalues within the gap.
+    sdelta = fmax(2.0 * (sqrt(a) + sqrt(b) * sqrt(c)), 1e-4 * lm);
   }
   __syncthreads();
   const double delta = sdelta;
+  double emax = 0.0;
   for (int64_t q = tid; q < (int64_t)n * n; q += nt) {
     const int i = (int)(q / n), j = (int)(q % n);
     const double r = (i == j ? 1.0 : 0.0) - T1[q];
@@ -278,10 +316,17 @@ __global__ void __launch_bounds__(1024) oa_update_kernel(double *T1, const doubl
     if (i != j && fabs(gap) > delta) e = (S[q] + lam[j] * r) / gap;
     else e = 0.5 * r;
     T1[q] = e;
+    emax = fmax(emax, fabs(e));
   }
+  // non-negative doubles order like their bit patterns
+  atomicMax(&emax_bits, (unsigned long long)__double_as_longlong(emax));
+  __syncthreads();
+  // the correction is at rounding level: this step is applied, later ones are skipped
+  if (tid == 0 && __longlong_as_double((long long)emax_bits) < 1e-14) *done = 1;
 }
 
-__global__ void add_inplace_kernel(double *X, const double *Y, int64_t count) {
+__global__ void add_inplace_kernel(double *X, const double *Y, int64_t count, const int *skip) {
+  if (*skip) return;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < count;
        q += (int64_t)gridDim.x * blockDim.x)
     X[q] += Y[q];
@@ -422,25 +467,28 @@ cudaError_t launch_sym_eig_fast(double *A, int32_t n, int32_t lda, double *w, do
   e = launch_f2d(V32, n, n, n, V, ldv, st);
   if (e != cudaSuccess) return e;
   double *Ac = T3;  // S
-  for (int it = 0; it < 2; ++it) {
-    e = launch_small_gemm<double>(true, false, n, n, n, 1.0, V, ldv, V, ldv, 0.0, T1, n, st);  // X^T X
+  int *done = nrounds + 1;  // set once a correction is at rounding level
+  e = cudaMemsetAsync(done, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  for (int it = 0; it < kRefineSteps; ++it) {
+    e = launch_small_gemm<double>(true, false, n, n, n, 1.0, V, ldv, V, ldv, 0.0, T1, n, st, done);  // X^T X
     if (e != cudaSuccess) return e;
-    e = launch_small_gemm<double>(false, false, n, n, n, 1.0, A, lda, V, ldv, 0.0, T2, n, st);  // A X
+    e = launch_small_gemm<double>(false, false, n, n, n, 1.0, A, lda, V, ldv, 0.0, T2, n, st, done);  // A X
     if (e != cudaSuccess) return e;
-    e = launch_small_gemm<double>(true, false, n, n, n, 1.0, V, ldv, T2, n, 0.0, Ac, n, st);  // S
+    e = launch_small_gemm<double>(true, false, n, n, n, 1.0, V, ldv, T2, n, 0.0, Ac, n, st, done);  // S
     if (e != cudaSuccess) return e;
     {
       ProfScope ps_(K_EIG, st);
-      oa_update_kernel<<<1, 1024, 0, st>>>(T1, Ac, A, lda, n, w);
+      oa_update_kernel<<<1, 1024, 0, st>>>(T1, Ac, A, lda, n, w, done);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = launch_small_gemm<double>(false, false, n, n, n, 1.0, V, ldv, T1, n, 0.0, T2, n, st);  // X E
+    e = launch_small_gemm<double>(false, false, n, n, n, 1.0, V, ldv, T1, n, 0.0, T2, n, st, done);  // X E
     if (e != cudaSuccess) return e;
     {
       ProfScope ps_(K_EIG, st);
       add_inplace_kernel<<<(unsigned)min64(1024, ((int64_t)n * n + 255) / 256), 256, 0, st>>>(
-          V, T2, (int64_t)n * n);
+          V, T2, (int64_t)n * n, done);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -264,54 +264,86 @@ __global__ void __launch_bounds__(gt::kThreads, 1) gemm_tf32x3_kernel(
 }
 
 // ---------------------------------------------------------------------------
-// Gram kernel: the row-major tall matrices arrive from TMA as 32 x 32 boxes in
+// Gram kernel.  The row-major tall matrices arrive from TMA as 32 x 32 boxes in
 // which the contiguous direction is the output index (a or b) and the rows are
 // the reduction index i.  The split warps transpose every box into the
 // K-major 128-byte-swizzled layout (row = a or b, 32 consecutive i per
 // 128-byte row, 16-byte chunk c of row r stored at chunk c ^ (r % 8)) while
 // forming hi and lo, so the MMA reads K-major operands.
-// smem: raw[2] (TMA) | hi/lo (one set, released by the MMA of the k-block)
+//
+// The tensor-core accumulator does not round like IEEE addition: summing a
+// long chain of small products into a large total drifts.  So each TMEM
+// accumulator takes only kSeg k-blocks (kSeg * 32 rows, 3 * 4 * kSeg MMA
+// updates) before the MMA moves to the other accumulator, and four drain warps
+// add the finished one into FP32 registers with ordinary (round-to-nearest)
+// additions.  Output tile 128 (a) x 128 (b).
+// Warps: 0 TMA, 1 MMA, 2-5 split, 6-9 drain.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(gt::kThreads, 1) gram_tf32x3_kernel(
-    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int npad_max,
-    int64_t rows_per_chunk, int64_t nrows_total, const float *__restrict__ w, int mrows, int ncols,
-    float *__restrict__ out, int64_t ldo, int64_t chunk_stride, int symmetric, Ctrl *ctrl) {
+namespace gg {
+constexpr int BN = 128;
+constexpr int kSeg = 4;
+constexpr int kThreads = 320;
+constexpr int kTileBytes = 128 * 32 * 4;  // 16 KB: 128 rows x 32 fp32
+}  // namespace gg
+
+__global__ void __launch_bounds__(gg::kThreads, 1) gram_tf32x3_kernel(
+    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int ntb,
+    int symmetric, int64_t rows_per_chunk, int64_t nrows_total, const float *__restrict__ w,
+    int mrows, int ncols, float *__restrict__ out, int64_t ldo, int64_t chunk_stride, Ctrl *ctrl) {
   using namespace tc;
   extern __shared__ __align__(1024) unsigned char gg_smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(gg_smem_raw) + 1023) & ~(uintptr_t)1023);
-  // symmetric Gram: tile a0 needs only the columns b >= a0 (the reduce mirrors)
-  const int b0 = symmetric ? (int)((int64_t)blockIdx.x * gt::BM) : 0;
-  const int npad = ((ncols - b0) + 31) / 32 * 32;
-  const int bbytes = npad * gt::BK * 4;
-  const int raw_bytes = gt::kABytes + bbytes;
-  const int raw_max = gt::kABytes + npad_max * gt::BK * 4;
-  unsigned char *raw0 = smem;
-  unsigned char *hilo = smem + 2 * (size_t)raw_max;  // A_hi | A_lo | B_hi | B_lo
-  uint64_t *bars = reinterpret_cast<uint64_t *>(hilo + 2 * (size_t)raw_max);
-  uint64_t *full = bars;          // [2]
-  uint64_t *rawfree = full + 2;   // [2]
-  uint64_t *ready = rawfree + 2;  // hi/lo written
-  uint64_t *hfree = ready + 1;    // MMA done with hi/lo
-  uint64_t *done = hfree + 1;
+  // raw[2] = {A 16 KB, B 16 KB}; hilo[2] = {A_hi, A_lo, B_hi, B_lo} 16 KB each
+  unsigned char *raw = smem;
+  unsigned char *hilo = smem + 2 * 2 * gg::kTileBytes;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(hilo + 2 * 4 * gg::kTileBytes);
+  uint64_t *full = bars;           // [2]
+  uint64_t *rawfree = full + 2;    // [2]
+  uint64_t *ready = rawfree + 2;   // [2]
+  uint64_t *hfree = ready + 2;     // [2]
+  uint64_t *accfull = hfree + 2;   // [2]
+  uint64_t *accfree = accfull + 2; // [2]
+  uint64_t *done = accfree + 2;    // [1]
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
   int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t m0 = (int64_t)blockIdx.x * gt::BM;  // first output row a of the tile
+  // output tile (ta, tb): symmetric -> tb >= ta enumerated row by row
+  int ta = 0, tb = 0;
+  {
+    int t = blockIdx.x;
+    if (symmetric) {
+      int rowlen = ntb;
+      while (t >= rowlen) {
+        t -= rowlen;
+        ++ta;
+        --rowlen;
+      }
+      tb = ta + t;
+    } else {
+      ta = t / ntb;
+      tb = t % ntb;
+    }
+  }
+  const int a0 = ta * gt::BM, b0 = tb * gg::BN;
+  const int npad = min(gg::BN, ((ncols - b0) + 31) / 32 * 32);
   const int64_t r0 = (int64_t)blockIdx.y * rows_per_chunk;
   const int64_t r1 = min64(nrows_total, r0 + rows_per_chunk);
   const int kblocks = r1 > r0 ? (int)((r1 - r0 + gt::BK - 1) / gt::BK) : 0;
-  const int n1 = npad > 256 ? 256 : npad;
-  const int n2 = npad - n1;
+  const int nseg = (kblocks + gg::kSeg - 1) / gg::kSeg;
+  const int bbytes = npad * 128;
+  const uint32_t raw_bytes = (uint32_t)(gt::kABytes + bbytes);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < 2; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&rawfree[s], 128);
+      mbar_init(&ready[s], 128);
+      mbar_init(&hfree[s], 1);
+      mbar_init(&accfull[s], 1);
+      mbar_init(&accfree[s], 128);
     }
-    mbar_init(ready, 128);
-    mbar_init(hfree, 1);
     mbar_init(done, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -320,7 +352,7 @@ __global__ void __launch_bounds__(gt::kThreads, 1) gram_tf32x3_kernel(
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"(512));
+                 "r"(256));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   fence_before();
@@ -335,17 +367,16 @@ __global__ void __launch_bounds__(gt::kThreads, 1) gram_tf32x3_kernel(
       for (int kb = 0; kb < kblocks; ++kb) {
         const int s = kb & 1;
         if (!mbar_wait(&rawfree[s], (uint32_t)(((kb >> 1) & 1) ^ 1), abortv, ctrl)) break;
-        unsigned char *rb = raw0 + (size_t)s * raw_max;
-        mbar_expect_tx(&full[s], (uint32_t)raw_bytes);
+        unsigned char *rb = raw + (size_t)s * 2 * gg::kTileBytes;
+        mbar_expect_tx(&full[s], raw_bytes);
         const int y = (int)(r0 + (int64_t)kb * gt::BK);
-        for (int m = 0; m < gt::BM / 32; ++m)
-          tma_load_2d(rb + m * 4096, &tmA, &full[s], (int)m0 + 32 * m, y);
+        for (int m = 0; m < 4; ++m) tma_load_2d(rb + m * 4096, &tmA, &full[s], a0 + 32 * m, y);
         for (int t = 0; t < npad / 32; ++t)
-          tma_load_2d(rb + gt::kABytes + t * 4096, &tmB, &full[s], b0 + 32 * t, y);
+          tma_load_2d(rb + gg::kTileBytes + t * 4096, &tmB, &full[s], b0 + 32 * t, y);
         ++issued;
       }
       const int first = issued > 2 ? issued - 2 : 0;
-      for (int q = first; q < issued; ++q) {  // copies in flight land before exit
+      for (int q = first; q < issued; ++q) {
         const uint64_t t0 = gtimer();
         while (!mbar_try_wait(&full[q & 1], (uint32_t)((q >> 1) & 1)) && gtimer() - t0 < kTimeoutNs) {
         }
@@ -353,59 +384,68 @@ __global__ void __launch_bounds__(gt::kThreads, 1) gram_tf32x3_kernel(
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t base = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(gt::BM >> 4) << 24);
-      const uint32_t id1 = base | ((uint32_t)(n1 >> 3) << 17);
-      const uint32_t id2 = base | ((uint32_t)((n2 > 0 ? n2 : 16) >> 3) << 17);
-      const uint32_t ahi = smem_u32(hilo);
-      const uint32_t alo = ahi + gt::kABytes;
-      const uint32_t bhi = ahi + 2 * gt::kABytes;
-      const uint32_t blo = bhi + bbytes;
-      for (int kb = 0; kb < kblocks; ++kb) {
-        if (!mbar_wait(ready, (uint32_t)(kb & 1), abortv, ctrl)) break;
+      const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(npad >> 3) << 17) |
+                             ((uint32_t)(gt::BM >> 4) << 24);
+      bool ok = true;
+      for (int kb = 0; kb < kblocks && ok; ++kb) {
+        const int seg = kb / gg::kSeg, buf = seg & 1;
+        const bool seg_first = (kb % gg::kSeg) == 0;
+        const bool seg_last = ((kb % gg::kSeg) == gg::kSeg - 1) || (kb == kblocks - 1);
+        if (seg_first) {
+          // the drain warps must have emptied this accumulator (its use seg/2 - 1)
+          if (!mbar_wait(&accfree[buf], (uint32_t)(((seg >> 1) & 1) ^ 1), abortv, ctrl)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+        }
+        const int s = kb & 1;
+        if (!mbar_wait(&ready[s], (uint32_t)((kb >> 1) & 1), abortv, ctrl)) {
+          ok = false;
+          break;
+        }
         fence_after();
+        const uint32_t base = smem_u32(hilo + (size_t)s * 4 * gg::kTileBytes);
+        const uint32_t ahi = base, alo = base + gg::kTileBytes;
+        const uint32_t bhi = base + 2 * gg::kTileBytes, blo = base + 3 * gg::kTileBytes;
+        const uint32_t dt = tmem + (uint32_t)(buf * gg::BN);
 #pragma unroll
         for (int kk = 0; kk < gt::BK / 8; ++kk) {
-          const uint32_t acc = (kb | kk) ? 1u : 0u;
+          const uint32_t acc = (!seg_first || kk) ? 1u : 0u;
           const uint64_t da_hi = sdesc2(ahi + kk * 32, 16, 1024);
-          const uint64_t da_lo = sdesc2(alo + kk * 32, 16, 1024);
-          mma_tf32(tmem, da_hi, sdesc2(bhi + kk * 32, 16, 1024), id1, acc);
-          mma_tf32(tmem, da_hi, sdesc2(blo + kk * 32, 16, 1024), id1, 1u);
-          mma_tf32(tmem, da_lo, sdesc2(bhi + kk * 32, 16, 1024), id1, 1u);
-          if (n2 > 0) {
-            mma_tf32(tmem + n1, da_hi, sdesc2(bhi + n1 * 128 + kk * 32, 16, 1024), id2, acc);
-            mma_tf32(tmem + n1, da_hi, sdesc2(blo + n1 * 128 + kk * 32, 16, 1024), id2, 1u);
-            mma_tf32(tmem + n1, da_lo, sdesc2(bhi + n1 * 128 + kk * 32, 16, 1024), id2, 1u);
-          }
+          mma_tf32(dt, da_hi, sdesc2(bhi + kk * 32, 16, 1024), idesc, acc);
+          mma_tf32(dt, da_hi, sdesc2(blo + kk * 32, 16, 1024), idesc, 1u);
+          mma_tf32(dt, sdesc2(alo + kk * 32, 16, 1024), sdesc2(bhi + kk * 32, 16, 1024), idesc, 1u);
         }
-        mma_commit(hfree);
+        mma_commit(&hfree[s]);
+        if (seg_last) mma_commit(&accfull[buf]);
       }
+      // every issued MMA has completed before TMEM is released
       mma_commit(done);
+      const uint64_t t0 = gtimer();
+      while (!mbar_try_wait(done, 0u) && gtimer() - t0 < kTimeoutNs) {
+      }
     }
-  } else {
+  } else if (warp < 6) {
+    // ---------------- split warps: raw (MN boxes) -> transposed hi / lo
     const int t = threadIdx.x - 64;
-    bool ok = true;
-    float *hiA = reinterpret_cast<float *>(hilo);
-    float *loA = hiA + gt::kABytes / 4;
-    float *hiB = loA + gt::kABytes / 4;
-    float *loB = hiB + bbytes / 4;
     for (int kb = 0; kb < kblocks; ++kb) {
       const int s = kb & 1;
-      if (!mbar_wait(&full[s], (uint32_t)((kb >> 1) & 1), abortv, ctrl)) {
-        ok = false;
-        break;
-      }
-      if (kb > 0 && !mbar_wait(hfree, (uint32_t)((kb - 1) & 1), abortv, ctrl)) {
-        ok = false;
-        break;
-      }
-      const float4 *rb = reinterpret_cast<const float4 *>(raw0 + (size_t)s * raw_max);
+      if (!mbar_wait(&full[s], (uint32_t)((kb >> 1) & 1), abortv, ctrl)) break;
+      if (kb >= 2 && !mbar_wait(&hfree[s], (uint32_t)(((kb >> 1) - 1) & 1), abortv, ctrl)) break;
+      const float4 *rb = reinterpret_cast<const float4 *>(raw + (size_t)s * 2 * gg::kTileBytes);
+      float *hA = reinterpret_cast<float *>(hilo + (size_t)s * 4 * gg::kTileBytes);
+      float *lA = hA + gg::kTileBytes / 4;
+      float *hB = lA + gg::kTileBytes / 4;
+      float *lB = hB + gg::kTileBytes / 4;
       const int64_t ibase = r0 + (int64_t)kb * gt::BK;
-      // A: 4 boxes; chunk q -> box m = q / 256, row i = (q % 256) / 8, physical chunk c = q % 8
-      for (int q = t; q < gt::kABytes / 16; q += 128) {
-        const int m = q >> 8, i = (q & 255) >> 3, c = q & 7;
+      for (int q = t; q < (gt::kABytes + bbytes) / 16; q += 128) {
+        const bool isA = q < gt::kABytes / 16;
+        const int qq = isA ? q : q - gt::kABytes / 16;
+        const int m = qq >> 8, i = (qq & 255) >> 3, c = qq & 7;
         const int a4 = c ^ (i & 7);
         float4 x = rb[q];
-        if (w) {
+        if (isA && w) {
           const int64_t gi = ibase + i;
           const float wi = gi < nrows_total ? w[gi] : 0.0f;
           x.x *= wi;
@@ -414,63 +454,60 @@ __global__ void __launch_bounds__(gt::kThreads, 1) gram_tf32x3_kernel(
           x.w *= wi;
         }
         const float xv[4] = {x.x, x.y, x.z, x.w};
+        float *hi = isA ? hA : hB;
+        float *lo = isA ? lA : lB;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          const int A = 32 * m + 4 * a4 + j;  // K-major row
-          const int off = A * 32 + ((((i >> 2) ^ (A & 7))) << 2) + (i & 3);
+          const int r = 32 * m + 4 * a4 + j;  // K-major row
+          const int off = r * 32 + (((i >> 2) ^ (r & 7)) << 2) + (i & 3);
           const float h = tf32_rna(xv[j]);
-          hiA[off] = h;
-          loA[off] = xv[j] - h;
-        }
-      }
-      const float4 *rbB = rb + gt::kABytes / 16;
-      for (int q = t; q < bbytes / 16; q += 128) {
-        const int m = q >> 8, i = (q & 255) >> 3, c = q & 7;
-        const int a4 = c ^ (i & 7);
-        const float4 x = rbB[q];
-        const float xv[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int Bq = 32 * m + 4 * a4 + j;
-          const int off = Bq * 32 + ((((i >> 2) ^ (Bq & 7))) << 2) + (i & 3);
-          const float h = tf32_rna(xv[j]);
-          hiB[off] = h;
-          loB[off] = xv[j] - h;
+          hi[off] = h;
+          lo[off] = xv[j] - h;
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(&rawfree[s]);
-      mbar_arrive(ready);
+      mbar_arrive(&ready[s]);
     }
+  } else {
+    // ---------------- drain warps: finished accumulators -> FP32 registers
     const int ew = warp & 3;
-    const int64_t r = m0 + 32 * ew + lane;
-    const bool rok = r < mrows;
-    float *orow = out + (int64_t)blockIdx.y * chunk_stride + r * ldo + b0;
-    if (ok && kblocks > 0 && mbar_wait(done, 0, abortv, ctrl)) {
-      fence_after();
-      for (int c = 0; c < npad; c += 32) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * ew) << 16) + (uint32_t)c, v);
-        if (rok) {
+    const int64_t r = a0 + 32 * ew + lane;
+    float acc[gg::BN];
 #pragma unroll
-          for (int q = 0; q < 32; ++q)
-            if (b0 + c + q < ncols) orow[c + q] = v[q];
+    for (int c = 0; c < gg::BN; ++c) acc[c] = 0.0f;
+    bool ok = true;
+    for (int seg = 0; seg < nseg; ++seg) {
+      const int buf = seg & 1;
+      if (!mbar_wait(&accfull[buf], (uint32_t)((seg >> 1) & 1), abortv, ctrl)) {
+        ok = false;
+        break;
+      }
+      fence_after();
+#pragma unroll
+      for (int c = 0; c < gg::BN; c += 32) {
+        if (c < npad) {
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)(32 * ew) << 16) + (uint32_t)(buf * gg::BN + c), v);
+#pragma unroll
+          for (int q = 0; q < 32; ++q) acc[c + q] += v[q];
         }
       }
-    } else if (kblocks == 0 && rok) {
-      for (int c = 0; b0 + c < ncols; ++c) orow[c] = 0.0f;
+      fence_before();
+      mbar_arrive(&accfree[buf]);
     }
-  }
-  if (warp == 1 && lane == 0) {
-    const uint64_t t0 = gtimer();
-    while (!mbar_try_wait(done, 0) && gtimer() - t0 < kTimeoutNs) {
+    if (r < mrows) {
+      float *orow = out + (int64_t)blockIdx.y * chunk_stride + r * ldo + b0;
+#pragma unroll
+      for (int c = 0; c < gg::BN; ++c)
+        if (b0 + c < ncols && (ok || kblocks == 0)) orow[c] = acc[c];
     }
   }
   fence_before();
   __syncthreads();
   fence_after();
   if (warp == 1)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
 }
 
 // ---------------------------------------------------------------------------
@@ -544,46 +581,52 @@ cudaError_t launch_tall_gemm_tc(const float *A, int64_t lda, int64_t n, int K, c
   return cudaGetLastError();
 }
 
-size_t gram_tc_partial_floats(int64_t n, int Ka, int Kb) {
-  const int mtiles = (Ka + gt::BM - 1) / gt::BM;
-  int chunks = (152 * 2 + mtiles - 1) / mtiles;
+static void gram_tc_grid(int64_t n, int Ka, int Kb, bool symmetric, int *tiles, int *ntb,
+                         int *chunks) {
+  const int nta = (Ka + gt::BM - 1) / gt::BM;
+  *ntb = (Kb + gg::BN - 1) / gg::BN;
+  *tiles = symmetric ? (*ntb) * (*ntb + 1) / 2 : nta * (*ntb);
+  int c = (152 * 2) / *tiles;  // at most two full waves of one CTA per SM
   const int64_t maxc = (n + 4 * gt::BK - 1) / (4 * gt::BK);
-  if (chunks > maxc) chunks = (int)maxc;
-  if (chunks < 1) chunks = 1;
+  if (c > maxc) c = (int)maxc;
+  if (c < 1) c = 1;
+  *chunks = c;
+}
+
+size_t gram_tc_partial_floats(int64_t n, int Ka, int Kb) {
+  int tiles, ntb, chunks;
+  gram_tc_grid(n, Ka, Kb, false, &tiles, &ntb, &chunks);
+  int t2, nb2, c2;
+  gram_tc_grid(n, Ka, Kb, Ka == Kb, &t2, &nb2, &c2);
+  if (c2 > chunks) chunks = c2;
   return (size_t)chunks * Ka * Kb;
 }
 
 // partial[c][a][b] = sum_{i in chunk c} w_i A[i, a] B[i, b]; C = sum_c partial (FP64).
-
 cudaError_t launch_gram_tc(const float *A, int64_t lda, int Ka, const float *B, int64_t ldb, int Kb,
                            int64_t n, const float *w, bool symmetric, float *partial, double *C,
                            int ldc, Ctrl *ctrl, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  const int npad = (Kb + 31) / 32 * 32;
-  if (!tc_gemm_supported(Kb)) return cudaErrorInvalidValue;
-  const int mtiles = (Ka + gt::BM - 1) / gt::BM;
-  int chunks = (152 * 2 + mtiles - 1) / mtiles;
-  const int64_t maxc = (n + 4 * gt::BK - 1) / (4 * gt::BK);
-  if (chunks > maxc) chunks = (int)maxc;
-  if (chunks < 1) chunks = 1;
-  // rows per chunk: a multiple of the 32-row k-block so chunks never overlap
+  if (symmetric && Ka != Kb) return cudaErrorInvalidValue;
+  int tiles, ntb, chunks;
+  gram_tc_grid(n, Ka, Kb, symmetric, &tiles, &ntb, &chunks);
   int64_t rpc = (n + chunks - 1) / chunks;
-  rpc = (rpc + gt::BK - 1) / gt::BK * gt::BK;
+  rpc = (rpc + gt::BK - 1) / gt::BK * gt::BK;  // chunks never share a 32-row k-block
   CUtensorMap tmA, tmB;
   if (!map_f32(&tmA, A, n, Ka, lda, 32, gt::BK)) return cudaErrorInvalidValue;
   if (!map_f32(&tmB, B, n, Kb, ldb, 32, gt::BK)) return cudaErrorInvalidValue;
-  const size_t smem = gemm_tc_smem(npad);  // raw[2] + one hi/lo set: same total
+  const size_t smem = 1024 + (size_t)2 * 2 * gg::kTileBytes + (size_t)2 * 4 * gg::kTileBytes + 256;
   auto kern = gram_tf32x3_kernel;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   {
     ProfScope ps_(K_GRAM_TC, st);
-    kern<<<dim3((unsigned)mtiles, (unsigned)chunks), gt::kThreads, smem, st>>>(
-        tmA, tmB, npad, rpc, n, w, Ka, Kb, partial, Kb, (int64_t)Ka * Kb, symmetric ? 1 : 0, ctrl);
+    kern<<<dim3((unsigned)tiles, (unsigned)chunks), gg::kThreads, smem, st>>>(
+        tmA, tmB, ntb, symmetric ? 1 : 0, rpc, n, w, Ka, Kb, partial, Kb, (int64_t)Ka * Kb, ctrl);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return launch_gram_reduce(partial, Ka, Kb, chunks, symmetric ? gt::BM : 0, C, ldc, st);
+  return launch_gram_reduce(partial, Ka, Kb, chunks, symmetric ? gg::BN : 0, C, ldc, st);
 }
 
 }  // namespace sne

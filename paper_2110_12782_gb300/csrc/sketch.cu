@@ -26,8 +26,9 @@ template <int F>
 __global__ void __launch_bounds__(256) fused_sketch_f32_kernel(
     const float *__restrict__ A, int64_t lda, const int32_t *__restrict__ ridx,
     const int32_t *__restrict__ nrows_dev, int64_t nrows_max, int32_t k,
-    const float *__restrict__ rs, const float *__restrict__ B, const int8_t *__restrict__ sign,
-    int32_t cols_out, int32_t z, float sv, float *__restrict__ out, int64_t ldo) {
+    const float *__restrict__ rs, const float *__restrict__ rs_lo, const float *__restrict__ B,
+    const int8_t *__restrict__ sign, int32_t cols_out, int32_t z, float sv,
+    float *__restrict__ out, int64_t ldo) {
   __shared__ __align__(16) float As[kFK][kFM + 4];
   __shared__ __align__(16) float Bs[kFK][kFN + 4];
   __shared__ float Fs[kFM][kFN + 1];
@@ -86,13 +87,18 @@ __global__ void __launch_bounds__(256) fused_sketch_f32_kernel(
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int64_t row = i0 + ty * 4 + i;
-    float s = 0.f;
-    if (row < nrows) s = rs[ridx ? ridx[row] : row];
+    float s = 0.f, s_lo = 0.f;
+    if (row < nrows) {
+      const int64_t src = ridx ? ridx[row] : row;
+      s = rs[src];
+      if (rs_lo) s_lo = rs_lo[src];
+    }
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int c = tx * 8 + j;
       float v = 0.f;
-      if (c < e_count) v = (float)sign[e_begin + c] * apply_f<F>(s * acc[i][j]);
+      // the scale is the pair s + s_lo, so the only rounding of x is its own
+      if (c < e_count) v = (float)sign[e_begin + c] * apply_f<F>(fmaf(s, acc[i][j], s_lo * acc[i][j]));
       Fs[ty * 4 + i][c] = v;
     }
   }
@@ -110,9 +116,9 @@ __global__ void __launch_bounds__(256) fused_sketch_f32_kernel(
 
 cudaError_t launch_fused_sketch_f32(const float *A, int64_t lda, const int32_t *ridx,
                                     const int32_t *nrows_dev, int64_t nrows, int32_t k,
-                                    const float *rs, const float *B, const int8_t *sign,
-                                    int32_t cols_out, int32_t z, float sv, int32_t f, float *out,
-                                    int64_t ldo, cudaStream_t st) {
+                                    const float *rs, const float *rs_lo, const float *B,
+                                    const int8_t *sign, int32_t cols_out, int32_t z, float sv,
+                                    int32_t f, float *out, int64_t ldo, cudaStream_t st) {
   if (nrows <= 0 || cols_out <= 0) return cudaSuccess;
   if (z <= 0 || z > kFN) return cudaErrorInvalidValue;
   const int cpt = kFN / z;
@@ -120,10 +126,10 @@ cudaError_t launch_fused_sketch_f32(const float *A, int64_t lda, const int32_t *
   ProfScope ps_(K_FUSED, st);
   if (f == SNE_F_TRUNC_LOG)
     fused_sketch_f32_kernel<SNE_F_TRUNC_LOG><<<grid, 256, 0, st>>>(
-        A, lda, ridx, nrows_dev, nrows, k, rs, B, sign, cols_out, z, sv, out, ldo);
+        A, lda, ridx, nrows_dev, nrows, k, rs, rs_lo, B, sign, cols_out, z, sv, out, ldo);
   else
     fused_sketch_f32_kernel<SNE_F_IDENTITY><<<grid, 256, 0, st>>>(
-        A, lda, ridx, nrows_dev, nrows, k, rs, B, sign, cols_out, z, sv, out, ldo);
+        A, lda, ridx, nrows_dev, nrows, k, rs, rs_lo, B, sign, cols_out, z, sv, out, ldo);
   return cudaGetLastError();
 }
 
@@ -149,6 +155,89 @@ cudaError_t launch_signed_gather_sum(const float *In, int64_t ldi, int32_t width
   if (cols <= 0 || width <= 0) return cudaSuccess;
   ProfScope ps_(K_GATHER, st);
   signed_gather_sum_kernel<<<cols, 256, 0, st>>>(In, ldi, width, idx, sign, z, sv, out, ldo);
+  return cudaGetLastError();
+}
+
+// R'(:, j)^T for the gathered vertices j = idx[i] (Eq. 11):
+//   out[i, :] = a_j U[j, :] (C_hi + C_lo)^T,  a_j = deg_j^beta in FP64 (0 if deg_j = 0).
+// C^T is carried as a pair of FP32 matrices so that its rounding, which every
+// column of R' would otherwise share, cancels; the sums over the k terms are
+// FP32 FMA chains, and each output is rounded to FP32 once.
+constexpr int kRpRows = 8;
+__global__ void __launch_bounds__(256) rprime_rows_kernel(
+    const float *__restrict__ U, int32_t k, const int32_t *__restrict__ idx, int32_t count,
+    const float *__restrict__ CThi, const float *__restrict__ CTlo, const float *__restrict__ deg,
+    double beta, float *__restrict__ out) {
+  extern __shared__ float us[];  // kRpRows x k
+  const int i0 = blockIdx.x * kRpRows;
+  const int rows = min(kRpRows, count - i0);
+  for (int e = threadIdx.x; e < kRpRows * k; e += blockDim.x) {
+    const int r = e / k, a = e % k;
+    us[e] = r < rows ? U[(int64_t)idx[i0 + r] * k + a] : 0.f;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    float hi[kRpRows], lo[kRpRows];
+#pragma unroll
+    for (int r = 0; r < kRpRows; ++r) hi[r] = lo[r] = 0.f;
+    for (int a = 0; a < k; ++a) {
+      const float ch = CThi[(int64_t)a * k + c], cl = CTlo[(int64_t)a * k + c];
+#pragma unroll
+      for (int r = 0; r < kRpRows; ++r) {
+        const float u = us[r * k + a];
+        hi[r] = fmaf(u, ch, hi[r]);
+        lo[r] = fmaf(u, cl, lo[r]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kRpRows; ++r) {
+      if (r >= rows) break;
+      const float dj = deg[idx[i0 + r]];
+      const double aj = dj > 0.f ? pow((double)dj, beta) : 0.0;
+      out[(int64_t)(i0 + r) * k + c] = (float)(aj * ((double)hi[r] + (double)lo[r]));
+    }
+  }
+}
+
+cudaError_t launch_rprime_rows(const float *U, int32_t k, const int32_t *idx, int32_t count,
+                               const float *CThi, const float *CTlo, const float *deg, double beta,
+                               float *out, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  const size_t smem = (size_t)kRpRows * k * sizeof(float);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(rprime_rows_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  ProfScope ps_(K_TALL_GEMM, st);
+  rprime_rows_kernel<<<(count + kRpRows - 1) / kRpRows, 256, smem, st>>>(U, k, idx, count, CThi,
+                                                                        CTlo, deg, beta, out);
+  return cudaGetLastError();
+}
+
+// FP64 version (FP32 input rows, FP64 sums): out[c, :] = sv * sum_t sign * In[idx, :]
+__global__ void signed_gather_sum64_kernel(const float *__restrict__ In, int64_t ldi, int32_t width,
+                                           const int32_t *__restrict__ idx,
+                                           const int8_t *__restrict__ sign, int32_t z, double sv,
+                                           double *__restrict__ out, int64_t ldo) {
+  const int c = blockIdx.x;
+  for (int q = threadIdx.x; q < width; q += blockDim.x) {
+    double s = 0.0;
+    for (int t = 0; t < z; ++t) {
+      const int64_t e = (int64_t)c * z + t;
+      s += (double)sign[e] * (double)In[(int64_t)idx[e] * ldi + q];
+    }
+    out[(int64_t)c * ldo + q] = sv * s;
+  }
+}
+
+cudaError_t launch_signed_gather_sum64(const float *In, int64_t ldi, int32_t width,
+                                       const int32_t *idx, const int8_t *sign, int32_t cols,
+                                       int32_t z, double sv, double *out, int64_t ldo,
+                                       cudaStream_t st) {
+  if (cols <= 0 || width <= 0) return cudaSuccess;
+  ProfScope ps_(K_GATHER, st);
+  signed_gather_sum64_kernel<<<cols, 256, 0, st>>>(In, ldi, width, idx, sign, z, sv, out, ldo);
   return cudaGetLastError();
 }
 

@@ -115,6 +115,12 @@ size_t gram_partial_floats(int64_t n, int32_t Ka, int32_t Kb);
 cudaError_t launch_gram(const float *A, int64_t lda, int32_t Ka, const float *B, int64_t ldb,
                         int32_t Kb, int64_t n, const float *w, bool symmetric, float *partial,
                         double *C, int32_t ldc, cudaStream_t st, Ctrl *ctrl = nullptr);
+// The same Gram with FP64 accuracy (double-float accumulation on the FP32
+// pipes), for sums whose errors later steps amplify; same scratch.
+cudaError_t launch_gram_accurate(const float *A, int64_t lda, int32_t Ka, const float *B,
+                                 int64_t ldb, int32_t Kb, int64_t n, const float *w,
+                                 bool symmetric, float *partial, double *C, int32_t ldc,
+                                 cudaStream_t st);
 // gemm_tc.cu: FP32-accurate (3 x TF32) tensor-core versions, used when
 // tc_gemm_supported(columns) and the operands are 16-byte aligned.
 bool tc_gemm_supported(int ncols);
@@ -139,10 +145,11 @@ cudaError_t launch_tall_gemm(const float *A, int64_t lda, const int32_t *ridx, i
                              const float *M, int32_t ldm, int32_t Kc, const float *rs, float *C,
                              int64_t ldc, cudaStream_t st);
 // Small dense GEMM (multi-CTA): C = alpha * op(A) op(B) + beta * C, row-major.
+// With `skip` (device flag) set the kernel returns without touching C.
 template <typename T>
 cudaError_t launch_small_gemm(bool ta, bool tb, int32_t M, int32_t N, int32_t K, T alpha,
                               const T *A, int32_t lda, const T *B, int32_t ldb, T beta, T *C,
-                              int32_t ldc, cudaStream_t st);
+                              int32_t ldc, cudaStream_t st, const int *skip = nullptr);
 // Single-CTA small factorizations (n <= 1024), matrices in global memory.
 template <typename T>
 cudaError_t launch_cholesky_upper(T *A, int32_t n, int32_t lda, Ctrl *ctrl, cudaStream_t st);
@@ -182,9 +189,13 @@ cudaError_t launch_check_finite_f(const float *x, int64_t count, Ctrl *ctrl, int
 // out[i, c] = sv * sum_{t<z} sign[c*z+t] * f(rs[r(i)] * <A[r(i), :], B[c*z+t, :]>)
 cudaError_t launch_fused_sketch_f32(const float *A, int64_t lda, const int32_t *ridx,
                                     const int32_t *nrows_dev, int64_t nrows, int32_t k,
-                                    const float *rs, const float *B, const int8_t *sign,
-                                    int32_t cols_out, int32_t z, float sv, int32_t f, float *out,
-                                    int64_t ldo, cudaStream_t st);
+                                    const float *rs, const float *rs_lo, const float *B,
+                                    const int8_t *sign, int32_t cols_out, int32_t z, float sv,
+                                    int32_t f, float *out, int64_t ldo, cudaStream_t st);
+// out[i, :] = deg_j^beta U[j, :] (CThi + CTlo), j = idx[i]  (R'(:, j)^T of Eq. 11)
+cudaError_t launch_rprime_rows(const float *U, int32_t k, const int32_t *idx, int32_t count,
+                               const float *CThi, const float *CTlo, const float *deg, double beta,
+                               float *out, cudaStream_t st);
 // sketch_tc.cu: mixed-precision fused sketch (BF16 or FP16 operands, FP32
 // accumulation on tcgen05).  Operands are row-normalized half copies made by
 // launch_to_half_rows; kpad is k rounded up to a multiple of 64; colf holds
@@ -199,6 +210,11 @@ cudaError_t launch_fused_sketch_tc(bool fp16, const void *Ahat, int64_t nrows_ma
                                    int ncols_eval, int cols_out, int z, const float *rowf,
                                    const float *colf, const int8_t *sign, float sv, int f, float *out,
                                    int64_t ldo, Ctrl *ctrl, cudaStream_t st);
+// The same sum of FP32 rows accumulated and written in FP64.
+cudaError_t launch_signed_gather_sum64(const float *In, int64_t ldi, int32_t width,
+                                       const int32_t *idx, const int8_t *sign, int32_t cols,
+                                       int32_t z, double sv, double *out, int64_t ldo,
+                                       cudaStream_t st);
 // out[c, :] = sv * sum_t sign[c*z+t] * In[idx[c*z+t], :]
 cudaError_t launch_signed_gather_sum(const float *In, int64_t ldi, int32_t width, const int32_t *idx,
                                      const int8_t *sign, int32_t cols, int32_t z, float sv,

@@ -38,7 +38,8 @@ EXPORTS = [
     "sne_sketch_from_factors", "sne_sparse_sign", "sne_gaussian", "sne_degrees",
     "sne_degree_power", "sne_spmm", "sne_validate_csr", "sne_status_reset", "sne_status",
     "sne_stats_read", "sne_embed_host", "sne_kernel_launches", "sne_profile_start",
-    "sne_profile_stop", "sne_freigs_static",
+    "sne_profile_stop", "sne_freigs_static", "sne_gram_workspace_bytes", "sne_gram",
+    "sne_tall_gemm_workspace_bytes", "sne_tall_gemm", "sne_sym_eig_workspace_bytes", "sne_sym_eig",
 ]
 
 
@@ -108,6 +109,12 @@ def lib() -> ctypes.CDLL:
             "sne_profile_start": [],
             "sne_profile_stop": [P(sne_kernel_time), ctypes.c_int, P(ctypes.c_int)],
             "sne_freigs_static": [P(sne_csr), P(sne_params), vp, vp, vp, vp],
+            "sne_gram_workspace_bytes": [i64, i32, i32, P(ctypes.c_size_t)],
+            "sne_gram": [i64, i32, i32, vp, i64, vp, i64, vp, vp, i32, i32, vp, ctypes.c_size_t, vp],
+            "sne_tall_gemm_workspace_bytes": [i32, i32, P(ctypes.c_size_t)],
+            "sne_tall_gemm": [i64, i32, i32, vp, i64, vp, i32, vp, i64, vp, ctypes.c_size_t, vp],
+            "sne_sym_eig_workspace_bytes": [i32, P(ctypes.c_size_t)],
+            "sne_sym_eig": [i32, vp, i32, vp, vp, i32, vp, ctypes.c_size_t, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -312,3 +319,81 @@ def sne_freigs_static(g: DeviceGraph, p: sne_params, U: torch.Tensor, lam: torch
                                    _ptr(lam, torch.float64, "lambda"),
                                    _ptr(status, torch.int32, "status", True), _stream(stream)),
            "sne_freigs_static")
+
+
+# ----------------------------------------------------------------------------- dense building blocks
+def _aligned_bytes(nbytes: int, device) -> torch.Tensor:
+    t = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+    off = (-t.data_ptr()) % 256
+    return t[off:off + nbytes]
+
+
+def _row_stride(t: torch.Tensor, name: str) -> int:
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError(f"{name} must be a row-major 2-D tensor")
+    return t.stride(0)
+
+
+def gram_workspace(n: int, ka: int, kb: int, device="cuda") -> torch.Tensor:
+    nb = ctypes.c_size_t(0)
+    _check(lib().sne_gram_workspace_bytes(n, ka, kb, ctypes.byref(nb)), "sne_gram_workspace_bytes")
+    return _aligned_bytes(nb.value, device)
+
+
+def sne_gram(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, ws: torch.Tensor,
+             w: torch.Tensor | None = None, accurate: bool = False, stream=None) -> None:
+    """C (FP64) = A^T diag(w) B for tall row-major FP32 A (n x ka) and B (n x kb);
+    ``accurate`` selects the double-float accumulation."""
+    for t, nm in ((A, "A"), (B, "B")):
+        if not (t.is_cuda and t.dtype == torch.float32):
+            raise ValueError(f"{nm} must be a CUDA float32 tensor")
+    if C.dtype != torch.float64 or not C.is_cuda:
+        raise ValueError("C must be a CUDA float64 tensor")
+    n, ka = A.shape
+    kb = B.shape[1]
+    if B.shape[0] != n or tuple(C.shape) != (ka, kb):
+        raise ValueError("shape mismatch")
+    _check(lib().sne_gram(n, ka, kb, A.data_ptr(), _row_stride(A, "A"), B.data_ptr(), _row_stride(B, "B"),
+                          _ptr(w, torch.float32, "w", True), C.data_ptr(), _row_stride(C, "C"),
+                          1 if accurate else 0, _ptr(ws, torch.uint8, "workspace"), ws.numel(),
+                          _stream(stream)), "sne_gram")
+
+
+def tall_gemm_workspace(ka: int, kc: int, device="cuda") -> torch.Tensor:
+    nb = ctypes.c_size_t(0)
+    _check(lib().sne_tall_gemm_workspace_bytes(ka, kc, ctypes.byref(nb)), "sne_tall_gemm_workspace_bytes")
+    return _aligned_bytes(nb.value, device)
+
+
+def sne_tall_gemm(A: torch.Tensor, M: torch.Tensor, C: torch.Tensor, ws: torch.Tensor, stream=None) -> None:
+    """C = A M for tall row-major FP32 A (n x ka) and small M (ka x kc)."""
+    for t, nm in ((A, "A"), (M, "M"), (C, "C")):
+        if not (t.is_cuda and t.dtype == torch.float32):
+            raise ValueError(f"{nm} must be a CUDA float32 tensor")
+    n, ka = A.shape
+    kc = M.shape[1]
+    if M.shape[0] != ka or tuple(C.shape) != (n, kc):
+        raise ValueError("shape mismatch")
+    _check(lib().sne_tall_gemm(n, ka, kc, A.data_ptr(), _row_stride(A, "A"), M.data_ptr(),
+                               _row_stride(M, "M"), C.data_ptr(), _row_stride(C, "C"),
+                               _ptr(ws, torch.uint8, "workspace"), ws.numel(), _stream(stream)),
+           "sne_tall_gemm")
+
+
+def sym_eig_workspace(n: int, device="cuda") -> torch.Tensor:
+    nb = ctypes.c_size_t(0)
+    _check(lib().sne_sym_eig_workspace_bytes(n, ctypes.byref(nb)), "sne_sym_eig_workspace_bytes")
+    return _aligned_bytes(nb.value, device)
+
+
+def sne_sym_eig(S: torch.Tensor, lam: torch.Tensor, V: torch.Tensor, ws: torch.Tensor, stream=None) -> None:
+    """Symmetric FP64 S = V diag(lam) V^T, lam ordered by |lam| descending."""
+    n = S.shape[0]
+    for t, nm in ((S, "S"), (lam, "lambda"), (V, "V")):
+        if not (t.is_cuda and t.dtype == torch.float64):
+            raise ValueError(f"{nm} must be a CUDA float64 tensor")
+    if tuple(S.shape) != (n, n) or tuple(V.shape) != (n, n) or lam.numel() != n:
+        raise ValueError("shape mismatch")
+    _check(lib().sne_sym_eig(n, S.data_ptr(), _row_stride(S, "S"), _ptr(lam, torch.float64, "lambda"),
+                             V.data_ptr(), _row_stride(V, "V"), _ptr(ws, torch.uint8, "workspace"),
+                             ws.numel(), _stream(stream)), "sne_sym_eig")

@@ -1,0 +1,175 @@
+"""The dense building blocks of Alg. 5 and Alg. 4 through the C-ABI, one by one,
+against their plain FP64 definitions (numpy) on the same FP32 inputs.
+
+Sizes run from a few rows (the FP32-FMA path) through several tiles with a
+ragged tail up to the benchmark's full size (n = 1,000,000 rows, 272
+columns).  The tall inputs mimic the basis matrices the pipeline feeds these
+blocks: a heavy-tailed first column (proportional to sqrt(degree) for a
+power-law degree sequence, as the top eigenvector of D^-1/2 A D^-1/2) and
+Gaussian columns with row scales spread over three decades.
+"""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sk():
+    from paper_2110_12782_gb300 import build
+    build.build()
+    from paper_2110_12782_gb300 import sketchne
+    sketchne.lib()
+    return sketchne
+
+
+def tall_basis(n, k, seed):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((n, k)).astype(np.float32)
+    A *= np.exp(rng.uniform(-3.5, 3.5, size=(n, 1))).astype(np.float32)
+    deg = np.floor(rng.pareto(1.1, size=n) + 1.0)
+    A[:, 0] = np.sqrt(deg / deg.sum())
+    A[:, 1:] /= np.linalg.norm(A[:, 1:], axis=0, keepdims=True)
+    return A
+
+
+def gram_error(C, ref):
+    d = np.sqrt(np.abs(np.diag(ref)))
+    if ref.shape[0] != ref.shape[1]:
+        raise ValueError
+    return float(np.max(np.abs(C - ref) / np.outer(d, d)))
+
+
+def cross_error(C, ref, A, B):
+    na = np.sqrt((A.astype(np.float64) ** 2).sum(axis=0))
+    nb = np.sqrt((B.astype(np.float64) ** 2).sum(axis=0))
+    return float(np.max(np.abs(C - ref) / np.outer(na, nb)))
+
+
+# The accurate form's error is that of one FP32 sum over a 16-row group, so it
+# is largest relative to the total when n is small and shrinks as n grows.
+TOL = {False: 1e-5, True: 1e-7}
+
+
+@pytest.mark.parametrize("accurate", [False, True])
+@pytest.mark.parametrize("n,k", [(300, 16), (4097, 144), (100_003, 272), (1_000_000, 272)])
+def test_gram_symmetric(sk, n, k, accurate):
+    A = tall_basis(n, k, seed=n)
+    ref = A.astype(np.float64).T @ A.astype(np.float64)
+    Ad = torch.from_numpy(A).cuda()
+    C = torch.empty(k, k, dtype=torch.float64, device="cuda")
+    ws = sk.gram_workspace(n, k, k)
+    sk.sne_gram(Ad, Ad, C, ws, accurate=accurate)
+    assert sk.sne_status(ws) == 0
+    err = gram_error(C.cpu().numpy(), ref)
+    print(f"gram n={n} k={k} accurate={accurate}: max |C - ref| / sqrt(ref_aa ref_bb) = {err:.2e}")
+    assert err < (1e-8 if accurate and n >= 1_000_000 else TOL[accurate])
+
+
+@pytest.mark.parametrize("accurate", [False, True])
+@pytest.mark.parametrize("n,k", [(4097, 144), (1_000_000, 256)])
+def test_gram_weighted(sk, n, k, accurate):
+    """U^T D^(-1+2 alpha) U of Eq. 11 with positive weights over four decades."""
+    A = tall_basis(n, k, seed=7 + n)
+    rng = np.random.default_rng(3)
+    w = np.exp(rng.uniform(-4.6, 4.6, size=n)).astype(np.float32)
+    ref = (A.astype(np.float64) * w[:, None].astype(np.float64)).T @ A.astype(np.float64)
+    Ad = torch.from_numpy(A).cuda()
+    C = torch.empty(k, k, dtype=torch.float64, device="cuda")
+    ws = sk.gram_workspace(n, k, k)
+    sk.sne_gram(Ad, Ad, C, ws, w=torch.from_numpy(w).cuda(), accurate=accurate)
+    assert sk.sne_status(ws) == 0
+    err = gram_error(C.cpu().numpy(), ref)
+    print(f"weighted gram n={n} k={k} accurate={accurate}: {err:.2e}")
+    assert err < TOL[accurate]
+
+
+@pytest.mark.parametrize("accurate", [False, True])
+@pytest.mark.parametrize("n,ka,kb", [(1000, 100, 37), (65_537, 272, 272), (1_000_000, 272, 272)])
+def test_gram_cross(sk, n, ka, kb, accurate):
+    """S = Q^T (X Q) of the Rayleigh-Ritz step: two different tall matrices."""
+    A = tall_basis(n, ka, seed=11)
+    B = tall_basis(n, kb, seed=12)
+    ref = A.astype(np.float64).T @ B.astype(np.float64)
+    C = torch.empty(ka, kb, dtype=torch.float64, device="cuda")
+    ws = sk.gram_workspace(n, ka, kb)
+    sk.sne_gram(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), C, ws, accurate=accurate)
+    assert sk.sne_status(ws) == 0
+    err = cross_error(C.cpu().numpy(), ref, A, B)
+    print(f"cross gram n={n} {ka}x{kb} accurate={accurate}: {err:.2e}")
+    assert err < TOL[accurate]
+
+
+@pytest.mark.parametrize("n,ka,kc", [(500, 40, 24), (4097, 272, 272), (1_000_000, 272, 256),
+                                     (1_000_000, 272, 128)])
+def test_tall_gemm(sk, n, ka, kc):
+    A = tall_basis(n, ka, seed=5)
+    rng = np.random.default_rng(6)
+    M = rng.standard_normal((ka, kc)).astype(np.float32)
+    C = torch.empty(n, kc, dtype=torch.float32, device="cuda")
+    ws = sk.tall_gemm_workspace(ka, kc)
+    sk.sne_tall_gemm(torch.from_numpy(A).cuda(), torch.from_numpy(M).cuda(), C, ws)
+    assert sk.sne_status(ws) == 0
+    rows = np.unique(np.concatenate([np.arange(min(n, 64)), np.arange(max(0, n - 64), n),
+                                     np.random.default_rng(9).choice(n, min(n, 4096), replace=False)]))
+    ref = A[rows].astype(np.float64) @ M.astype(np.float64)
+    got = C[torch.as_tensor(rows, device="cuda")].cpu().numpy().astype(np.float64)
+    scale = np.sqrt((A[rows].astype(np.float64) ** 2) @ (M.astype(np.float64) ** 2))
+    err = float(np.max(np.abs(got - ref) / scale))
+    print(f"tall gemm n={n} {ka}x{kc}: {err:.2e}")
+    # 3 x TF32 products; the tensor-core accumulator rounds each of the
+    # 3 * ka / 8 updates of a K-chain, about 0.5 ulp of the running sum each
+    assert err < 3e-5
+
+
+def clustered_symmetric(n, seed, n_plus=19, n_minus=18, n_zero=23):
+    """V diag(lam) V^T with eigenvalue clusters at +1, -1 and 0 (each split by
+    1e-9), as the Rayleigh-Ritz matrix of a graph with many small components."""
+    rng = np.random.default_rng(seed)
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = rng.uniform(-0.9, 0.9, size=n)
+    lam[:n_plus] = 1.0 - 1e-9 * rng.random(n_plus)
+    lam[n_plus:n_plus + n_minus] = -1.0 + 1e-9 * rng.random(n_minus)
+    lam[n_plus + n_minus:n_plus + n_minus + n_zero] = 1e-9 * rng.standard_normal(n_zero)
+    S = (V * lam) @ V.T
+    return 0.5 * (S + S.T), lam, V
+
+
+@pytest.mark.parametrize("n", [8, 144, 272, 320, 600])
+def test_sym_eig_clustered(sk, n):
+    c = min(19, n // 4)
+    S, lam_true, V_true = clustered_symmetric(n, seed=n, n_plus=c, n_minus=c, n_zero=c)
+    Sd = torch.from_numpy(S).cuda()
+    lam = torch.empty(n, dtype=torch.float64, device="cuda")
+    V = torch.empty(n, n, dtype=torch.float64, device="cuda")
+    ws = sk.sym_eig_workspace(n)
+    sk.sne_sym_eig(Sd, lam, V, ws)
+    assert sk.sne_status(ws) == 0
+    l, Vh = lam.cpu().numpy(), V.cpu().numpy()
+    assert np.all(np.diff(np.abs(l)) <= 1e-12)
+    orth = np.abs(Vh.T @ Vh - np.eye(n)).max()
+    lam_err = np.abs(np.sort(l) - np.sort(lam_true)).max()
+    res = np.linalg.norm(S @ Vh - Vh * l[None, :], axis=0)
+    # eigenvalues isolated by more than 1e-3 are resolved to FP64 accuracy.
+    # Pairs closer than 1e-4 max|lambda| keep the FP32 solver's mixing, which
+    # is bounded by its rounding: residual and eigenvalue error at FP32 level.
+    # Inside a cluster (gaps of 1e-9) any orthonormal basis of the cluster's
+    # invariant subspace is correct, and that subspace must be exact.
+    gaps = (np.abs(l[:, None] - l[None, :]) + np.diag(np.full(n, np.inf))).min(axis=1)
+    iso = gaps > 1e-3
+    sub_err = 0.0
+    for center in (1.0, -1.0, 0.0):
+        cols_true = np.abs(lam_true - center) < 1e-6
+        cols_got = np.abs(l - center) < 1e-6
+        assert cols_true.sum() == cols_got.sum()
+        P = V_true[:, cols_true]
+        Vc = Vh[:, cols_got]
+        sub_err = max(sub_err, np.abs(Vc - P @ (P.T @ Vc)).max())
+    print(f"sym eig n={n}: |V^T V - I| {orth:.1e}, |lam - ref| {lam_err:.1e}, residual isolated "
+          f"{res[iso].max():.1e} all {res.max():.1e}, cluster subspace {sub_err:.1e}")
+    assert orth < 1e-11
+    assert lam_err < 1e-7
+    assert res[iso].max() < 1e-10
+    assert res.max() < 5e-6
+    assert sub_err < 1e-9

@@ -254,3 +254,30 @@ def test_validate_flags_bad_graphs(sk):
     sk.sne_status_reset(ws)
     sk.sne_validate_csr(Gc, ws)
     assert sk.sne_status(ws) == sk.SNE_ERR_GRAPH
+
+
+@pytest.fixture(scope="module")
+def cl_k256():
+    """Chung-Lu n = 30,000 (mean degree 20, exponent 2.1) at the benchmark's
+    k = 256, d = 128, h = 272, l = 1128: several row blocks, 2176 sketch
+    columns and ~7,800 unique O rows, small enough for the dense oracle."""
+    g = synth.chung_lu(30_000, 20.0, 2.1, seed=3)
+    p = o.Params(k=256, d=128, q=3)
+    A = o.adjacency(g.row_ptr, g.col_idx, g.n)
+    U, lam = o.freigs(o.normalized_operator(A, 0.5), p.k, p.q, p.s_eig, p.seed)
+    U = U.astype(np.float32).astype(np.float64)
+    pr = p.resolved()
+    fac = o.netmf_factors(U, lam, o.degrees(A), o.volume(A), pr.alpha, pr.T, pr.b)
+    S = o.gen_sparse_sign(g.n, pr.h, pr.zeta, pr.seed, o.STREAM_S)
+    O = o.gen_sparse_sign(g.n, pr.l, pr.zeta, pr.seed, o.STREAM_O)
+    return g, p, U, lam, o.sketch_Y_rows(fac.Lp, fac.Rp, S), o.sketch_Z(fac.Lp, fac.Rp, O), S, O
+
+
+def test_sketch_k256_matches_oracle(sk, cl_k256):
+    g, p, U, lam, Yref, Zref, S, O = cl_k256
+    Y, Z, _, _, st = run_sketch(sk, g, p, U, lam, want_E=False)
+    assert st.v_s == len(S.p) and st.v_o == len(O.p)
+    ey, ez = rel(Y, Yref), rel(Z, Zref)
+    print(f"k=256 sketch: Y rel {ey:.2e}, Z rel {ez:.2e}")
+    assert ey < SKETCH_RTOL
+    assert ez < SKETCH_RTOL
