@@ -449,7 +449,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cl1m", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
-    ap.add_argument("--orth", default="eigsvd", choices=["eigsvd", "cholqr"])
+    ap.add_argument("--orth", default="cholqr", choices=["eigsvd", "cholqr"],
+                    help="orthonormalization inside freigs (Alg. 5): Cholesky QR (default) or "
+                         "eigSVD as printed; both give the same subspace")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-seconds", type=float, default=8.0)

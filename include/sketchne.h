@@ -150,10 +150,15 @@ int sne_degrees(const sne_csr *g, float *deg, double *vol, sne_stream_t stream);
 /* out_i = deg_i^beta, 0 where deg_i = 0 (FP32 [n]). */
 int sne_degree_power(const float *deg, int64_t n, double beta, float *out, sne_stream_t stream);
 
-/* One SpMM of Alg. 5: Y = D^-a A D^-a B, given dpow_i = d_i^-a.  B, Y: n x ncols
- * FP32, distinct buffers. */
-int sne_spmm(const sne_csr *g, const float *dpow, const float *B, int32_t ncols, float *Y,
-             sne_stream_t stream);
+/* Per-nonzero weights of X = D^-a A D^-a for sne_spmm: w_nz[p] = dpow[col_p]
+ * * val_p (val_p = 1 for an unweighted graph); w_nz: nnz FP32. */
+int sne_spmm_weights(const sne_csr *g, const float *dpow, float *w_nz, sne_stream_t stream);
+
+/* One SpMM of Alg. 5: Y = D^-a A D^-a B, given dpow_i = d_i^-a and optionally
+ * the per-nonzero weights of sne_spmm_weights (NULL: formed on the fly, one
+ * more dependent load per nonzero).  B, Y: n x ncols FP32, distinct buffers. */
+int sne_spmm(const sne_csr *g, const float *dpow, const float *w_nz, const float *B, int32_t ncols,
+             float *Y, sne_stream_t stream);
 
 /* Checks the CSR on the device (monotone row_ptr, indices in range, symmetric
  * pattern and weights) and records SNE_ERR_GRAPH in the workspace status word

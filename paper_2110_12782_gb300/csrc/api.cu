@@ -76,7 +76,7 @@ struct Bump {
 
 struct Bufs {
   Ctrl *ctrl;
-  float *deg, *dpow, *rsc, *rsc_lo, *wgt;
+  float *deg, *dpow, *wnz, *rsc, *rsc_lo, *wgt;
   float *A, *B, *C;  // tall buffers
   float *partial;
   double *m64[5];
@@ -107,6 +107,7 @@ size_t carve(const Dims &D, int mode, void *base, Bufs *b) {
   const int64_t n = D.n;
   x.deg = bp.take<float>(n);
   x.dpow = bp.take<float>(n);
+  x.wnz = mode != SNE_WS_SKETCH ? bp.take<float>((size_t)D.nnz) : nullptr;
   x.rsc = bp.take<float>(n);
   x.rsc_lo = bp.take<float>(n);
   x.wgt = bp.take<float>(n);
@@ -305,13 +306,14 @@ int run_freigs(const sne_csr &g, const sne_params &p, const Dims &D, const Bufs 
   const int64_t ld = D.Wab;
   float *Q = b.A, *T1 = b.B, *T2 = b.C;
   CK(launch_degree_power(b.deg, D.n, -p.alpha, b.dpow, 1.0f, st));
+  CK(launch_spmm_weights(g, b.dpow, b.wnz, st));                  // d_j^-alpha a_ij per nonzero
   CK(launch_gaussian(D.n, K, p.seed, 1, T1, ld, st));              // Omega
-  CK(launch_spmm(g, b.dpow, T1, ld, K, T2, K, st));                // Y = X Omega
+  CK(launch_spmm(g, b.dpow, b.wnz, T1, ld, K, T2, K, st));                // Y = X Omega
   int rc = orth_tall(D, b, p.orth, false, T2, K, K, Q, ld, st);    // Q = eigSVD(Y)
   if (rc) return rc;
   for (int it = 0; it < p.q; ++it) {
-    CK(launch_spmm(g, b.dpow, Q, ld, K, T1, ld, st));              // X Q
-    CK(launch_spmm(g, b.dpow, T1, ld, K, T2, K, st));              // X X Q
+    CK(launch_spmm(g, b.dpow, b.wnz, Q, ld, K, T1, ld, st));              // X Q
+    CK(launch_spmm(g, b.dpow, b.wnz, T1, ld, K, T2, K, st));              // X X Q
     rc = orth_tall(D, b, p.orth, false, T2, K, K, Q, ld, st);      // Q = eigSVD(X X Q)
     if (rc) return rc;
   }
@@ -323,7 +325,7 @@ int run_freigs(const sne_csr &g, const sne_params &p, const Dims &D, const Bufs 
   rc = orth_tall(D, b, SNE_ORTH_CHOLQR, false, T2, K, K, Q, ld, st);
   if (rc) return rc;
   // Rayleigh-Ritz: S = Q^T X Q (FP64), eig(S), U = Q U_hat, top k by |lambda|
-  CK(launch_spmm(g, b.dpow, Q, ld, K, T1, ld, st));
+  CK(launch_spmm(g, b.dpow, b.wnz, Q, ld, K, T1, ld, st));
   CK(launch_gram(Q, ld, K, T1, ld, K, D.n, nullptr, false, b.partial, b.m64[0], K, st, b.ctrl));
   CK(launch_symmetrize(b.m64[0], K, K, st));
   CK(launch_sym_eig<double>(b.m64[0], K, K, b.w64, b.m64[1], K, b.eigscr, b.ctrl, st));
@@ -556,12 +558,20 @@ int sne_degree_power(const float *deg, int64_t n, double beta, float *out, sne_s
              : SNE_ERR_CUDA;
 }
 
-int sne_spmm(const sne_csr *g, const float *dpow, const float *B, int32_t ncols, float *Y,
-             sne_stream_t stream) {
+int sne_spmm_weights(const sne_csr *g, const float *dpow, float *w_nz, sne_stream_t stream) {
+  int rc = check_graph(g);
+  if (rc) return rc;
+  if (!dpow || (!w_nz && g->nnz > 0)) return SNE_ERR_ARG;
+  return launch_spmm_weights(*g, dpow, w_nz, (cudaStream_t)stream) == cudaSuccess ? SNE_OK
+                                                                                 : SNE_ERR_CUDA;
+}
+
+int sne_spmm(const sne_csr *g, const float *dpow, const float *w_nz, const float *B, int32_t ncols,
+             float *Y, sne_stream_t stream) {
   int rc = check_graph(g);
   if (rc) return rc;
   if (!dpow || !B || !Y || ncols <= 0 || B == Y) return SNE_ERR_ARG;
-  return launch_spmm(*g, dpow, B, ncols, ncols, Y, ncols, (cudaStream_t)stream) == cudaSuccess
+  return launch_spmm(*g, dpow, w_nz, B, ncols, ncols, Y, ncols, (cudaStream_t)stream) == cudaSuccess
              ? SNE_OK
              : SNE_ERR_CUDA;
 }

@@ -572,12 +572,13 @@ __global__ void __launch_bounds__(1024) cholesky_upper_kernel(T *A, int n, int l
     const T inv = piv;
     for (int c = j + 1 + tid; c < n; c += nt) A[(int64_t)j * lda + c] *= inv;
     __syncthreads();
-    // trailing update of the upper triangle: A[r][c] -= R[j][r] R[j][c], j < r <= c
-    const int m = n - j - 1;
-    const int64_t cnt = (int64_t)m * m;
-    for (int64_t e = tid; e < cnt; e += nt) {
-      const int r = j + 1 + (int)(e / m), c = j + 1 + (int)(e % m);
-      if (c >= r) A[(int64_t)r * lda + c] -= A[(int64_t)j * lda + r] * A[(int64_t)j * lda + c];
+    // trailing update of the upper triangle: A[r][c] -= R[j][r] R[j][c], j < r <= c;
+    // warp per row r, lanes over c (coalesced, no index division)
+    const T *rj = A + (int64_t)j * lda;
+    for (int r = j + 1 + (tid >> 5); r < n; r += (nt >> 5)) {
+      const T f = rj[r];
+      T *ar = A + (int64_t)r * lda;
+      for (int c = r + (tid & 31); c < n; c += 32) ar[c] -= f * rj[c];
     }
     __syncthreads();
   }

@@ -340,13 +340,15 @@ __device__ __forceinline__ int packed_upper(int n, int i, int j) {  // j >= i
   return i * n - i * (i - 1) / 2 + (j - i);
 }
 
+constexpr int kCholColBufs = 16;  // warps that build columns of R^-1 at once
+
 template <typename T>
 __global__ void __launch_bounds__(1024) chol_inv_packed_kernel(const T *__restrict__ A, int n, int lda,
                                                                T *__restrict__ Rinv, int ldi,
                                                                Ctrl *ctrl) {
   extern __shared__ __align__(16) unsigned char csm[];
   T *U = reinterpret_cast<T *>(csm);       // n(n+1)/2
-  T *tmp = U + n * (n + 1) / 2;            // n
+  T *tmp = U + n * (n + 1) / 2;            // kCholColBufs columns of n
   __shared__ T piv;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int i = 0; i < n; ++i)
@@ -377,29 +379,40 @@ __global__ void __launch_bounds__(1024) chol_inv_packed_kernel(const T *__restri
     }
     __syncthreads();
   }
-  // in-place inverse of the upper triangular factor, column by column
-  for (int j = 0; j < n; ++j) {
-    for (int k = tid; k < j; k += nt) tmp[k] = U[packed_upper(n, k, j)];
-    __syncthreads();
-    const T xjj = T(1) / U[packed_upper(n, j, j)];
-    for (int i = tid; i < j; i += nt) {
-      T s = 0;
-      for (int k = i; k < j; ++k) s += U[packed_upper(n, i, k)] * tmp[k];
-      U[packed_upper(n, i, j)] = -xjj * s;
+  // X = R^-1 (upper triangular) by back substitution, one warp per column:
+  // X[j][j] = 1 / R[j][j], X[i][j] = -(sum_{k=i+1..j} R[i][k] X[k][j]) / R[i][i]
+  // for i = j-1 .. 0; the warp splits each sum over its lanes.
+  {
+    const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+    T *xcol = tmp + (size_t)(warp % kCholColBufs) * n;
+    if (warp < kCholColBufs) {
+      for (int j = warp; j < n; j += min(nw, kCholColBufs)) {
+        if (lane == 0) xcol[j] = T(1) / U[packed_upper(n, j, j)];
+        __syncwarp();
+        for (int i = j - 1; i >= 0; --i) {
+          const T *urow = U + packed_upper(n, i, i) - i;  // urow[k] = R[i][k], k >= i
+          T s = 0;
+          for (int k = i + 1 + lane; k <= j; k += 32) s += urow[k] * xcol[k];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+          if (lane == 0) xcol[i] = -s / urow[i];
+          __syncwarp();
+        }
+        for (int i = lane; i < n; i += 32) Rinv[(int64_t)i * ldi + j] = (i <= j) ? xcol[i] : T(0);
+        __syncwarp();
+      }
     }
-    __syncthreads();
-    if (tid == 0) U[packed_upper(n, j, j)] = xjj;
-    __syncthreads();
-  }
-  for (int64_t q = tid; q < (int64_t)n * n; q += nt) {
-    const int i = (int)(q / n), j = (int)(q % n);
-    Rinv[(int64_t)i * ldi + j] = (j >= i) ? U[packed_upper(n, i, j)] : T(0);
   }
 }
 
 template <typename T>
+size_t chol_inv_smem(int n) {
+  return ((size_t)n * (n + 1) / 2 + (size_t)kCholColBufs * n) * sizeof(T);
+}
+
+template <typename T>
 bool chol_inv_fits(int n) {
-  return ((size_t)n * (n + 1) / 2 + n) * sizeof(T) <= 200 * 1024;
+  return chol_inv_smem<T>(n) <= 220 * 1024;
 }
 
 template <typename T>
@@ -407,7 +420,7 @@ cudaError_t launch_chol_inverse(const T *A, int32_t n, int32_t lda, T *Rinv, int
                                 Ctrl *ctrl, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   if (chol_inv_fits<T>(n)) {
-    const size_t smem = ((size_t)n * (n + 1) / 2 + n) * sizeof(T);
+    const size_t smem = chol_inv_smem<T>(n);
     cudaError_t e = cudaFuncSetAttribute(chol_inv_packed_kernel<T>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -67,11 +67,14 @@ cudaError_t launch_degree_power(const float *deg, int64_t n, double beta, float 
 // Y[i, :] = s_i * sum_{p in row i} w_p s_{col_p} B[col_p, :],  s = d^-a.
 // One warp per row; each lane owns VPL float4 column groups of the row; the
 // row's (col, weight) pairs are fetched 32 at a time and broadcast by shuffle.
+// On power-law graphs the dense operand does not fit in L2 and the kernel is
+// bound by the latency of its gathers: the per-nonzero weights come
+// precomputed (one dependent load less) and two blocks stay resident per SM.
 template <int VPL>
-__global__ void __launch_bounds__(256) spmm_vec4_kernel(
+__global__ void __launch_bounds__(256, 2) spmm_vec4_kernel(
     int64_t n, const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
-    const float *__restrict__ val, const float *__restrict__ dpow, const float *__restrict__ B,
-    int64_t ldb, int32_t nvec, float *__restrict__ Y, int64_t ldy) {
+    const float *__restrict__ val, const float *__restrict__ dpow, const float *__restrict__ wnz,
+    const float *__restrict__ B, int64_t ldb, int32_t nvec, float *__restrict__ Y, int64_t ldy) {
   const int lane = threadIdx.x & 31;
   const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (row >= n) return;
@@ -85,7 +88,7 @@ __global__ void __launch_bounds__(256) spmm_vec4_kernel(
     float w = 0.f;
     if (p < end) {
       c = col[p];
-      w = dpow[c] * (val ? val[p] : 1.0f);
+      w = wnz ? wnz[p] : dpow[c] * (val ? val[p] : 1.0f);
     }
     const int cnt = (int)min64(32, end - p0);
     int t = 0;
@@ -167,8 +170,24 @@ __global__ void __launch_bounds__(256) spmm_scalar_kernel(
   }
 }
 
-cudaError_t launch_spmm(const sne_csr &g, const float *dpow, const float *B, int64_t ldb,
-                        int32_t ncols, float *Y, int64_t ldy, cudaStream_t st) {
+__global__ void spmm_weights_kernel(int64_t nnz, const int32_t *__restrict__ col,
+                                    const float *__restrict__ val, const float *__restrict__ dpow,
+                                    float *__restrict__ wnz) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += stride)
+    wnz[p] = dpow[col[p]] * (val ? val[p] : 1.0f);
+}
+
+cudaError_t launch_spmm_weights(const sne_csr &g, const float *dpow, float *wnz, cudaStream_t st) {
+  if (g.nnz <= 0) return cudaSuccess;
+  ProfScope ps_(K_MISC, st);
+  spmm_weights_kernel<<<(unsigned)min64(152 * 16, (g.nnz + 255) / 256), 256, 0, st>>>(
+      g.nnz, g.col_idx, g.val, dpow, wnz);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spmm(const sne_csr &g, const float *dpow, const float *wnz, const float *B,
+                        int64_t ldb, int32_t ncols, float *Y, int64_t ldy, cudaStream_t st) {
   if (g.n <= 0 || ncols <= 0) return cudaSuccess;
 
   ProfScope ps_(K_SPMM, st);
@@ -180,8 +199,8 @@ cudaError_t launch_spmm(const sne_csr &g, const float *dpow, const float *B, int
     const int vpl = (nvec + 31) / 32;
 #define SNE_SPMM_CASE(V)                                                                     \
   case V:                                                                                    \
-    spmm_vec4_kernel<V><<<blocks, 256, 0, st>>>(g.n, g.row_ptr, g.col_idx, g.val, dpow, B, ldb, \
-                                                nvec, Y, ldy);                               \
+    spmm_vec4_kernel<V><<<blocks, 256, 0, st>>>(g.n, g.row_ptr, g.col_idx, g.val, dpow, wnz, B, \
+                                                ldb, nvec, Y, ldy);                          \
     break;
     switch (vpl) {
       SNE_SPMM_CASE(1)

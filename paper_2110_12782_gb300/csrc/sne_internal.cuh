@@ -104,8 +104,11 @@ cudaError_t launch_unique(const int32_t *keys, int32_t count, int32_t *uniq, int
 cudaError_t launch_degrees(const sne_csr &g, float *deg, double *vol, cudaStream_t st);
 cudaError_t launch_degree_power(const float *deg, int64_t n, double beta, float *out, float scale,
                                 cudaStream_t st);
-cudaError_t launch_spmm(const sne_csr &g, const float *dpow, const float *B, int64_t ldb,
-                        int32_t ncols, float *Y, int64_t ldy, cudaStream_t st);
+// wnz: per-nonzero weights dpow[col_p] * val_p (launch_spmm_weights), or NULL
+// to form them on the fly.
+cudaError_t launch_spmm_weights(const sne_csr &g, const float *dpow, float *wnz, cudaStream_t st);
+cudaError_t launch_spmm(const sne_csr &g, const float *dpow, const float *wnz, const float *B,
+                        int64_t ldb, int32_t ncols, float *Y, int64_t ldy, cudaStream_t st);
 cudaError_t launch_validate(const sne_csr &g, Ctrl *ctrl, cudaStream_t st);
 
 // dense.cu

@@ -36,7 +36,7 @@ SNE_WS_EMBED, SNE_WS_FREIGS, SNE_WS_SKETCH, SNE_WS_EMBED_HOST = 0, 1, 2, 3
 EXPORTS = [
     "sne_params_init", "sne_error_string", "sne_workspace_bytes", "sne_embed", "sne_freigs",
     "sne_sketch_from_factors", "sne_sparse_sign", "sne_gaussian", "sne_degrees",
-    "sne_degree_power", "sne_spmm", "sne_validate_csr", "sne_status_reset", "sne_status",
+    "sne_degree_power", "sne_spmm_weights", "sne_spmm", "sne_validate_csr", "sne_status_reset", "sne_status",
     "sne_stats_read", "sne_embed_host", "sne_kernel_launches", "sne_profile_start",
     "sne_profile_stop", "sne_freigs_static", "sne_gram_workspace_bytes", "sne_gram",
     "sne_tall_gemm_workspace_bytes", "sne_tall_gemm", "sne_sym_eig_workspace_bytes", "sne_sym_eig",
@@ -99,7 +99,8 @@ def lib() -> ctypes.CDLL:
             "sne_gaussian": [i64, i32, u64, i32, vp, vp],
             "sne_degrees": [P(sne_csr), vp, vp, vp],
             "sne_degree_power": [vp, i64, dbl, vp, vp],
-            "sne_spmm": [P(sne_csr), vp, vp, i32, vp, vp],
+            "sne_spmm_weights": [P(sne_csr), vp, vp, vp],
+            "sne_spmm": [P(sne_csr), vp, vp, vp, i32, vp, vp],
             "sne_validate_csr": [P(sne_csr), vp, ctypes.c_size_t, vp],
             "sne_status_reset": [vp, vp],
             "sne_status": [vp, vp],
@@ -250,10 +251,17 @@ def sne_degree_power(deg: torch.Tensor, beta: float, out: torch.Tensor, stream=N
            "sne_degree_power")
 
 
-def sne_spmm(g: DeviceGraph, dpow: torch.Tensor, B: torch.Tensor, Y: torch.Tensor, stream=None) -> None:
+def sne_spmm_weights(g: DeviceGraph, dpow: torch.Tensor, w_nz: torch.Tensor, stream=None) -> None:
+    _check(lib().sne_spmm_weights(ctypes.byref(g.csr), _ptr(dpow, torch.float32, "dpow"),
+                                  _ptr(w_nz, torch.float32, "w_nz"), _stream(stream)),
+           "sne_spmm_weights")
+
+
+def sne_spmm(g: DeviceGraph, dpow: torch.Tensor, B: torch.Tensor, Y: torch.Tensor,
+             w_nz: torch.Tensor | None = None, stream=None) -> None:
     _check(lib().sne_spmm(ctypes.byref(g.csr), _ptr(dpow, torch.float32, "dpow"),
-                          _ptr(B, torch.float32, "B"), B.shape[1], _ptr(Y, torch.float32, "Y"),
-                          _stream(stream)), "sne_spmm")
+                          _ptr(w_nz, torch.float32, "w_nz", True), _ptr(B, torch.float32, "B"),
+                          B.shape[1], _ptr(Y, torch.float32, "Y"), _stream(stream)), "sne_spmm")
 
 
 def sne_validate_csr(g: DeviceGraph, ws: torch.Tensor, stream=None) -> None:

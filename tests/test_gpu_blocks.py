@@ -173,3 +173,37 @@ def test_sym_eig_clustered(sk, n):
     assert res[iso].max() < 1e-10
     assert res.max() < 5e-6
     assert sub_err < 1e-9
+
+
+@pytest.mark.parametrize("weights", [False, True])
+@pytest.mark.parametrize("width", [272, 144, 36])
+def test_spmm_fullsize(sk, width, weights):
+    """X B with X = D^-1/2 A D^-1/2 on the Chung-Lu graph of the benchmark
+    (n = 1,000,000, mean degree 20, exponent 2.1; the hubs are the first rows):
+    sampled rows, hubs included, against FP64."""
+    from oracle import sketchne_oracle as o
+    from paper_2110_12782_gb300 import synth
+    g = synth.chung_lu(1_000_000, 20.0, 2.1, seed=0)
+    G = sk.DeviceGraph.from_numpy(g.row_ptr, g.col_idx)
+    deg = torch.empty(g.n, device="cuda")
+    vol = torch.empty(1, dtype=torch.float64, device="cuda")
+    sk.sne_degrees(G, deg, vol)
+    dpow = torch.empty(g.n, device="cuda")
+    sk.sne_degree_power(deg, -0.5, dpow)
+    rng = np.random.default_rng(width)
+    B = rng.standard_normal((g.n, width)).astype(np.float32)
+    Y = torch.empty(g.n, width, device="cuda")
+    w_nz = None
+    if weights:
+        w_nz = torch.empty(g.nnz, device="cuda")
+        sk.sne_spmm_weights(G, dpow, w_nz)
+    sk.sne_spmm(G, dpow, torch.from_numpy(B).cuda(), Y, w_nz=w_nz)
+    rows = np.unique(np.concatenate([np.arange(64), np.arange(g.n - 64, g.n),
+                                     rng.choice(g.n, 4096, replace=False)]))
+    X = o.normalized_operator(o.adjacency(g.row_ptr, g.col_idx, g.n), 0.5)
+    ref = X[rows] @ B.astype(np.float64)
+    got = Y[torch.as_tensor(rows, device="cuda")].cpu().numpy()
+    scale = np.sqrt(abs(X[rows]).power(2) @ (B.astype(np.float64) ** 2)) + 1e-30
+    err = float(np.max(np.abs(got - ref) / scale))
+    print(f"spmm n=1M width {width}: {err:.2e}")
+    assert err < 1e-5
