@@ -119,6 +119,27 @@ int sne_embed(const sne_csr *g, const sne_params *p, void *workspace, size_t ws_
 int sne_embed_host(const sne_csr *g_host, const sne_params *p, void *workspace, size_t ws_bytes,
                    float *E_host, double *sigma_host, sne_stream_t stream);
 
+/* Alg. 6 lines 1-5 for a batch of G independent graphs (many graphs of uneven
+ * sizes, one call).  graphs: HOST array of G sne_csr (each with device arrays);
+ * E, sigma: HOST arrays of G device pointers (E[i]: n_i x d FP32, sigma[i]: d
+ * FP64); status: DEVICE int32 [G] receiving each graph's status word, or NULL.
+ * The paper embeds one graph per call; this entry point has no counterpart
+ * there.  The graphs run concurrently on `lanes` streams forked from `stream`
+ * (0 = the library's choice, at most 16): largest first, each on the lane
+ * with the least estimated work, and the caller's stream waits for all of
+ * them, so the outputs are complete when `stream` reaches the end of the call.
+ * Each graph's results equal those of sne_embed on that graph.  The lanes are
+ * created on the first call on a device (make it before any stream capture);
+ * after that the call enqueues work only, and a batch can be captured into a
+ * CUDA graph.  Workspace: sne_embed_batched_workspace_bytes (same G, graphs,
+ * p and lanes); every lane owns a slice sized for its largest graph.  Errors:
+ * those of sne_embed, checked for every graph before anything is enqueued. */
+int sne_embed_batched_workspace_bytes(int32_t G, const sne_csr *graphs, const sne_params *p,
+                                      int32_t lanes, size_t *bytes);
+int sne_embed_batched(int32_t G, const sne_csr *graphs, const sne_params *p, int32_t lanes,
+                      void *workspace, size_t ws_bytes, float *const *E, double *const *sigma,
+                      int32_t *status, sne_stream_t stream);
+
 /* Alg. 5 on X = D^-alpha A D^-alpha: U: n x k FP32 (orthonormal columns),
  * lambda: k FP64, ordered by |lambda| descending. */
 int sne_freigs(const sne_csr *g, const sne_params *p, void *workspace, size_t ws_bytes,

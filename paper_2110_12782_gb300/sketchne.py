@@ -40,6 +40,7 @@ EXPORTS = [
     "sne_stats_read", "sne_embed_host", "sne_kernel_launches", "sne_profile_start",
     "sne_profile_stop", "sne_freigs_static", "sne_gram_workspace_bytes", "sne_gram",
     "sne_tall_gemm_workspace_bytes", "sne_tall_gemm", "sne_sym_eig_workspace_bytes", "sne_sym_eig",
+    "sne_embed_batched_workspace_bytes", "sne_embed_batched",
 ]
 
 
@@ -116,6 +117,10 @@ def lib() -> ctypes.CDLL:
             "sne_tall_gemm": [i64, i32, i32, vp, i64, vp, i32, vp, i64, vp, ctypes.c_size_t, vp],
             "sne_sym_eig_workspace_bytes": [i32, P(ctypes.c_size_t)],
             "sne_sym_eig": [i32, vp, i32, vp, vp, i32, vp, ctypes.c_size_t, vp],
+            "sne_embed_batched_workspace_bytes": [i32, P(sne_csr), P(sne_params), i32,
+                                                  P(ctypes.c_size_t)],
+            "sne_embed_batched": [i32, P(sne_csr), P(sne_params), i32, vp, ctypes.c_size_t,
+                                  P(ctypes.c_void_p), P(ctypes.c_void_p), vp, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -405,3 +410,33 @@ def sne_sym_eig(S: torch.Tensor, lam: torch.Tensor, V: torch.Tensor, ws: torch.T
     _check(lib().sne_sym_eig(n, S.data_ptr(), _row_stride(S, "S"), _ptr(lam, torch.float64, "lambda"),
                              V.data_ptr(), _row_stride(V, "V"), _ptr(ws, torch.uint8, "workspace"),
                              ws.numel(), _stream(stream)), "sne_sym_eig")
+
+
+# ----------------------------------------------------------------------------- batches of graphs
+def _csr_array(graphs):
+    arr = (sne_csr * len(graphs))()
+    for i, g in enumerate(graphs):
+        arr[i] = g.csr
+    return arr
+
+
+def batched_workspace(graphs, p: sne_params, lanes: int = 0, device="cuda") -> torch.Tensor:
+    nb = ctypes.c_size_t(0)
+    _check(lib().sne_embed_batched_workspace_bytes(len(graphs), _csr_array(graphs), ctypes.byref(p),
+                                                   lanes, ctypes.byref(nb)),
+           "sne_embed_batched_workspace_bytes")
+    return _aligned_bytes(nb.value, device)
+
+
+def sne_embed_batched(graphs, p: sne_params, ws: torch.Tensor, E, sigma, status: torch.Tensor | None = None,
+                      lanes: int = 0, stream=None) -> None:
+    """Alg. 6 lines 1-5 for every DeviceGraph of ``graphs`` (outputs E[i], sigma[i])."""
+    G = len(graphs)
+    if len(E) != G or len(sigma) != G:
+        raise ValueError("one E and one sigma per graph")
+    e_ptrs = (ctypes.c_void_p * G)(*[_ptr(e, torch.float32, "E") for e in E])
+    s_ptrs = (ctypes.c_void_p * G)(*[_ptr(s_, torch.float64, "sigma") for s_ in sigma])
+    _check(lib().sne_embed_batched(G, _csr_array(graphs), ctypes.byref(p), lanes,
+                                   _ptr(ws, torch.uint8, "workspace"), ws.numel(), e_ptrs, s_ptrs,
+                                   _ptr(status, torch.int32, "status", True), _stream(stream)),
+           "sne_embed_batched")
