@@ -289,7 +289,10 @@ int orth_tall(const Dims &D, const Bufs &b, int method, bool fp64, const float *
                                                                    w, b.ctrl); }
     CK(cudaGetLastError());
   } else if (fp64) {
-    CK(launch_chol_inverse<double>(b.m64[0], w, w, b.m64[1], w, b.m64[2], b.ctrl, st));
+    // pivoted, cut at 1e-8 of the largest diagonal: Y is rank-deficient when
+    // trunc_log(L'R') has rank below h (a graph with more components than
+    // sketch columns); then the trailing columns of Q are zero
+    CK(launch_chol_inverse<double>(b.m64[0], w, w, b.m64[1], w, b.m64[2], b.ctrl, st, 1e-8));
     CK(launch_d2f(b.m64[1], w, w, w, b.m32[2], w, st));
   } else {
     CK(launch_d2f(b.m64[0], w, w, w, b.m32[0], w, st));
@@ -423,7 +426,10 @@ int run_sketch(const sne_csr &g, const sne_params &p, const Dims &D, const Bufs 
   CK(launch_small_gemm<double>(false, false, l, h, h, 1.0, b.Tm, h, b.m64[4], h, 0.0, b.G64, h, st));
   CK(launch_f2d(Z, l, l, l, b.Z64, l, st));
   CK(launch_small_gemm<double>(true, false, h, h, l, 1.0, b.G64, h, b.G64, h, 0.0, b.m64[0], h, st));
-  CK(launch_chol_inverse<double>(b.m64[0], h, h, b.m64[1], h, b.m64[2], b.ctrl, st));  // R^-1, G^T G = R^T R
+  // (G^T G)^+ = M M^T with M = P R^-1 from the pivoted Cholesky G^T G = P R^T R P^T;
+  // zero columns of G (directions Q lacks) are cut, which gives the
+  // minimum-norm least-squares solutions
+  CK(launch_chol_inverse<double>(b.m64[0], h, h, b.m64[1], h, b.m64[2], b.ctrl, st, 1e-12));
   CK(launch_small_gemm<double>(false, true, h, h, h, 1.0, b.m64[1], h, b.m64[1], h, 0.0, b.m64[2], h,
                                st));                                               // (G^T G)^-1
   CK(launch_small_gemm<double>(false, true, h, l, h, 1.0, b.m64[2], h, b.G64, h, 0.0, b.Gp, l, st));

@@ -549,97 +549,6 @@ template cudaError_t launch_small_gemm<double>(bool, bool, int32_t, int32_t, int
                                                double, double *, int32_t, cudaStream_t, const int *);
 
 // ---------------------------------------------------------------------------
-// Cholesky A = R^T R (R upper triangular, written over A, zeros below).
-// Right-looking, one CTA; a non-positive or non-finite pivot is recorded as
-// SNE_ERR_NUMERIC and replaced by 1 so that the rest stays finite.
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(1024) cholesky_upper_kernel(T *A, int n, int lda, Ctrl *ctrl) {
-  __shared__ T piv;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int j = 0; j < n; ++j) {
-    if (tid == 0) {
-      T d = A[(int64_t)j * lda + j];
-      if (!(d > T(0)) || !isfinite((double)d)) {
-        record_error(ctrl, SNE_ERR_NUMERIC, W_CHOL);
-        d = T(1);
-      }
-      d = sqrt(d);
-      A[(int64_t)j * lda + j] = d;
-      piv = T(1) / d;
-    }
-    __syncthreads();
-    const T inv = piv;
-    for (int c = j + 1 + tid; c < n; c += nt) A[(int64_t)j * lda + c] *= inv;
-    __syncthreads();
-    // trailing update of the upper triangle: A[r][c] -= R[j][r] R[j][c], j < r <= c;
-    // warp per row r, lanes over c (coalesced, no index division)
-    const T *rj = A + (int64_t)j * lda;
-    for (int r = j + 1 + (tid >> 5); r < n; r += (nt >> 5)) {
-      const T f = rj[r];
-      T *ar = A + (int64_t)r * lda;
-      for (int c = r + (tid & 31); c < n; c += 32) ar[c] -= f * rj[c];
-    }
-    __syncthreads();
-  }
-  for (int64_t e = tid; e < (int64_t)n * n; e += nt) {
-    const int r = (int)(e / n), c = (int)(e % n);
-    if (c < r) A[(int64_t)r * lda + c] = T(0);
-  }
-}
-
-template <typename T>
-cudaError_t launch_cholesky_upper(T *A, int32_t n, int32_t lda, Ctrl *ctrl, cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
-  ProfScope ps_(K_CHOL, st);
-  cholesky_upper_kernel<T><<<1, 1024, 0, st>>>(A, n, lda, ctrl);
-  return cudaGetLastError();
-}
-template cudaError_t launch_cholesky_upper<float>(float *, int32_t, int32_t, Ctrl *, cudaStream_t);
-template cudaError_t launch_cholesky_upper<double>(double *, int32_t, int32_t, Ctrl *, cudaStream_t);
-
-// Rinv = R^-1 for upper triangular R: one warp per column c solves R x = e_c
-// by back substitution, x kept in shared memory, dot products across lanes.
-template <typename T>
-__global__ void __launch_bounds__(256) triu_inverse_kernel(const T *__restrict__ R, int n, int ldr,
-                                                           T *__restrict__ X, int ldx, Ctrl *ctrl) {
-  extern __shared__ __align__(16) unsigned char tri_smem[];
-  T *xs = reinterpret_cast<T *>(tri_smem) + (threadIdx.x >> 5) * n;
-  const int lane = threadIdx.x & 31;
-  const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (c >= n) return;
-  for (int i = c; i >= 0; --i) {
-    T s = 0;
-    for (int k = i + 1 + lane; k <= c; k += 32) s += R[(int64_t)i * ldr + k] * xs[k];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) {
-      const T d = R[(int64_t)i * ldr + i];
-      if (d == T(0)) record_error(ctrl, SNE_ERR_NUMERIC, W_TRIINV);
-      xs[i] = ((i == c ? T(1) : T(0)) - s) / d;
-    }
-    __syncwarp();
-  }
-  for (int i = lane; i < n; i += 32) X[(int64_t)i * ldx + c] = i <= c ? xs[i] : T(0);
-}
-
-template <typename T>
-cudaError_t launch_triu_inverse(const T *R, int32_t n, int32_t ldr, T *Rinv, int32_t ldi,
-                                Ctrl *ctrl, cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
-  const size_t smem = (size_t)8 * n * sizeof(T);
-  cudaError_t e = cudaFuncSetAttribute(triu_inverse_kernel<T>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  ProfScope ps_(K_TRIINV, st);
-  triu_inverse_kernel<T><<<ceil_div(n, 8), 256, smem, st>>>(R, n, ldr, Rinv, ldi, ctrl);
-  return cudaGetLastError();
-}
-template cudaError_t launch_triu_inverse<float>(const float *, int32_t, int32_t, float *, int32_t,
-                                                Ctrl *, cudaStream_t);
-template cudaError_t launch_triu_inverse<double>(const double *, int32_t, int32_t, double *,
-                                                 int32_t, Ctrl *, cudaStream_t);
-
-// ---------------------------------------------------------------------------
 // Symmetric eigendecomposition, one CTA of 1024 threads.
 //  1. Householder tridiagonalization: for column k, the reflector
 //     H_k = I - 2 v v^T (|v| = 1) maps A[k+1:, k] to alpha e_1; the trailing

@@ -342,104 +342,194 @@ __device__ __forceinline__ int packed_upper(int n, int i, int j) {  // j >= i
 
 constexpr int kCholColBufs = 16;  // warps that build columns of R^-1 at once
 
-template <typename T>
-__global__ void __launch_bounds__(1024) chol_inv_packed_kernel(const T *__restrict__ A, int n, int lda,
-                                                               T *__restrict__ Rinv, int ldi,
-                                                               Ctrl *ctrl) {
+// Upper-triangle storage of the matrix being factored: packed in shared memory
+// when it fits, else dense (row-major, leading dimension n) in global scratch.
+template <typename T, bool PACKED>
+struct CholStore {
+  T *base;
+  int n;
+  __device__ __forceinline__ T &at(int i, int j) const {  // i <= j
+    return PACKED ? base[packed_upper(n, i, j)] : base[(int64_t)i * n + j];
+  }
+  __device__ __forceinline__ T *row(int i) const {  // row(i)[c] = at(i, c), c >= i
+    return PACKED ? base + packed_upper(n, i, i) - i : base + (int64_t)i * n;
+  }
+};
+
+// A = R^T R and M = P R^-1 (one CTA).  Without pivoting (tol < 0), P = I and a
+// non-positive or non-finite pivot is recorded as SNE_ERR_NUMERIC and replaced
+// by 1.  With pivoting (tol >= 0; diagonal pivoting as in LAPACK's pstrf), step
+// j swaps the largest remaining diagonal entry into place and the factorization
+// stops at the numerical rank r, the first step whose largest remaining
+// diagonal is at most tol times the largest diagonal of A; then M = P [R11^-1 0;
+// 0 0], so that A^+ = M M^T on the range of A and Y M is an orthonormal basis of
+// range(Y) padded with zero columns (A = Y^T Y).
+template <typename T, bool PACKED>
+__global__ void __launch_bounds__(1024) chol_inv_kernel(const T *__restrict__ A, int n, int lda,
+                                                        T *__restrict__ Rinv, int ldi,
+                                                        T *__restrict__ scratch, double tol,
+                                                        Ctrl *ctrl) {
   extern __shared__ __align__(16) unsigned char csm[];
-  T *U = reinterpret_cast<T *>(csm);       // n(n+1)/2
-  T *tmp = U + n * (n + 1) / 2;            // kCholColBufs columns of n
+  T *packed = reinterpret_cast<T *>(csm);
+  T *colbuf = packed + (PACKED ? (size_t)n * (n + 1) / 2 : 0);  // kCholColBufs x n
+  int *perm = reinterpret_cast<int *>(colbuf + (size_t)kCholColBufs * n);
   __shared__ T piv;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  __shared__ T wmax[32];
+  __shared__ int widx[32];
+  __shared__ int rank_s;
+  __shared__ double dmax0_s;
+  const CholStore<T, PACKED> U{PACKED ? packed : scratch, n};
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const bool pivoting = tol >= 0.0;
   for (int i = 0; i < n; ++i)
-    for (int j = i + tid; j < n; j += nt) U[packed_upper(n, i, j)] = A[(int64_t)i * lda + j];
+    for (int j = i + tid; j < n; j += nt) U.at(i, j) = A[(int64_t)i * lda + j];
+  for (int i = tid; i < n; i += nt) perm[i] = i;
+  if (tid == 0) {
+    rank_s = n;
+    double m = 0.0;
+    for (int i = 0; i < n; ++i) m = fmax(m, (double)A[(int64_t)i * lda + i]);
+    dmax0_s = m;
+  }
   __syncthreads();
-  // right-looking Cholesky
+  const double cut = tol * dmax0_s;
   for (int j = 0; j < n; ++j) {
+    if (pivoting) {
+      // largest remaining diagonal entry
+      T best = -INFINITY;
+      int bi = j;
+      for (int i = j + tid; i < n; i += nt) {
+        const T v = U.at(i, i);
+        if (v > best) {
+          best = v;
+          bi = i;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) {
+          best = ov;
+          bi = oi;
+        }
+      }
+      if (lane == 0) {
+        wmax[warp] = best;
+        widx[warp] = bi;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        T bv = wmax[0];
+        int ib = widx[0];
+        for (int w = 1; w < (nt >> 5); ++w)
+          if (wmax[w] > bv || (wmax[w] == bv && widx[w] < ib)) {
+            bv = wmax[w];
+            ib = widx[w];
+          }
+        widx[0] = ib;
+        if (!((double)bv > cut) || !isfinite((double)bv)) rank_s = j;
+      }
+      __syncthreads();
+      if (rank_s == j) break;
+      const int p = widx[0];
+      if (p != j) {
+        // swap rows and columns j and p of the symmetric matrix (and the
+        // columns j, p of the rows of R already computed)
+        for (int k = tid; k < n; k += nt) {
+          if (k == j || k == p) continue;
+          T &x = k < j ? U.at(k, j) : U.at(j, k);
+          T &y = k < p ? U.at(k, p) : U.at(p, k);
+          const T t = x;
+          x = y;
+          y = t;
+        }
+        if (tid == 0) {
+          const T t = U.at(j, j);
+          U.at(j, j) = U.at(p, p);
+          U.at(p, p) = t;
+          const int q = perm[j];
+          perm[j] = perm[p];
+          perm[p] = q;
+        }
+        __syncthreads();
+      }
+    }
     if (tid == 0) {
-      T d = U[packed_upper(n, j, j)];
+      T d = U.at(j, j);
       if (!(d > T(0)) || !isfinite((double)d)) {
         record_error(ctrl, SNE_ERR_NUMERIC, W_CHOL);
         d = T(1);
       }
       d = sqrt(d);
-      U[packed_upper(n, j, j)] = d;
+      U.at(j, j) = d;
       piv = T(1) / d;
     }
     __syncthreads();
     const T inv = piv;
-    for (int c = j + 1 + tid; c < n; c += nt) U[packed_upper(n, j, c)] *= inv;
+    for (int c = j + 1 + tid; c < n; c += nt) U.at(j, c) *= inv;
     __syncthreads();
     // trailing update U(r, c) -= U(j, r) U(j, c), j < r <= c: warp per row r
-    for (int rr = j + 1 + (tid >> 5); rr < n; rr += (nt >> 5)) {
-      const T ujr = U[packed_upper(n, j, rr)];
-      T *urow = U + packed_upper(n, rr, rr) - rr;  // urow[c] = U(rr, c) for c >= rr
-      const T *ujrow = U + packed_upper(n, j, j) - j;
-      for (int cc = rr + (tid & 31); cc < n; cc += 32) urow[cc] -= ujr * ujrow[cc];
+    const T *ujrow = U.row(j);
+    for (int rr = j + 1 + warp; rr < n; rr += (nt >> 5)) {
+      const T ujr = ujrow[rr];
+      T *urow = U.row(rr);
+      for (int cc = rr + lane; cc < n; cc += 32) urow[cc] -= ujr * ujrow[cc];
     }
     __syncthreads();
   }
-  // X = R^-1 (upper triangular) by back substitution, one warp per column:
-  // X[j][j] = 1 / R[j][j], X[i][j] = -(sum_{k=i+1..j} R[i][k] X[k][j]) / R[i][i]
-  // for i = j-1 .. 0; the warp splits each sum over its lanes.
-  {
-    const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
-    T *xcol = tmp + (size_t)(warp % kCholColBufs) * n;
-    if (warp < kCholColBufs) {
-      for (int j = warp; j < n; j += min(nw, kCholColBufs)) {
-        if (lane == 0) xcol[j] = T(1) / U[packed_upper(n, j, j)];
+  const int r = rank_s;
+  // X = R11^-1 (upper triangular, r x r) by back substitution, one warp per
+  // column: X[j][j] = 1 / R[j][j], X[i][j] = -(sum_{k=i+1..j} R[i][k] X[k][j]) /
+  // R[i][i] for i = j-1 .. 0; the warp splits each sum over its lanes.  Column j
+  // of M is written to the rows perm[i].
+  if (warp < kCholColBufs) {
+    T *xcol = colbuf + (size_t)warp * n;
+    for (int j = warp; j < n; j += min(nt >> 5, kCholColBufs)) {
+      if (j < r) {
+        if (lane == 0) xcol[j] = T(1) / U.at(j, j);
         __syncwarp();
         for (int i = j - 1; i >= 0; --i) {
-          const T *urow = U + packed_upper(n, i, i) - i;  // urow[k] = R[i][k], k >= i
-          T s = 0;
-          for (int k = i + 1 + lane; k <= j; k += 32) s += urow[k] * xcol[k];
+          const T *urow = U.row(i);
+          T sum = 0;
+          for (int k = i + 1 + lane; k <= j; k += 32) sum += urow[k] * xcol[k];
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-          if (lane == 0) xcol[i] = -s / urow[i];
+          for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+          if (lane == 0) xcol[i] = -sum / urow[i];
           __syncwarp();
         }
-        for (int i = lane; i < n; i += 32) Rinv[(int64_t)i * ldi + j] = (i <= j) ? xcol[i] : T(0);
-        __syncwarp();
       }
+      for (int i = lane; i < n; i += 32)
+        Rinv[(int64_t)perm[i] * ldi + j] = (j < r && i <= j) ? xcol[i] : T(0);
+      __syncwarp();
     }
   }
 }
 
 template <typename T>
-size_t chol_inv_smem(int n) {
-  return ((size_t)n * (n + 1) / 2 + (size_t)kCholColBufs * n) * sizeof(T);
-}
-
-template <typename T>
-bool chol_inv_fits(int n) {
-  return chol_inv_smem<T>(n) <= 220 * 1024;
+size_t chol_inv_smem(int n, bool packed) {
+  return ((packed ? (size_t)n * (n + 1) / 2 : 0) + (size_t)kCholColBufs * n) * sizeof(T) +
+         (size_t)n * sizeof(int);
 }
 
 template <typename T>
 cudaError_t launch_chol_inverse(const T *A, int32_t n, int32_t lda, T *Rinv, int32_t ldi, T *scratch,
-                                Ctrl *ctrl, cudaStream_t st) {
+                                Ctrl *ctrl, cudaStream_t st, double tol) {
   if (n <= 0) return cudaSuccess;
-  if (chol_inv_fits<T>(n)) {
-    const size_t smem = chol_inv_smem<T>(n);
-    cudaError_t e = cudaFuncSetAttribute(chol_inv_packed_kernel<T>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    ProfScope ps_(K_CHOL, st);
-    chol_inv_packed_kernel<T><<<1, 1024, smem, st>>>(A, n, lda, Rinv, ldi, ctrl);
-    return cudaGetLastError();
-  }
-  // global-memory path: factor a copy, then invert
-  cudaError_t e = cudaMemcpy2DAsync(scratch, n * sizeof(T), A, lda * sizeof(T), n * sizeof(T), n,
-                                    cudaMemcpyDeviceToDevice, st);
+  if (n > 1024) return cudaErrorInvalidValue;
+  const bool packed = chol_inv_smem<T>(n, true) <= 220 * 1024;
+  if (!packed && !scratch) return cudaErrorInvalidValue;
+  const size_t smem = chol_inv_smem<T>(n, packed);
+  auto kern = packed ? chol_inv_kernel<T, true> : chol_inv_kernel<T, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  e = launch_cholesky_upper<T>(scratch, n, n, ctrl, st);
-  if (e != cudaSuccess) return e;
-  return launch_triu_inverse<T>(scratch, n, n, Rinv, ldi, ctrl, st);
+  ProfScope ps_(K_CHOL, st);
+  kern<<<1, 1024, smem, st>>>(A, n, lda, Rinv, ldi, scratch, tol, ctrl);
+  return cudaGetLastError();
 }
 template cudaError_t launch_chol_inverse<float>(const float *, int32_t, int32_t, float *, int32_t,
-                                                float *, Ctrl *, cudaStream_t);
+                                                float *, Ctrl *, cudaStream_t, double);
 template cudaError_t launch_chol_inverse<double>(const double *, int32_t, int32_t, double *, int32_t,
-                                                 double *, Ctrl *, cudaStream_t);
+                                                 double *, Ctrl *, cudaStream_t, double);
 
 // ---------------------------------------------------------------------------
 // Public eigensolver entry (replaces the tridiagonal QR for n <= 320)

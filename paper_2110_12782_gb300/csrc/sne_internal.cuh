@@ -153,12 +153,6 @@ template <typename T>
 cudaError_t launch_small_gemm(bool ta, bool tb, int32_t M, int32_t N, int32_t K, T alpha,
                               const T *A, int32_t lda, const T *B, int32_t ldb, T beta, T *C,
                               int32_t ldc, cudaStream_t st, const int *skip = nullptr);
-// Single-CTA small factorizations (n <= 1024), matrices in global memory.
-template <typename T>
-cudaError_t launch_cholesky_upper(T *A, int32_t n, int32_t lda, Ctrl *ctrl, cudaStream_t st);
-template <typename T>
-cudaError_t launch_triu_inverse(const T *R, int32_t n, int32_t ldr, T *Rinv, int32_t ldi,
-                                Ctrl *ctrl, cudaStream_t st);
 // Symmetric eigendecomposition: A (n x n) = V diag(w) V^T, w unordered.
 // V is returned row-major n x n (column j = eigenvector j), ldv = n.  A may be
 // overwritten.  scratch: eig_scratch_bytes(n) bytes, 256-byte aligned.
@@ -171,11 +165,13 @@ cudaError_t launch_sym_eig_fast(float *A, int32_t n, int32_t lda, float *w, floa
 cudaError_t launch_sym_eig_fast(double *A, int32_t n, int32_t lda, double *w, double *V,
                                 int32_t ldv, void *scratch, Ctrl *ctrl, cudaStream_t st);
 constexpr int kFastEigMaxN = 320;
-// Rinv = R^-1 where A = R^T R (Cholesky); scratch: n*n T (used only for n too
-// large for shared memory).
+// M = R^-1 where A = R^T R (Cholesky); scratch: n*n T (used only for n too
+// large for shared memory).  tol >= 0 selects diagonal pivoting with a rank
+// cut at tol * max(diag A): then M = P [R11^-1 0; 0 0] (zero columns past the
+// numerical rank) and no pivot is ever non-positive.
 template <typename T>
 cudaError_t launch_chol_inverse(const T *A, int32_t n, int32_t lda, T *Rinv, int32_t ldi, T *scratch,
-                                Ctrl *ctrl, cudaStream_t st);
+                                Ctrl *ctrl, cudaStream_t st, double tol = -1.0);
 // Orders eigenpairs: perm[j] = index of the j-th largest (|w| if by_abs else w).
 template <typename T>
 cudaError_t launch_eig_order(const T *w, int32_t n, bool by_abs, int32_t *perm, cudaStream_t st);

@@ -281,3 +281,38 @@ def test_sketch_k256_matches_oracle(sk, cl_k256):
     print(f"k=256 sketch: Y rel {ey:.2e}, Z rel {ez:.2e}")
     assert ey < SKETCH_RTOL
     assert ez < SKETCH_RTOL
+
+
+def test_rank_deficient_sketch_matches_oracle(sk):
+    """40 cliques of 4..8 vertices and 40 single edges, k = 120 = the dimension
+    of the |lambda| = 1 eigenspace: U_k spans the component indicators, L'R' is
+    constant on every component, and trunc_log(L'R') has rank 80 < h = 96.  The
+    sketch QR and the least-squares solves must still reproduce the oracle (whose
+    Householder QR and lstsq are rank-revealing)."""
+    edges, off = [], 0
+    for i in range(40):
+        m = 4 + i % 5
+        edges += [(off + a, off + b) for a in range(m) for b in range(a + 1, m)]
+        off += m
+    for i in range(40):
+        edges.append((off, off + 1))
+        off += 2
+    g = synth.from_edges(off, np.array(edges))
+    p = o.Params(k=120, d=40, h=96, l=200)
+    ref = o.embed(g.row_ptr, g.col_idx, g.n, p)
+    assert np.linalg.matrix_rank(ref.sp.Y) < p.h
+    for orth in ("cholqr", "eigsvd"):
+        q = gpu_params(sk, p, orth=sk.SNE_ORTH_CHOLQR if orth == "cholqr" else sk.SNE_ORTH_EIGSVD)
+        G = dev_graph(sk, g)
+        ws = sk.workspace(g.n, g.nnz, q, sk.SNE_WS_EMBED)
+        E = torch.empty(g.n, p.d, dtype=torch.float32, device="cuda")
+        sig = torch.empty(p.d, dtype=torch.float64, device="cuda")
+        sk.sne_embed(G, q, ws, E, sig)
+        st = sk.sne_stats_read(ws)
+        assert st.status == 0, (orth, sk.sne_error_string(st.status), st.where)
+        s = sig.cpu().numpy()
+        assert np.allclose(s, ref.sigma, rtol=1e-4), (orth, s[:8], ref.sigma[:8])
+        Eh = E.cpu().numpy()
+        for blk in (8, 16, 24, 32):
+            sines = o.principal_angle_sines(Eh[:, :blk], ref.E[:, :blk])
+            assert sines.max() < ANGLE_TOL, (orth, blk, sines.max())
