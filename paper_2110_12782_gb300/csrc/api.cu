@@ -121,7 +121,8 @@ size_t carve(const Dims &D, int mode, void *base, Bufs *b) {
     pf = std::max(pf, gram_partial_floats(n, D.k, D.k));
   }
   x.partial = bp.take<float>(pf);
-  const size_t S2 = (size_t)D.Sm * D.Sm;
+  // n x n plus room for the Cholesky scratch tail (1/R[i][i], permutation, rank)
+  const size_t S2 = (size_t)D.Sm * D.Sm + 2 * (size_t)D.Sm + 8;
   for (auto &m : x.m64) m = bp.take<double>(S2);
   x.eigscr = bp.take<char>(std::max(eig_scratch_bytes(D.Sm), (S2 + 4 * (size_t)D.Sm) * 8 + 1024));
   for (auto &m : x.m32) m = bp.take<float>(S2);

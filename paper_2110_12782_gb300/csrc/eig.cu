@@ -340,7 +340,7 @@ __device__ __forceinline__ int packed_upper(int n, int i, int j) {  // j >= i
   return i * n - i * (i - 1) / 2 + (j - i);
 }
 
-constexpr int kCholColBufs = 16;  // warps that build columns of R^-1 at once
+constexpr int kCholColBufs = 32;  // warps that build columns of R^-1 at once
 
 // Upper-triangle storage of the matrix being factored: packed in shared memory
 // when it fits, else dense (row-major, leading dimension n) in global scratch.
@@ -371,8 +371,9 @@ __global__ void __launch_bounds__(1024) chol_inv_kernel(const T *__restrict__ A,
                                                         Ctrl *ctrl) {
   extern __shared__ __align__(16) unsigned char csm[];
   T *packed = reinterpret_cast<T *>(csm);
-  T *colbuf = packed + (PACKED ? (size_t)n * (n + 1) / 2 : 0);  // kCholColBufs x n
-  int *perm = reinterpret_cast<int *>(colbuf + (size_t)kCholColBufs * n);
+  T *colbuf = packed + (PACKED ? (size_t)n * (n + 1) / 2 : 0);  // kCholColBufs x n (PACKED)
+  T *dinv = colbuf + (PACKED ? (size_t)kCholColBufs * n : 0);   // n: 1 / R[i][i]
+  int *perm = reinterpret_cast<int *>(dinv + n);
   __shared__ T piv;
   __shared__ T wmax[32];
   __shared__ int widx[32];
@@ -478,6 +479,18 @@ __global__ void __launch_bounds__(1024) chol_inv_kernel(const T *__restrict__ A,
     __syncthreads();
   }
   const int r = rank_s;
+  for (int i = tid; i < n; i += nt) dinv[i] = i < r ? T(1) / U.at(i, i) : T(0);
+  if (!PACKED) {
+    // the multi-CTA back substitution (chol_backsub_kernel) follows
+    int *gperm = reinterpret_cast<int *>(scratch + (size_t)n * n + n);
+    for (int i = tid; i < n; i += nt) {
+      gperm[i] = perm[i];
+      scratch[(size_t)n * n + i] = dinv[i];
+    }
+    if (tid == 0) gperm[n] = r;
+    return;
+  }
+  __syncthreads();
   // X = R11^-1 (upper triangular, r x r) by back substitution, one warp per
   // column: X[j][j] = 1 / R[j][j], X[i][j] = -(sum_{k=i+1..j} R[i][k] X[k][j]) /
   // R[i][i] for i = j-1 .. 0; the warp splits each sum over its lanes.  Column j
@@ -486,7 +499,7 @@ __global__ void __launch_bounds__(1024) chol_inv_kernel(const T *__restrict__ A,
     T *xcol = colbuf + (size_t)warp * n;
     for (int j = warp; j < n; j += min(nt >> 5, kCholColBufs)) {
       if (j < r) {
-        if (lane == 0) xcol[j] = T(1) / U.at(j, j);
+        if (lane == 0) xcol[j] = dinv[j];
         __syncwarp();
         for (int i = j - 1; i >= 0; --i) {
           const T *urow = U.row(i);
@@ -494,7 +507,7 @@ __global__ void __launch_bounds__(1024) chol_inv_kernel(const T *__restrict__ A,
           for (int k = i + 1 + lane; k <= j; k += 32) sum += urow[k] * xcol[k];
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-          if (lane == 0) xcol[i] = -sum / urow[i];
+          if (lane == 0) xcol[i] = -sum * dinv[i];
           __syncwarp();
         }
       }
@@ -505,9 +518,41 @@ __global__ void __launch_bounds__(1024) chol_inv_kernel(const T *__restrict__ A,
   }
 }
 
+// Back substitution for the factor left in global scratch by chol_inv_kernel
+// (dense n x n R, then dinv[n], then perm[n] and the rank): one warp per
+// column of M = P [R11^-1 0; 0 0], eight columns per CTA.
+template <typename T>
+__global__ void __launch_bounds__(256) chol_backsub_kernel(const T *__restrict__ scratch, int n,
+                                                           T *__restrict__ Rinv, int ldi) {
+  extern __shared__ __align__(16) unsigned char bsm[];
+  T *xcol = reinterpret_cast<T *>(bsm) + (threadIdx.x >> 5) * n;
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (j >= n) return;
+  const T *R = scratch;
+  const T *dinv = scratch + (size_t)n * n;
+  const int *perm = reinterpret_cast<const int *>(dinv + n);
+  const int r = perm[n];
+  if (j < r) {
+    if (lane == 0) xcol[j] = dinv[j];
+    __syncwarp();
+    for (int i = j - 1; i >= 0; --i) {
+      const T *urow = R + (size_t)i * n;
+      T sum = 0;
+      for (int k = i + 1 + lane; k <= j; k += 32) sum += urow[k] * xcol[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      if (lane == 0) xcol[i] = -sum * dinv[i];
+      __syncwarp();
+    }
+  }
+  for (int i = lane; i < n; i += 32)
+    Rinv[(int64_t)perm[i] * ldi + j] = (j < r && i <= j) ? xcol[i] : T(0);
+}
+
 template <typename T>
 size_t chol_inv_smem(int n, bool packed) {
-  return ((packed ? (size_t)n * (n + 1) / 2 : 0) + (size_t)kCholColBufs * n) * sizeof(T) +
+  return ((packed ? (size_t)n * (n + 1) / 2 + (size_t)kCholColBufs * n : 0) + n) * sizeof(T) +
          (size_t)n * sizeof(int);
 }
 
@@ -524,6 +569,13 @@ cudaError_t launch_chol_inverse(const T *A, int32_t n, int32_t lda, T *Rinv, int
   if (e != cudaSuccess) return e;
   ProfScope ps_(K_CHOL, st);
   kern<<<1, 1024, smem, st>>>(A, n, lda, Rinv, ldi, scratch, tol, ctrl);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || packed) return e;
+  const size_t bsmem = (size_t)8 * n * sizeof(T);
+  e = cudaFuncSetAttribute(chol_backsub_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)bsmem);
+  if (e != cudaSuccess) return e;
+  chol_backsub_kernel<T><<<(n + 7) / 8, 256, bsmem, st>>>(scratch, n, Rinv, ldi);
   return cudaGetLastError();
 }
 template cudaError_t launch_chol_inverse<float>(const float *, int32_t, int32_t, float *, int32_t,

@@ -14,14 +14,19 @@
 //            through a ring of shared-memory stages (128-byte swizzle);
 //   warp 1   allocates 512 TMEM columns (two 128 x 256 FP32 accumulators)
 //            and issues tcgen05.mma (M 128, N 256, K 16) from one thread;
-//   warps 2-5  epilogue: tcgen05.ld of the accumulator rows, x = scale * acc,
+//   warps 2-17 epilogue: tcgen05.ld of the accumulator rows, x = scale * acc,
 //            f(x), sign, and the z-column segmented sums in registers, then
-//            the Y (or Y') row segment is stored.
+//            the Y (or Y') row segment is stored.  Warp w reads TMEM lane
+//            quarter w % 4 and 64 of the 256 columns; sixteen warps keep
+//            enough loads, MUFU logs and stores in flight per scheduler.
 // Double-buffered accumulators let the epilogue of tile j overlap the MMAs
-// of tile j+1.  Every mbarrier wait is bounded (about 2 s of %globaltimer);
+// of tile j+1.  When the rows are few (the Z core: v_O rows, thousands of
+// columns) blockIdx.y splits a row tile's column tiles over several CTAs.  Every mbarrier wait is bounded (about 2 s of %globaltimer);
 // on timeout the CTA records SNE_ERR_TIMEOUT, stops issuing work, waits for
 // its in-flight MMAs and copies, frees TMEM and returns.
 #include <cuda.h>
+
+#include <algorithm>
 
 #include "sne_internal.cuh"
 #include "tc_ptx.cuh"
@@ -66,7 +71,7 @@ __global__ void __launch_bounds__(tc::kThreadsSketch, 1) fused_sketch_tc_kernel(
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 256);
+      mbar_init(&tempty[b], 512);
     }
     mbar_init(done, 1);
     *abort_flag = 0;
@@ -94,7 +99,7 @@ __global__ void __launch_bounds__(tc::kThreadsSketch, 1) fused_sketch_tc_kernel(
       int it = 0;
       int issued = 0;
       bool ok = true;
-      for (int j = 0; j < ntiles && ok; ++j) {
+      for (int j = blockIdx.y; j < ntiles && ok; j += gridDim.y) {
         for (int kb = 0; kb < kblocks; ++kb, ++it) {
           const int s = it % stages;
           const uint32_t ph = (uint32_t)((it / stages) & 1);
@@ -124,9 +129,10 @@ __global__ void __launch_bounds__(tc::kThreadsSketch, 1) fused_sketch_tc_kernel(
       // ---------------- MMA issuer
       bool ok = mbar_wait(a_full, 0, abortv, ctrl);
       int it = 0;
-      for (int j = 0; j < ntiles && ok; ++j) {
-        const int buf = j & 1;
-        const uint32_t use = (uint32_t)(j >> 1);
+      int jj = 0;  // local tile count (accumulator buffer and phase)
+      for (int j = blockIdx.y; j < ntiles && ok; j += gridDim.y, ++jj) {
+        const int buf = jj & 1;
+        const uint32_t use = (uint32_t)(jj >> 1);
         if (!mbar_wait(&tempty[buf], (use & 1u) ^ 1u, abortv, ctrl)) {
           ok = false;
           break;
@@ -157,24 +163,31 @@ __global__ void __launch_bounds__(tc::kThreadsSketch, 1) fused_sketch_tc_kernel(
       }
     }
   } else {
-    // ---------------- epilogue warps 2..9: warp w reads TMEM lane quarter
-    // w % 4 (rows 32(w%4) .. +32) and half (w - 2) / 4 of the 256 columns
+    // ---------------- epilogue warps 2..17: warp w reads TMEM lane quarter
+    // w % 4 (rows 32(w%4) .. +32) and quarter (w - 2) / 4 of the 256 columns
     const int ew = warp & 3;
-    const int half = (warp - 2) >> 2;
+    const int quarter = (warp - 2) >> 2;
     const int64_t row = row0 + 32 * ew + lane;
     const bool row_ok = row < nrows;
     const float rf = row_ok ? rowf[row] : 0.0f;
     constexpr int G = 32 / Z;        // output columns per 32-column chunk
-    for (int j = 0; j < ntiles; ++j) {
-      const int buf = j & 1;
-      const uint32_t use = (uint32_t)(j >> 1);
+    int jj = 0;
+    for (int j = blockIdx.y; j < ntiles; j += gridDim.y, ++jj) {
+      const int buf = jj & 1;
+      const uint32_t use = (uint32_t)(jj >> 1);
       if (!mbar_wait(&tfull[buf], use & 1u, abortv, ctrl)) break;
       fence_after();
-      const int ebase = j * BN + half * 128;
-#pragma unroll 1
-      for (int c = 0; c < 4; ++c) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * ew) << 16) + (uint32_t)(buf * BN + half * 128 + c * 32), v);
+      const int ebase = j * BN + quarter * 64;
+      float v[2][32];
+      const uint32_t taddr = tmem + ((uint32_t)(32 * ew) << 16) + (uint32_t)(buf * BN + quarter * 64);
+      tmem_ld32_nw(taddr, v[0]);
+      tmem_ld32_nw(taddr + 32, v[1]);
+      tmem_wait_ld();
+      // the accumulator is in registers: release it to the MMA warp early
+      fence_before();
+      mbar_arrive(&tempty[buf]);
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
         const float4 *cf4 = reinterpret_cast<const float4 *>(colf + ebase + c * 32);
         float acc[G];
 #pragma unroll
@@ -186,7 +199,7 @@ __global__ void __launch_bounds__(tc::kThreadsSketch, 1) fused_sketch_tc_kernel(
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const int t = 4 * q + u;
-            const float x = rf * fabsf(cfv[u]) * v[t];
+            const float x = rf * fabsf(cfv[u]) * v[c][t];
             const float l = tc::fx2<F>(x);
             // trunc_log is >= 0, so the sign of cf can be copied onto it
             if (F == SNE_F_TRUNC_LOG) acc[t / Z] += copysignf(l, cfv[u]);
@@ -210,8 +223,6 @@ __global__ void __launch_bounds__(tc::kThreadsSketch, 1) fused_sketch_tc_kernel(
           }
         }
       }
-      fence_before();
-      mbar_arrive(&tempty[buf]);
     }
   }
   fence_before();
@@ -348,7 +359,13 @@ cudaError_t launch_fused_sketch_tc(bool fp16, const void *Ahat, int64_t nrows_ma
   const uint32_t fmt = fp16 ? 0u : 1u;
   const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(tc::BN >> 3) << 17) |
                          ((uint32_t)(tc::BM >> 4) << 24);
-  const unsigned grid = (unsigned)((nrows_max + tc::BM - 1) / tc::BM);
+  const unsigned grid_x = (unsigned)((nrows_max + tc::BM - 1) / tc::BM);
+  // few row tiles (the Z core): spread their column tiles over CTAs so that
+  // at least two CTAs per SM's worth of work exists
+  const int ntiles = (ncols_eval + tc::BN - 1) / tc::BN;
+  const unsigned splits = (unsigned)std::max(
+      1, std::min(ntiles, (int)((2 * 152 + grid_x - 1) / grid_x)));
+  const dim3 grid(grid_x, splits);
   const int kblocks = kpad / tc::BK;
   // f = trunc_log: the kernel sums signed log2 values; ln 2 joins sv here
   const float out_scale = (f == SNE_F_TRUNC_LOG) ? sv * 0.69314718055994530942f : sv;
