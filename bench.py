@@ -46,6 +46,10 @@ WORKLOADS = {
     "cl1m": dict(kind="chung_lu", n=1_000_000, avg=20.0, gamma=2.1, d=128, k=256, T=10, q=20,
                  label="Chung-Lu n=1M avg-degree 20 gamma 2.1, T=10 b=1 k=256 d=128 zeta=8 "
                        "h=2d+16 l=d+1000 q=20 alpha=0.5, row block 8192"),
+    "cl200k": dict(kind="chung_lu", n=200_000, avg=20.0, gamma=2.1, d=128, k=256, T=10, q=20,
+                   label="Chung-Lu n=200k avg-degree 20 gamma 2.1, T=10 b=1 k=256 d=128 zeta=8 "
+                         "h=2d+16 l=d+1000 q=20 alpha=0.5 (the n=1M workload at 1/5 size, for "
+                         "kernel captures)"),
     "sbm4096": dict(kind="sbm", n=4096, d=32, k=128, T=10, q=20,
                     label="SBM n=4096 8 blocks p_in=0.01 p_out=0.001, T=10 b=1 k=128 d=32 zeta=8"),
     "batch64": dict(kind="batch", count=64, d=64, k=64, T=10, q=20,
