@@ -645,11 +645,11 @@ __global__ void __launch_bounds__(1024) sym_eig_kernel(T *A, int n, int lda, T *
     const T beta = block_sum(part2, red);
     for (int i = m0 + tid; i < n; i += nt) p[i] = T(2) * p[i] - T(2) * beta * vv[i];  // w
     __syncthreads();
-    const int m = n - m0;
-    const int64_t cnt = (int64_t)m * m;
-    for (int64_t q = tid; q < cnt; q += nt) {
-      const int i = m0 + (int)(q / m), j = m0 + (int)(q % m);
-      A[(int64_t)i * lda + j] -= vv[i] * p[j] + p[i] * vv[j];
+    // trailing update, warp per row, lanes over columns (no index division)
+    for (int i = m0 + warp; i < n; i += nwarps) {
+      const T vi = vv[i], pi = p[i];
+      T *ai = A + (int64_t)i * lda;
+      for (int j = m0 + lane; j < n; j += 32) ai[j] -= vi * p[j] + pi * vv[j];
     }
     for (int i = m0 + tid; i < n; i += nt) A[(int64_t)i * lda + k] = vv[i];
     if (tid == 0) {

@@ -186,41 +186,36 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const float *__restrict__ 
   for (int i = tid; i < n; i += nt) w[i] = Ap[packed_lower(i, i)];
 }
 
-// V = J_1 J_2 ... J_R (row block per CTA, rows held in shared memory)
-constexpr int kVRows = 16;
-__global__ void __launch_bounds__(256) jacobi_vectors_kernel(const Rot *__restrict__ rot,
-                                                             const int *__restrict__ nrounds, int n,
-                                                             float *__restrict__ V, int ldv) {
-  extern __shared__ __align__(16) float vs[];  // kVRows x (n + 1)
-  const int ld = n + 1;
-  const int r0 = blockIdx.x * kVRows;
-  const int rows = min(kVRows, n - r0);
-  const int tid = threadIdx.x;
-  for (int e = tid; e < kVRows * ld; e += blockDim.x) {
-    const int rr = e / ld, cc = e % ld;
-    vs[e] = (rr < rows && r0 + rr == cc) ? 1.0f : 0.0f;
-  }
-  __syncthreads();
+// V = J_1 J_2 ... J_R.  Rows of V are independent (row i of V is e_i^T times
+// the rotations), so one warp owns a row, held in shared memory, and applies
+// each round's m/2 disjoint rotations across its lanes, with only warp-level
+// synchronization between rounds.
+constexpr int kVWarps = 8;
+__global__ void __launch_bounds__(32 * kVWarps) jacobi_vectors_kernel(
+    const Rot *__restrict__ rot, const int *__restrict__ nrounds, int n, float *__restrict__ V,
+    int ldv) {
+  extern __shared__ __align__(16) float vs[];  // kVWarps x n
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * kVWarps + warp;
+  if (row >= n) return;
+  float *v = vs + (size_t)warp * n;
+  for (int c = lane; c < n; c += 32) v[c] = (c == row) ? 1.0f : 0.0f;
+  __syncwarp();
   const int m = n + (n & 1);
   const int P = m / 2;
   const int R = *nrounds;
   for (int r = 0; r < R; ++r) {
     const Rot *rr = rot + (int64_t)r * P;
-    for (int it = tid; it < rows * P; it += blockDim.x) {
-      const int row = it / P, t = it % P;
+    for (int t = lane; t < P; t += 32) {
       const Rot g = rr[t];
       if (g.s == 0.0f || g.q >= n) continue;
-      float *v = vs + row * ld;
       const float vp = v[g.p], vq = v[g.q];
       v[g.p] = g.c * vp - g.s * vq;
       v[g.q] = g.s * vp + g.c * vq;
     }
-    __syncthreads();
+    __syncwarp();
   }
-  for (int e = tid; e < rows * n; e += blockDim.x) {
-    const int rr = e / n, cc = e % n;
-    V[(int64_t)(r0 + rr) * ldv + cc] = vs[rr * ld + cc];
-  }
+  for (int c = lane; c < n; c += 32) V[(int64_t)row * ldv + c] = v[c];
 }
 
 cudaError_t launch_jacobi_f32(const float *A, int32_t n, int32_t lda, float *w, float *V, int32_t ldv,
@@ -237,13 +232,13 @@ cudaError_t launch_jacobi_f32(const float *A, int32_t n, int32_t lda, float *w, 
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t vsm = (size_t)kVRows * (n + 1) * sizeof(float);
+  const size_t vsm = (size_t)kVWarps * n * sizeof(float);
   e = cudaFuncSetAttribute(jacobi_vectors_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)vsm);
   if (e != cudaSuccess) return e;
   {
     ProfScope ps_(K_EIG, st);
-    jacobi_vectors_kernel<<<(n + kVRows - 1) / kVRows, 256, vsm, st>>>(
+    jacobi_vectors_kernel<<<(n + kVWarps - 1) / kVWarps, 32 * kVWarps, vsm, st>>>(
         reinterpret_cast<const Rot *>(rot_scratch), nrounds, n, V, ldv);
   }
   return cudaGetLastError();

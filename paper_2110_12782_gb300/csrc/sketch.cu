@@ -114,6 +114,122 @@ __global__ void __launch_bounds__(256) fused_sketch_f32_kernel(
   }
 }
 
+// Register-tiled form: CTA tile 128 rows x 128 evaluated columns, 256
+// threads with 8 x 8 outputs each, k in steps of 8 through two shared-memory
+// buffers (the next step's operands are loaded into registers while the
+// current one is multiplied).  A thread's 8 columns are consecutive, so for
+// z = 1, 2, 4, 8 the segmented sum over z columns stays in registers; for
+// z = 16, 32 it adds the partial sums of 2 or 4 neighbouring lanes.
+constexpr int kGM = 128, kGN = 128, kGK = 8;
+
+template <int F, int Z>
+__global__ void __launch_bounds__(256, 2) fused_sketch_f32_tiled_kernel(
+    const float *__restrict__ A, int64_t lda, const int32_t *__restrict__ ridx,
+    const int32_t *__restrict__ nrows_dev, int64_t nrows_max, int32_t k,
+    const float *__restrict__ rs, const float *__restrict__ rs_lo, const float *__restrict__ B,
+    const int8_t *__restrict__ sign, int32_t cols_out, float sv, float *__restrict__ out,
+    int64_t ldo) {
+  __shared__ __align__(16) float As[2][kGK][kGM + 4];
+  __shared__ __align__(16) float Bs[2][kGK][kGN + 4];
+  const int64_t nrows = nrows_dev ? (int64_t)(*nrows_dev) : nrows_max;
+  const int64_t i0 = (int64_t)blockIdx.x * kGM;
+  if (i0 >= nrows) return;
+  constexpr int CPT = kGN / Z;  // output columns per CTA
+  const int c_begin = blockIdx.y * CPT;
+  const int e_begin = c_begin * Z;
+  const int e_count = min(CPT, cols_out - c_begin) * Z;
+  const int tid = threadIdx.x;
+  const int ty = tid >> 4, tx = tid & 15;  // rows ty*8.., columns tx*8..
+  // loader: thread t brings row (t >> 1) of A's tile and column (t >> 1) of
+  // B's tile, k-part 4 (t & 1) .. +4, as one float4 each
+  const int lr = tid >> 1, lk = 4 * (tid & 1);
+  const int64_t arow = i0 + lr;
+  const bool a_ok = arow < nrows;
+  const float *ap = A + (a_ok ? (ridx ? (int64_t)ridx[arow] : arow) : 0) * lda;
+  const bool b_ok = lr < e_count;
+  const float *bp = B + (int64_t)(e_begin + (b_ok ? lr : 0)) * k;
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 pa = (a_ok && lk < k) ? __ldg(reinterpret_cast<const float4 *>(ap + lk)) : zero4;
+  float4 pb = (b_ok && lk < k) ? __ldg(reinterpret_cast<const float4 *>(bp + lk)) : zero4;
+  int buf = 0;
+  for (int k0 = 0; k0 < k; k0 += kGK) {
+    As[buf][lk + 0][lr] = pa.x;
+    As[buf][lk + 1][lr] = pa.y;
+    As[buf][lk + 2][lr] = pa.z;
+    As[buf][lk + 3][lr] = pa.w;
+    Bs[buf][lk + 0][lr] = pb.x;
+    Bs[buf][lk + 1][lr] = pb.y;
+    Bs[buf][lk + 2][lr] = pb.z;
+    Bs[buf][lk + 3][lr] = pb.w;
+    __syncthreads();
+    const int kn = k0 + kGK + lk;
+    pa = (a_ok && kn < k) ? __ldg(reinterpret_cast<const float4 *>(ap + kn)) : zero4;
+    pb = (b_ok && kn < k) ? __ldg(reinterpret_cast<const float4 *>(bp + kn)) : zero4;
+#pragma unroll
+    for (int kk = 0; kk < kGK; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 8]);
+      const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 8 + 4]);
+      const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 8]);
+      const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 8 + 4]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    buf ^= 1;
+  }
+  // epilogue: x = (s + s_lo) acc, f, sign, segmented sums over Z columns
+  float sg[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int c = tx * 8 + j;
+    sg[j] = c < e_count ? (float)sign[e_begin + c] : 0.f;
+  }
+  constexpr int PER = Z < 8 ? 8 / Z : 1;  // outputs per thread per row
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int64_t row = i0 + ty * 8 + i;
+    const bool rok = row < nrows;
+    float s = 0.f, s_lo = 0.f;
+    if (rok) {
+      const int64_t src = ridx ? ridx[row] : row;
+      s = rs[src];
+      if (rs_lo) s_lo = rs_lo[src];
+    }
+    float part[PER];
+#pragma unroll
+    for (int g = 0; g < PER; ++g) part[g] = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float x = fmaf(s, acc[i][j], s_lo * acc[i][j]);
+      part[Z < 8 ? j / Z : 0] += sg[j] * apply_f<F>(x);
+    }
+    if (Z > 8) {
+      // combine the Z / 8 lanes of one output column (consecutive tx)
+#pragma unroll
+      for (int o = 1; o < Z / 8; o <<= 1) part[0] += __shfl_xor_sync(0xffffffffu, part[0], o);
+    }
+    if (!rok) continue;
+    if (Z <= 8) {
+#pragma unroll
+      for (int g = 0; g < PER; ++g) {
+        const int oc = c_begin + (tx * 8) / Z + g;
+        if (tx * 8 + g * Z < e_count) out[row * ldo + oc] = sv * part[g];
+      }
+    } else if ((tx & (Z / 8 - 1)) == 0) {
+      const int oc = c_begin + (tx * 8) / Z;
+      if (tx * 8 < e_count) out[row * ldo + oc] = sv * part[0];
+    }
+  }
+}
+
 cudaError_t launch_fused_sketch_f32(const float *A, int64_t lda, const int32_t *ridx,
                                     const int32_t *nrows_dev, int64_t nrows, int32_t k,
                                     const float *rs, const float *rs_lo, const float *B,
@@ -121,6 +237,33 @@ cudaError_t launch_fused_sketch_f32(const float *A, int64_t lda, const int32_t *
                                     int32_t f, float *out, int64_t ldo, cudaStream_t st) {
   if (nrows <= 0 || cols_out <= 0) return cudaSuccess;
   if (z <= 0 || z > kFN) return cudaErrorInvalidValue;
+  if (k % 4 == 0 && lda % 4 == 0 && (uintptr_t)A % 16 == 0 && (uintptr_t)B % 16 == 0 &&
+      (z == 1 || z == 2 || z == 4 || z == 8 || z == 16 || z == 32)) {
+    const int cptz = kGN / z;
+    dim3 grid2((unsigned)((nrows + kGM - 1) / kGM), (unsigned)((cols_out + cptz - 1) / cptz));
+    ProfScope ps_(K_FUSED, st);
+#define SNE_F32_CASE(FV, ZV)                                                                    \
+  fused_sketch_f32_tiled_kernel<FV, ZV><<<grid2, 256, 0, st>>>(A, lda, ridx, nrows_dev, nrows, k, \
+                                                             rs, rs_lo, B, sign, cols_out, sv,  \
+                                                             out, ldo)
+#define SNE_F32_Z(FV)                         \
+  switch (z) {                                \
+    case 1: SNE_F32_CASE(FV, 1); break;       \
+    case 2: SNE_F32_CASE(FV, 2); break;       \
+    case 4: SNE_F32_CASE(FV, 4); break;       \
+    case 8: SNE_F32_CASE(FV, 8); break;       \
+    case 16: SNE_F32_CASE(FV, 16); break;     \
+    default: SNE_F32_CASE(FV, 32); break;     \
+  }
+    if (f == SNE_F_TRUNC_LOG) {
+      SNE_F32_Z(SNE_F_TRUNC_LOG)
+    } else {
+      SNE_F32_Z(SNE_F_IDENTITY)
+    }
+#undef SNE_F32_Z
+#undef SNE_F32_CASE
+    return cudaGetLastError();
+  }
   const int cpt = kFN / z;
   dim3 grid((unsigned)((nrows + kFM - 1) / kFM), (unsigned)((cols_out + cpt - 1) / cpt));
   ProfScope ps_(K_FUSED, st);

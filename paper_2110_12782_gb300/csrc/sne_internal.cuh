@@ -165,6 +165,7 @@ cudaError_t launch_sym_eig_fast(float *A, int32_t n, int32_t lda, float *w, floa
 cudaError_t launch_sym_eig_fast(double *A, int32_t n, int32_t lda, double *w, double *V,
                                 int32_t ldv, void *scratch, Ctrl *ctrl, cudaStream_t st);
 constexpr int kFastEigMaxN = 320;
+
 // M = R^-1 where A = R^T R (Cholesky); scratch: n*n + 2n + 8 T (used only for
 // n too large for shared memory).  tol >= 0 selects diagonal pivoting with a rank
 // cut at tol * max(diag A): then M = P [R11^-1 0; 0 0] (zero columns past the
