@@ -248,6 +248,19 @@ int sne_tall_gemm(int64_t n, int32_t ka, int32_t kc, const float *A, int64_t lda
                   int32_t ldm, float *C, int64_t ldc, void *workspace, size_t ws_bytes,
                   sne_stream_t stream);
 
+/* Cholesky factor inverse of Cholesky QR (Alg. 4 line 5's orth(Y) = Y R^-1)
+ * and of the normal equations of Alg. 4 line 8: for a symmetric positive
+ * semidefinite A (n x n, lda; n <= 1024; FP64 if fp64 else FP32; only the
+ * upper triangle is read) writes M (n x n, ldm, same type) with M^T A M = I.
+ * tol < 0: A = R^T R and M = R^-1 (upper triangular); a non-positive pivot sets
+ * SNE_ERR_NUMERIC.  tol >= 0: diagonal pivoting stopped at the numerical rank r
+ * (the first remaining diagonal <= tol * max_i A_ii); M = P [R11^-1 0; 0 0],
+ * so M^T A M = diag(I_r, 0) and the last n - r columns of M are zero.  Errors
+ * as sne_gram. */
+int sne_chol_inverse_workspace_bytes(int32_t n, int32_t fp64, size_t *bytes);
+int sne_chol_inverse(int32_t n, const void *A, int32_t lda, void *M, int32_t ldm, int32_t fp64,
+                     double tol, void *workspace, size_t ws_bytes, sne_stream_t stream);
+
 /* Eigendecomposition of a symmetric FP64 matrix S (n x n, lds; n <= 1024) as
  * in the Rayleigh-Ritz step of Alg. 5: lambda (n) ordered by |lambda|
  * descending, V (n x n, ldv) with column j the eigenvector of lambda[j].  S is

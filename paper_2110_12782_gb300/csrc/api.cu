@@ -290,9 +290,12 @@ int orth_tall(const Dims &D, const Bufs &b, int method, bool fp64, const float *
                                                                    w, b.ctrl); }
     CK(cudaGetLastError());
   } else if (fp64) {
-    // pivoted, cut at 1e-8 of the largest diagonal: Y is rank-deficient when
-    // trunc_log(L'R') has rank below h (a graph with more components than
-    // sketch columns); then the trailing columns of Q are zero
+    // the sketch QR, in FP64: Y can be ill-conditioned (with half-precision
+    // operands its small singular values are rounding noise), and an FP32
+    // Cholesky of Y^T Y loses kappa(Y)^2 eps_32.  Pivoted and cut at 1e-8 of
+    // the largest diagonal: Y is rank-deficient when trunc_log(L'R') has rank
+    // below h (a graph with more components than sketch columns), and then the
+    // trailing columns of Q are zero.
     CK(launch_chol_inverse<double>(b.m64[0], w, w, b.m64[1], w, b.m64[2], b.ctrl, st, 1e-8));
     CK(launch_d2f(b.m64[1], w, w, w, b.m32[2], w, st));
   } else {

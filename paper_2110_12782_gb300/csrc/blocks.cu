@@ -133,4 +133,33 @@ int sne_sym_eig(int32_t n, const double *S, int32_t lds, double *lambda, double 
   return cudaGetLastError() == cudaSuccess ? SNE_OK : SNE_ERR_CUDA;
 }
 
+int sne_chol_inverse_workspace_bytes(int32_t n, int32_t fp64, size_t *bytes) {
+  if (!bytes || n <= 0 || n > 1024) return SNE_ERR_ARG;
+  const size_t el = fp64 ? sizeof(double) : sizeof(float);
+  *bytes = align256(sizeof(Ctrl)) + align256(((size_t)n * n + 2 * (size_t)n + 8) * el);
+  return SNE_OK;
+}
+
+int sne_chol_inverse(int32_t n, const void *A, int32_t lda, void *M, int32_t ldm, int32_t fp64,
+                     double tol, void *ws, size_t ws_bytes, sne_stream_t stream) {
+  if (n <= 0 || n > 1024 || !A || !M || lda < n || ldm < n) return SNE_ERR_ARG;
+  size_t need = 0;
+  int rc = sne_chol_inverse_workspace_bytes(n, fp64, &need);
+  if (rc) return rc;
+  rc = check_ws_(ws, ws_bytes, need);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  Ctrl *ctrl = reinterpret_cast<Ctrl *>(ws);
+  if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st) != cudaSuccess) return SNE_ERR_CUDA;
+  void *scratch = static_cast<char *>(ws) + align256(sizeof(Ctrl));
+  cudaError_t e =
+      fp64 ? launch_chol_inverse<double>(static_cast<const double *>(A), n, lda,
+                                         static_cast<double *>(M), ldm,
+                                         static_cast<double *>(scratch), ctrl, st, tol)
+           : launch_chol_inverse<float>(static_cast<const float *>(A), n, lda,
+                                        static_cast<float *>(M), ldm,
+                                        static_cast<float *>(scratch), ctrl, st, tol);
+  return e == cudaSuccess ? SNE_OK : SNE_ERR_CUDA;
+}
+
 }  // extern "C"

@@ -545,6 +545,126 @@ __global__ void __launch_bounds__(256) chol_backsub_kernel(const T *__restrict__
     Rinv[(int64_t)perm[i] * ldi + j] = (j < r && i <= j) ? xcol[i] : T(0);
 }
 
+// Unpivoted Cholesky and R^-1 by blocks of kCB columns, packed upper triangle
+// in shared memory (one CTA).
+//  Factorization: within a panel of kCB columns every thread derives the pivot
+//  d_j = sqrt(U(j, j)) itself (kept in diag[j]; U(j, j) is left as is), scales
+//  row j and updates the panel's remaining rows, two block barriers per column;
+//  the rows below the panel then take the panel's rank-kCB update in one pass
+//  (kCB products per element in registers, one read-modify-write).
+//  Inverse: X = R^-1 in place by block columns (as LAPACK's trtri): for block
+//  column J, X_JJ = R_JJ^-1, then X(0:J, J) = -X(0:J, 0:J) R(0:J, J) X_JJ, using
+//  the already inverted leading block.
+constexpr int kCB = 16;
+
+template <typename T>
+__global__ void __launch_bounds__(1024) chol_inv_blocked_kernel(const T *__restrict__ A, int n,
+                                                                int lda, T *__restrict__ Rinv,
+                                                                int ldi, Ctrl *ctrl) {
+  extern __shared__ __align__(16) unsigned char cbm[];
+  T *U = reinterpret_cast<T *>(cbm);                    // packed upper, n(n+1)/2
+  T *diag = U + (size_t)n * (n + 1) / 2;                // n: d_j = R[j][j]
+  T *tb = diag + n;                                     // n x kCB scratch
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int nw = nt >> 5;
+  auto at = [&](int i, int j) -> T & { return U[packed_upper(n, i, j)]; };
+  for (int i = warp; i < n; i += nw) {
+    T *ui = U + packed_upper(n, i, i) - i;
+    for (int j = i + lane; j < n; j += 32) ui[j] = A[(int64_t)i * lda + j];
+  }
+  __syncthreads();
+  // ---- factorization
+  for (int j0 = 0; j0 < n; j0 += kCB) {
+    const int j1 = min(n, j0 + kCB);
+    for (int j = j0; j < j1; ++j) {
+      T d2 = at(j, j);
+      if (!(d2 > T(0)) || !isfinite((double)d2)) {
+        if (tid == 0) record_error(ctrl, SNE_ERR_NUMERIC, W_CHOL);
+        d2 = T(1);
+      }
+      const T d = sqrt(d2), inv = T(1) / d;
+      if (tid == 0) diag[j] = d;
+      T *uj = U + packed_upper(n, j, j) - j;
+      for (int c = j + 1 + tid; c < n; c += nt) uj[c] *= inv;
+      __syncthreads();
+      // remaining rows of the panel: U(r, c) -= U(j, r) U(j, c), j < r < j1, c >= r
+      for (int r = j + 1 + warp; r < j1; r += nw) {
+        const T f = uj[r];
+        T *ur = U + packed_upper(n, r, r) - r;
+        for (int c = r + lane; c < n; c += 32) ur[c] -= f * uj[c];
+      }
+      __syncthreads();
+    }
+    // rows below the panel: U(r, c) -= sum_{k=j0}^{j1-1} U(k, r) U(k, c), j1 <= r <= c
+    const int nk = j1 - j0;
+    for (int r = j1 + warp; r < n; r += nw) {
+      T ukr[kCB];
+#pragma unroll
+      for (int q = 0; q < kCB; ++q) ukr[q] = q < nk ? at(j0 + q, r) : T(0);
+      T *ur = U + packed_upper(n, r, r) - r;
+      for (int c = r + lane; c < n; c += 32) {
+        T acc = 0;
+#pragma unroll
+        for (int q = 0; q < kCB; ++q)
+          if (q < nk) acc += ukr[q] * U[packed_upper(n, j0 + q, j0 + q) - (j0 + q) + c];
+        ur[c] -= acc;
+      }
+    }
+    __syncthreads();
+  }
+  // ---- inverse in place: the diagonal of U becomes 1 / d
+  for (int J0 = 0; J0 < n; J0 += kCB) {
+    const int J1 = min(n, J0 + kCB), nb = J1 - J0;
+    // X_JJ = R_JJ^-1 (one warp, column by column: x_jj = 1/d_j, x_ij for i < j)
+    if (warp == 0) {
+      for (int jj = 0; jj < nb; ++jj) {
+        const int j = J0 + jj;
+        // column j of X_JJ, rows i = j .. J0 (bottom-up), lane i - J0 holds x_ij
+        T x = (lane == jj) ? T(1) / diag[j] : T(0);
+        for (int ii = jj - 1; ii >= 0; --ii) {
+          const int i = J0 + ii;
+          // x_ij = -(sum_{k=i+1..j} R_ik x_kj) / d_i
+          T part = (lane > ii && lane <= jj) ? at(i, J0 + lane) * x : T(0);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+          if (lane == ii) x = -part / diag[i];
+        }
+        if (lane < nb) tb[(size_t)lane * kCB + jj] = x;  // X_JJ[ii][jj]
+      }
+    }
+    __syncthreads();
+    // T(0:J0, jj) = X(0:J0, 0:J0) R(0:J0, J0 + jj)  (X upper, in U's leading block,
+    // whose diagonal already holds 1/d)
+    T *tcol = tb + (size_t)kCB * kCB;  // J0 x kCB
+    for (int e = tid; e < J0 * nb; e += nt) {
+      const int i = e / nb, jj = e % nb;
+      T acc = 0;
+      for (int k = i; k < J0; ++k) acc += at(i, k) * at(k, J0 + jj);
+      tcol[(size_t)i * kCB + jj] = acc;
+    }
+    __syncthreads();
+    // X(0:J0, J) = -T X_JJ; X_JJ into the diagonal block
+    for (int e = tid; e < J0 * nb; e += nt) {
+      const int i = e / nb, jj = e % nb;
+      T acc = 0;
+      for (int k = 0; k <= jj; ++k) acc += tcol[(size_t)i * kCB + k] * tb[(size_t)k * kCB + jj];
+      at(i, J0 + jj) = -acc;
+    }
+    for (int e = tid; e < nb * nb; e += nt) {
+      const int ii = e / nb, jj = e % nb;
+      if (jj >= ii) at(J0 + ii, J0 + jj) = tb[(size_t)ii * kCB + jj];
+    }
+    __syncthreads();
+  }
+  for (int i = warp; i < n; i += nw)
+    for (int j = lane; j < n; j += 32) Rinv[(int64_t)i * ldi + j] = j >= i ? at(i, j) : T(0);
+}
+
+template <typename T>
+size_t chol_blocked_smem(int n) {
+  return ((size_t)n * (n + 1) / 2 + n + (size_t)kCB * kCB + (size_t)n * kCB) * sizeof(T);
+}
+
 template <typename T>
 size_t chol_inv_smem(int n, bool packed) {
   return ((packed ? (size_t)n * (n + 1) / 2 + (size_t)kCholColBufs * n : 0) + n) * sizeof(T) +
@@ -556,6 +676,15 @@ cudaError_t launch_chol_inverse(const T *A, int32_t n, int32_t lda, T *Rinv, int
                                 Ctrl *ctrl, cudaStream_t st, double tol) {
   if (n <= 0) return cudaSuccess;
   if (n > 1024) return cudaErrorInvalidValue;
+  if (tol < 0.0 && chol_blocked_smem<T>(n) <= 220 * 1024) {
+    const size_t smem = chol_blocked_smem<T>(n);
+    cudaError_t e = cudaFuncSetAttribute(chol_inv_blocked_kernel<T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    ProfScope ps_(K_CHOL, st);
+    chol_inv_blocked_kernel<T><<<1, 1024, smem, st>>>(A, n, lda, Rinv, ldi, ctrl);
+    return cudaGetLastError();
+  }
   const bool packed = chol_inv_smem<T>(n, true) <= 220 * 1024;
   if (!packed && !scratch) return cudaErrorInvalidValue;
   const size_t smem = chol_inv_smem<T>(n, packed);

@@ -433,37 +433,45 @@ __global__ void __launch_bounds__(gg::kThreads, 1) gram_tf32x3_kernel(
       const int s = kb & 1;
       if (!mbar_wait(&full[s], (uint32_t)((kb >> 1) & 1), abortv, ctrl)) break;
       if (kb >= 2 && !mbar_wait(&hfree[s], (uint32_t)(((kb >> 1) - 1) & 1), abortv, ctrl)) break;
-      const float4 *rb = reinterpret_cast<const float4 *>(raw + (size_t)s * 2 * gg::kTileBytes);
+      const float *rawf = reinterpret_cast<const float *>(raw + (size_t)s * 2 * gg::kTileBytes);
       float *hA = reinterpret_cast<float *>(hilo + (size_t)s * 4 * gg::kTileBytes);
       float *lA = hA + gg::kTileBytes / 4;
       float *hB = lA + gg::kTileBytes / 4;
       float *lB = hB + gg::kTileBytes / 4;
       const int64_t ibase = r0 + (int64_t)kb * gt::BK;
-      for (int q = t; q < (gt::kABytes + bbytes) / 16; q += 128) {
-        const bool isA = q < gt::kABytes / 16;
-        const int qq = isA ? q : q - gt::kABytes / 16;
-        const int m = qq >> 8, i = (qq & 255) >> 3, c = qq & 7;
-        const int a4 = c ^ (i & 7);
-        float4 x = rb[q];
-        if (isA && w) {
-          const int64_t gi = ibase + i;
-          const float wi = gi < nrows_total ? w[gi] : 0.0f;
-          x.x *= wi;
-          x.y *= wi;
-          x.z *= wi;
-          x.w *= wi;
-        }
-        const float xv[4] = {x.x, x.y, x.z, x.w};
-        float *hi = isA ? hA : hB;
-        float *lo = isA ? lA : lB;
+      // task (box m, K-chunk ic, output index a): the 4 values A[i][a], i = 4 ic ..
+      // 4 ic + 3, read with conflict-free scalar loads (the 32 lanes of a warp
+      // take the 32 a of one raw row) and written as one 16-byte hi and one lo
+      // store into the K-major swizzled row r = 32 m + a (chunk ic ^ (r % 8))
+      const int ntask = (4 + npad / 32) * 256;
+      for (int tau = t; tau < ntask; tau += 128) {
+        const bool isA = tau < 4 * 256;
+        const int tt = isA ? tau : tau - 4 * 256;
+        const int m = tt >> 8, ic = (tt >> 5) & 7, a = tt & 31;
+        const float *box = rawf + (isA ? 0 : gg::kTileBytes / 4) + m * 1024;
+        float x[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int r = 32 * m + 4 * a4 + j;  // K-major row
-          const int off = r * 32 + (((i >> 2) ^ (r & 7)) << 2) + (i & 3);
-          const float h = tf32_rna(xv[j]);
-          hi[off] = h;
-          lo[off] = xv[j] - h;
+        for (int u = 0; u < 4; ++u) {
+          const int i = 4 * ic + u;
+          x[u] = box[i * 32 + ((((a >> 2) ^ (i & 7)) << 2) | (a & 3))];
         }
+        if (isA && w) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int64_t gi = ibase + 4 * ic + u;
+            x[u] *= gi < nrows_total ? __ldg(w + gi) : 0.0f;
+          }
+        }
+        float4 h, l;
+        h.x = tf32_rna(x[0]);
+        h.y = tf32_rna(x[1]);
+        h.z = tf32_rna(x[2]);
+        h.w = tf32_rna(x[3]);
+        l = make_float4(x[0] - h.x, x[1] - h.y, x[2] - h.z, x[3] - h.w);
+        const int r = 32 * m + a;
+        const int off = r * 32 + ((ic ^ (r & 7)) << 2);
+        *reinterpret_cast<float4 *>((isA ? hA : hB) + off) = h;
+        *reinterpret_cast<float4 *>((isA ? lA : lB) + off) = l;
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(&rawfree[s]);

@@ -40,7 +40,8 @@ EXPORTS = [
     "sne_stats_read", "sne_embed_host", "sne_kernel_launches", "sne_profile_start",
     "sne_profile_stop", "sne_freigs_static", "sne_gram_workspace_bytes", "sne_gram",
     "sne_tall_gemm_workspace_bytes", "sne_tall_gemm", "sne_sym_eig_workspace_bytes", "sne_sym_eig",
-    "sne_embed_batched_workspace_bytes", "sne_embed_batched",
+    "sne_embed_batched_workspace_bytes", "sne_embed_batched", "sne_chol_inverse_workspace_bytes",
+    "sne_chol_inverse",
 ]
 
 
@@ -117,6 +118,8 @@ def lib() -> ctypes.CDLL:
             "sne_tall_gemm": [i64, i32, i32, vp, i64, vp, i32, vp, i64, vp, ctypes.c_size_t, vp],
             "sne_sym_eig_workspace_bytes": [i32, P(ctypes.c_size_t)],
             "sne_sym_eig": [i32, vp, i32, vp, vp, i32, vp, ctypes.c_size_t, vp],
+            "sne_chol_inverse_workspace_bytes": [i32, i32, P(ctypes.c_size_t)],
+            "sne_chol_inverse": [i32, vp, i32, vp, i32, i32, dbl, vp, ctypes.c_size_t, vp],
             "sne_embed_batched_workspace_bytes": [i32, P(sne_csr), P(sne_params), i32,
                                                   P(ctypes.c_size_t)],
             "sne_embed_batched": [i32, P(sne_csr), P(sne_params), i32, vp, ctypes.c_size_t,
@@ -440,3 +443,24 @@ def sne_embed_batched(graphs, p: sne_params, ws: torch.Tensor, E, sigma, status:
                                    _ptr(ws, torch.uint8, "workspace"), ws.numel(), e_ptrs, s_ptrs,
                                    _ptr(status, torch.int32, "status", True), _stream(stream)),
            "sne_embed_batched")
+
+
+def chol_inverse_workspace(n: int, fp64: bool, device="cuda") -> torch.Tensor:
+    nb = ctypes.c_size_t(0)
+    _check(lib().sne_chol_inverse_workspace_bytes(n, 1 if fp64 else 0, ctypes.byref(nb)),
+           "sne_chol_inverse_workspace_bytes")
+    return _aligned_bytes(nb.value, device)
+
+
+def sne_chol_inverse(A: torch.Tensor, M: torch.Tensor, ws: torch.Tensor, tol: float = -1.0,
+                     stream=None) -> None:
+    """M with M^T A M = I (tol < 0) or diag(I_r, 0) (pivoted, rank cut at tol)."""
+    if A.dtype != M.dtype or A.dtype not in (torch.float32, torch.float64):
+        raise ValueError("A and M must both be float32 or both float64")
+    n = A.shape[0]
+    if tuple(A.shape) != (n, n) or tuple(M.shape) != (n, n):
+        raise ValueError("shape mismatch")
+    _check(lib().sne_chol_inverse(n, A.data_ptr(), _row_stride(A, "A"), M.data_ptr(), _row_stride(M, "M"),
+                                  1 if A.dtype == torch.float64 else 0, tol,
+                                  _ptr(ws, torch.uint8, "workspace"), ws.numel(), _stream(stream)),
+           "sne_chol_inverse")

@@ -207,3 +207,44 @@ def test_spmm_fullsize(sk, width, weights):
     err = float(np.max(np.abs(got - ref) / scale))
     print(f"spmm n=1M width {width}: {err:.2e}")
     assert err < 1e-5
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("n", [5, 16, 17, 100, 272, 300])
+@pytest.mark.parametrize("pivot", [False, True])
+def test_chol_inverse(sk, n, dtype, pivot):
+    """M^T A M = I for the Cholesky-QR factor inverse, unpivoted (blocked
+    shared-memory kernel, or global memory when A does not fit) and pivoted."""
+    rng = np.random.default_rng(n)
+    Y = rng.standard_normal((3 * n, n)) * np.exp(rng.uniform(-1, 1, size=n))[None, :]
+    A = Y.T @ Y
+    Ad = torch.tensor(A, dtype=dtype, device="cuda")
+    M = torch.empty_like(Ad)
+    ws = sk.chol_inverse_workspace(n, dtype == torch.float64)
+    sk.sne_chol_inverse(Ad, M, ws, tol=(1e-12 if pivot else -1.0))
+    assert sk.sne_status(ws) == 0
+    Mh = M.cpu().numpy().astype(np.float64)
+    err = np.abs(Mh.T @ A @ Mh - np.eye(n)).max()
+    if not pivot:
+        assert np.allclose(np.tril(Mh, -1), 0)
+    tol = 2e-3 if dtype == torch.float32 else 1e-10
+    print(f"chol inverse n={n} {dtype} pivot={pivot}: |M^T A M - I| {err:.1e}")
+    assert err < tol
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_chol_inverse_rank_deficient(sk, dtype):
+    n, r = 96, 80
+    rng = np.random.default_rng(3)
+    Y = rng.standard_normal((200, r)) @ rng.standard_normal((r, n))
+    A = Y.T @ Y
+    Ad = torch.tensor(A, dtype=dtype, device="cuda")
+    M = torch.empty_like(Ad)
+    ws = sk.chol_inverse_workspace(n, dtype == torch.float64)
+    sk.sne_chol_inverse(Ad, M, ws, tol=(1e-6 if dtype == torch.float32 else 1e-10))
+    assert sk.sne_status(ws) == 0
+    Mh = M.cpu().numpy().astype(np.float64)
+    G = Mh.T @ A @ Mh
+    nz = np.abs(Mh).max(axis=0) > 0
+    assert nz.sum() == r
+    assert np.abs(G[np.ix_(nz, nz)] - np.eye(r)).max() < (1e-2 if dtype == torch.float32 else 1e-8)
