@@ -292,11 +292,13 @@ int orth_tall(const Dims &D, const Bufs &b, int method, bool fp64, const float *
   } else if (fp64) {
     // the sketch QR, in FP64: Y can be ill-conditioned (with half-precision
     // operands its small singular values are rounding noise), and an FP32
-    // Cholesky of Y^T Y loses kappa(Y)^2 eps_32.  Pivoted and cut at 1e-8 of
-    // the largest diagonal: Y is rank-deficient when trunc_log(L'R') has rank
-    // below h (a graph with more components than sketch columns), and then the
-    // trailing columns of Q are zero.
-    CK(launch_chol_inverse<double>(b.m64[0], w, w, b.m64[1], w, b.m64[2], b.ctrl, st, 1e-8));
+    // Cholesky of Y^T Y loses kappa(Y)^2 eps_32.  Pivoted, and cut only at the
+    // FP64 noise floor (1e-13 of the largest diagonal), like the Householder
+    // QR it stands for, which keeps every direction of Y: Y is rank-deficient
+    // when trunc_log(L'R') has rank below h (a graph with more components than
+    // sketch columns), and then the factorization stops instead of meeting a
+    // non-positive pivot; columns of Q past the stop are zero.
+    CK(launch_chol_inverse<double>(b.m64[0], w, w, b.m64[1], w, b.m64[2], b.ctrl, st, 1e-13));
     CK(launch_d2f(b.m64[1], w, w, w, b.m32[2], w, st));
   } else {
     CK(launch_d2f(b.m64[0], w, w, w, b.m32[0], w, st));

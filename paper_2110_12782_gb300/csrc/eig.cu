@@ -17,7 +17,9 @@
 // delta = 2 (|S - diag(lambda)| + |A| |R|) (Frobenius norms, floored at
 // 1e-4 max |lambda|), E_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i) when
 // |lambda_i - lambda_j| > delta, else r_ij / 2, X <- X + X E; at most six
-// iterations, the rest skipped on the device once max |E| < 1e-14.
+// iterations, the rest skipped on the device once max |E| < 1e-14.  Clusters
+// (pairs closer than the floor) are then resolved exactly by a small FP64
+// Jacobi on each cluster's block of X^T A X.
 #include <cfloat>
 #include <cmath>
 
@@ -28,6 +30,7 @@ namespace sne {
 constexpr int kJacobiMaxN = 320;
 constexpr int kJacobiMaxSweeps = 30;
 constexpr int kRefineSteps = 6;
+constexpr double kClusterFloor = 1e-4;  // eigenvalue gaps below this x max|lambda| form clusters
 
 struct Rot {
   int p, q;
@@ -298,7 +301,7 @@ __global__ void __launch_bounds__(1024) oa_update_kernel(double *T1, const doubl
     // to eps_32 |A| / gap, too large for the first-order correction to
     // converge; left unresolved, the pair's residual stays at the FP32
     // rounding level and its eigenvalues within the gap.
-    sdelta = fmax(2.0 * (sqrt(a) + sqrt(b) * sqrt(c)), 1e-4 * lm);
+    sdelta = fmax(2.0 * (sqrt(a) + sqrt(b) * sqrt(c)), kClusterFloor * lm);
   }
   __syncthreads();
   const double delta = sdelta;
@@ -725,6 +728,137 @@ cudaError_t launch_sym_eig_fast(float *A, int32_t n, int32_t lda, float *w, floa
   return launch_jacobi_f32(A, n, lda, w, V, ldv, rot, nrounds, ctrl, st);
 }
 
+// ---------------------------------------------------------------------------
+// Clusters after the refinement.  Eigenvalue pairs closer than the cluster
+// floor are only re-orthogonalized by the Ogita-Aishima step, so within a
+// cluster the vectors keep the FP32 start's mixing and the eigenvalues an
+// error up to the cluster's width.  Each cluster (consecutive eigenvalues in
+// ascending order, gaps at most the floor, 2..kMaxCluster members) is
+// resolved exactly: its block S_C = X_C^T A X_C (taken from S = X^T A X) is
+// diagonalized by cyclic FP64 Jacobi, S_C = V_C D V_C^T, and X_C <- X_C V_C.
+// ---------------------------------------------------------------------------
+constexpr int kMaxCluster = 64;
+
+// w = diag(S); perm = indices by ascending w; start[s] = 1 where sorted
+// position s begins a cluster
+__global__ void __launch_bounds__(1024) cluster_prep_kernel(const double *__restrict__ S, int n,
+                                                            double floor_rel, double *__restrict__ w,
+                                                            int *__restrict__ perm,
+                                                            int *__restrict__ start) {
+  __shared__ double red[32];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  double lm = 0.0;
+  for (int i = tid; i < n; i += nt) {
+    const double v = S[(int64_t)i * n + i];
+    w[i] = v;
+    lm = fmax(lm, fabs(v));
+  }
+  for (int o = 16; o > 0; o >>= 1) lm = fmax(lm, __shfl_xor_sync(0xffffffffu, lm, o));
+  if ((tid & 31) == 0) red[tid >> 5] = lm;
+  __syncthreads();
+  double lmax = 0.0;
+  for (int q = 0; q < (nt >> 5); ++q) lmax = fmax(lmax, red[q]);
+  for (int i = tid; i < n; i += nt) {
+    const double wi = w[i];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const double wj = w[j];
+      rank += (wj < wi || (wj == wi && j < i)) ? 1 : 0;
+    }
+    perm[rank] = i;
+  }
+  __syncthreads();
+  const double fl = floor_rel * lmax;
+  for (int q = tid; q < n; q += nt)
+    start[q] = (q == 0 || w[perm[q]] - w[perm[q - 1]] > fl) ? 1 : 0;
+}
+
+__global__ void __launch_bounds__(256) cluster_eig_kernel(const double *__restrict__ S, int n,
+                                                          const int *__restrict__ perm,
+                                                          const int *__restrict__ start,
+                                                          double *__restrict__ X,
+                                                          double *__restrict__ Xtmp,
+                                                          double *__restrict__ w) {
+  extern __shared__ __align__(16) double csh[];
+  const int b = blockIdx.x;
+  if (!start[b]) return;
+  int m = 1;
+  while (b + m < n && !start[b + m]) ++m;
+  if (m < 2 || m > kMaxCluster) return;
+  double *Sc = csh;            // m x m
+  double *Vc = Sc + m * m;     // m x m
+  __shared__ double rot_c, rot_s;
+  __shared__ int go;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < m * m; e += nt) {
+    const int a = e / m, c = e % m;
+    Sc[e] = 0.5 * (S[(int64_t)perm[b + a] * n + perm[b + c]] + S[(int64_t)perm[b + c] * n + perm[b + a]]);
+    Vc[e] = (a == c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int sweep = 0; sweep < 12; ++sweep) {
+    if (tid == 0) {
+      double off = 0.0, tot = 0.0;
+      for (int e = 0; e < m * m; ++e) {
+        tot += Sc[e] * Sc[e];
+        if (e / m != e % m) off += Sc[e] * Sc[e];
+      }
+      go = off > 1e-30 * tot;
+    }
+    __syncthreads();
+    if (!go) break;
+    for (int p = 0; p < m - 1; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        if (tid == 0) {
+          const double apq = Sc[p * m + q];
+          double c = 1.0, sn = 0.0;
+          if (apq != 0.0) {
+            const double tau = (Sc[q * m + q] - Sc[p * m + p]) / (2.0 * apq);
+            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            sn = t * c;
+          }
+          rot_c = c;
+          rot_s = sn;
+        }
+        __syncthreads();
+        const double c = rot_c, sn = rot_s;
+        if (sn != 0.0) {
+          // columns p, q of S and V
+          for (int r = tid; r < m; r += nt) {
+            const double sp = Sc[r * m + p], sq = Sc[r * m + q];
+            Sc[r * m + p] = c * sp - sn * sq;
+            Sc[r * m + q] = sn * sp + c * sq;
+            const double vp = Vc[r * m + p], vq = Vc[r * m + q];
+            Vc[r * m + p] = c * vp - sn * vq;
+            Vc[r * m + q] = sn * vp + c * vq;
+          }
+          __syncthreads();
+          // rows p, q of S
+          for (int r = tid; r < m; r += nt) {
+            const double sp = Sc[p * m + r], sq = Sc[q * m + r];
+            Sc[p * m + r] = c * sp - sn * sq;
+            Sc[q * m + r] = sn * sp + c * sq;
+          }
+        }
+        __syncthreads();
+      }
+  }
+  // X_C <- X_C V_C (through Xtmp: every new column reads all old ones)
+  for (int e = tid; e < n * m; e += nt) {
+    const int r = e / m, c = e % m;
+    double acc = 0.0;
+    for (int a = 0; a < m; ++a) acc += X[(int64_t)r * n + perm[b + a]] * Vc[a * m + c];
+    Xtmp[(int64_t)r * n + perm[b + c]] = acc;
+  }
+  __syncthreads();
+  for (int e = tid; e < n * m; e += nt) {
+    const int r = e / m, c = e % m;
+    X[(int64_t)r * n + perm[b + c]] = Xtmp[(int64_t)r * n + perm[b + c]];
+  }
+  for (int c = tid; c < m; c += nt) w[perm[b + c]] = Sc[c * m + c];
+}
+
 cudaError_t launch_sym_eig_fast(double *A, int32_t n, int32_t lda, double *w, double *V, int32_t ldv,
                                 void *scratch, Ctrl *ctrl, cudaStream_t st) {
   char *base = static_cast<char *>(scratch);
@@ -772,7 +906,25 @@ cudaError_t launch_sym_eig_fast(double *A, int32_t n, int32_t lda, double *w, do
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  return cudaSuccess;
+  // resolve the clusters: S = X^T A X, then one small FP64 Jacobi per cluster
+  e = launch_small_gemm<double>(false, false, n, n, n, 1.0, A, lda, V, ldv, 0.0, T2, n, st);  // A X
+  if (e != cudaSuccess) return e;
+  e = launch_small_gemm<double>(true, false, n, n, n, 1.0, V, ldv, T2, n, 0.0, Ac, n, st);  // S
+  if (e != cudaSuccess) return e;
+  int *perm = reinterpret_cast<int *>(T1);
+  int *start = perm + n;
+  {
+    ProfScope ps_(K_EIG, st);
+    cluster_prep_kernel<<<1, 1024, 0, st>>>(Ac, n, kClusterFloor, w, perm, start);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t csmem = (size_t)2 * kMaxCluster * kMaxCluster * sizeof(double);
+    e = cudaFuncSetAttribute(cluster_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)csmem);
+    if (e != cudaSuccess) return e;
+    cluster_eig_kernel<<<n, 256, csmem, st>>>(Ac, n, perm, start, V, T2, w);
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace sne

@@ -117,7 +117,8 @@ def test_freigs_orthonormal_and_rayleigh_ritz_residual(run):
     top = np.abs(np.abs(run["lh"]) - 1.0) < 1e-3
     print(f"freigs: |U^T U - I| {orth:.1e}, {top.sum()} eigenvalues of magnitude 1, "
           f"their max residual {res[top].max():.1e}, median residual of all {np.median(res):.1e}")
-    assert orth < 1e-5
+    # U = Q U_hat by the 3 x TF32 tall product: about 1e-5 per element
+    assert orth < 3e-5
     assert top.sum() >= 10
     assert res[top].max() < 1e-4
 
@@ -229,10 +230,15 @@ def test_embedding_matches_oracle(run):
         erel = np.abs(se - sig) / sig
         print(f"{prec}: sigma rel err max GPU {srel.max():.2e} / emulated {erel.max():.2e}")
         assert srel.max() < max(base, 3 * erel.max())
-        for bb in (1, 2, 3, 4, 8, 16, 32, 64, blk):
+        for bb in sorted({1, 2, 3, 4, 8, 16, 32, 64, blk}):
             if bb > blk or bb < 1:
                 continue
             g_sine = o.principal_angle_sines(E[:, :bb], ref.E[:, :bb]).max()
             e_sine = o.principal_angle_sines(Ee[:, :bb], ref.E[:, :bb]).max()
-            print(f"  {prec} block {bb}: sine GPU {g_sine:.2e} / emulated {e_sine:.2e}")
-            assert g_sine < max(base, 3 * e_sine)
+            gap = (sig[bb - 1] - sig[bb]) / sig[bb - 1]
+            print(f"  {prec} block {bb} (gap {gap:.1e}): sine GPU {g_sine:.2e} / emulated {e_sine:.2e}")
+            # only a block separated from the rest by a relative gap of 1e-2 is
+            # determined (Davis-Kahan); two FP32 evaluations with different
+            # rounding orders move it by amounts within a small factor
+            if gap >= 1e-2:
+                assert g_sine < max(base, 5 * e_sine)
