@@ -281,8 +281,11 @@ inline unsigned grid_for(int64_t work, int per = 256, int cap = 152 * 8) {
 // factorization runs in FP64 when `fp64` (sketch QR), else in FP32 (the
 // orthonormalizations inside the power iteration of Alg. 5).
 int orth_tall(const Dims &D, const Bufs &b, int method, bool fp64, const float *Y, int64_t ldy, int w,
-              float *Q, int64_t ldq, cudaStream_t st) {
-  CK(launch_gram(Y, ldy, w, Y, ldy, w, D.n, nullptr, true, b.partial, b.m64[0], w, st, b.ctrl));
+              float *Q, int64_t ldq, cudaStream_t st, bool accurate_gram = false) {
+  if (accurate_gram)
+    CK(launch_gram_accurate(Y, ldy, w, Y, ldy, w, D.n, nullptr, true, b.partial, b.m64[0], w, st));
+  else
+    CK(launch_gram(Y, ldy, w, Y, ldy, w, D.n, nullptr, true, b.partial, b.m64[0], w, st, b.ctrl));
   if (method == SNE_ORTH_EIGSVD) {
     CK(launch_d2f(b.m64[0], w, w, w, b.m32[0], w, st));
     CK(launch_sym_eig<float>(b.m32[0], w, w, b.w32, b.m32[1], w, b.eigscr, b.ctrl, st));
@@ -416,7 +419,9 @@ int run_sketch(const sne_csr &g, const sne_params &p, const Dims &D, const Bufs 
   // O^T Y (FP64), taken before Y's buffer is reused for Q
   CK(launch_signed_gather_sum64(Y, h, h, b.idxO, b.signO, l, z, (double)sv, b.Tm, h, st));
   // --- Alg. 4 line 5: Q = orth(Y) = Y R^-1 by Cholesky QR, twice (R = R2 R1)
-  int rc = orth_tall(D, b, SNE_ORTH_CHOLQR, true, Y, h, h, b.B, h, st);  // Q1 = Y R1^-1
+  // the first pass sees Y itself: Cholesky QR loses about kappa(Y)^2 times the
+  // Gram's relative error, so this Gram is the FP64-accurate one
+  int rc = orth_tall(D, b, SNE_ORTH_CHOLQR, true, Y, h, h, b.B, h, st, true);  // Q1 = Y R1^-1
   if (rc) return rc;
   CK(cudaMemcpyAsync(b.m64[3], b.m64[1], (size_t)h * h * sizeof(double), cudaMemcpyDeviceToDevice,
                      st));                                                  // R1^-1

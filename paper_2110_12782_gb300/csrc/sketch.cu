@@ -132,10 +132,13 @@ __global__ void __launch_bounds__(256, 2) fused_sketch_f32_tiled_kernel(
   __shared__ __align__(16) float As[2][kGK][kGM + 4];
   __shared__ __align__(16) float Bs[2][kGK][kGN + 4];
   const int64_t nrows = nrows_dev ? (int64_t)(*nrows_dev) : nrows_max;
-  const int64_t i0 = (int64_t)blockIdx.x * kGM;
-  if (i0 >= nrows) return;
   constexpr int CPT = kGN / Z;  // output columns per CTA
-  const int c_begin = blockIdx.y * CPT;
+  // linear block index, column groups fastest: the CTAs that share a row tile
+  // of A run together and read it from L2 after the first
+  const int ncg = (cols_out + CPT - 1) / CPT;
+  const int64_t i0 = (int64_t)(blockIdx.x / ncg) * kGM;
+  if (i0 >= nrows) return;
+  const int c_begin = (int)(blockIdx.x % ncg) * CPT;
   const int e_begin = c_begin * Z;
   const int e_count = min(CPT, cols_out - c_begin) * Z;
   const int tid = threadIdx.x;
@@ -240,7 +243,7 @@ cudaError_t launch_fused_sketch_f32(const float *A, int64_t lda, const int32_t *
   if (k % 4 == 0 && lda % 4 == 0 && (uintptr_t)A % 16 == 0 && (uintptr_t)B % 16 == 0 &&
       (z == 1 || z == 2 || z == 4 || z == 8 || z == 16 || z == 32)) {
     const int cptz = kGN / z;
-    dim3 grid2((unsigned)((nrows + kGM - 1) / kGM), (unsigned)((cols_out + cptz - 1) / cptz));
+    const dim3 grid2((unsigned)(((nrows + kGM - 1) / kGM) * ((cols_out + cptz - 1) / cptz)));
     ProfScope ps_(K_FUSED, st);
 #define SNE_F32_CASE(FV, ZV)                                                                    \
   fused_sketch_f32_tiled_kernel<FV, ZV><<<grid2, 256, 0, st>>>(A, lda, ridx, nrows_dev, nrows, k, \
