@@ -199,6 +199,26 @@ def cpu_cores() -> int:
         return os.cpu_count() or 1
 
 
+# --------------------------------------------------------------------------- multi-rank
+def max_over_ranks(x: float, world: int) -> float:
+    """The largest of the ranks' values: the job takes as long as its slowest
+    rank.  NCCL reduces device tensors, gloo host tensors."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_step: float, world: int, steps: int, total_ms: float) -> float:
+    """Whole-job throughput: every rank processes `units_per_step` per step (an
+    independent replica), over the slowest rank's total time."""
+    return world * steps * units_per_step / (total_ms / 1e3)
+
+
 # --------------------------------------------------------------------------- reference arm
 def run_reference(args, rank: int) -> None:
     if rank != 0:
@@ -298,12 +318,8 @@ def run_ours(args, rank: int, world: int) -> None:
     launches = sk.sne_kernel_launches() - launches0
     clk = clocks.stop()
     sk.check_status(ws, "timed steps")
-    total_ms = float(sum(times))
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps * entries / (total_ms / 1e3)
+    total_ms = max_over_ranks(float(sum(times)), world)
+    value = job_value(entries, world, args.steps, total_ms)
 
     # ---- per-kernel-class times (events on the launching stream), same steps
     sk.sne_profile_start()
@@ -331,11 +347,7 @@ def run_ours(args, rank: int, world: int) -> None:
         torch.cuda.synchronize()
         e2e_t.append(time.perf_counter() - t0)
     sk.check_status(ws_h, "e2e steps")
-    e2e_total = float(sum(e2e_t))
-    if world > 1:
-        t = torch.tensor([e2e_total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = max_over_ranks(float(sum(e2e_t)), world)
     h2d = 8 * (g.n + 1) + 4 * g.nnz
     d2h = 4 * g.n * p.d + 8 * p.d
 
@@ -400,8 +412,9 @@ def run_ours(args, rank: int, world: int) -> None:
         # agreement of the two embeddings on the leading singular values
         s32 = sig.cpu().numpy()
         s16 = sigm.cpu().numpy()
-        mixed = {"precision": "fp16", "ms_per_step": float(np.mean(mt)),
-                 "value": world * entries / (float(np.mean(mt)) / 1e3),
+        mixed_total = max_over_ranks(float(sum(mt)), world)
+        mixed = {"precision": "fp16", "ms_per_step": mixed_total / args.steps,
+                 "value": job_value(entries, world, args.steps, mixed_total),
                  "sigma_rel_diff_vs_fp32": float(np.max(np.abs(s16 - s32) / np.abs(s32))),
                  "kernel_ms_per_step": {k: v[2] / args.steps for k, v in
                                         sorted(profm.items(), key=lambda kv: -kv[1][2])}}
@@ -439,7 +452,7 @@ def run_ours(args, rank: int, world: int) -> None:
                        "entries_per_step": entries, "precision": args.precision, "orth": args.orth,
                        "l2": "flushed between steps (256 MB write)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "e2e": {"value": world * args.steps * entries / e2e_total, "unit": UNIT,
+            "e2e": {"value": job_value(entries, world, args.steps, 1e3 * e2e_total), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": 1e3 * e2e_total / args.steps},
             "gpu_launches": int(launches),
@@ -518,12 +531,8 @@ def run_ours_batch(args, rank: int, world: int) -> None:
     sk.sne_embed_batched(dev, p, ws, E, sig, status=status)
     torch.cuda.synchronize()
     launches = (sk.sne_kernel_launches() - l0) * args.steps
-    total_ms = float(sum(times))
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps * entries / (total_ms / 1e3)
+    total_ms = max_over_ranks(float(sum(times)), world)
+    value = job_value(entries, world, args.steps, total_ms)
     # per-class times (eager batched calls; lanes overlap, so shares are of summed kernel time)
     sk.sne_profile_start()
     for _ in range(args.steps):
@@ -552,7 +561,7 @@ def run_ours_batch(args, rank: int, world: int) -> None:
             a.copy_(b, non_blocking=True)
         torch.cuda.synchronize()
         e2e_t.append(time.perf_counter() - t0)
-    e2e_total = float(sum(e2e_t))
+    e2e_total = max_over_ranks(float(sum(e2e_t)), world)
     h2d = sum(8 * (g.n + 1) + 4 * g.nnz for g in graphs)
     d2h = sum(4 * g.n * p.d + 8 * p.d for g in graphs)
     peaks, peak_kind = measured_peaks()
@@ -570,7 +579,7 @@ def run_ours_batch(args, rank: int, world: int) -> None:
                        "precision": args.precision, "orth": args.orth, "cuda_graph": True,
                        "l2": "flushed between steps (256 MB write)",
                        "parallelism": "replicas" if world > 1 else "single GPU, stream lanes"},
-            "e2e": {"value": world * args.steps * entries / e2e_total, "unit": UNIT,
+            "e2e": {"value": job_value(entries, world, args.steps, 1e3 * e2e_total), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": 1e3 * e2e_total / args.steps},
             "gpu_launches": int(launches),
