@@ -319,13 +319,15 @@ int run_freigs(const sne_csr &g, const sne_params &p, const Dims &D, const Bufs 
   float *Q = b.A, *T1 = b.B, *T2 = b.C;
   CK(launch_degree_power(b.deg, D.n, -p.alpha, b.dpow, 1.0f, st));
   CK(launch_spmm_weights(g, b.dpow, b.wnz, st));                  // d_j^-alpha a_ij per nonzero
+  CK(launch_spmm_hot_threshold(b.dpow, D.n, (int64_t)K * 4, b.ctrl, st));  // rows kept in L2
+  const uint32_t *hot = &b.ctrl->hot_bits;
   CK(launch_gaussian(D.n, K, p.seed, 1, T1, ld, st));              // Omega
-  CK(launch_spmm(g, b.dpow, b.wnz, T1, ld, K, T2, K, st));                // Y = X Omega
+  CK(launch_spmm(g, b.dpow, b.wnz, T1, ld, K, T2, K, st, hot));   // Y = X Omega
   int rc = orth_tall(D, b, p.orth, false, T2, K, K, Q, ld, st);    // Q = eigSVD(Y)
   if (rc) return rc;
   for (int it = 0; it < p.q; ++it) {
-    CK(launch_spmm(g, b.dpow, b.wnz, Q, ld, K, T1, ld, st));              // X Q
-    CK(launch_spmm(g, b.dpow, b.wnz, T1, ld, K, T2, K, st));              // X X Q
+    CK(launch_spmm(g, b.dpow, b.wnz, Q, ld, K, T1, ld, st, hot));  // X Q
+    CK(launch_spmm(g, b.dpow, b.wnz, T1, ld, K, T2, K, st, hot));  // X X Q
     rc = orth_tall(D, b, p.orth, false, T2, K, K, Q, ld, st);      // Q = eigSVD(X X Q)
     if (rc) return rc;
   }
@@ -337,7 +339,7 @@ int run_freigs(const sne_csr &g, const sne_params &p, const Dims &D, const Bufs 
   rc = orth_tall(D, b, SNE_ORTH_CHOLQR, false, T2, K, K, Q, ld, st);
   if (rc) return rc;
   // Rayleigh-Ritz: S = Q^T X Q (FP64), eig(S), U = Q U_hat, top k by |lambda|
-  CK(launch_spmm(g, b.dpow, b.wnz, Q, ld, K, T1, ld, st));
+  CK(launch_spmm(g, b.dpow, b.wnz, Q, ld, K, T1, ld, st, hot));
   CK(launch_gram(Q, ld, K, T1, ld, K, D.n, nullptr, false, b.partial, b.m64[0], K, st, b.ctrl));
   CK(launch_symmetrize(b.m64[0], K, K, st));
   CK(launch_sym_eig<double>(b.m64[0], K, K, b.w64, b.m64[1], K, b.eigscr, b.ctrl, st));

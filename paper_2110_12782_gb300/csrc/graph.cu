@@ -64,20 +64,61 @@ cudaError_t launch_degree_power(const float *deg, int64_t n, double beta, float 
   return cudaGetLastError();
 }
 
+// L2 priorities of the SpMM's loads and stores (PTX createpolicy / cache_hint).
+__device__ __forceinline__ uint64_t l2_policy_normal() {
+  uint64_t pol;
+  asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ uint64_t l2_policy_first() {
+  uint64_t pol;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ float4 ld_nc_f4(const float4 *ptr, uint64_t pol) {
+  float4 v;
+  asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+      : "l"(ptr), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ float ld_nc_f32(const float *ptr, uint64_t pol) {
+  float v;
+  asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(ptr), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ int32_t ld_nc_s32(const int32_t *ptr, uint64_t pol) {
+  int32_t v;
+  asm("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(ptr), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st_f4(float4 *ptr, float4 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(ptr), "f"(v.x),
+               "f"(v.y), "f"(v.z), "f"(v.w), "l"(pol)
+               : "memory");
+}
+
 // Y[i, :] = s_i * sum_{p in row i} w_p s_{col_p} B[col_p, :],  s = d^-a.
 // One warp per row; each lane owns VPL float4 column groups of the row; the
 // row's (col, weight) pairs are fetched 32 at a time and broadcast by shuffle.
 // On power-law graphs the dense operand does not fit in L2 and the kernel is
 // bound by the latency of its gathers: the per-nonzero weights come
 // precomputed (one dependent load less) and two blocks stay resident per SM.
+// Row j of B is gathered deg(j) times, so L2 holds the rows of the vertices of
+// largest degree best: those rows (weight bits below *hot) load with the
+// normal priority, while the other rows, the CSR arrays and Y go evict-first
+// and do not push them out.
 template <int VPL>
 __global__ void __launch_bounds__(256, 2) spmm_vec4_kernel(
     int64_t n, const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
     const float *__restrict__ val, const float *__restrict__ dpow, const float *__restrict__ wnz,
-    const float *__restrict__ B, int64_t ldb, int32_t nvec, float *__restrict__ Y, int64_t ldy) {
+    const float *__restrict__ B, int64_t ldb, int32_t nvec, float *__restrict__ Y, int64_t ldy,
+    const uint32_t *__restrict__ hot) {
   const int lane = threadIdx.x & 31;
   const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (row >= n) return;
+  const uint64_t pol_keep = l2_policy_normal(), pol_stream = l2_policy_first();
+  const uint32_t thr = hot ? *hot : 0xffffffffu;
   float4 acc[VPL];
 #pragma unroll
   for (int v = 0; v < VPL; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -87,8 +128,8 @@ __global__ void __launch_bounds__(256, 2) spmm_vec4_kernel(
     int32_t c = 0;
     float w = 0.f;
     if (p < end) {
-      c = col[p];
-      w = wnz ? wnz[p] : dpow[c] * (val ? val[p] : 1.0f);
+      c = ld_nc_s32(col + p, pol_stream);
+      w = wnz ? ld_nc_f32(wnz + p, pol_stream) : dpow[c] * (val ? val[p] : 1.0f);
     }
     const int cnt = (int)min64(32, end - p0);
     int t = 0;
@@ -97,14 +138,16 @@ __global__ void __launch_bounds__(256, 2) spmm_vec4_kernel(
       const int32_t c1 = __shfl_sync(0xffffffffu, c, t + 1);
       const float w0 = __shfl_sync(0xffffffffu, w, t);
       const float w1 = __shfl_sync(0xffffffffu, w, t + 1);
+      const uint64_t pl0 = __float_as_uint(w0) < thr ? pol_keep : pol_stream;
+      const uint64_t pl1 = __float_as_uint(w1) < thr ? pol_keep : pol_stream;
       const float4 *r0 = reinterpret_cast<const float4 *>(B + (int64_t)c0 * ldb);
       const float4 *r1 = reinterpret_cast<const float4 *>(B + (int64_t)c1 * ldb);
 #pragma unroll
       for (int v = 0; v < VPL; ++v) {
         const int q = lane + 32 * v;
         if (q < nvec) {
-          const float4 x0 = __ldg(r0 + q);
-          const float4 x1 = __ldg(r1 + q);
+          const float4 x0 = ld_nc_f4(r0 + q, pl0);
+          const float4 x1 = ld_nc_f4(r1 + q, pl1);
           acc[v].x += w0 * x0.x + w1 * x1.x;
           acc[v].y += w0 * x0.y + w1 * x1.y;
           acc[v].z += w0 * x0.z + w1 * x1.z;
@@ -115,12 +158,13 @@ __global__ void __launch_bounds__(256, 2) spmm_vec4_kernel(
     for (; t < cnt; ++t) {
       const int32_t c0 = __shfl_sync(0xffffffffu, c, t);
       const float w0 = __shfl_sync(0xffffffffu, w, t);
+      const uint64_t pl0 = __float_as_uint(w0) < thr ? pol_keep : pol_stream;
       const float4 *r0 = reinterpret_cast<const float4 *>(B + (int64_t)c0 * ldb);
 #pragma unroll
       for (int v = 0; v < VPL; ++v) {
         const int q = lane + 32 * v;
         if (q < nvec) {
-          const float4 x0 = __ldg(r0 + q);
+          const float4 x0 = ld_nc_f4(r0 + q, pl0);
           acc[v].x += w0 * x0.x;
           acc[v].y += w0 * x0.y;
           acc[v].z += w0 * x0.z;
@@ -134,7 +178,9 @@ __global__ void __launch_bounds__(256, 2) spmm_vec4_kernel(
 #pragma unroll
   for (int v = 0; v < VPL; ++v) {
     const int q = lane + 32 * v;
-    if (q < nvec) yr[q] = make_float4(si * acc[v].x, si * acc[v].y, si * acc[v].z, si * acc[v].w);
+    if (q < nvec)
+      st_f4(yr + q, make_float4(si * acc[v].x, si * acc[v].y, si * acc[v].z, si * acc[v].w),
+            pol_stream);
   }
 }
 
@@ -186,8 +232,59 @@ cudaError_t launch_spmm_weights(const sne_csr &g, const float *dpow, float *wnz,
   return cudaGetLastError();
 }
 
+// The keep bound: a strided sample of kHotSample values of d^-a, sorted
+// (bitonic, one CTA); the bound is the sample's quantile at the fraction of
+// vertices whose rows fit kSpmmKeepBytes, so that weights strictly below it
+// (the largest degrees) are kept.  With weighted edges the per-nonzero weight
+// val_p d_j^-a only approximates the degree order, which moves rows between
+// the two L2 classes and never changes a result.
+constexpr int kHotSample = 2048;
+constexpr int64_t kSpmmKeepBytes = 80ll << 20;  // of the 129 MB L2
+
+__global__ void __launch_bounds__(1024) spmm_hot_threshold_kernel(const float *__restrict__ dpow,
+                                                                   int64_t n, int64_t keep_rows,
+                                                                   Ctrl *ctrl) {
+  __shared__ uint32_t sv[kHotSample];
+  const int tid = threadIdx.x;
+  if (keep_rows >= n) {
+    if (tid == 0) ctrl->hot_bits = 0xffffffffu;
+    return;
+  }
+  for (int i = tid; i < kHotSample; i += blockDim.x)
+    sv[i] = __float_as_uint(dpow[(int64_t)((double)i * (double)n / kHotSample)]);
+  __syncthreads();
+  for (int k = 2; k <= kHotSample; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < kHotSample; i += blockDim.x) {
+        const int l = i ^ j;
+        if (l > i) {
+          const uint32_t a = sv[i], b = sv[l];
+          if ((a > b) == ((i & k) == 0)) {
+            sv[i] = b;
+            sv[l] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (tid == 0) {
+    const int at = (int)((double)keep_rows / (double)n * kHotSample);  // < kHotSample
+    ctrl->hot_bits = sv[at < 0 ? 0 : at];
+  }
+}
+
+cudaError_t launch_spmm_hot_threshold(const float *dpow, int64_t n, int64_t row_bytes, Ctrl *ctrl,
+                                      cudaStream_t st) {
+  if (n <= 0 || row_bytes <= 0) return cudaSuccess;
+  ProfScope ps_(K_MISC, st);
+  spmm_hot_threshold_kernel<<<1, 1024, 0, st>>>(dpow, n, kSpmmKeepBytes / row_bytes, ctrl);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_spmm(const sne_csr &g, const float *dpow, const float *wnz, const float *B,
-                        int64_t ldb, int32_t ncols, float *Y, int64_t ldy, cudaStream_t st) {
+                        int64_t ldb, int32_t ncols, float *Y, int64_t ldy, cudaStream_t st,
+                        const uint32_t *hot) {
   if (g.n <= 0 || ncols <= 0) return cudaSuccess;
 
   ProfScope ps_(K_SPMM, st);
@@ -200,7 +297,7 @@ cudaError_t launch_spmm(const sne_csr &g, const float *dpow, const float *wnz, c
 #define SNE_SPMM_CASE(V)                                                                     \
   case V:                                                                                    \
     spmm_vec4_kernel<V><<<blocks, 256, 0, st>>>(g.n, g.row_ptr, g.col_idx, g.val, dpow, wnz, B, \
-                                                ldb, nvec, Y, ldy);                          \
+                                                ldb, nvec, Y, ldy, hot);                     \
     break;
     switch (vpl) {
       SNE_SPMM_CASE(1)

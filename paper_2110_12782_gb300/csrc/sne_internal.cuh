@@ -22,7 +22,8 @@ struct Ctrl {
   int32_t v_s;     // unique rows of S (Alg. 4 line 3)
   int32_t v_o;     // unique rows of O (Alg. 4 line 6)
   double vol;      // vol(G)
-  int32_t pad[58];
+  uint32_t hot_bits;  // SpMM L2 split: weights whose bits are below it mark kept rows
+  int32_t pad[57];
 };
 static_assert(sizeof(Ctrl) == 256, "control block is 256 bytes");
 
@@ -107,8 +108,17 @@ cudaError_t launch_degree_power(const float *deg, int64_t n, double beta, float 
 // wnz: per-nonzero weights dpow[col_p] * val_p (launch_spmm_weights), or NULL
 // to form them on the fly.
 cudaError_t launch_spmm_weights(const sne_csr &g, const float *dpow, float *wnz, cudaStream_t st);
+// Picks the rows of the dense SpMM operand that stay in L2: the vertices of
+// largest degree (smallest d^-a), as many as fill kSpmmKeepBytes at
+// `row_bytes` a row; writes the bit pattern bound to ctrl->hot_bits.
+cudaError_t launch_spmm_hot_threshold(const float *dpow, int64_t n, int64_t row_bytes, Ctrl *ctrl,
+                                      cudaStream_t st);
+// hot: that bound (a gathered row whose weight bits are below it is loaded with
+// the normal L2 priority, every other row and the CSR streams evict-first), or
+// NULL to load every row with the normal priority.
 cudaError_t launch_spmm(const sne_csr &g, const float *dpow, const float *wnz, const float *B,
-                        int64_t ldb, int32_t ncols, float *Y, int64_t ldy, cudaStream_t st);
+                        int64_t ldb, int32_t ncols, float *Y, int64_t ldy, cudaStream_t st,
+                        const uint32_t *hot = nullptr);
 cudaError_t launch_validate(const sne_csr &g, Ctrl *ctrl, cudaStream_t st);
 
 // dense.cu

@@ -209,6 +209,36 @@ def test_spmm_fullsize(sk, width, weights):
     assert err < 1e-5
 
 
+def test_freigs_with_l2_row_split(sk):
+    """freigs on a Chung-Lu graph (n = 300,000, mean degree 20, exponent 2.1)
+    whose 272-column SpMM operand (326 MB) holds more rows than the SpMM keeps
+    in L2 (80 MB), so that its gathers split between the normal and the
+    evict-first class: U orthonormal, and the eigenpairs of magnitude 1
+    converged (Rayleigh-Ritz residual)."""
+    from oracle import sketchne_oracle as o
+    from paper_2110_12782_gb300 import synth
+    g = synth.chung_lu(300_000, 20.0, 2.1, seed=1)
+    G = sk.DeviceGraph.from_numpy(g.row_ptr, g.col_idx)
+    k = 256
+    p = sk.sne_params_init(128, k, orth=sk.SNE_ORTH_CHOLQR)
+    ws = sk.workspace(g.n, g.nnz, p, sk.SNE_WS_FREIGS)
+    U = torch.empty(g.n, k, dtype=torch.float32, device="cuda")
+    lam = torch.empty(k, dtype=torch.float64, device="cuda")
+    sk.sne_freigs(G, p, ws, U, lam)
+    assert sk.sne_status(ws) == 0
+    eye = torch.eye(k, dtype=torch.float64, device="cuda")
+    orth = float((U.T.double() @ U.double() - eye).abs().max())
+    Uh = U.cpu().numpy().astype(np.float64)
+    lh = lam.cpu().numpy()
+    X = o.normalized_operator(o.adjacency(g.row_ptr, g.col_idx, g.n), 0.5)
+    res = np.linalg.norm(X @ Uh - Uh * lh[None, :], axis=0)
+    top = np.abs(np.abs(lh) - 1.0) < 1e-3
+    print(f"freigs n=300k: |U^T U - I| {orth:.1e}, {top.sum()} eigenvalues of magnitude 1, "
+          f"their max residual {res[top].max() if top.any() else 0:.1e}, median {np.median(res):.1e}")
+    assert orth < 3e-5
+    assert top.sum() >= 1 and res[top].max() < 1e-4
+
+
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
 @pytest.mark.parametrize("n", [5, 16, 17, 100, 272, 300])
 @pytest.mark.parametrize("pivot", [False, True])
