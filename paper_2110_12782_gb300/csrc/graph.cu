@@ -250,8 +250,12 @@ __global__ void __launch_bounds__(1024) spmm_hot_threshold_kernel(const float *_
     if (tid == 0) ctrl->hot_bits = 0xffffffffu;
     return;
   }
-  for (int i = tid; i < kHotSample; i += blockDim.x)
-    sv[i] = __float_as_uint(dpow[(int64_t)((double)i * (double)n / kHotSample)]);
+  // d^-a = 0 marks an isolated vertex, whose row is never gathered: it sorts
+  // last so that it takes no place in the kept set
+  for (int i = tid; i < kHotSample; i += blockDim.x) {
+    const uint32_t b = __float_as_uint(dpow[(int64_t)((double)i * (double)n / kHotSample)]);
+    sv[i] = b == 0u ? 0xffffffffu : b;
+  }
   __syncthreads();
   for (int k = 2; k <= kHotSample; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
