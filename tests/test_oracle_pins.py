@@ -330,3 +330,31 @@ def test_embedding_dominant_subspace_matches_dense_svd():
     resid = np.linalg.norm(F - Ud @ (Ud.T @ F))
     optimum = math.sqrt(float(np.sum(sv[8:] ** 2)))
     assert optimum <= resid <= 1.1 * optimum
+
+
+def test_principal_angle_sines_known_angles():
+    # span{e1, e2} against span{e1, cos(t) e2 + sin(t) e3}: principal angles
+    # (t, 0) by construction; the spans do not depend on the bases chosen
+    rng = np.random.default_rng(11)
+    n, t = 7, 0.3
+    E = np.eye(n)
+    A = E[:, :2]
+    B = np.stack([E[:, 0], np.cos(t) * E[:, 1] + np.sin(t) * E[:, 2]], axis=1)
+    s = o.principal_angle_sines(A @ rng.standard_normal((2, 2)), B @ rng.standard_normal((2, 2)))
+    assert np.allclose(s, [np.sin(t), 0.0], atol=1e-7)
+    # orthogonal spans: every angle is pi/2; a span against itself: 0
+    assert np.allclose(o.principal_angle_sines(E[:, :3], E[:, 3:6]), 1.0)
+    assert o.principal_angle_sines(A, A[:, ::-1]).max() < 1e-7
+    # a rotation by t in the (e1, e4) plane and by 2t in the (e2, e5) plane
+    C = np.stack([np.cos(t) * E[:, 0] + np.sin(t) * E[:, 3],
+                  np.cos(2 * t) * E[:, 1] + np.sin(2 * t) * E[:, 4]], axis=1)
+    assert np.allclose(o.principal_angle_sines(A, C), [np.sin(2 * t), np.sin(t)], atol=1e-12)
+
+
+def test_sketch_rows_equal_dense_definition():
+    g, fac = _small_factors()
+    S = o.gen_sparse_sign(g.n, 40, 8, seed=5, stream=2)
+    rows = np.array([0, 3, 17, g.n - 1])
+    got = o.sketch_Y_rows(fac.Lp[rows], fac.Rp, S)
+    ref = o.trunc_log(fac.Lp[rows] @ fac.Rp) @ S.dense()
+    assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref)
