@@ -90,3 +90,59 @@ def test_host_side_argument_errors_enqueue_nothing(L):
     assert L.sne_sparse_sign(0, 10, 8, 0, 2, None, None, None) == sk.SNE_ERR_ARG
     assert L.sne_sparse_sign(1000, 10, 65, 0, 2, 256, 512, None) == sk.SNE_ERR_SIZE
     assert L.sne_status(None, None) == sk.SNE_ERR_WORKSPACE
+
+
+def test_building_block_argument_errors_on_the_host(L):
+    """The dense building blocks reject bad sizes, leading dimensions, flags and
+    workspaces before any CUDA call (fake device addresses, never read)."""
+    ARG, WS = sk.SNE_ERR_ARG, sk.SNE_ERR_WORKSPACE
+    nb = ctypes.c_size_t(0)
+    assert L.sne_gram_workspace_bytes(1000, 16, 16, ctypes.byref(nb)) == 0 and nb.value > 0
+    assert L.sne_gram_workspace_bytes(0, 16, 16, ctypes.byref(nb)) == ARG
+    A, C = 1 << 20, 1 << 21
+    need = nb.value
+    assert L.sne_gram(0, 16, 16, A, 16, A, 16, None, C, 16, 0, 256, need, None) == ARG
+    assert L.sne_gram(1000, 16, 16, A, 8, A, 16, None, C, 16, 0, 256, need, None) == ARG  # lda < ka
+    assert L.sne_gram(1000, 16, 16, A, 16, A, 16, None, C, 16, 2, 256, need, None) == ARG  # flag
+    assert L.sne_gram(1000, 16, 16, None, 16, A, 16, None, C, 16, 0, 256, need, None) == ARG
+    assert L.sne_gram(1000, 16, 16, A, 16, A, 16, None, C, 16, 0, None, need, None) == WS
+    assert L.sne_gram(1000, 16, 16, A, 16, A, 16, None, C, 16, 0, 257, need, None) == WS  # unaligned
+    assert L.sne_gram(1000, 16, 16, A, 16, A, 16, None, C, 16, 0, 256, need - 1, None) == WS
+    assert L.sne_tall_gemm_workspace_bytes(16, 8, ctypes.byref(nb)) == 0
+    assert L.sne_tall_gemm(1000, 16, 8, A, 16, A, 4, C, 8, 256, nb.value, None) == ARG  # ldm < kc
+    assert L.sne_tall_gemm(1000, 16, 8, A, 16, A, 8, C, 8, 256, nb.value - 1, None) == WS
+    assert L.sne_sym_eig_workspace_bytes(1025, ctypes.byref(nb)) == ARG
+    assert L.sne_sym_eig_workspace_bytes(272, ctypes.byref(nb)) == 0
+    assert L.sne_sym_eig(272, A, 271, C, C, 272, 256, nb.value, None) == ARG  # lds < n
+    assert L.sne_sym_eig(272, A, 272, C, C, 272, 256, nb.value - 1, None) == WS
+    assert L.sne_chol_inverse_workspace_bytes(300, 1, ctypes.byref(nb)) == 0
+    assert L.sne_chol_inverse(300, A, 300, C, 299, 1, -1.0, 256, nb.value, None) == ARG
+    assert L.sne_chol_inverse(300, A, 300, C, 300, 1, -1.0, 256, nb.value - 1, None) == WS
+
+
+def test_batched_argument_errors_on_the_host(L):
+    p = sk.sne_params_init(16, 32)
+    graphs = (sk.sne_csr * 2)(sk.sne_csr(5000, 40000, 256, 512, None),
+                              sk.sne_csr(3000, 20000, 768, 1024, None))
+    nb = ctypes.c_size_t(0)
+    assert L.sne_embed_batched_workspace_bytes(2, graphs, ctypes.byref(p), 0, ctypes.byref(nb)) == 0
+    one = ctypes.c_size_t(0)
+    assert L.sne_embed_batched_workspace_bytes(2, graphs, ctypes.byref(p), 1, ctypes.byref(one)) == 0
+    # two lanes hold both graphs' workspaces, one lane only the larger one
+    assert nb.value > one.value > 0
+    assert L.sne_embed_batched_workspace_bytes(0, graphs, ctypes.byref(p), 0, ctypes.byref(nb)) == \
+        sk.SNE_ERR_ARG
+    assert L.sne_embed_batched_workspace_bytes(2, graphs, ctypes.byref(p), 17, ctypes.byref(nb)) == \
+        sk.SNE_ERR_ARG
+    bad = (sk.sne_csr * 1)(sk.sne_csr(0, 0, 256, None, None))
+    assert L.sne_embed_batched_workspace_bytes(1, bad, ctypes.byref(p), 0, ctypes.byref(nb)) == \
+        sk.SNE_ERR_ARG
+    E = (ctypes.c_void_p * 2)(1 << 20, None)
+    S = (ctypes.c_void_p * 2)(1 << 21, 1 << 22)
+    assert L.sne_embed_batched(2, graphs, ctypes.byref(p), 0, 256, 1 << 40, E, S, None, None) == \
+        sk.SNE_ERR_ARG
+    E = (ctypes.c_void_p * 2)(1 << 20, 1 << 23)
+    assert L.sne_embed_batched(2, graphs, ctypes.byref(p), 0, None, 1 << 40, E, S, None, None) == \
+        sk.SNE_ERR_WORKSPACE
+    assert L.sne_embed_batched(2, graphs, ctypes.byref(p), 0, 256, 1000, E, S, None, None) == \
+        sk.SNE_ERR_WORKSPACE
