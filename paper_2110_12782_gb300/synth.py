@@ -17,8 +17,9 @@ Graph families (stand-ins for the paper's datasets of Table 1):
   ``w_i ~ (i + i0)^(-1/(gamma-1))`` are scaled so that their sum is
   ``n * avg_degree`` after capping every weight at ``sqrt(n * avg_degree)``;
   endpoint pairs are drawn i.i.d. with probability proportional to ``w``,
-  self-loops and repeats are dropped, and drawing continues until
-  ``n * avg_degree / 2`` distinct edges exist (realized mean degree = target).
+  self-loops and repeats are dropped, and drawing continues until at least
+  ``n * avg_degree / 2`` distinct edges exist (the last batch of draws
+  overshoots, so the realized mean degree is up to about 1% above the target).
   Vertex ids are therefore sorted by expected degree (id 0 is the largest hub).
 * ``complete_graph``, ``complete_bipartite_union``, ``from_edges``: small
   graphs with closed-form spectra, used to pin the oracle.
