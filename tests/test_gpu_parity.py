@@ -164,6 +164,25 @@ def test_sketch_Y_Z_E_match_oracle_with_oracle_factors(sk, c1):
     assert np.allclose(Ud.T @ Ud, np.eye(Ud.shape[1]), atol=1e-4)
 
 
+
+def test_sketch_matches_oracle_at_alpha_04(sk):
+    """Eq. 11 with a full core: at alpha = 0.4, G = U^T D^(-0.2) U is not the
+    identity, so K = G Lambda and the Horner sum are dense k x k matrices.
+    Y, Z, the singular values and the 8 block directions of the SBM (relative
+    gap 7%) against the oracle, from the oracle's factors."""
+    g = synth.named("sbm4096")
+    p = o.Params(k=128, d=32, alpha=0.4)
+    ref = o.embed(g.row_ptr, g.col_idx, g.n, p)
+    Y, Z, E, sig, st = run_sketch(sk, g, p, ref.U_k, ref.lam)
+    assert st.v_s == len(ref.sp.S.p) and st.v_o == len(ref.sp.O.p)
+    assert rel(Y, ref.sp.Y) < SKETCH_RTOL
+    assert rel(Z, ref.sp.Z) < SKETCH_RTOL
+    assert np.allclose(sig[:8], ref.sigma[:8], rtol=1e-3)
+    sines = o.principal_angle_sines(E[:, :8], ref.E[:, :8])
+    print(f"alpha 0.4: Y rel {rel(Y, ref.sp.Y):.1e}, Z rel {rel(Z, ref.sp.Z):.1e}, "
+          f"8-block sine {sines.max():.1e}")
+    assert sines.max() < ANGLE_TOL
+
 def test_identity_f_single_pass_is_exact(sk):
     # f = identity, rank(L'R') = k = h: Y has full column rank and spans
     # range(L'), so the sketch recovers the SVD of L'R' exactly
