@@ -165,14 +165,19 @@ def test_sketch_Y_Z_E_match_oracle_with_oracle_factors(sk, c1):
 
 
 
-def test_sketch_matches_oracle_at_alpha_04(sk):
+@pytest.fixture(scope="module")
+def c1_alpha04():
+    g = synth.named("sbm4096")
+    p = o.Params(k=128, d=32, alpha=0.4)
+    return g, p, o.embed(g.row_ptr, g.col_idx, g.n, p)
+
+
+def test_sketch_matches_oracle_at_alpha_04(sk, c1_alpha04):
     """Eq. 11 with a full core: at alpha = 0.4, G = U^T D^(-0.2) U is not the
     identity, so K = G Lambda and the Horner sum are dense k x k matrices.
     Y, Z, the singular values and the 8 block directions of the SBM (relative
     gap 7%) against the oracle, from the oracle's factors."""
-    g = synth.named("sbm4096")
-    p = o.Params(k=128, d=32, alpha=0.4)
-    ref = o.embed(g.row_ptr, g.col_idx, g.n, p)
+    g, p, ref = c1_alpha04
     Y, Z, E, sig, st = run_sketch(sk, g, p, ref.U_k, ref.lam)
     assert st.v_s == len(ref.sp.S.p) and st.v_o == len(ref.sp.O.p)
     assert rel(Y, ref.sp.Y) < SKETCH_RTOL
@@ -231,6 +236,29 @@ def test_freigs_matches_oracle(sk, c1, orth):
     assert sines.max() < ANGLE_TOL
     assert np.allclose(U.T @ U, np.eye(pr.k), atol=1e-4)
 
+
+
+def test_freigs_matches_oracle_at_alpha_04(sk, c1_alpha04):
+    """Alg. 5 on D^-0.4 A D^-0.4 (largest eigenvalue 1.56, not 1): the top
+    eigenvalues and the leading 8-dimensional subspace against the oracle's
+    freigs from the same Omega."""
+    g, p, ref = c1_alpha04
+    pr = p.resolved()
+    G = dev_graph(sk, g)
+    q = gpu_params(sk, p, orth=sk.SNE_ORTH_CHOLQR)
+    ws = sk.workspace(g.n, g.nnz, q, sk.SNE_WS_FREIGS)
+    U = torch.empty(g.n, pr.k, dtype=torch.float32, device="cuda")
+    lam = torch.empty(pr.k, dtype=torch.float64, device="cuda")
+    sk.sne_freigs(G, q, ws, U, lam)
+    assert sk.sne_status(ws) == 0
+    U = U.cpu().numpy().astype(np.float64)
+    lam = lam.cpu().numpy()
+    scale = abs(ref.lam[0])
+    print(f"alpha 0.4 freigs: top-8 eigenvalue error {np.max(np.abs(lam[:8] - ref.lam[:8])):.1e}")
+    assert np.allclose(lam[:8], ref.lam[:8], atol=1e-5 * scale)
+    assert np.max(np.abs(lam - ref.lam)) < 5e-3 * scale
+    assert o.principal_angle_sines(U[:, :8], ref.U_k[:, :8]).max() < ANGLE_TOL
+    assert np.allclose(U.T @ U, np.eye(pr.k), atol=1e-4)
 
 def test_embed_matches_oracle(sk, c1):
     g, p, ref = c1
