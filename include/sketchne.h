@@ -79,7 +79,7 @@ typedef struct sne_params {
   uint64_t seed;
 } sne_params;
 
-/* Counters filled by sne_stats() (host struct). */
+/* Counters filled by sne_stats_read() (host struct). */
 typedef struct sne_stats {
   int32_t status;   /* device status word (SNE_OK or SNE_ERR_*) */
   int32_t where;    /* id of the kernel that set the status (0 = none) */
