@@ -116,16 +116,19 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def profiled_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary table
-    (profiles/traffic.json), or None when the kernel is not listed."""
+def profiled_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
+    summary table (profiles/traffic.json), or None when the table has no
+    capture of that kernel on that workload."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         tab = json.load(f)
     ent = tab.get(kernel)
-    return None if ent is None else ent.get("dram_bytes_per_launch")
+    if ent is None or ent.get("workload") != workload:
+        return None
+    return ent.get("dram_bytes_per_launch")
 
 
 def measured_peaks() -> tuple[dict, str]:
@@ -375,7 +378,7 @@ def run_ours(args, rank: int, world: int) -> None:
                 achieved = work / (per_step_ms / 1e3) / 1e12
                 peak = alu_peak_tflops(float(peaks.get("sm_max_mhz", 2070.0)))
             roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak,
-                        "unit": unit, "frac": achieved / peak, "traffic": profiled_traffic(dom),
+                        "unit": unit, "frac": achieved / peak, "traffic": profiled_traffic(dom, args.workload),
                         "peak_source": {"alu": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
                                         "tensor_tf32x3": f"{peak_kind} bf16 x 1.1/2.25 / 3"}.get(
                                             bound, f"{peak_kind}"),
@@ -583,7 +586,9 @@ def run_ours_batch(args, rank: int, world: int) -> None:
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": 1e3 * e2e_total / args.steps},
             "gpu_launches": int(launches),
-            "roofline": {"kernel": dom, "note": "lanes overlap; see the single-graph workload "
+            "roofline": {"kernel": dom, "bound": None, "achieved": None, "peak": None,
+                         "unit": None, "frac": None, "traffic": None,
+                         "note": "lanes overlap; see the single-graph workload "
                          "for per-kernel rooflines", "peak_source": peak_kind},
             "cpu_baseline": None,
             "clocks": clk,
