@@ -15,7 +15,7 @@ Paper: "SketchNE: Embedding Billion-Scale Networks Accurately in One Hour"
 (arXiv 2110.12782).  Section, equation and algorithm numbers below are the
 paper's.
 
-Readings of points the paper leaves open (each is also listed in the design doc):
+Readings of points the paper leaves open:
 
 * ``unique`` (Alg. 3) returns the coordinates sorted ascending.
 * ``randperm(n, z)`` (Alg. 3) is z distinct rows drawn uniformly without
