@@ -143,8 +143,9 @@ def measured_peaks() -> tuple[dict, str]:
 # --------------------------------------------------------------------------- algorithmic work
 def algorithmic_work(cls: str, n: int, nnz: int, p, v_s: int, v_o: int) -> tuple[float, str, str]:
     """Algorithmic work of one step for a kernel class: bytes for the SpMM (row
-    pointers, column indices, per-nonzero weights, the row scales, one read of
-    the dense operand and one write of the result per call), flops for the
+    pointers, column indices, the vector d^-a, one read of the dense operand and
+    one write of the result per call; the per-nonzero weights the kernel streams
+    are derived data and not counted), flops for the
     products (2 n K K' per Gram or tall product, symmetric Grams counted in full)
     and for Eq. 4 (2k per evaluated entry of L'R')."""
     K = p.k + p.s_eig
