@@ -4,6 +4,7 @@ return before any CUDA work)."""
 import ctypes
 import os
 import re
+import types
 
 import pytest
 
@@ -146,3 +147,20 @@ def test_batched_argument_errors_on_the_host(L):
         sk.SNE_ERR_WORKSPACE
     assert L.sne_embed_batched(2, graphs, ctypes.byref(p), 0, 256, 1000, E, S, None, None) == \
         sk.SNE_ERR_WORKSPACE
+
+
+def test_no_cpu_fallback(L, monkeypatch):
+    """Host tensors are refused before any call, and a missing library is an
+    error, never a silent switch to another implementation."""
+    import torch
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        sk.DeviceGraph(torch.zeros(5, dtype=torch.int64), torch.zeros(4, dtype=torch.int32))
+    p = sk.sne_params_init(8, 16)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        g = types.SimpleNamespace(csr=sk.sne_csr(4, 0, None, None, None))
+        sk.sne_spmm(g, torch.zeros(4), torch.zeros(4, 4), torch.zeros(4, 4))
+    monkeypatch.setattr(sk, "_lib", None)
+    monkeypatch.setattr(sk, "LIB_PATH", os.path.join(ROOT, "no_such_library.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        sk.sne_params_init(8, 16)
+    assert p.d == 8
