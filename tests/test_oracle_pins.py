@@ -358,3 +358,32 @@ def test_sketch_rows_equal_dense_definition():
     got = o.sketch_Y_rows(fac.Lp[rows], fac.Rp, S)
     ref = o.trunc_log(fac.Lp[rows] @ fac.Rp) @ S.dense()
     assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_lemire_rejection_leaves_exactly_one_preimage(monkeypatch):
+    """Lemire's theorem for bounds n > 2^63: every output v in [0, n) keeps
+    exactly floor(2^64 / n) = 1 accepted 64-bit draw.  The draws mapping to v
+    (x with floor(x n / 2^64) = v) are fed to the oracle one at a time and the
+    accepted ones counted, so a wrong rejection threshold or a missing rejection
+    leaves some v with 0 or 2 preimages."""
+    rng = np.random.default_rng(5)
+    for n in [(1 << 63) + 1, (1 << 63) + 12345, (1 << 64) - 5, 3 << 62]:
+        assert (1 << 64) // n == 1
+        vs = [0, 1, 2, n - 1, n - 2] + [int(v) for v in rng.integers(0, n, size=60, dtype=np.uint64)
+                                        if int(v) < n]
+        for v in vs:
+            lo_x = -((-v << 64) // n)                 # ceil(v 2^64 / n)
+            hi_x = -((-(v + 1) << 64) // n)           # ceil((v+1) 2^64 / n)
+            accepted = 0
+            for x in range(lo_x, min(hi_x, 1 << 64)):
+                # the draw under test at counter 0; any later draw is 2^64 - 1,
+                # which is accepted for these n (its low word 2^64 - n equals
+                # the threshold 2^64 mod n), so a rejection ends after one redraw
+                monkeypatch.setattr(o, "draw",
+                                    lambda key, ctr, x=x: x if ctr == 0 else (1 << 64) - 1)
+                val, ctr2 = o.bounded(0, 0, n)
+                assert ctr2 in (1, 2)
+                if ctr2 == 1:
+                    assert val == v
+                    accepted += 1
+            assert accepted == 1, (n, v, lo_x, hi_x)
