@@ -177,7 +177,11 @@ int sne_spmm_weights(const sne_csr *g, const float *dpow, float *w_nz, sne_strea
 
 /* One SpMM of Alg. 5: Y = D^-a A D^-a B, given dpow_i = d_i^-a and optionally
  * the per-nonzero weights of sne_spmm_weights (NULL: formed on the fly, one
- * more dependent load per nonzero).  B, Y: n x ncols FP32, distinct buffers. */
+ * more dependent load per nonzero).  B, Y: n x ncols FP32 row-major, distinct
+ * buffers.  The CSR arrays and Y pass through L2 evict-first and the rows of B
+ * at the normal priority (inside sne_embed and sne_freigs only the rows of the
+ * vertices of largest degree keep the normal priority, as many as fill 80 MB);
+ * the priorities never change a result. */
 int sne_spmm(const sne_csr *g, const float *dpow, const float *w_nz, const float *B, int32_t ncols,
              float *Y, sne_stream_t stream);
 
