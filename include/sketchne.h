@@ -37,7 +37,8 @@ typedef struct CUstream_st *sne_stream_t; /* the same type as cudaStream_t */
 enum {
   SNE_OK = 0,
   SNE_ERR_ARG = -1,       /* bad argument (NULL pointer, negative size, ...) */
-  SNE_ERR_GRAPH = -2,     /* CSR not valid: row_ptr not monotone, index out of range, asymmetric */
+  SNE_ERR_GRAPH = -2,     /* CSR not valid (row_ptr not monotone, index out of range, asymmetric),
+                             or no edges for an embedding (vol(G) = 0, Eq. 1 undefined) */
   SNE_ERR_SIZE = -3,      /* inconsistent sizes: k+s > n, d > h, h > l, z > 64, ... */
   SNE_ERR_WORKSPACE = -4, /* workspace NULL, too small or not 256-byte aligned */
   SNE_ERR_CUDA = -5,      /* a CUDA launch or runtime call failed */

@@ -24,7 +24,8 @@ Readings of points the paper leaves open:
 * ``freigs`` (Alg. 5) returns the k eigenpairs of largest |lambda| (the
   quantity of Lemma 4 / Theorem 1), ordered by |lambda| descending.
 * For an isolated vertex (degree 0) every power of its degree is taken as 0
-  (pseudo-inverse), so its rows of X, L', R', Y and E are 0.
+  (pseudo-inverse), so its rows of X, L', R', Y and E are 0.  A graph with no
+  edges at all (vol(G) = 0, Eq. 1 undefined) is rejected.
 * trunc_log(x) = max(0, ln x), with trunc_log(x) = 0 for x <= 1 (including
   x <= 0, where log is undefined).
 * eigSVD (Alg. 5, from frPCA) is  B = Y^T Y, eig(B) = V D V^T,
@@ -428,6 +429,8 @@ def embed(row_ptr, col_idx, n, params: Params, val=None, U_k=None, lam=None) -> 
     A = adjacency(row_ptr, col_idx, n, val)
     deg = degrees(A)
     vol = volume(A)
+    if not vol > 0:
+        raise ValueError("a graph without edges has vol(G) = 0: Eq. 1 is undefined")
     if U_k is None:
         X = normalized_operator(A, p.alpha)
         U_k, lam = freigs(X, p.k, p.q, p.s_eig, p.seed)

@@ -185,6 +185,10 @@ int check_graph(const sne_csr *g) {
   return SNE_OK;
 }
 
+// The embedding needs at least one edge: with none, vol(G) = 0 and the matrix
+// of Eq. 1 (and every power of X in Alg. 5) is undefined.
+int check_has_edges(const sne_csr *g) { return g->nnz > 0 ? SNE_OK : SNE_ERR_GRAPH; }
+
 int check_ws(void *ws, size_t bytes, size_t need) {
   if (!ws || ((uintptr_t)ws % 256) != 0 || bytes < need) return SNE_ERR_WORKSPACE;
   return SNE_OK;
@@ -493,7 +497,7 @@ const char *sne_error_string(int code) {
   switch (code) {
     case SNE_OK: return "ok";
     case SNE_ERR_ARG: return "invalid argument";
-    case SNE_ERR_GRAPH: return "invalid graph (CSR not monotone, out of range or asymmetric)";
+    case SNE_ERR_GRAPH: return "invalid graph (CSR not monotone, out of range or asymmetric, or no edges)";
     case SNE_ERR_SIZE: return "inconsistent or unsupported sizes";
     case SNE_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
     case SNE_ERR_CUDA: return "CUDA error";
@@ -609,6 +613,8 @@ int sne_freigs(const sne_csr *g, const sne_params *p, void *ws, size_t ws_bytes,
                double *lambda, sne_stream_t stream) {
   int rc = check_graph(g);
   if (rc) return rc;
+  rc = check_has_edges(g);
+  if (rc) return rc;
   Dims D;
   rc = make_dims(g->n, g->nnz, p, SNE_WS_FREIGS, &D);
   if (rc) return rc;
@@ -628,6 +634,8 @@ int sne_sketch_from_factors(const sne_csr *g, const sne_params *p, const float *
                             float *E, double *sigma, sne_stream_t stream) {
   int rc = check_graph(g);
   if (rc) return rc;
+  rc = check_has_edges(g);
+  if (rc) return rc;
   Dims D;
   rc = make_dims(g->n, g->nnz, p, SNE_WS_SKETCH, &D);
   if (rc) return rc;
@@ -645,6 +653,8 @@ int sne_sketch_from_factors(const sne_csr *g, const sne_params *p, const float *
 int sne_embed(const sne_csr *g, const sne_params *p, void *ws, size_t ws_bytes, float *E,
               double *sigma, sne_stream_t stream) {
   int rc = check_graph(g);
+  if (rc) return rc;
+  rc = check_has_edges(g);
   if (rc) return rc;
   Dims D;
   rc = make_dims(g->n, g->nnz, p, SNE_WS_EMBED, &D);
@@ -668,6 +678,8 @@ int sne_embed(const sne_csr *g, const sne_params *p, void *ws, size_t ws_bytes, 
 int sne_embed_host(const sne_csr *g, const sne_params *p, void *ws, size_t ws_bytes, float *E_host,
                    double *sigma_host, sne_stream_t stream) {
   int rc = check_graph(g);
+  if (rc) return rc;
+  rc = check_has_edges(g);
   if (rc) return rc;
   Dims D;
   rc = make_dims(g->n, g->nnz, p, SNE_WS_EMBED_HOST, &D);
@@ -729,6 +741,8 @@ int static_workspace_ptr(void **out) {
 extern "C" int sne_freigs_static(const sne_csr *g, const sne_params *p, float *U, double *lambda,
                                  int32_t *status, sne_stream_t stream) {
   int rc = check_graph(g);
+  if (rc) return rc;
+  rc = check_has_edges(g);
   if (rc) return rc;
   Dims D;
   rc = make_dims(g->n, g->nnz, p, SNE_WS_FREIGS, &D);

@@ -76,6 +76,7 @@ int make_plan(int32_t G, const sne_csr *graphs, const sne_params *p, int32_t lan
   for (int i = 0; i < G; ++i) {
     const sne_csr &g = graphs[i];
     if (g.n <= 0 || g.nnz < 0 || !g.row_ptr || (g.nnz > 0 && !g.col_idx)) return SNE_ERR_ARG;
+    if (g.nnz == 0) return SNE_ERR_GRAPH;  // no edges: vol(G) = 0, Eq. 1 undefined
     const int rc = sne_workspace_bytes(g.n, g.nnz, p, SNE_WS_EMBED, &wsb[i]);
     if (rc) return rc;
     cost[i] = graph_cost(g, *p);

@@ -164,3 +164,21 @@ def test_no_cpu_fallback(L, monkeypatch):
     with pytest.raises(RuntimeError, match="missing"):
         sk.sne_params_init(8, 16)
     assert p.d == 8
+
+
+def test_graph_without_edges_is_rejected_on_the_host(L):
+    """vol(G) = 0 leaves Eq. 1 undefined: every embedding entry point returns
+    SNE_ERR_GRAPH for a graph with no edges before touching the device."""
+    p = sk.sne_params_init(8, 16)
+    g = sk.sne_csr(1000, 0, 256, None, None)  # fake row_ptr address, never read
+    GR = sk.SNE_ERR_GRAPH
+    assert L.sne_embed(ctypes.byref(g), ctypes.byref(p), 256, 1 << 40, 512, 768, None) == GR
+    assert L.sne_embed_host(ctypes.byref(g), ctypes.byref(p), 256, 1 << 40, 512, 768, None) == GR
+    assert L.sne_freigs(ctypes.byref(g), ctypes.byref(p), 256, 1 << 40, 512, 768, None) == GR
+    assert L.sne_sketch_from_factors(ctypes.byref(g), ctypes.byref(p), 512, 768, 256, 1 << 40,
+                                     None, None, None, None, None) == GR
+    assert L.sne_freigs_static(ctypes.byref(g), ctypes.byref(p), 512, 768, None, None) == GR
+    graphs = (sk.sne_csr * 1)(g)
+    nb = ctypes.c_size_t(0)
+    assert L.sne_embed_batched_workspace_bytes(1, graphs, ctypes.byref(p), 0, ctypes.byref(nb)) == GR
+    assert "no edges" in sk.sne_error_string(GR)

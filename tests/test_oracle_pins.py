@@ -286,6 +286,14 @@ def test_single_pass_invariant_to_sign_scale_and_w_symmetric():
     assert np.linalg.norm(a.W - a.W.T) <= 1e-12 * np.linalg.norm(a.W)
 
 
+def test_graph_without_edges_is_rejected():
+    # Eq. 1 divides by vol(G) = sum of degrees; with no edges it is undefined
+    n = 50
+    with pytest.raises(ValueError, match="vol"):
+        o.embed(np.zeros(n + 1, dtype=np.int64), np.zeros(0, dtype=np.int32), n,
+                o.Params(k=8, d=4, q=2, h=12, l=40))
+
+
 def test_isolated_vertices_have_zero_rows():
     g0 = synth.sbm(200, 2, 0.2, 0.02, seed=8)
     # append 5 isolated vertices
