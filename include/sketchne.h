@@ -213,10 +213,13 @@ int sne_stats_read(const void *workspace, sne_stats *out, sne_stream_t stream);
  * the array's device address once (cudaGetSymbolAddress) and caches it; make
  * that first call before any stream capture.  Every call shares the array, so
  * calls that overlap on the GPU (other streams, other host threads) race: the
- * caller must serialize them.  The call clears the status word it uses, runs
- * Alg. 5 exactly as sne_freigs does, and, if `status` (a DEVICE int32) is not
- * NULL, copies the device status word (SNE_OK or SNE_ERR_*) into it.
- * U: n x k FP32 and lambda: k FP64 as in sne_freigs. */
+ * caller must serialize them.  The call clears the status word it uses and
+ * performs the same computation as sne_freigs, with the same outputs.
+ * `status` (a DEVICE int32, or NULL) receives the device status word (SNE_OK
+ * or SNE_ERR_*) at the end of the enqueued work, and is written only when
+ * the call returns SNE_OK: on any other return value nothing past the failing
+ * step is enqueued, the return value is the result and `status` keeps its
+ * previous contents.  U: n x k FP32 and lambda: k FP64 as in sne_freigs. */
 int sne_freigs_static(const sne_csr *g, const sne_params *p, float *U, double *lambda,
                       int32_t *status, sne_stream_t stream);
 

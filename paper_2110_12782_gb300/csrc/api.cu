@@ -270,7 +270,8 @@ __global__ void core_transpose_kernel(const double *Csum, int k, const double *l
   }
 }
 
-inline unsigned grid_for(int64_t work, int per = 256, int cap = 152 * 8) {
+inline unsigned grid_for(int64_t work, int per = 256, int cap = 0) {
+  if (cap <= 0) cap = sm_count() * 8;
   int64_t b = (work + per - 1) / per;
   if (b < 1) b = 1;
   if (b > cap) b = cap;

@@ -25,7 +25,7 @@ static inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b)
 static void gram_grid(int64_t n, int Ka, int Kb, bool symmetric, int *tiles, int *chunks) {
   const int ta = ceil_div(Ka, kGT), tb = ceil_div(Kb, kGT);
   *tiles = symmetric ? ta * (ta + 1) / 2 : ta * tb;
-  int want = (152 * 10 + *tiles - 1) / *tiles;
+  int want = (sm_count() * 10 + *tiles - 1) / *tiles;
   const int maxc = ceil_div(n, 4 * kGR);
   if (want > maxc) want = maxc;
   if (want < 1) want = 1;
@@ -895,7 +895,7 @@ cudaError_t launch_check_finite_f(const float *x, int64_t count, Ctrl *ctrl, int
                                   cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   ProfScope ps_(K_MISC, st);
-  check_finite_kernel<<<(unsigned)min64(152 * 4, (count + 255) / 256), 256, 0, st>>>(
+  check_finite_kernel<<<(unsigned)min64(sm_count() * 4, (count + 255) / 256), 256, 0, st>>>(
       x, count, ctrl, where);
   return cudaGetLastError();
 }

@@ -594,7 +594,7 @@ static void gram_tc_grid(int64_t n, int Ka, int Kb, bool symmetric, int *tiles, 
   const int nta = (Ka + gt::BM - 1) / gt::BM;
   *ntb = (Kb + gg::BN - 1) / gg::BN;
   *tiles = symmetric ? (*ntb) * (*ntb + 1) / 2 : nta * (*ntb);
-  int c = (152 * 2) / *tiles;  // at most two full waves of one CTA per SM
+  int c = (sm_count() * 2) / *tiles;  // at most two full waves of one CTA per SM
   const int64_t maxc = (n + 4 * gt::BK - 1) / (4 * gt::BK);
   if (c > maxc) c = (int)maxc;
   if (c < 1) c = 1;

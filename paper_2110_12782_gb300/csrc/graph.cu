@@ -39,7 +39,7 @@ cudaError_t launch_degrees(const sne_csr &g, float *deg, double *vol, cudaStream
   if (e != cudaSuccess) return e;
   if (g.n <= 0) return cudaSuccess;
   int64_t blocks = (g.n + 255) / 256;
-  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks > sm_count() * 8) blocks = sm_count() * 8;
   ProfScope ps_(K_MISC, st);
   degrees_kernel<<<(unsigned)blocks, 256, 0, st>>>(g.n, g.row_ptr, g.val, deg, vol);
   return cudaGetLastError();
@@ -58,7 +58,7 @@ cudaError_t launch_degree_power(const float *deg, int64_t n, double beta, float 
                                 cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   int64_t blocks = (n + 255) / 256;
-  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks > sm_count() * 8) blocks = sm_count() * 8;
   ProfScope ps_(K_MISC, st);
   degree_power_kernel<<<(unsigned)blocks, 256, 0, st>>>(deg, n, (float)beta, scale, out);
   return cudaGetLastError();
@@ -227,7 +227,7 @@ __global__ void spmm_weights_kernel(int64_t nnz, const int32_t *__restrict__ col
 cudaError_t launch_spmm_weights(const sne_csr &g, const float *dpow, float *wnz, cudaStream_t st) {
   if (g.nnz <= 0) return cudaSuccess;
   ProfScope ps_(K_MISC, st);
-  spmm_weights_kernel<<<(unsigned)min64(152 * 16, (g.nnz + 255) / 256), 256, 0, st>>>(
+  spmm_weights_kernel<<<(unsigned)min64(sm_count() * 16, (g.nnz + 255) / 256), 256, 0, st>>>(
       g.nnz, g.col_idx, g.val, dpow, wnz);
   return cudaGetLastError();
 }
@@ -374,7 +374,7 @@ __global__ void validate_kernel(int64_t n, int64_t nnz, const int64_t *__restric
 cudaError_t launch_validate(const sne_csr &g, Ctrl *ctrl, cudaStream_t st) {
   if (g.n <= 0) return cudaSuccess;
   int64_t blocks = (g.n + 255) / 256;
-  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks > sm_count() * 8) blocks = sm_count() * 8;
   ProfScope ps_(K_MISC, st);
   validate_kernel<<<(unsigned)blocks, 256, 0, st>>>(g.n, g.nnz, g.row_ptr, g.col_idx, g.val, ctrl);
   return cudaGetLastError();

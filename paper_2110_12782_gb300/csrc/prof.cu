@@ -21,6 +21,8 @@ struct Rec {
 };
 std::vector<Rec> g_recs;
 std::vector<cudaEvent_t> g_pool;
+constexpr int kMaxDev = 64;
+std::atomic<int> g_sms[kMaxDev];
 
 cudaEvent_t take_event() {
   if (!g_pool.empty()) {
@@ -38,6 +40,18 @@ const char *kClassNames[K_COUNT] = {"spmm",   "gram",  "tall_gemm", "small_gemm"
                                     "rng", "unique", "misc", "fused_sketch_tc", "gram_tc",
                                     "tall_gemm_tc"};
 }  // namespace
+
+int sm_count() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 148;
+  int v = g_sms[dev].load(std::memory_order_relaxed);
+  if (v <= 0) {
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+      v = 148;
+    g_sms[dev].store(v, std::memory_order_relaxed);
+  }
+  return v;
+}
 
 ProfScope::ProfScope(int cls, cudaStream_t st, int nk) : cls_(cls), nk_(nk), st_(st) {
   g_launches.fetch_add(nk, std::memory_order_relaxed);

@@ -41,7 +41,7 @@ cudaError_t launch_gaussian(int64_t n, int32_t cols, uint64_t seed, int32_t stre
   const int64_t npairs = (n * (int64_t)cols + 1) / 2;
   if (npairs <= 0) return cudaSuccess;
   int64_t blocks = (npairs + 255) / 256;
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks > sm_count() * 32) blocks = sm_count() * 32;
   ProfScope ps_(K_RNG, st);
   gaussian_kernel<<<(unsigned)blocks, 256, 0, st>>>(n, cols, stream_key(seed, stream_id), out, ld);
   return cudaGetLastError();

@@ -364,7 +364,7 @@ cudaError_t launch_fused_sketch_tc(bool fp16, const void *Ahat, int64_t nrows_ma
   // at least two CTAs per SM's worth of work exists
   const int ntiles = (ncols_eval + tc::BN - 1) / tc::BN;
   const unsigned splits = (unsigned)std::max(
-      1, std::min(ntiles, (int)((2 * 152 + grid_x - 1) / grid_x)));
+      1, std::min(ntiles, (int)((2 * sm_count() + grid_x - 1) / grid_x)));
   const dim3 grid(grid_x, splits);
   const int kblocks = kpad / tc::BK;
   // f = trunc_log: the kernel sums signed log2 values; ln 2 joins sv here

@@ -40,6 +40,10 @@ enum Where : int32_t {
   W_TC = 9,
 };
 
+// Number of SMs of the current device (queried once per device and cached);
+// grids are sized in multiples of it.
+int sm_count();
+
 __device__ __forceinline__ void record_error(Ctrl *c, int32_t code, int32_t where) {
   if (c == nullptr) return;
   if (atomicCAS(&c->status, 0, code) == 0) c->where = where;

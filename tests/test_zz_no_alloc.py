@@ -55,9 +55,12 @@ def test_static_freigs_rejects_graphs_beyond_the_static_workspace(sk):
     n = 200_000
     p = sk.sne_params_init(32, 128)
     assert sk.sne_workspace_bytes(n, 10 * n, p, sk.SNE_WS_FREIGS) > (32 << 20)
-    rp = torch.zeros(n + 1, dtype=torch.int64, device="cuda")
-    ci = torch.zeros(1, dtype=torch.int32, device="cuda")
-    G = sk.DeviceGraph(rp, ci[:0])
+    # one edge 0-1 (stored both ways), so that the call gets past the check
+    # that the graph has edges and reaches the static-workspace size check
+    rp = torch.full((n + 1,), 2, dtype=torch.int64, device="cuda")
+    rp[0], rp[1] = 0, 1
+    ci = torch.tensor([1, 0], dtype=torch.int32, device="cuda")
+    G = sk.DeviceGraph(rp, ci)
     U = torch.empty(n, p.k, dtype=torch.float32, device="cuda")
     lam = torch.empty(p.k, dtype=torch.float64, device="cuda")
     with pytest.raises(sk.SketchNEError) as e:
