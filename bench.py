@@ -174,9 +174,15 @@ def algorithmic_work(cls: str, n: int, nnz: int, p, v_s: int, v_o: int) -> tuple
     return 0.0, "alu", "TFLOP/s"
 
 
-def alu_peak_tflops(sm_mhz: float) -> float:
-    """FP32 FFMA peak: 152 SMs x 128 FP32 lanes x 2 flops x clock."""
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+def device_sms() -> int:
+    """SM count of the current device."""
+    import torch
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+
+
+def alu_peak_tflops(sm_mhz: float, sms: int) -> float:
+    """FP32 FFMA peak: SMs x 128 FP32 lanes x 2 flops x clock."""
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
 # --------------------------------------------------------------------------- oracle timing
@@ -277,10 +283,11 @@ def run_ours(args, rank: int, world: int) -> None:
     build.build()
     w = WORKLOADS[args.workload]
     g = make_graph(w)
-    prec = {"fp32": sk.SNE_FP32, "bf16": sk.SNE_BF16, "fp16": sk.SNE_FP16}[args.precision]
+    prec = sk.PRECISIONS[args.precision]
     orth = {"eigsvd": sk.SNE_ORTH_EIGSVD, "cholqr": sk.SNE_ORTH_CHOLQR}[args.orth]
     p = sk.sne_params_init(w["d"], w["k"], q=w["q"], T=w["T"], precision=prec, orth=orth,
                            row_block=8192)
+    sms = device_sms()
     G = sk.DeviceGraph.from_numpy(g.row_ptr, g.col_idx)
     ws = sk.workspace(g.n, g.nnz, p, sk.SNE_WS_EMBED)
     E = torch.empty(g.n, p.d, dtype=torch.float32, device="cuda")
@@ -381,18 +388,19 @@ def run_ours(args, rank: int, world: int) -> None:
                 peak = float(peaks["bf16_tflops"]) * (1.1 / 2.25) / 3.0
             else:
                 achieved = work / (per_step_ms / 1e3) / 1e12
-                peak = alu_peak_tflops(float(peaks.get("sm_max_mhz", 2070.0)))
+                peak = alu_peak_tflops(float(peaks.get("sm_max_mhz", 2070.0)), sms)
             roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak,
                         "unit": unit, "frac": achieved / peak, "traffic": profiled_traffic(dom, args.workload),
-                        "peak_source": {"alu": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                        "peak_source": {"alu": f"derived: {sms} SMs x 128 FP32 lanes x 2 x max SM clock",
                                         "tensor_tf32x3": f"{peak_kind} bf16 x 1.1/2.25 / 3"}.get(
                                             bound, f"{peak_kind}"),
                         "share_of_step": ms / prof_total if prof_total else None}
 
-    # ---- mixed precision (FP16 reconstruction) on the same graph and steps
+    # ---- mixed precision (half-precision reconstruction) on the same graph and steps
     mixed = None
     if not args.no_mixed and prec == sk.SNE_FP32:
-        pm = sk.sne_params_init(w["d"], w["k"], q=w["q"], T=w["T"], precision=sk.SNE_FP16, orth=orth,
+        pm = sk.sne_params_init(w["d"], w["k"], q=w["q"], T=w["T"],
+                                precision=sk.PRECISIONS[args.mixed_precision], orth=orth,
                                 row_block=8192)
         wsm = sk.workspace(g.n, g.nnz, pm, sk.SNE_WS_EMBED)
         Em = torch.empty_like(E)
@@ -421,7 +429,7 @@ def run_ours(args, rank: int, world: int) -> None:
         s32 = sig.cpu().numpy()
         s16 = sigm.cpu().numpy()
         mixed_total = max_over_ranks(float(sum(mt)), world)
-        mixed = {"precision": "fp16", "ms_per_step": mixed_total / args.steps,
+        mixed = {"precision": args.mixed_precision, "ms_per_step": mixed_total / args.steps,
                  "value": job_value(entries, world, args.steps, mixed_total),
                  "sigma_rel_diff_vs_fp32": float(np.max(np.abs(s16 - s32) / np.abs(s32))),
                  "kernel_ms_per_step": {k: v[2] / args.steps for k, v in
@@ -429,12 +437,16 @@ def run_ours(args, rank: int, world: int) -> None:
         if "fused_sketch_tc" in profm:
             ms = profm["fused_sketch_tc"][2] / args.steps
             work, _, _ = algorithmic_work("fused_sketch_tc", g.n, g.nnz, p, st.v_s, st.v_o)
-            ach = work / (ms / 1e3) / 1e12
-            pk = float(peaks["bf16_tflops"])
+            # hi/lo pair operands: three tensor-core products per entry
+            products = 3 if args.mixed_precision.endswith("x2") else 1
+            ach = products * work / (ms / 1e3) / 1e12
+            # the kernel runs inside seconds-long embeddings: sustained peak
+            pk = float(peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]))
             mixed["roofline_fused_sketch"] = {
                 "kernel": "fused_sketch_tc", "bound": "tensor", "achieved": ach, "peak": pk,
-                "unit": "TFLOP/s", "frac": ach / pk,
-                "peak_source": f"{peak_kind} bf16 dense (FP16 has the same tensor rate)",
+                "unit": "TFLOP/s", "frac": ach / pk, "products_per_entry": products,
+                "algorithmic_tflops": work / (ms / 1e3) / 1e12,
+                "peak_source": f"{peak_kind} bf16 dense sustained (FP16 has the same tensor rate)",
                 "ms_per_step": ms}
 
     cpu = None
@@ -488,7 +500,7 @@ def run_ours_batch(args, rank: int, world: int) -> None:
     w = WORKLOADS[args.workload]
     graphs = synth.batched_mix(w["count"])
     orth = {"eigsvd": sk.SNE_ORTH_EIGSVD, "cholqr": sk.SNE_ORTH_CHOLQR}[args.orth]
-    prec = {"fp32": sk.SNE_FP32, "bf16": sk.SNE_BF16, "fp16": sk.SNE_FP16}[args.precision]
+    prec = sk.PRECISIONS[args.precision]
     p = sk.sne_params_init(w["d"], w["k"], q=w["q"], T=w["T"], precision=prec, orth=orth)
     dev = [sk.DeviceGraph.from_numpy(g.row_ptr, g.col_idx) for g in graphs]
     E = [torch.empty(g.n, p.d, dtype=torch.float32, device="cuda") for g in graphs]
@@ -611,7 +623,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cl1m", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--precision", default="fp32",
+                    choices=["fp32", "bf16", "fp16", "bf16x2", "fp16x2"])
+    ap.add_argument("--mixed-precision", default="fp16x2",
+                    choices=["bf16", "fp16", "bf16x2", "fp16x2"],
+                    help="precision of the mixed arm (pairs: hi/lo operands, three products)")
     ap.add_argument("--orth", default="cholqr", choices=["eigsvd", "cholqr"],
                     help="orthonormalization inside freigs (Alg. 5): Cholesky QR (default) or "
                          "eigSVD as printed; both give the same subspace")

@@ -46,7 +46,12 @@ enum {
   SNE_ERR_NUMERIC = -7    /* NaN/Inf or a non-positive pivot in a small solve */
 };
 
-enum { SNE_FP32 = 0, SNE_BF16 = 1, SNE_FP16 = 2 };          /* reconstruction GEMM precision */
+/* Precision of the L'R' reconstruction GEMM of Eq. 4 and the Z core: FP32
+ * (FP32 FMA), or half-precision operands on the tensor cores with FP32
+ * accumulation: BF16 / FP16 (one product), or BF16X2 / FP16X2 (each operand a
+ * pair hi + lo of that type, lo the rounding error of hi; three products
+ * hi*hi + lo*hi + hi*lo, about twice the operand precision). */
+enum { SNE_FP32 = 0, SNE_BF16 = 1, SNE_FP16 = 2, SNE_BF16X2 = 3, SNE_FP16X2 = 4 };
 enum { SNE_F_TRUNC_LOG = 0, SNE_F_IDENTITY = 1 };          /* elementwise f of Problem 1 */
 enum { SNE_ORTH_EIGSVD = 0, SNE_ORTH_CHOLQR = 1 };         /* orthonormalization inside Alg. 5 */
 
@@ -69,7 +74,7 @@ typedef struct sne_csr {
  *  zeta   sparse-sign column density z (Alg. 3); the library uses z = min(n, zeta) <= 64
  *  s_eig  oversampling of Alg. 5 (k + s_eig columns of Omega)
  *  row_block  rows of L' per batch of Eq. 4 (0 = library's choice)
- *  precision  SNE_FP32 | SNE_BF16 | SNE_FP16 for the L'R' reconstruction
+ *  precision  SNE_FP32 | SNE_BF16 | SNE_FP16 | SNE_BF16X2 | SNE_FP16X2 (L'R' reconstruction)
  *  f      SNE_F_TRUNC_LOG (NetMF) or SNE_F_IDENTITY (Problem 1 with f = id)
  *  orth   SNE_ORTH_EIGSVD (Alg. 5 as printed) or SNE_ORTH_CHOLQR
  *  alpha  exponent of the modified Laplacian D^-alpha A D^-alpha, in (0, 0.5]

@@ -19,8 +19,10 @@ namespace {
 struct Dims {
   int64_t n, nnz;
   int k, K, h, l, z, d, nS, nO, Sm, Wab;
-  bool half;  // mixed-precision reconstruction (BF16 / FP16)
-  int kpad;   // k rounded up to a multiple of 64 for the tensor-core operands
+  bool half;   // mixed-precision reconstruction (BF16 / FP16 operands)
+  bool split;  // operands as hi/lo pairs (SNE_BF16X2 / SNE_FP16X2)
+  bool fp16;   // FP16 (else BF16) operands
+  int kpad;    // k rounded up to a multiple of 64 for the tensor-core operands
 };
 
 int make_dims(int64_t n, int64_t nnz, const sne_params *p, int mode, Dims *D) {
@@ -29,7 +31,8 @@ int make_dims(int64_t n, int64_t nnz, const sne_params *p, int mode, Dims *D) {
   if (p->k <= 0 || p->d <= 0 || p->h <= 0 || p->l <= 0 || p->zeta <= 0 || p->T <= 0 ||
       p->q < 0 || p->s_eig < 0 || !(p->b > 0) || !(p->alpha > 0) || p->alpha > 1.0)
     return SNE_ERR_ARG;
-  if (p->precision != SNE_FP32 && p->precision != SNE_BF16 && p->precision != SNE_FP16)
+  if (p->precision != SNE_FP32 && p->precision != SNE_BF16 && p->precision != SNE_FP16 &&
+      p->precision != SNE_BF16X2 && p->precision != SNE_FP16X2)
     return SNE_ERR_ARG;
   if (p->f != SNE_F_TRUNC_LOG && p->f != SNE_F_IDENTITY) return SNE_ERR_ARG;
   if (p->orth != SNE_ORTH_EIGSVD && p->orth != SNE_ORTH_CHOLQR) return SNE_ERR_ARG;
@@ -52,12 +55,17 @@ int make_dims(int64_t n, int64_t nnz, const sne_params *p, int mode, Dims *D) {
   }
   d.Sm = std::max(std::max(d.K, d.h), d.k);
   d.half = p->precision != SNE_FP32;
+  d.split = p->precision == SNE_BF16X2 || p->precision == SNE_FP16X2;
+  d.fp16 = p->precision == SNE_FP16 || p->precision == SNE_FP16X2;
   d.kpad = (d.k + 63) / 64 * 64;
   if (d.half && mode != SNE_WS_FREIGS) {
     if (!(d.z == 1 || d.z == 2 || d.z == 4 || d.z == 8 || d.z == 16 || d.z == 32)) return SNE_ERR_SIZE;
-    if (d.kpad > 384) return SNE_ERR_SIZE;
+    // the A tile stays in shared memory: k <= 384 (k <= 320 for hi/lo pairs)
+    if (d.kpad > (d.split ? 320 : 384)) return SNE_ERR_SIZE;
   }
-  d.Wab = (mode == SNE_WS_SKETCH) ? d.h : (mode == SNE_WS_FREIGS ? d.K : std::max(d.K, d.h));
+  // the tall buffers also hold the centred rows L~ (n x k) during the sketch
+  d.Wab = (mode == SNE_WS_SKETCH) ? std::max(d.h, d.k)
+                                  : (mode == SNE_WS_FREIGS ? d.K : std::max(d.K, d.h));
   *D = d;
   return SNE_OK;
 }
@@ -90,8 +98,13 @@ struct Bufs {
   int8_t *signS, *signO;
   float *RpS, *RpO, *Yo, *Zf, *Gf;
   double *G64, *Gp, *Tm, *Z64;
-  void *Ah, *AhO, *BhS, *BhO;  // half operands of the tensor-core sketch
-  float *rowfA, *rowfO, *colfS, *colfO;
+  void *Ah, *AhO, *BhS, *BhO;  // half operands of the tensor-core sketch (hi parts)
+  void *Al, *AlO, *BlS, *BlO;  // their lo parts (split precisions)
+  float *rowfA, *rowfO;
+  double *cpart, *cstats;      // centring: partial sums, statistics (w, p, q, gamma, s)
+  float *ws_hi, *ws_lo;        // s w as an FP32 pair
+  float2 *rowdat, *rowdatO;    // (rho, mask) per row of L~ and of L~(p_O, :)
+  float4 *coldatS, *coldatO;   // (scale, kappa, sign, 0) per evaluated column
   int64_t *h_rowptr;  // device staging of a host graph (SNE_WS_EMBED_HOST)
   int32_t *h_col;
   float *h_val, *h_E;
@@ -150,15 +163,27 @@ size_t carve(const Dims &D, int mode, void *base, Bufs *b) {
     x.Gp = bp.take<double>((size_t)D.h * D.l);
     x.Tm = bp.take<double>((size_t)D.h * D.l);
     x.Z64 = bp.take<double>((size_t)D.l * D.l);
+    x.cpart = bp.take<double>(center_partial_doubles(n, D.k));
+    x.cstats = bp.take<double>(3 * (size_t)D.k + 2);
+    x.ws_hi = bp.take<float>(D.k);
+    x.ws_lo = bp.take<float>(D.k);
+    x.rowdat = bp.take<float2>(n);
+    x.rowdatO = bp.take<float2>(vmax);
+    x.coldatS = bp.take<float4>(D.nS + 256);
+    x.coldatO = bp.take<float4>(D.nO + 256);
     if (D.half) {
       x.Ah = bp.take<uint16_t>((size_t)n * D.kpad);
       x.AhO = bp.take<uint16_t>((size_t)vmax * D.kpad);
       x.BhS = bp.take<uint16_t>((size_t)D.nS * D.kpad);
       x.BhO = bp.take<uint16_t>((size_t)D.nO * D.kpad);
+      if (D.split) {
+        x.Al = bp.take<uint16_t>((size_t)n * D.kpad);
+        x.AlO = bp.take<uint16_t>((size_t)vmax * D.kpad);
+        x.BlS = bp.take<uint16_t>((size_t)D.nS * D.kpad);
+        x.BlO = bp.take<uint16_t>((size_t)D.nO * D.kpad);
+      }
       x.rowfA = bp.take<float>(n);
       x.rowfO = bp.take<float>(vmax);
-      x.colfS = bp.take<float>(D.nS + 256);
-      x.colfO = bp.take<float>(D.nO + 256);
     }
   }
   if (host_mode) {
@@ -384,40 +409,57 @@ int run_sketch(const sne_csr &g, const sne_params &p, const Dims &D, const Bufs 
   }
   { ProfScope ps_(K_MISC, st); core_transpose_kernel<<<grid_for((int64_t)k * k), 256, 0, st>>>(cur, k, lam, b.m32[3], b.m32[2]); }  // C^T
   CK(cudaGetLastError());
+  // --- centring of L'R' (the degree-weighted mean row w of W = D^(-1+a) U):
+  // x - c0 = s (W_i - w) C (W_j - w)^T + rho_i + kappa_j, c0 = 1 for trunc_log
+  const bool tlog = p.f == SNE_F_TRUNC_LOG;
+  const double c0 = tlog ? 1.0 : 0.0;
+  CK(launch_center_stats(U, k, k, D.n, b.deg, p.alpha, &b.ctrl->vol, lam, cur, 1.0 / (p.b * p.T),
+                         c0, b.cpart, b.cstats, b.ws_hi, b.ws_lo, st));
   // --- Alg. 3: S (stream 2) and O (stream 3); unique coordinates
   CK(launch_sparse_sign(D.n, h, z, p.seed, 2, b.idxS, b.signS, b.ctrl, st));
   CK(launch_sparse_sign(D.n, l, z, p.seed, 3, b.idxO, b.signO, b.ctrl, st));
   CK(launch_unique(b.idxS, D.nS, b.uniqS, &b.ctrl->v_s, b.posS, b.ctrl, W_UNIQUE, st));
   CK(launch_unique(b.idxO, D.nO, b.uniqO, &b.ctrl->v_o, b.posO, b.ctrl, W_UNIQUE, st));
-  // R'(:, idx)^T = a_idx U(idx, :) C^T
-  CK(launch_rprime_rows(U, k, b.idxS, D.nS, b.m32[3], b.m32[2], b.deg, -1.0 + p.alpha, b.RpS, st));
-  CK(launch_rprime_rows(U, k, b.idxO, D.nO, b.m32[3], b.m32[2], b.deg, -1.0 + p.alpha, b.RpO, st));
+  // centred columns R~(:, idx)^T = (W_idx - w) C^T and their (scale, kappa, sign);
+  // the padding past the last column reads as zero
+  CK(cudaMemsetAsync(b.coldatS, 0, (size_t)(D.nS + 256) * sizeof(float4), st));
+  CK(cudaMemsetAsync(b.coldatO, 0, (size_t)(D.nO + 256) * sizeof(float4), st));
+  CK(launch_rtilde_rows(U, k, b.idxS, D.nS, b.m32[3], b.m32[2], b.deg, -1.0 + p.alpha, b.cstats,
+                        b.signS, b.RpS, b.coldatS, st));
+  CK(launch_rtilde_rows(U, k, b.idxO, D.nO, b.m32[3], b.m32[2], b.deg, -1.0 + p.alpha, b.cstats,
+                        b.signO, b.RpO, b.coldatO, st));
   // --- Alg. 4 line 4: Y = f(L' R'(:, p)) S(p, :)
   // --- Alg. 4 line 7: Y' = f(L'(p,:) R'(:,p)) O(p,:) on the rows p = p_O
   float *Y = Yout ? Yout : b.A;
   const int64_t vmax = min64(D.n, D.nO);
   if (!D.half) {
-    CK(launch_fused_sketch_f32(U, k, nullptr, nullptr, D.n, k, b.rsc, b.rsc_lo, b.RpS, b.signS, h, z, sv, p.f,
-                               Y, h, st));
-    CK(launch_fused_sketch_f32(U, k, b.uniqO, &b.ctrl->v_o, vmax, k, b.rsc, b.rsc_lo, b.RpO, b.signO, l, z,
-                               sv, p.f, b.Yo, l, st));
+    // centred rows L~ = s (W - w) (FP32) in the free tall buffer
+    float *Lt = b.B;
+    CK(launch_center_rows(0, false, U, k, k, nullptr, nullptr, D.n, b.rsc, b.rsc_lo, b.ws_hi,
+                          b.ws_lo, b.cstats, tlog, c0, Lt, k, nullptr, nullptr, 0, nullptr,
+                          b.rowdat, st));
+    CK(launch_fused_sketch_f32(Lt, k, nullptr, nullptr, D.n, k, b.rowdat, b.RpS, b.coldatS, h, z,
+                               sv, p.f, Y, h, st));
+    CK(launch_fused_sketch_f32(Lt, k, b.uniqO, &b.ctrl->v_o, vmax, k, b.rowdat, b.RpO, b.coldatO,
+                               l, z, sv, p.f, b.Yo, l, st));
   } else {
-    const bool fp16 = p.precision == SNE_FP16;
-    CK(launch_to_half_rows(fp16, U, k, nullptr, nullptr, D.n, k, D.kpad, b.rsc, nullptr, b.Ah,
-                           b.rowfA, st));
-    CK(launch_to_half_rows(fp16, U, k, b.uniqO, &b.ctrl->v_o, vmax, k, D.kpad, b.rsc, nullptr,
-                           b.AhO, b.rowfO, st));
-    // column factors carry the sparse signs; zero padding up to the 256-column tile
-    CK(cudaMemsetAsync(b.colfS, 0, (size_t)(D.nS + 256) * sizeof(float), st));
-    CK(cudaMemsetAsync(b.colfO, 0, (size_t)(D.nO + 256) * sizeof(float), st));
-    CK(launch_to_half_rows(fp16, b.RpS, k, nullptr, nullptr, D.nS, k, D.kpad, nullptr, b.signS,
-                           b.BhS, b.colfS, st));
-    CK(launch_to_half_rows(fp16, b.RpO, k, nullptr, nullptr, D.nO, k, D.kpad, nullptr, b.signO,
-                           b.BhO, b.colfO, st));
-    CK(launch_fused_sketch_tc(fp16, b.Ah, D.n, nullptr, D.kpad, b.BhS, D.nS, h, z, b.rowfA, b.colfS,
-                              b.signS, sv, p.f, Y, h, b.ctrl, st));
-    CK(launch_fused_sketch_tc(fp16, b.AhO, vmax, &b.ctrl->v_o, D.kpad, b.BhO, D.nO, l, z, b.rowfO,
-                              b.colfO, b.signO, sv, p.f, b.Yo, l, b.ctrl, st));
+    const int outk = D.fp16 ? 1 : 2;
+    CK(launch_center_rows(outk, D.split, U, k, k, nullptr, nullptr, D.n, b.rsc, b.rsc_lo, b.ws_hi,
+                          b.ws_lo, b.cstats, tlog, c0, nullptr, 0, b.Ah, b.Al, D.kpad, b.rowfA,
+                          b.rowdat, st));
+    CK(launch_center_rows(outk, D.split, U, k, k, b.uniqO, &b.ctrl->v_o, vmax, b.rsc, b.rsc_lo,
+                          b.ws_hi, b.ws_lo, b.cstats, tlog, c0, nullptr, 0, b.AhO, b.AlO, D.kpad,
+                          b.rowfO, b.rowdatO, st));
+    // column scales go to coldat[e].x
+    CK(launch_split_rows(D.fp16, D.split, b.RpS, k, D.nS, k, D.kpad, b.BhS, b.BlS,
+                         reinterpret_cast<float *>(b.coldatS), 4, st));
+    CK(launch_split_rows(D.fp16, D.split, b.RpO, k, D.nO, k, D.kpad, b.BhO, b.BlO,
+                         reinterpret_cast<float *>(b.coldatO), 4, st));
+    CK(launch_fused_sketch_tc(D.fp16, D.split, b.Ah, b.Al, D.n, nullptr, D.kpad, b.BhS, b.BlS,
+                              D.nS, h, z, b.rowfA, b.rowdat, b.coldatS, sv, p.f, Y, h, b.ctrl, st));
+    CK(launch_fused_sketch_tc(D.fp16, D.split, b.AhO, b.AlO, vmax, &b.ctrl->v_o, D.kpad, b.BhO,
+                              b.BlO, D.nO, l, z, b.rowfO, b.rowdatO, b.coldatO, sv, p.f, b.Yo, l,
+                              b.ctrl, st));
   }
   // --- Z = O(p,:)^T Y'  (Alg. 4 line 7)
   float *Z = Zout ? Zout : b.Zf;

@@ -3,11 +3,17 @@
 //
 // The sparse-sign matrix is kept as its list of (column, slot) nonzeros: entry
 // e = c*z + t has row idx[e] and sign[e].  The kernel evaluates one column of
-// L R per nonzero, B[e, :] = R(:, idx[e])^T, so that
-//   out[i, c] = sv * sum_{t<z} sign[c*z+t] * f(rs_i * <A[i, :], B[c*z+t, :]>)
+// L'R' per nonzero, so that
+//   out[i, c] = sv * sum_{t<z} sgn[c*z+t] * f(x_{i, idx[c*z+t]})
 // is a sum over z consecutive evaluated columns.  This equals
-// f(L R(:, p)) S(p, :) of Eq. 4 exactly: duplicated coordinates only repeat
+// f(L'R'(:, p)) S(p, :) of Eq. 4 exactly: duplicated coordinates only repeat
 // an evaluation.  M-hat is never stored.
+//
+// The entries are evaluated in the centred form of center.cu:
+//   x_ie - c0 = <A[i, :], B[e, :]> + rho_i + mask_i kappa_e,
+// A = L~ (rows s (W_i - w)), B = B~ (rows (W_j - w) C^T), rowdat[i] =
+// (rho_i, mask_i), coldat[e] = (scale, kappa_e, sgn_e, 0); trunc_log(x) is
+// log1p(x - 1) for x - 1 > 0 (c0 = 1) and the identity is x itself (c0 = 0).
 #include "sne_internal.cuh"
 
 namespace sne {
@@ -16,18 +22,19 @@ constexpr int kFM = 64;    // rows per CTA
 constexpr int kFN = 128;   // evaluated columns per CTA
 constexpr int kFK = 16;    // k step
 
+// f from r = x - c0
 template <int F>
-__device__ __forceinline__ float apply_f(float x) {
-  if (F == SNE_F_TRUNC_LOG) return x > 1.0f ? logf(x) : 0.0f;
-  return x;
+__device__ __forceinline__ float apply_f(float r) {
+  if (F == SNE_F_TRUNC_LOG) return r > 0.0f ? log1pf(r) : 0.0f;
+  return r;
 }
 
 template <int F>
 __global__ void __launch_bounds__(256) fused_sketch_f32_kernel(
     const float *__restrict__ A, int64_t lda, const int32_t *__restrict__ ridx,
     const int32_t *__restrict__ nrows_dev, int64_t nrows_max, int32_t k,
-    const float *__restrict__ rs, const float *__restrict__ rs_lo, const float *__restrict__ B,
-    const int8_t *__restrict__ sign, int32_t cols_out, int32_t z, float sv,
+    const float2 *__restrict__ rowdat, const float *__restrict__ B,
+    const float4 *__restrict__ coldat, int32_t cols_out, int32_t z, float sv,
     float *__restrict__ out, int64_t ldo) {
   __shared__ __align__(16) float As[kFK][kFM + 4];
   __shared__ __align__(16) float Bs[kFK][kFN + 4];
@@ -83,22 +90,20 @@ __global__ void __launch_bounds__(256) fused_sketch_f32_kernel(
     }
     __syncthreads();
   }
-  // epilogue: scale, f, sign -> shared; then segmented sums over z columns
+  // epilogue: r = x - c0, f, sign -> shared; then segmented sums over z columns
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int64_t row = i0 + ty * 4 + i;
-    float s = 0.f, s_lo = 0.f;
-    if (row < nrows) {
-      const int64_t src = ridx ? ridx[row] : row;
-      s = rs[src];
-      if (rs_lo) s_lo = rs_lo[src];
-    }
+    float2 rd = make_float2(0.f, 0.f);
+    if (row < nrows) rd = rowdat[ridx ? ridx[row] : row];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int c = tx * 8 + j;
       float v = 0.f;
-      // the scale is the pair s + s_lo, so the only rounding of x is its own
-      if (c < e_count) v = (float)sign[e_begin + c] * apply_f<F>(fmaf(s, acc[i][j], s_lo * acc[i][j]));
+      if (c < e_count) {
+        const float4 cd = coldat[e_begin + c];
+        v = cd.z * apply_f<F>(acc[i][j] + fmaf(rd.y, cd.y, rd.x));
+      }
       Fs[ty * 4 + i][c] = v;
     }
   }
@@ -126,8 +131,8 @@ template <int F, int Z>
 __global__ void __launch_bounds__(256, 2) fused_sketch_f32_tiled_kernel(
     const float *__restrict__ A, int64_t lda, const int32_t *__restrict__ ridx,
     const int32_t *__restrict__ nrows_dev, int64_t nrows_max, int32_t k,
-    const float *__restrict__ rs, const float *__restrict__ rs_lo, const float *__restrict__ B,
-    const int8_t *__restrict__ sign, int32_t cols_out, float sv, float *__restrict__ out,
+    const float2 *__restrict__ rowdat, const float *__restrict__ B,
+    const float4 *__restrict__ coldat, int32_t cols_out, float sv, float *__restrict__ out,
     int64_t ldo) {
   __shared__ __align__(16) float As[2][kGK][kGM + 4];
   __shared__ __align__(16) float Bs[2][kGK][kGN + 4];
@@ -188,31 +193,29 @@ __global__ void __launch_bounds__(256, 2) fused_sketch_f32_tiled_kernel(
     }
     buf ^= 1;
   }
-  // epilogue: x = (s + s_lo) acc, f, sign, segmented sums over Z columns
-  float sg[8];
+  // epilogue: r = acc + rho_i + mask_i kappa_e, f, sign, segmented sums over Z columns
+  float sg[8], kp[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const int c = tx * 8 + j;
-    sg[j] = c < e_count ? (float)sign[e_begin + c] : 0.f;
+    const float4 cd = c < e_count ? coldat[e_begin + c] : make_float4(0.f, 0.f, 0.f, 0.f);
+    kp[j] = cd.y;
+    sg[j] = cd.z;
   }
   constexpr int PER = Z < 8 ? 8 / Z : 1;  // outputs per thread per row
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const int64_t row = i0 + ty * 8 + i;
     const bool rok = row < nrows;
-    float s = 0.f, s_lo = 0.f;
-    if (rok) {
-      const int64_t src = ridx ? ridx[row] : row;
-      s = rs[src];
-      if (rs_lo) s_lo = rs_lo[src];
-    }
+    float2 rd = make_float2(0.f, 0.f);
+    if (rok) rd = rowdat[ridx ? ridx[row] : row];
     float part[PER];
 #pragma unroll
     for (int g = 0; g < PER; ++g) part[g] = 0.f;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const float x = fmaf(s, acc[i][j], s_lo * acc[i][j]);
-      part[Z < 8 ? j / Z : 0] += sg[j] * apply_f<F>(x);
+      const float r = acc[i][j] + fmaf(rd.y, kp[j], rd.x);
+      part[Z < 8 ? j / Z : 0] += sg[j] * apply_f<F>(r);
     }
     if (Z > 8) {
       // combine the Z / 8 lanes of one output column (consecutive tx)
@@ -235,9 +238,9 @@ __global__ void __launch_bounds__(256, 2) fused_sketch_f32_tiled_kernel(
 
 cudaError_t launch_fused_sketch_f32(const float *A, int64_t lda, const int32_t *ridx,
                                     const int32_t *nrows_dev, int64_t nrows, int32_t k,
-                                    const float *rs, const float *rs_lo, const float *B,
-                                    const int8_t *sign, int32_t cols_out, int32_t z, float sv,
-                                    int32_t f, float *out, int64_t ldo, cudaStream_t st) {
+                                    const float2 *rowdat, const float *B, const float4 *coldat,
+                                    int32_t cols_out, int32_t z, float sv, int32_t f, float *out,
+                                    int64_t ldo, cudaStream_t st) {
   if (nrows <= 0 || cols_out <= 0) return cudaSuccess;
   if (z <= 0 || z > kFN) return cudaErrorInvalidValue;
   if (k % 4 == 0 && lda % 4 == 0 && (uintptr_t)A % 16 == 0 && (uintptr_t)B % 16 == 0 &&
@@ -247,7 +250,7 @@ cudaError_t launch_fused_sketch_f32(const float *A, int64_t lda, const int32_t *
     ProfScope ps_(K_FUSED, st);
 #define SNE_F32_CASE(FV, ZV)                                                                    \
   fused_sketch_f32_tiled_kernel<FV, ZV><<<grid2, 256, 0, st>>>(A, lda, ridx, nrows_dev, nrows, k, \
-                                                             rs, rs_lo, B, sign, cols_out, sv,  \
+                                                             rowdat, B, coldat, cols_out, sv,   \
                                                              out, ldo)
 #define SNE_F32_Z(FV)                         \
   switch (z) {                                \
@@ -272,10 +275,10 @@ cudaError_t launch_fused_sketch_f32(const float *A, int64_t lda, const int32_t *
   ProfScope ps_(K_FUSED, st);
   if (f == SNE_F_TRUNC_LOG)
     fused_sketch_f32_kernel<SNE_F_TRUNC_LOG><<<grid, 256, 0, st>>>(
-        A, lda, ridx, nrows_dev, nrows, k, rs, rs_lo, B, sign, cols_out, z, sv, out, ldo);
+        A, lda, ridx, nrows_dev, nrows, k, rowdat, B, coldat, cols_out, z, sv, out, ldo);
   else
     fused_sketch_f32_kernel<SNE_F_IDENTITY><<<grid, 256, 0, st>>>(
-        A, lda, ridx, nrows_dev, nrows, k, rs, rs_lo, B, sign, cols_out, z, sv, out, ldo);
+        A, lda, ridx, nrows_dev, nrows, k, rowdat, B, coldat, cols_out, z, sv, out, ldo);
   return cudaGetLastError();
 }
 
@@ -304,22 +307,35 @@ cudaError_t launch_signed_gather_sum(const float *In, int64_t ldi, int32_t width
   return cudaGetLastError();
 }
 
-// R'(:, j)^T for the gathered vertices j = idx[i] (Eq. 11):
-//   out[i, :] = a_j U[j, :] (C_hi + C_lo)^T,  a_j = deg_j^beta in FP64 (0 if deg_j = 0).
-// C^T is carried as a pair of FP32 matrices so that its rounding, which every
-// column of R' would otherwise share, cancels; the sums over the k terms are
-// FP32 FMA chains, and each output is rounded to FP32 once.
+// Centred columns of R' for the gathered vertices j = idx[e] (Eq. 11):
+//   out[e, :] = (W_j - w) (C_hi + C_lo)^T,  W_j = d_j^beta U[j, :],
+//   coldat[e] = (1, kappa_e, sgn_e, 0),  kappa_e = s q (W_j - w)^T,
+// with w, q = w C and s from the centring statistics (stats: w | p | q |
+// gamma | s).  W_j - w is formed in FP64 and rounded to FP32 once; the sums
+// over the k terms are FP32 FMA chains against the FP32 pair C^T = C_hi + C_lo
+// (so that the rounding of C, which every column would otherwise share,
+// cancels), each output rounded to FP32 once; kappa_e is summed in FP64 from
+// the same rounded W_j - w.  A vertex of degree 0 has R'(:, j) = 0, so its
+// columns get sgn_e = 0.
 constexpr int kRpRows = 8;
-__global__ void __launch_bounds__(256) rprime_rows_kernel(
+__global__ void __launch_bounds__(256) rtilde_rows_kernel(
     const float *__restrict__ U, int32_t k, const int32_t *__restrict__ idx, int32_t count,
     const float *__restrict__ CThi, const float *__restrict__ CTlo, const float *__restrict__ deg,
-    double beta, float *__restrict__ out) {
+    double beta, const double *__restrict__ stats, const int8_t *__restrict__ sign,
+    float *__restrict__ out, float4 *__restrict__ coldat) {
   extern __shared__ float us[];  // kRpRows x k
   const int i0 = blockIdx.x * kRpRows;
   const int rows = min(kRpRows, count - i0);
   for (int e = threadIdx.x; e < kRpRows * k; e += blockDim.x) {
     const int r = e / k, a = e % k;
-    us[e] = r < rows ? U[(int64_t)idx[i0 + r] * k + a] : 0.f;
+    float v = 0.f;
+    if (r < rows) {
+      const int j = idx[i0 + r];
+      const float dj = deg[j];
+      const double aj = dj > 0.f ? pow((double)dj, beta) : 0.0;
+      v = (float)(aj * (double)U[(int64_t)j * k + a] - stats[a]);
+    }
+    us[e] = v;
   }
   __syncthreads();
   for (int c = threadIdx.x; c < k; c += blockDim.x) {
@@ -338,26 +354,40 @@ __global__ void __launch_bounds__(256) rprime_rows_kernel(
 #pragma unroll
     for (int r = 0; r < kRpRows; ++r) {
       if (r >= rows) break;
-      const float dj = deg[idx[i0 + r]];
-      const double aj = dj > 0.f ? pow((double)dj, beta) : 0.0;
-      out[(int64_t)(i0 + r) * k + c] = (float)(aj * ((double)hi[r] + (double)lo[r]));
+      out[(int64_t)(i0 + r) * k + c] = (float)((double)hi[r] + (double)lo[r]);
+    }
+  }
+  // kappa_e: one warp per row
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp < rows) {
+    const double *q = stats + 2 * k;
+    double acc = 0.0;
+    for (int a = lane; a < k; a += 32) acc = fma(q[a], (double)us[warp * k + a], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      const int e = i0 + warp;
+      const int j = idx[e];
+      const float sg = deg[j] > 0.f ? (float)sign[e] : 0.f;
+      coldat[e] = make_float4(1.0f, (float)(stats[3 * k + 1] * acc), sg, 0.f);
     }
   }
 }
 
-cudaError_t launch_rprime_rows(const float *U, int32_t k, const int32_t *idx, int32_t count,
+cudaError_t launch_rtilde_rows(const float *U, int32_t k, const int32_t *idx, int32_t count,
                                const float *CThi, const float *CTlo, const float *deg, double beta,
-                               float *out, cudaStream_t st) {
+                               const double *stats, const int8_t *sign, float *out, float4 *coldat,
+                               cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   const size_t smem = (size_t)kRpRows * k * sizeof(float);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(rprime_rows_kernel,
+    cudaError_t e = cudaFuncSetAttribute(rtilde_rows_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   ProfScope ps_(K_TALL_GEMM, st);
-  rprime_rows_kernel<<<(count + kRpRows - 1) / kRpRows, 256, smem, st>>>(U, k, idx, count, CThi,
-                                                                        CTlo, deg, beta, out);
+  rtilde_rows_kernel<<<(count + kRpRows - 1) / kRpRows, 256, smem, st>>>(
+      U, k, idx, count, CThi, CTlo, deg, beta, stats, sign, out, coldat);
   return cudaGetLastError();
 }
 

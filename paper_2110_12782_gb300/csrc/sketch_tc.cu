@@ -1,29 +1,32 @@
 // Mixed-precision fused reconstruct + f + sparse-sign sketch (Eq. 4 and the
 // Z core of Alg. 4) on the fifth-generation tensor cores of sm_103a.
 //
-// The reconstruction L' R'(:, p) runs as a BF16 or FP16 GEMM with FP32
-// accumulation.  Per-row and per-column scaling keeps both operands in
-// [-1, 1]: A_hat[i, :] = U[i, :] / max|U[i, :]| with row factor
-// rowf_i = max|U[i, :]| * vol/(bT) * d_i^(-1+alpha), and
-// B_hat[e, :] = R'(:, idx_e)^T / colf_e with colf_e = max|R'(:, idx_e)|, so
-// that x_ie = rowf_i * colf_e * <A_hat_i, B_hat_e> is formed in FP32 before f.
+// The entries are evaluated in the centred form of center.cu,
+//   x_ie - c0 = rowf_i colf_e <A_i, B_e> + rho_i + mask_i kappa_e,
+// where A_i = L~_i / rowf_i and B_e = B~_e / colf_e are the centred factors
+// scaled by powers of two into [-1, 1] and stored in BF16 or FP16.  With
+// SPLIT each operand is a pair hi + lo (lo = the rounding error of hi, in the
+// same type) and the accumulator takes A_hi B_hi + A_lo B_hi + A_hi B_lo, so
+// the product keeps about twice the operand precision (FP16 pairs: 22 bits);
+// without SPLIT one product A_hi B_hi.  Accumulation is FP32 in TMEM.
 //
 // One CTA owns a tile of 128 rows and walks over all evaluated columns in
 // tiles of 256:
-//   warp 0   TMA producer: the 128 x k A tile once, then 256 x 64 B k-blocks
-//            through a ring of shared-memory stages (128-byte swizzle);
+//   warp 0   TMA producer: the 128 x k A tile (hi, and lo) once, then
+//            256 x 64 B k-blocks (hi, then lo) through a ring of
+//            shared-memory stages (128-byte swizzle);
 //   warp 1   allocates 512 TMEM columns (two 128 x 256 FP32 accumulators)
 //            and issues tcgen05.mma (M 128, N 256, K 16) from one thread;
-//   warps 2-17 epilogue: tcgen05.ld of the accumulator rows, x = scale * acc,
-//            f(x), sign, and the z-column segmented sums in registers, then
+//   warps 2-17 epilogue: tcgen05.ld of the accumulator rows, r = x - c0,
+//            f(r), sign, and the z-column segmented sums in registers, then
 //            the Y (or Y') row segment is stored.  Warp w reads TMEM lane
-//            quarter w % 4 and 64 of the 256 columns; sixteen warps keep
-//            enough loads, MUFU logs and stores in flight per scheduler.
+//            quarter w % 4 and 64 of the 256 columns.
 // Double-buffered accumulators let the epilogue of tile j overlap the MMAs
 // of tile j+1.  When the rows are few (the Z core: v_O rows, thousands of
-// columns) blockIdx.y splits a row tile's column tiles over several CTAs.  Every mbarrier wait is bounded (about 2 s of %globaltimer);
-// on timeout the CTA records SNE_ERR_TIMEOUT, stops issuing work, waits for
-// its in-flight MMAs and copies, frees TMEM and returns.
+// columns) blockIdx.y splits a row tile's column tiles over several CTAs.
+// Every mbarrier wait is bounded (about 2 s of %globaltimer); on timeout the
+// CTA records SNE_ERR_TIMEOUT, stops issuing work, waits for its in-flight
+// MMAs and copies, frees TMEM and returns.
 #include <cuda.h>
 
 #include <algorithm>
@@ -35,18 +38,21 @@ namespace sne {
 
 // PTX helpers: tc_ptx.cuh
 
-template <int F, int Z>
+template <int F, int Z, bool SPLIT>
 __global__ void __launch_bounds__(tc::kThreadsSketch, 1) fused_sketch_tc_kernel(
-    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
+    const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmB2,
     int64_t nrows_max, const int32_t *__restrict__ nrows_dev, int kblocks, int stages,
-    int ncols_eval, int cols_out, const float *__restrict__ rowf, const float *__restrict__ colf,
-    float out_scale, uint32_t idesc, float *__restrict__ out, int64_t ldo, Ctrl *ctrl) {
+    int ncols_eval, int cols_out, const float *__restrict__ rowf,
+    const float2 *__restrict__ rowdat, const float4 *__restrict__ coldat, float out_scale,
+    uint32_t idesc, float *__restrict__ out, int64_t ldo, Ctrl *ctrl) {
   using namespace tc;
+  constexpr int NPART = SPLIT ? 2 : 1;
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
-  unsigned char *sA = smem;
-  unsigned char *sB = sA + (size_t)kblocks * kABlockBytes;
+  unsigned char *sA = smem;                                     // hi k-blocks, then lo
+  unsigned char *sB = sA + (size_t)NPART * kblocks * kABlockBytes;
   uint64_t *bars = reinterpret_cast<uint64_t *>(sB + (size_t)stages * kBStageBytes);
   uint64_t *a_full = bars;
   uint64_t *full = bars + 1;
@@ -62,6 +68,7 @@ __global__ void __launch_bounds__(tc::kThreadsSketch, 1) fused_sketch_tc_kernel(
   const int64_t row0 = (int64_t)blockIdx.x * BM;
   if (row0 >= nrows) return;  // uniform for the CTA
   const int ntiles = (ncols_eval + BN - 1) / BN;
+  const int steps = kblocks * NPART;  // B stages per column tile
 
   if (threadIdx.x == 0) {
     mbar_init(a_full, 1);
@@ -93,14 +100,19 @@ __global__ void __launch_bounds__(tc::kThreadsSketch, 1) fused_sketch_tc_kernel(
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer
-      mbar_expect_tx(a_full, (uint32_t)(kblocks * kABlockBytes));
-      for (int kb = 0; kb < kblocks; ++kb)
+      mbar_expect_tx(a_full, (uint32_t)(NPART * kblocks * kABlockBytes));
+      for (int kb = 0; kb < kblocks; ++kb) {
         tma_load_2d(sA + (size_t)kb * kABlockBytes, &tmA, a_full, kb * BK, (int)row0);
+        if (SPLIT)
+          tma_load_2d(sA + (size_t)(kblocks + kb) * kABlockBytes, &tmA2, a_full, kb * BK,
+                      (int)row0);
+      }
       int it = 0;
       int issued = 0;
       bool ok = true;
       for (int j = blockIdx.y; j < ntiles && ok; j += gridDim.y) {
-        for (int kb = 0; kb < kblocks; ++kb, ++it) {
+        for (int q = 0; q < steps; ++q, ++it) {
+          const int kb = q / NPART, part = q % NPART;
           const int s = it % stages;
           const uint32_t ph = (uint32_t)((it / stages) & 1);
           if (!mbar_wait(&empty[s], ph ^ 1u, abortv, ctrl)) {
@@ -108,7 +120,7 @@ __global__ void __launch_bounds__(tc::kThreadsSketch, 1) fused_sketch_tc_kernel(
             break;
           }
           mbar_expect_tx(&full[s], (uint32_t)kBStageBytes);
-          tma_load_2d(sB + (size_t)s * kBStageBytes, &tmB, &full[s], kb * BK, j * BN);
+          tma_load_2d(sB + (size_t)s * kBStageBytes, part ? &tmB2 : &tmB, &full[s], kb * BK, j * BN);
           ++issued;
         }
       }
@@ -139,18 +151,33 @@ __global__ void __launch_bounds__(tc::kThreadsSketch, 1) fused_sketch_tc_kernel(
         }
         fence_after();
         const uint32_t dt = tmem + (uint32_t)(buf * BN);
-        for (int kb = 0; kb < kblocks; ++kb, ++it) {
+        for (int q = 0; q < steps; ++q, ++it) {
+          const int kb = q / NPART, part = q % NPART;
           const int s = it % stages;
           if (!mbar_wait(&full[s], (uint32_t)((it / stages) & 1), abortv, ctrl)) {
             ok = false;
             break;
           }
           fence_after();
-          const uint32_t a0 = smem_u32(sA + (size_t)kb * kABlockBytes);
+          const uint32_t ahi = smem_u32(sA + (size_t)kb * kABlockBytes);
           const uint32_t b0 = smem_u32(sB + (size_t)s * kBStageBytes);
+          if (part == 0) {
+            // A_hi B_hi (the first product of the tile starts the accumulator)
 #pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk)
-            mma_f16(dt, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), idesc, (kb | kk) ? 1u : 0u);
+            for (int kk = 0; kk < BK / 16; ++kk)
+              mma_f16(dt, sdesc(ahi + kk * 32), sdesc(b0 + kk * 32), idesc, (kb | kk) ? 1u : 0u);
+            if (SPLIT) {
+              const uint32_t alo = smem_u32(sA + (size_t)(kblocks + kb) * kABlockBytes);
+#pragma unroll
+              for (int kk = 0; kk < BK / 16; ++kk)
+                mma_f16(dt, sdesc(alo + kk * 32), sdesc(b0 + kk * 32), idesc, 1u);
+            }
+          } else {
+            // A_hi B_lo
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk)
+              mma_f16(dt, sdesc(ahi + kk * 32), sdesc(b0 + kk * 32), idesc, 1u);
+          }
           mma_commit(&empty[s]);
         }
         if (!ok) break;
@@ -170,6 +197,7 @@ __global__ void __launch_bounds__(tc::kThreadsSketch, 1) fused_sketch_tc_kernel(
     const int64_t row = row0 + 32 * ew + lane;
     const bool row_ok = row < nrows;
     const float rf = row_ok ? rowf[row] : 0.0f;
+    const float2 rd = row_ok ? rowdat[row] : make_float2(0.0f, 0.0f);
     constexpr int G = 32 / Z;        // output columns per 32-column chunk
     int jj = 0;
     for (int j = blockIdx.y; j < ntiles; j += gridDim.y, ++jj) {
@@ -188,23 +216,15 @@ __global__ void __launch_bounds__(tc::kThreadsSketch, 1) fused_sketch_tc_kernel(
       mbar_arrive(&tempty[buf]);
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
-        const float4 *cf4 = reinterpret_cast<const float4 *>(colf + ebase + c * 32);
+        const float4 *cd4 = coldat + ebase + c * 32;
         float acc[G];
 #pragma unroll
         for (int g = 0; g < G; ++g) acc[g] = 0.0f;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const float4 cf = __ldg(cf4 + q);
-          const float cfv[4] = {cf.x, cf.y, cf.z, cf.w};
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int t = 4 * q + u;
-            const float x = rf * fabsf(cfv[u]) * v[c][t];
-            const float l = tc::fx2<F>(x);
-            // trunc_log is >= 0, so the sign of cf can be copied onto it
-            if (F == SNE_F_TRUNC_LOG) acc[t / Z] += copysignf(l, cfv[u]);
-            else acc[t / Z] += (cfv[u] < 0.0f) ? -l : l;
-          }
+        for (int t = 0; t < 32; ++t) {
+          const float4 cd = __ldg(cd4 + t);  // (colf, kappa, sgn, 0), the same for the warp
+          const float r = fmaf(v[c][t], rf * cd.x, fmaf(rd.y, cd.y, rd.x));
+          acc[t / Z] = fmaf(cd.z, tc::fr<F>(r), acc[t / Z]);
         }
         // G consecutive outputs of this row: columns (ebase + 32 c) / Z ..
         const int oc0 = (ebase + 32 * c) / Z;
@@ -230,68 +250,6 @@ __global__ void __launch_bounds__(tc::kThreadsSketch, 1) fused_sketch_tc_kernel(
   fence_after();
   if (warp == 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
-}
-
-// ---------------------------------------------------------------------------
-// Row-normalized half-precision copies of the GEMM operands
-// ---------------------------------------------------------------------------
-template <typename H>
-__device__ __forceinline__ H to_h(float x);
-template <>
-__device__ __forceinline__ __nv_bfloat16 to_h<__nv_bfloat16>(float x) {
-  return __float2bfloat16_rn(x);
-}
-template <>
-__device__ __forceinline__ __half to_h<__half>(float x) {
-  return __float2half_rn(x);
-}
-
-// dst[r, :kpad] = src[s(r), :k] / max|src[s(r), :k]| (zero padded); scale[r] =
-// max|src[s(r), :]| * extra[s(r)].  Rows r >= *nrows_dev (when given) are zero.
-template <typename H>
-__global__ void __launch_bounds__(256) to_half_rows_kernel(
-    const float *__restrict__ src, int64_t lds, const int32_t *__restrict__ ridx,
-    const int32_t *__restrict__ nrows_dev, int64_t nrows_max, int k, int kpad,
-    const float *__restrict__ extra, const int8_t *__restrict__ sgn, H *__restrict__ dst,
-    float *__restrict__ scale) {
-  const int lane = threadIdx.x & 31;
-  const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (r >= nrows_max) return;
-  const int64_t nrows = nrows_dev ? (int64_t)(*nrows_dev) : nrows_max;
-  H *d = dst + r * kpad;
-  if (r >= nrows) {
-    for (int c = lane; c < kpad; c += 32) d[c] = to_h<H>(0.0f);
-    if (lane == 0) scale[r] = 0.0f;
-    return;
-  }
-  const int64_t s = ridx ? (int64_t)ridx[r] : r;
-  const float *x = src + s * lds;
-  float m = 0.0f;
-  for (int c = lane; c < k; c += 32) m = fmaxf(m, fabsf(x[c]));
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  const float inv = m > 0.0f ? 1.0f / m : 0.0f;
-  for (int c = lane; c < kpad; c += 32) d[c] = to_h<H>(c < k ? x[c] * inv : 0.0f);
-  if (lane == 0) {
-    const float sc = m * (extra ? extra[s] : 1.0f);
-    scale[r] = (sgn && sgn[r] < 0) ? -sc : sc;
-  }
-}
-
-cudaError_t launch_to_half_rows(bool fp16, const float *src, int64_t lds, const int32_t *ridx,
-                                const int32_t *nrows_dev, int64_t nrows_max, int k, int kpad,
-                                const float *extra, const int8_t *sgn, void *dst, float *scale,
-                                cudaStream_t st) {
-  if (nrows_max <= 0) return cudaSuccess;
-  const unsigned blocks = (unsigned)((nrows_max + 7) / 8);
-  ProfScope ps_(K_MISC, st);
-  if (fp16)
-    to_half_rows_kernel<__half><<<blocks, 256, 0, st>>>(src, lds, ridx, nrows_dev, nrows_max, k, kpad,
-                                                        extra, sgn, static_cast<__half *>(dst), scale);
-  else
-    to_half_rows_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(
-        src, lds, ridx, nrows_dev, nrows_max, k, kpad, extra, sgn, static_cast<__nv_bfloat16 *>(dst),
-        scale);
-  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -330,31 +288,42 @@ static bool make_map(CUtensorMap *tm, bool fp16, const void *ptr, int64_t rows, 
   return r == CUDA_SUCCESS;
 }
 
-size_t fused_tc_smem_bytes(int kpad, int *stages_out) {
+size_t fused_tc_smem_bytes(int kpad, bool split, int *stages_out) {
   const int kblocks = kpad / tc::BK;
+  const size_t abytes = (size_t)(split ? 2 : 1) * kblocks * tc::kABlockBytes;
+  // 1 KB alignment slack and 256 bytes of barriers next to A and the B ring
+  const size_t budget = 227 * 1024 - 1024 - 256;
   int stages = 4;
-  while (stages > 2 && (size_t)kblocks * tc::kABlockBytes + (size_t)stages * tc::kBStageBytes >
-                           200 * 1024)
-    --stages;
+  while (stages > 2 && abytes + (size_t)stages * tc::kBStageBytes > budget) --stages;
   if (stages_out) *stages_out = stages;
-  return 1024 + (size_t)kblocks * tc::kABlockBytes + (size_t)stages * tc::kBStageBytes + 256;
+  return 1024 + abytes + (size_t)stages * tc::kBStageBytes + 256;
 }
 
-cudaError_t launch_fused_sketch_tc(bool fp16, const void *Ahat, int64_t nrows_max,
-                                   const int32_t *nrows_dev, int kpad, const void *Bhat,
-                                   int ncols_eval, int cols_out, int z, const float *rowf,
-                                   const float *colf, const int8_t *sign, float sv, int f, float *out,
-                                   int64_t ldo, Ctrl *ctrl, cudaStream_t st) {
+cudaError_t launch_fused_sketch_tc(bool fp16, bool split, const void *Ahi, const void *Alo,
+                                   int64_t nrows_max, const int32_t *nrows_dev, int kpad,
+                                   const void *Bhi, const void *Blo, int ncols_eval, int cols_out,
+                                   int z, const float *rowf, const float2 *rowdat,
+                                   const float4 *coldat, float sv, int f, float *out, int64_t ldo,
+                                   Ctrl *ctrl, cudaStream_t st) {
   if (nrows_max <= 0 || cols_out <= 0) return cudaSuccess;
   if (kpad % tc::BK != 0 || kpad <= 0) return cudaErrorInvalidValue;
   if (!(z == 1 || z == 2 || z == 4 || z == 8 || z == 16 || z == 32)) return cudaErrorInvalidValue;
-  if (((uintptr_t)Ahat % 16) || ((uintptr_t)Bhat % 16)) return cudaErrorInvalidValue;
+  if (((uintptr_t)Ahi % 16) || ((uintptr_t)Bhi % 16)) return cudaErrorInvalidValue;
+  if (split && (!Alo || !Blo || ((uintptr_t)Alo % 16) || ((uintptr_t)Blo % 16)))
+    return cudaErrorInvalidValue;
   int stages = 0;
-  const size_t smem = fused_tc_smem_bytes(kpad, &stages);
+  const size_t smem = fused_tc_smem_bytes(kpad, split, &stages);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  CUtensorMap tmA, tmB;
-  if (!make_map(&tmA, fp16, Ahat, nrows_max, kpad, tc::BM)) return cudaErrorInvalidValue;
-  if (!make_map(&tmB, fp16, Bhat, ncols_eval, kpad, tc::BN)) return cudaErrorInvalidValue;
+  CUtensorMap tmA, tmA2, tmB, tmB2;
+  if (!make_map(&tmA, fp16, Ahi, nrows_max, kpad, tc::BM)) return cudaErrorInvalidValue;
+  if (!make_map(&tmB, fp16, Bhi, ncols_eval, kpad, tc::BN)) return cudaErrorInvalidValue;
+  if (split) {
+    if (!make_map(&tmA2, fp16, Alo, nrows_max, kpad, tc::BM)) return cudaErrorInvalidValue;
+    if (!make_map(&tmB2, fp16, Blo, ncols_eval, kpad, tc::BN)) return cudaErrorInvalidValue;
+  } else {
+    tmA2 = tmA;
+    tmB2 = tmB;
+  }
   // instruction descriptor: D F32, A/B F16 (0) or BF16 (1), K-major, N = 256, M = 128
   const uint32_t fmt = fp16 ? 0u : 1u;
   const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(tc::BN >> 3) << 17) |
@@ -367,33 +336,40 @@ cudaError_t launch_fused_sketch_tc(bool fp16, const void *Ahat, int64_t nrows_ma
       1, std::min(ntiles, (int)((2 * sm_count() + grid_x - 1) / grid_x)));
   const dim3 grid(grid_x, splits);
   const int kblocks = kpad / tc::BK;
-  // f = trunc_log: the kernel sums signed log2 values; ln 2 joins sv here
-  const float out_scale = (f == SNE_F_TRUNC_LOG) ? sv * 0.69314718055994530942f : sv;
-  (void)sign;
-#define SNE_TC_LAUNCH(FV, ZV)                                                                     \
+  const float out_scale = sv;
+#define SNE_TC_LAUNCH(FV, ZV, SV)                                                                 \
   do {                                                                                            \
-    auto kern = fused_sketch_tc_kernel<FV, ZV>;                                                   \
+    auto kern = fused_sketch_tc_kernel<FV, ZV, SV>;                                               \
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
                                          (int)smem);                                              \
     if (e != cudaSuccess) return e;                                                               \
     ProfScope ps_(K_FUSED_TC, st);                                                                \
-    kern<<<grid, tc::kThreadsSketch, smem, st>>>(tmA, tmB, nrows_max, nrows_dev, kblocks, stages, \
-                                                 ncols_eval, cols_out, rowf, colf, out_scale,     \
-                                                 idesc, out, ldo, ctrl);                          \
+    kern<<<grid, tc::kThreadsSketch, smem, st>>>(tmA, tmA2, tmB, tmB2, nrows_max, nrows_dev,      \
+                                                 kblocks, stages, ncols_eval, cols_out, rowf,     \
+                                                 rowdat, coldat, out_scale, idesc, out, ldo,      \
+                                                 ctrl);                                           \
   } while (0)
-#define SNE_TC_Z(FV)             \
-  switch (z) {                   \
-    case 1: SNE_TC_LAUNCH(FV, 1); break;  \
-    case 2: SNE_TC_LAUNCH(FV, 2); break;  \
-    case 4: SNE_TC_LAUNCH(FV, 4); break;  \
-    case 8: SNE_TC_LAUNCH(FV, 8); break;  \
-    case 16: SNE_TC_LAUNCH(FV, 16); break; \
-    default: SNE_TC_LAUNCH(FV, 32); break; \
+#define SNE_TC_Z(FV, SV)                        \
+  switch (z) {                                  \
+    case 1: SNE_TC_LAUNCH(FV, 1, SV); break;    \
+    case 2: SNE_TC_LAUNCH(FV, 2, SV); break;    \
+    case 4: SNE_TC_LAUNCH(FV, 4, SV); break;    \
+    case 8: SNE_TC_LAUNCH(FV, 8, SV); break;    \
+    case 16: SNE_TC_LAUNCH(FV, 16, SV); break;  \
+    default: SNE_TC_LAUNCH(FV, 32, SV); break;  \
   }
   if (f == SNE_F_TRUNC_LOG) {
-    SNE_TC_Z(SNE_F_TRUNC_LOG)
+    if (split) {
+      SNE_TC_Z(SNE_F_TRUNC_LOG, true)
+    } else {
+      SNE_TC_Z(SNE_F_TRUNC_LOG, false)
+    }
   } else {
-    SNE_TC_Z(SNE_F_IDENTITY)
+    if (split) {
+      SNE_TC_Z(SNE_F_IDENTITY, true)
+    } else {
+      SNE_TC_Z(SNE_F_IDENTITY, false)
+    }
   }
 #undef SNE_TC_Z
 #undef SNE_TC_LAUNCH

@@ -199,31 +199,55 @@ cudaError_t launch_symmetrize(double *A, int32_t n, int32_t lda, cudaStream_t st
 cudaError_t launch_check_finite_f(const float *x, int64_t count, Ctrl *ctrl, int32_t where,
                                   cudaStream_t st);
 
+// center.cu: centred evaluation of L'R' (x - c0 = s (W_i - w) C (W_j - w)^T +
+// rho_i + kappa_j with W = D^(-1+a) U and w the degree-weighted mean row).
+// stats (FP64, 3k + 2): w | p = C w^T | q = w C | gamma = s w C w^T - c0 | s.
+size_t center_partial_doubles(int64_t n, int k);
+cudaError_t launch_center_stats(const float *U, int64_t ldu, int k, int64_t n, const float *deg,
+                                double alpha, const double *vol_dev, const double *lam,
+                                const double *Csum, double smult, double c0, double *partial,
+                                double *stats, float *ws_hi, float *ws_lo, cudaStream_t st);
+// Rows r < nrows_max (source row ridx[r] or r) of L~ = s (W - w): out = 0 FP32
+// (Lt, ld ldl); out = 1 FP16, 2 BF16 rows of L~ / rowf (rowf a power of two)
+// into Ahi (and Alo, the rounding error of Ahi, when split), kpad columns.
+// rowdat[r] = (rho_r, mask_r).  rsc + rsc_lo = s d^(-1+a) (0 for isolated
+// vertices), ws_hi + ws_lo = s w.
+cudaError_t launch_center_rows(int out, bool split, const float *U, int64_t ldu, int k,
+                               const int32_t *ridx, const int32_t *nrows_dev, int64_t nrows_max,
+                               const float *rsc, const float *rsc_lo, const float *ws_hi,
+                               const float *ws_lo, const double *stats, bool trunc_log, double c0,
+                               float *Lt, int64_t ldl, void *Ahi, void *Alo, int kpad, float *rowf,
+                               float2 *rowdat, cudaStream_t st);
+// FP32 rows -> FP16/BF16 rows / sc (sc a power of two, written to
+// scale[r * sstride]) as hi (+ lo) with kpad columns.
+cudaError_t launch_split_rows(bool fp16, bool split, const float *src, int64_t lds, int64_t rows,
+                              int k, int kpad, void *hi, void *lo, float *scale, int sstride,
+                              cudaStream_t st);
+
 // sketch.cu
-// out[i, c] = sv * sum_{t<z} sign[c*z+t] * f(rs[r(i)] * <A[r(i), :], B[c*z+t, :]>)
+// out[i, c] = sv * sum_{t<z} sgn_e f(<A[r(i), :], B[e, :]> + rho_r(i) + mask_r(i) kappa_e),
+// e = c*z + t, rowdat[r] = (rho, mask), coldat[e] = (scale, kappa, sgn, 0).
 cudaError_t launch_fused_sketch_f32(const float *A, int64_t lda, const int32_t *ridx,
                                     const int32_t *nrows_dev, int64_t nrows, int32_t k,
-                                    const float *rs, const float *rs_lo, const float *B,
-                                    const int8_t *sign, int32_t cols_out, int32_t z, float sv,
-                                    int32_t f, float *out, int64_t ldo, cudaStream_t st);
-// out[i, :] = deg_j^beta U[j, :] (CThi + CTlo), j = idx[i]  (R'(:, j)^T of Eq. 11)
-cudaError_t launch_rprime_rows(const float *U, int32_t k, const int32_t *idx, int32_t count,
+                                    const float2 *rowdat, const float *B, const float4 *coldat,
+                                    int32_t cols_out, int32_t z, float sv, int32_t f, float *out,
+                                    int64_t ldo, cudaStream_t st);
+// Centred columns of R' for j = idx[e]: out[e, :] = (W_j - w) C^T (C^T as
+// the FP32 pair CThi + CTlo), coldat[e] = (1, kappa_e, sgn_e, 0).
+cudaError_t launch_rtilde_rows(const float *U, int32_t k, const int32_t *idx, int32_t count,
                                const float *CThi, const float *CTlo, const float *deg, double beta,
-                               float *out, cudaStream_t st);
-// sketch_tc.cu: mixed-precision fused sketch (BF16 or FP16 operands, FP32
-// accumulation on tcgen05).  Operands are row-normalized half copies made by
-// launch_to_half_rows; kpad is k rounded up to a multiple of 64; colf holds
-// sign_e * colf_e and is readable (zero padded) up to a multiple of 256.
-// scale[r] = max|src row| * extra[s(r)], negated where sgn[r] < 0 (sgn may be NULL).
-cudaError_t launch_to_half_rows(bool fp16, const float *src, int64_t lds, const int32_t *ridx,
-                                const int32_t *nrows_dev, int64_t nrows_max, int k, int kpad,
-                                const float *extra, const int8_t *sgn, void *dst, float *scale,
-                                cudaStream_t st);
-cudaError_t launch_fused_sketch_tc(bool fp16, const void *Ahat, int64_t nrows_max,
-                                   const int32_t *nrows_dev, int kpad, const void *Bhat,
-                                   int ncols_eval, int cols_out, int z, const float *rowf,
-                                   const float *colf, const int8_t *sign, float sv, int f, float *out,
-                                   int64_t ldo, Ctrl *ctrl, cudaStream_t st);
+                               const double *stats, const int8_t *sign, float *out, float4 *coldat,
+                               cudaStream_t st);
+// sketch_tc.cu: the same sums with half-precision operands (BF16 or FP16,
+// optionally hi/lo pairs) on tcgen05 with FP32 accumulation; A rows scaled by
+// rowf, B rows by coldat[e].x; kpad = k rounded up to 64; coldat readable
+// (zero padded) up to a multiple of 256 entries.
+cudaError_t launch_fused_sketch_tc(bool fp16, bool split, const void *Ahi, const void *Alo,
+                                   int64_t nrows_max, const int32_t *nrows_dev, int kpad,
+                                   const void *Bhi, const void *Blo, int ncols_eval, int cols_out,
+                                   int z, const float *rowf, const float2 *rowdat,
+                                   const float4 *coldat, float sv, int f, float *out, int64_t ldo,
+                                   Ctrl *ctrl, cudaStream_t st);
 // The same sum of FP32 rows accumulated and written in FP64.
 cudaError_t launch_signed_gather_sum64(const float *In, int64_t ldi, int32_t width,
                                        const int32_t *idx, const int8_t *sign, int32_t cols,

@@ -166,17 +166,23 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// f in log2 units (the caller multiplies the sums by ln 2)
+// f of r = x - c0: trunc_log(x) = log1p(r) for r > 0, else 0; the identity r.
+// u = fl(1 + r) carries the rounding error e = r - (u - 1), which is exact
+// (u - 1 is exact and within a factor of two of r), and
+// log1p(r) = log(u) + log1p(e/u) ~ log(u) + e with |e/u| <= 2^-24 (the 1/u
+// factor matters only where u is far from 1, where e is below 2^-24 of log u).
+// The full-accuracy logf keeps its relative accuracy near u = 1, where
+// lg2.approx has an absolute error of about 1e-7 (so a relative error that
+// grows without bound as r -> 0): measured on sm_103a, logf(u) + e is within
+// 1.3e-7 relative of log1p(r) for r in [2^-26, 4].
 template <int F>
-__device__ __forceinline__ float fx2(float x) {
-  if (F == SNE_F_TRUNC_LOG) return x > 1.0f ? __log2f(x) : 0.0f;
-  return x;
-}
-
-template <int F>
-__device__ __forceinline__ float fx(float x) {
-  if (F == SNE_F_TRUNC_LOG) return x > 1.0f ? __logf(x) : 0.0f;
-  return x;
+__device__ __forceinline__ float fr(float r) {
+  if (F == SNE_F_TRUNC_LOG) {
+    const float u = __fadd_rn(1.0f, r);
+    const float e = __fsub_rn(r, __fsub_rn(u, 1.0f));
+    return r > 0.0f ? __fadd_rn(logf(u), e) : 0.0f;
+  }
+  return r;
 }
 
 }  // namespace tc

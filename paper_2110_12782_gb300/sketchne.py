@@ -28,7 +28,9 @@ SNE_ERR_CUDA = -5
 SNE_ERR_TIMEOUT = -6
 SNE_ERR_NUMERIC = -7
 
-SNE_FP32, SNE_BF16, SNE_FP16 = 0, 1, 2
+SNE_FP32, SNE_BF16, SNE_FP16, SNE_BF16X2, SNE_FP16X2 = 0, 1, 2, 3, 4
+PRECISIONS = {"fp32": SNE_FP32, "bf16": SNE_BF16, "fp16": SNE_FP16, "bf16x2": SNE_BF16X2,
+              "fp16x2": SNE_FP16X2}
 SNE_F_TRUNC_LOG, SNE_F_IDENTITY = 0, 1
 SNE_ORTH_EIGSVD, SNE_ORTH_CHOLQR = 0, 1
 SNE_WS_EMBED, SNE_WS_FREIGS, SNE_WS_SKETCH, SNE_WS_EMBED_HOST = 0, 1, 2, 3

@@ -182,3 +182,17 @@ def test_graph_without_edges_is_rejected_on_the_host(L):
     nb = ctypes.c_size_t(0)
     assert L.sne_embed_batched_workspace_bytes(1, graphs, ctypes.byref(p), 0, ctypes.byref(nb)) == GR
     assert "no edges" in sk.sne_error_string(GR)
+
+
+def test_pair_precision_rejects_k_beyond_the_resident_tile(L):
+    """hi/lo pair operands keep 2 x k half columns of the 128-row A tile in
+    shared memory, so the pair precisions take k <= 320 (single: k <= 384)."""
+    for prec, k, ok in ((sk.SNE_FP16X2, 320, True), (sk.SNE_FP16X2, 384, False),
+                        (sk.SNE_BF16X2, 384, False), (sk.SNE_FP16, 384, True)):
+        q = sk.sne_params_init(64, k, precision=prec)
+        if ok:
+            assert sk.sne_workspace_bytes(100_000, 1_000_000, q, sk.SNE_WS_SKETCH) > 0
+        else:
+            with pytest.raises(sk.SketchNEError) as e:
+                sk.sne_workspace_bytes(100_000, 1_000_000, q, sk.SNE_WS_SKETCH)
+            assert e.value.code == sk.SNE_ERR_SIZE
