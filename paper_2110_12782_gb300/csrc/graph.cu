@@ -1,6 +1,8 @@
 // Graph kernels: degrees and vol(G) (Sec. 2), the implicit SpMM with the
 // modified Laplacian X = D^-a A D^-a (Alg. 5, Sec. 4.4 "Parallelization"),
 // and CSR validation.
+#include <cstdlib>
+
 #include "sne_internal.cuh"
 
 namespace sne {
@@ -184,6 +186,67 @@ __global__ void __launch_bounds__(256, 2) spmm_vec4_kernel(
   }
 }
 
+// Column-blocked SpMM for operands larger than L2: Y[:, cb] = X B[:, cb] for
+// column blocks of CB = 4 * LPN columns, one block after the other
+// (blockIdx.y; the hardware dispatches the CTAs of one block before the next),
+// so that the gathered rows of one column block (n * CB * 4 bytes, 64 MB at
+// n = 10^6 and CB = 16) stay in L2 while the CSR arrays and the outputs stream
+// past evict-first.  Every row of B is then read from DRAM once per SpMM
+// instead of once per L2 miss of its deg(j) gathers.  One warp per row: the 32
+// lanes form 32 / LPN groups, each gathering the CB-column segment of a
+// different nonzero as LPN float4 (two nonzeros per group in flight), and the
+// groups' partial sums are added by shuffles at the end of the row.
+template <int LPN>
+__global__ void __launch_bounds__(256) spmm_colblock_kernel(
+    int64_t n, const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+    const float *__restrict__ val, const float *__restrict__ dpow, const float *__restrict__ wnz,
+    const float *__restrict__ B, int64_t ldb, float *__restrict__ Y, int64_t ldy) {
+  constexpr int NG = 32 / LPN;  // nonzero groups per warp
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / LPN, sub = lane % LPN;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= n) return;
+  const uint64_t pol_keep = l2_policy_normal(), pol_stream = l2_policy_first();
+  const int64_t c0 = (int64_t)blockIdx.y * (4 * LPN);  // first column of the block
+  const float *Bc = B + c0 + 4 * sub;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int64_t beg = row_ptr[row], end = row_ptr[row + 1];
+  int64_t p = beg + grp;
+  for (; p + NG < end; p += 2 * NG) {
+    const int32_t ca = ld_nc_s32(col + p, pol_stream);
+    const int32_t cb = ld_nc_s32(col + p + NG, pol_stream);
+    const float wa = wnz ? ld_nc_f32(wnz + p, pol_stream) : dpow[ca] * (val ? val[p] : 1.0f);
+    const float wb = wnz ? ld_nc_f32(wnz + p + NG, pol_stream) : dpow[cb] * (val ? val[p + NG] : 1.0f);
+    const float4 xa = ld_nc_f4(reinterpret_cast<const float4 *>(Bc + (int64_t)ca * ldb), pol_keep);
+    const float4 xb = ld_nc_f4(reinterpret_cast<const float4 *>(Bc + (int64_t)cb * ldb), pol_keep);
+    acc.x += wa * xa.x + wb * xb.x;
+    acc.y += wa * xa.y + wb * xb.y;
+    acc.z += wa * xa.z + wb * xb.z;
+    acc.w += wa * xa.w + wb * xb.w;
+  }
+  if (p < end) {
+    const int32_t ca = ld_nc_s32(col + p, pol_stream);
+    const float wa = wnz ? ld_nc_f32(wnz + p, pol_stream) : dpow[ca] * (val ? val[p] : 1.0f);
+    const float4 xa = ld_nc_f4(reinterpret_cast<const float4 *>(Bc + (int64_t)ca * ldb), pol_keep);
+    acc.x += wa * xa.x;
+    acc.y += wa * xa.y;
+    acc.z += wa * xa.z;
+    acc.w += wa * xa.w;
+  }
+#pragma unroll
+  for (int o = LPN; o < 32; o <<= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
+    acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
+  }
+  if (grp == 0) {
+    const float si = dpow[row];
+    st_f4(reinterpret_cast<float4 *>(Y + row * ldy + c0 + 4 * sub),
+          make_float4(si * acc.x, si * acc.y, si * acc.z, si * acc.w), pol_stream);
+  }
+}
+
 // Scalar fallback for widths that are not a multiple of 4 (or unaligned).
 __global__ void __launch_bounds__(256) spmm_scalar_kernel(
     int64_t n, const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
@@ -286,6 +349,19 @@ cudaError_t launch_spmm_hot_threshold(const float *dpow, int64_t n, int64_t row_
   return cudaGetLastError();
 }
 
+// Column-block width of the SpMM for operands beyond L2 (16; SNE_SPMM_CB=8 or
+// 0 selects 8 columns or the row-at-once kernel, for measurements).
+constexpr double kSpmmBlockFromBytes = 256.0 * 1024 * 1024;
+static int spmm_col_block() {
+  static int cb = -1;
+  if (cb < 0) {
+    const char *v = getenv("SNE_SPMM_CB");
+    cb = 16;
+    if (v && (v[0] == '0' || v[0] == '8') && v[1] == 0) cb = v[0] - '0';
+  }
+  return cb;
+}
+
 cudaError_t launch_spmm(const sne_csr &g, const float *dpow, const float *wnz, const float *B,
                         int64_t ldb, int32_t ncols, float *Y, int64_t ldy, cudaStream_t st,
                         const uint32_t *hot) {
@@ -296,6 +372,18 @@ cudaError_t launch_spmm(const sne_csr &g, const float *dpow, const float *wnz, c
   const bool vec = (ncols % 4 == 0) && (ldb % 4 == 0) && (ldy % 4 == 0) &&
                    ((uintptr_t)B % 16 == 0) && ((uintptr_t)Y % 16 == 0);
   const int nvec = ncols / 4;
+  // operands well beyond L2 (129 MB): column blocks of 16 that fit in it
+  const int cb = spmm_col_block();
+  if (vec && cb > 0 && ncols % cb == 0 && (double)g.n * ncols * 4.0 > kSpmmBlockFromBytes) {
+    const dim3 grid(blocks, (unsigned)(ncols / cb));
+    if (cb == 16)
+      spmm_colblock_kernel<4><<<grid, 256, 0, st>>>(g.n, g.row_ptr, g.col_idx, g.val, dpow, wnz, B,
+                                                    ldb, Y, ldy);
+    else
+      spmm_colblock_kernel<2><<<grid, 256, 0, st>>>(g.n, g.row_ptr, g.col_idx, g.val, dpow, wnz, B,
+                                                    ldb, Y, ldy);
+    return cudaGetLastError();
+  }
   if (vec && nvec <= 32 * 12) {
     const int vpl = (nvec + 31) / 32;
 #define SNE_SPMM_CASE(V)                                                                     \

@@ -278,6 +278,38 @@ def test_embed_matches_oracle(sk, c1):
     assert np.allclose(sig[:blk], ref.sigma[:blk], rtol=1e-3)
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_embed_host_equals_embed_and_matches_oracle(sk, c1, pinned):
+    """sne_embed_host (graph and outputs in host memory, the copies inside the
+    call) runs the same kernels on the same data as sne_embed: E and sigma are
+    equal bit for bit, and so match the oracle at the stated tolerance."""
+    g, p, ref = c1
+    pr = p.resolved()
+    G = dev_graph(sk, g)
+    q = gpu_params(sk, p)
+    ws = sk.workspace(g.n, g.nnz, q, sk.SNE_WS_EMBED)
+    E = torch.empty(g.n, pr.d, dtype=torch.float32, device="cuda")
+    sig = torch.empty(pr.d, dtype=torch.float64, device="cuda")
+    sk.sne_embed(G, q, ws, E, sig)
+    assert sk.sne_status(ws) == 0
+    rp = torch.from_numpy(g.row_ptr)
+    ci = torch.from_numpy(g.col_idx)
+    Eh = torch.full((g.n, pr.d), float("nan"), dtype=torch.float32)
+    sh = torch.full((pr.d,), float("nan"), dtype=torch.float64)
+    if pinned:
+        rp, ci, Eh, sh = rp.pin_memory(), ci.pin_memory(), Eh.pin_memory(), sh.pin_memory()
+    wsh = sk.workspace(g.n, g.nnz, q, sk.SNE_WS_EMBED_HOST)
+    sk.sne_embed_host(rp, ci, None, g.n, q, wsh, Eh, sh)
+    torch.cuda.synchronize()
+    assert sk.sne_status(wsh) == 0
+    assert torch.equal(Eh, E.cpu())
+    assert torch.equal(sh, sig.cpu())
+    blk = leading_gap_block(ref.sigma, pr.d)
+    sines = o.principal_angle_sines(Eh.numpy()[:, :blk], ref.E[:, :blk])
+    assert sines.max() < ANGLE_TOL, (blk, sines)
+    assert np.allclose(sh.numpy()[:blk], ref.sigma[:blk], rtol=1e-3)
+
+
 # ---------------------------------------------------------------- validation
 def test_validate_flags_bad_graphs(sk):
     g = synth.sbm(300, 3, 0.05, 0.01, seed=2)

@@ -322,6 +322,44 @@ def test_theorem1_bound_holds():
         assert lhs <= o.theorem1_bound(ev, k, deg, o.volume(A), g.n, alpha, 10, 1.0)
 
 
+def test_theorem1_bound_hand_values():
+    """The right-hand side of Theorem 1 at two tiny graphs, worked by hand
+    from the known spectra (not from the oracle's eigensolver):
+
+    * K_4, alpha = 1/2, k = 1, T = 2, b = 1: D^-1/2 A D^-1/2 has eigenvalues
+      1 and -1/3 (three times), so the tail is sqrt(3 / 9) = 1/sqrt(3); every
+      degree is 3, vol = 12, c = n (d_max/d_min)^0 = 4.  Then
+      (c^T - 1)(1 + n/(c-1)) - nT = 15 * 7/3 - 8 = 27,
+      B = 27 * 12 / sqrt(3) = 108 sqrt(3), and the bound is
+      d_min^0 B / ((c - 1) b T) = 108 sqrt(3) / 6 = 18 sqrt(3).
+    * K_{2,4}, alpha = 1/4, k = 1, T = 2, b = 1: D^-a A D^-a is
+      (2*4)^(-1/4) times the all-ones biadjacency block, eigenvalues
+      +-(2*4)^(1/2 - 1/4) = +-8^(1/4) and 0, so the tail is 8^(1/4); degrees 4
+      (twice) and 2 (four times), vol = 16, d_min^(-1+2a) = 2^(-1/2),
+      c = 6 (4/2)^(1/2) = 6 sqrt(2), c^2 = 72.  The bound is
+      2^(-1/2) 8^(1/4) (71 (1 + 6/(6 sqrt(2) - 1)) - 12) 16 / ((6 sqrt(2) - 1) 2)
+      = 147.32...
+    A dropped (c - 1), a wrong power of c or of d_min, or a missing vol moves
+    either value."""
+    deg = np.full(4, 3.0)
+    ev = np.array([1.0, 1 / 3, 1 / 3, 1 / 3])
+    assert math.isclose(o.theorem1_bound(ev, 1, deg, 12.0, 4, 0.5, 2, 1.0), 18 * math.sqrt(3),
+                        rel_tol=1e-12)
+    deg = np.array([4.0, 4.0, 2.0, 2.0, 2.0, 2.0])
+    ev = np.array([8 ** 0.25, 8 ** 0.25, 0, 0, 0, 0])
+    r2 = math.sqrt(2.0)
+    want = 2 ** -0.5 * 8 ** 0.25 * (71 * (1 + 6 / (6 * r2 - 1)) - 12) * 16 / ((6 * r2 - 1) * 2)
+    assert math.isclose(want, 147.32, rel_tol=1e-4)
+    assert math.isclose(o.theorem1_bound(ev, 1, deg, 16.0, 6, 0.25, 2, 1.0), want, rel_tol=1e-12)
+    # the spectra used above are those of the graphs
+    for g, alpha, spec in ((synth.complete_graph(4), 0.5, [1.0, -1 / 3, -1 / 3, -1 / 3]),
+                           (synth.complete_bipartite_union([(2, 4)]), 0.25,
+                            [8 ** 0.25, -(8 ** 0.25), 0, 0, 0, 0])):
+        A = o.adjacency(g.row_ptr, g.col_idx, g.n)
+        X = o.normalized_operator(A, alpha).toarray()
+        assert np.allclose(np.sort(np.linalg.eigvalsh(X)), np.sort(spec), atol=1e-12)
+
+
 def test_embedding_dominant_subspace_matches_dense_svd():
     # the four block directions of trunc_log(L'R') are separated from the rest
     # by a wide gap; the single-pass sketch recovers them (randomized, so loose
