@@ -84,7 +84,7 @@ struct Bump {
 
 struct Bufs {
   Ctrl *ctrl;
-  float *deg, *dpow, *wnz, *rsc, *rsc_lo, *wgt;
+  float *deg, *dpow, *wnz, *rsc, *rsc_lo, *wgt, *wgt_lo;
   float *A, *B, *C;  // tall buffers
   float *partial;
   double *m64[5];
@@ -124,6 +124,7 @@ size_t carve(const Dims &D, int mode, void *base, Bufs *b) {
   x.rsc = bp.take<float>(n);
   x.rsc_lo = bp.take<float>(n);
   x.wgt = bp.take<float>(n);
+  x.wgt_lo = bp.take<float>(n);
   x.A = bp.take<float>((size_t)n * D.Wab);
   x.B = bp.take<float>((size_t)n * D.Wab);
   if (mode != SNE_WS_SKETCH) x.C = bp.take<float>((size_t)n * D.K);
@@ -313,7 +314,8 @@ inline unsigned grid_for(int64_t work, int per = 256, int cap = 0) {
 int orth_tall(const Dims &D, const Bufs &b, int method, bool fp64, const float *Y, int64_t ldy, int w,
               float *Q, int64_t ldq, cudaStream_t st, bool accurate_gram = false) {
   if (accurate_gram)
-    CK(launch_gram_accurate(Y, ldy, w, Y, ldy, w, D.n, nullptr, true, b.partial, b.m64[0], w, st));
+    CK(launch_gram_accurate(Y, ldy, w, Y, ldy, w, D.n, nullptr, nullptr, true, b.partial, b.m64[0], w,
+                            st));
   else
     CK(launch_gram(Y, ldy, w, Y, ldy, w, D.n, nullptr, true, b.partial, b.m64[0], w, st, b.ctrl));
   if (method == SNE_ORTH_EIGSVD) {
@@ -388,14 +390,17 @@ int run_sketch(const sne_csr &g, const sne_params &p, const Dims &D, const Bufs 
   const int k = D.k, h = D.h, l = D.l, z = D.z;
   const float sv = 1.0f / sqrtf((float)z);
   // --- Eq. 11 factors
-  CK(launch_degree_power(b.deg, D.n, -1.0 + 2.0 * p.alpha, b.wgt, 1.0f, st));  // d^(-1+2alpha)
+  // d^(-1+2alpha) in FP64, as the FP32 pair (wgt, wgt_lo)
+  { ProfScope ps_(K_MISC, st); rowscale_kernel<<<grid_for(D.n), 256, 0, st>>>(b.deg, D.n, -1.0 + 2.0 * p.alpha, nullptr,
+                                                 1.0, b.wgt, b.wgt_lo); }
+  CK(cudaGetLastError());
   { ProfScope ps_(K_MISC, st); rowscale_kernel<<<grid_for(D.n), 256, 0, st>>>(b.deg, D.n, -1.0 + p.alpha, &b.ctrl->vol,
                                                  1.0 / (p.b * p.T), b.rsc, b.rsc_lo); }    // vol/(bT) a
   CK(cudaGetLastError());
   // G = U^T D^(-1+2 alpha) U in FP64 accuracy: most entries of L'R' lie just
   // above the trunc_log threshold, where an error in the core C shifts every
   // one of them, and the Horner sum multiplies the error of G by up to T^2/2
-  CK(launch_gram_accurate(U, k, k, U, k, k, D.n, b.wgt, true, b.partial, b.m64[0], k, st));
+  CK(launch_gram_accurate(U, k, k, U, k, k, D.n, b.wgt, b.wgt_lo, true, b.partial, b.m64[0], k, st));
   { ProfScope ps_(K_MISC, st); scale_cols_kernel<<<grid_for((int64_t)k * k), 256, 0, st>>>(b.m64[0], k, lam, b.m64[1]); }  // K
   { ProfScope ps_(K_MISC, st); eye_kernel<<<grid_for((int64_t)k * k), 256, 0, st>>>(b.m64[2], k); }                        // I
   CK(cudaGetLastError());

@@ -63,7 +63,7 @@ int sne_gram(int64_t n, int32_t ka, int32_t kb, const float *A, int64_t lda, con
   float *partial = reinterpret_cast<float *>(static_cast<char *>(ws) + align256(sizeof(Ctrl)));
   const bool sym = A == B && ka == kb && lda == ldb;
   if (accurate)
-    return launch_gram_accurate(A, lda, ka, B, ldb, kb, n, w, sym, partial, C, ldc,
+    return launch_gram_accurate(A, lda, ka, B, ldb, kb, n, w, nullptr, sym, partial, C, ldc,
                                 (cudaStream_t)stream) == cudaSuccess
                ? SNE_OK
                : SNE_ERR_CUDA;

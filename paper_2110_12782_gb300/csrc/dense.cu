@@ -184,19 +184,27 @@ cudaError_t launch_gram_reduce(const float *partial, int Ka, int Kb, int chunks,
 // ---------------------------------------------------------------------------
 constexpr int kDThreads = 128;
 
+// (hi, lo) += x with the rounding error of hi + x carried into lo (TwoSum;
+// the _rn intrinsics keep the compiler from contracting or reordering it)
 __device__ __forceinline__ void two_sum_into(float &hi, float &lo, float x) {
-  const float s = hi + x;
-  const float bp = s - hi;
-  const float ap = s - bp;
-  lo += (hi - ap) + (x - bp);
+  const float s = __fadd_rn(hi, x);
+  const float bp = __fsub_rn(s, hi);
+  const float ap = __fsub_rn(s, bp);
+  lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, ap), __fsub_rn(x, bp)));
   hi = s;
 }
 
+// With weights (WEIGHTED), row i of A is scaled by w_i = w_hi[i] + w_lo[i] (an
+// FP32 pair carrying the weight to FP64 accuracy): the scaled entry is kept as
+// the pair (fl(w_hi a), fma(w_hi, a, -fl(w_hi a)) + w_lo a), whose second part
+// enters the products' error terms.
+template <bool WEIGHTED>
 __global__ void __launch_bounds__(kDThreads) gram_df_partial_kernel(
     const float *__restrict__ A, int64_t lda, int32_t Ka, const float *__restrict__ B, int64_t ldb,
-    int32_t Kb, int64_t n, const float *__restrict__ w, int symmetric, int32_t tiles_a,
-    int64_t rows_per_chunk, double *__restrict__ partial) {
+    int32_t Kb, int64_t n, const float *__restrict__ w, const float *__restrict__ w_lo,
+    int symmetric, int32_t tiles_a, int64_t rows_per_chunk, double *__restrict__ partial) {
   __shared__ __align__(16) float As[kGR][kGT];
+  __shared__ __align__(16) float Al[WEIGHTED ? kGR : 1][kGT];
   __shared__ __align__(16) float Bs[kGR][kGT];
   int ta, tb;
   int t = blockIdx.x;
@@ -228,6 +236,7 @@ __global__ void __launch_bounds__(kDThreads) gram_df_partial_kernel(
   const bool vec = (lda % 4 == 0) && (ldb % 4 == 0) && ((uintptr_t)A % 16 == 0) &&
                    ((uintptr_t)B % 16 == 0);
   float4 pre[8];
+  float2 wpre[4];  // (w_hi, w_lo) of the A rows this thread fetches
   auto fetch = [&](int64_t rs) {
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
@@ -248,14 +257,9 @@ __global__ void __launch_bounds__(kDThreads) gram_df_partial_kernel(
           if (cbase + 2 < K) v.z = src[cbase + 2];
           if (cbase + 3 < K) v.w = src[cbase + 3];
         }
-        if (isA && w) {
-          const float wr = w[row];
-          v.x *= wr;
-          v.y *= wr;
-          v.z *= wr;
-          v.w *= wr;
-        }
       }
+      if (WEIGHTED && isA)
+        wpre[m] = row < r1 ? make_float2(w[row], w_lo ? w_lo[row] : 0.f) : make_float2(0.f, 0.f);
       pre[m] = v;
     }
   };
@@ -265,33 +269,49 @@ __global__ void __launch_bounds__(kDThreads) gram_df_partial_kernel(
     for (int m = 0; m < 8; ++m) {
       const int q = tid + kDThreads * m;
       const int r = (q >> 4) & 31, c = 4 * (q & 15);
-      *reinterpret_cast<float4 *>(q < 512 ? &As[r][c] : &Bs[r][c]) = pre[m];
+      if (WEIGHTED && q < 512) {
+        // w a as the pair (hi, lo), elementwise
+        const float wh = wpre[m].x, wl = wpre[m].y;
+        const float4 a = pre[m];
+        float4 h, l;
+        h.x = __fmul_rn(wh, a.x); l.x = __fmaf_rn(wl, a.x, __fmaf_rn(wh, a.x, -h.x));
+        h.y = __fmul_rn(wh, a.y); l.y = __fmaf_rn(wl, a.y, __fmaf_rn(wh, a.y, -h.y));
+        h.z = __fmul_rn(wh, a.z); l.z = __fmaf_rn(wl, a.z, __fmaf_rn(wh, a.z, -h.z));
+        h.w = __fmul_rn(wh, a.w); l.w = __fmaf_rn(wl, a.w, __fmaf_rn(wh, a.w, -h.w));
+        *reinterpret_cast<float4 *>(&As[r][c]) = h;
+        *reinterpret_cast<float4 *>(&Al[WEIGHTED ? r : 0][c]) = l;
+      } else {
+        *reinterpret_cast<float4 *>(q < 512 ? &As[r][c] : &Bs[r][c]) = pre[m];
+      }
     }
     __syncthreads();
     if (rs + kGR < r1) fetch(rs + kGR);  // in flight while this stage is summed
-#pragma unroll
-    for (int g = 0; g < kGR; g += 16) {
-      float acc[4][8];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-#pragma unroll
-      for (int r = g; r < g + 16; ++r) {
-        const float4 av = *reinterpret_cast<const float4 *>(&As[r][ty * 4]);
-        const float4 b_lo = *reinterpret_cast<const float4 *>(&Bs[r][tx * 8]);
-        const float4 b_hi = *reinterpret_cast<const float4 *>(&Bs[r][tx * 8 + 4]);
-        const float a4[4] = {av.x, av.y, av.z, av.w};
-        const float b8[8] = {b_lo.x, b_lo.y, b_lo.z, b_lo.w, b_hi.x, b_hi.y, b_hi.z, b_hi.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a4[i], b8[j], acc[i][j]);
+    // every product is split exactly into p + e (p = fl(a b), e = fma(a, b, -p))
+    // and p is added into the pair (hi, lo) by TwoSum, e into lo: no rounding
+    // of a product or of a running sum is lost, only the final rounding of
+    // lo, whose terms are about 2^-24 of the sum's
+#pragma unroll 4
+    for (int r = 0; r < kGR; ++r) {
+      const float4 av = *reinterpret_cast<const float4 *>(&As[r][ty * 4]);
+      const float4 b_lo = *reinterpret_cast<const float4 *>(&Bs[r][tx * 8]);
+      const float4 b_hi = *reinterpret_cast<const float4 *>(&Bs[r][tx * 8 + 4]);
+      const float a4[4] = {av.x, av.y, av.z, av.w};
+      const float b8[8] = {b_lo.x, b_lo.y, b_lo.z, b_lo.w, b_hi.x, b_hi.y, b_hi.z, b_hi.w};
+      float al4[4] = {0.f, 0.f, 0.f, 0.f};
+      if (WEIGHTED) {
+        const float4 alv = *reinterpret_cast<const float4 *>(&Al[WEIGHTED ? r : 0][ty * 4]);
+        al4[0] = alv.x; al4[1] = alv.y; al4[2] = alv.z; al4[3] = alv.w;
       }
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) two_sum_into(hi[i][j], lo[i][j], acc[i][j]);
+        for (int j = 0; j < 8; ++j) {
+          const float pr = __fmul_rn(a4[i], b8[j]);
+          float er = __fmaf_rn(a4[i], b8[j], -pr);
+          if (WEIGHTED) er = __fmaf_rn(al4[i], b8[j], er);
+          two_sum_into(hi[i][j], lo[i][j], pr);
+          lo[i][j] = __fadd_rn(lo[i][j], er);
+        }
     }
     __syncthreads();
   }
@@ -328,8 +348,8 @@ __global__ void gram_reduce64_kernel(const double *__restrict__ partial, int32_t
 
 cudaError_t launch_gram_accurate(const float *A, int64_t lda, int32_t Ka, const float *B,
                                  int64_t ldb, int32_t Kb, int64_t n, const float *w,
-                                 bool symmetric, float *partial, double *C, int32_t ldc,
-                                 cudaStream_t st) {
+                                 const float *w_lo, bool symmetric, float *partial, double *C,
+                                 int32_t ldc, cudaStream_t st) {
   if (symmetric && (A != B || Ka != Kb || lda != ldb)) return cudaErrorInvalidValue;
   if (n <= 0 || Ka <= 0 || Kb <= 0) return cudaErrorInvalidValue;
   int tiles, chunks;
@@ -339,8 +359,13 @@ cudaError_t launch_gram_accurate(const float *A, int64_t lda, int32_t Ka, const 
   double *p64 = reinterpret_cast<double *>(partial);
   {
     ProfScope ps_(K_GRAM, st, 2);
-    gram_df_partial_kernel<<<dim3(tiles, chunks), kDThreads, 0, st>>>(
-        A, lda, Ka, B, ldb, Kb, n, w, symmetric ? 1 : 0, ceil_div(Ka, kGT), rpc, p64);
+    if (w)
+      gram_df_partial_kernel<true><<<dim3(tiles, chunks), kDThreads, 0, st>>>(
+          A, lda, Ka, B, ldb, Kb, n, w, w_lo, symmetric ? 1 : 0, ceil_div(Ka, kGT), rpc, p64);
+    else
+      gram_df_partial_kernel<false><<<dim3(tiles, chunks), kDThreads, 0, st>>>(
+          A, lda, Ka, B, ldb, Kb, n, nullptr, nullptr, symmetric ? 1 : 0, ceil_div(Ka, kGT), rpc,
+          p64);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int64_t total = (int64_t)Ka * Kb;

@@ -349,15 +349,17 @@ cudaError_t launch_spmm_hot_threshold(const float *dpow, int64_t n, int64_t row_
   return cudaGetLastError();
 }
 
-// Column-block width of the SpMM for operands beyond L2 (16; SNE_SPMM_CB=8 or
-// 0 selects 8 columns or the row-at-once kernel, for measurements).
+// Column-block width of the SpMM for operands beyond L2: 0 (the row-at-once
+// kernel) unless SNE_SPMM_CB=16 or 8 selects the column-blocked kernel, which
+// measured slower (CTA dispatch of one CTA per 8 rows and column block).
 constexpr double kSpmmBlockFromBytes = 256.0 * 1024 * 1024;
 static int spmm_col_block() {
   static int cb = -1;
   if (cb < 0) {
     const char *v = getenv("SNE_SPMM_CB");
-    cb = 16;
-    if (v && (v[0] == '0' || v[0] == '8') && v[1] == 0) cb = v[0] - '0';
+    cb = 0;
+    if (v && v[0] == '8' && v[1] == 0) cb = 8;
+    if (v && v[0] == '1' && v[1] == '6' && v[2] == 0) cb = 16;
   }
   return cb;
 }
