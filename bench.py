@@ -206,6 +206,31 @@ def oracle_sample_rate(g, p, U_k: np.ndarray, lam: np.ndarray, budget_s: float) 
     return {"value": done * v / spent, "rows": done, "seconds": spent, "v": v}
 
 
+def sketch_error_vs_oracle(sk, g, G, p, U, lam, Uh, lh, op, precisions, rows=1024) -> dict:
+    """Relative Frobenius error of Y = trunc_log(L'R'(:, p)) S (Eq. 4) on a
+    seeded sample of rows against the FP64 oracle, for each reconstruction
+    precision, from the same eigenpairs (this run's freigs), so that the
+    comparison isolates the sketch arithmetic."""
+    import torch
+    from oracle import sketchne_oracle as o
+    sel = np.sort(np.random.default_rng(1).choice(g.n, size=min(rows, g.n), replace=False))
+    A = o.adjacency(g.row_ptr, g.col_idx, g.n)
+    fac = o.netmf_factors(Uh, lh, o.degrees(A), o.volume(A), op.alpha, op.T, op.b)
+    S = o.gen_sparse_sign(g.n, op.h, op.zeta, op.seed, o.STREAM_S)
+    ref = o.sketch_Y_rows(fac.Lp[sel], fac.Rp, S)
+    out = {"rows": int(len(sel)), "seed": 1, "metric": "relative Frobenius error of Y rows"}
+    for prec in precisions:
+        q = sk.sne_params_init(p.d, p.k, q=p.q, T=p.T, precision=sk.PRECISIONS[prec], orth=p.orth)
+        wss = sk.workspace(g.n, g.nnz, q, sk.SNE_WS_SKETCH)
+        Y = torch.empty(g.n, q.h, dtype=torch.float32, device="cuda")
+        sk.sne_sketch_from_factors(G, q, U, lam, wss, Y=Y)
+        sk.check_status(wss, f"sketch {prec}")
+        got = Y[torch.as_tensor(sel, device="cuda")].cpu().double().numpy()
+        out[prec] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        del wss, Y
+    return out
+
+
 def cpu_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -450,17 +475,23 @@ def run_ours(args, rank: int, world: int) -> None:
                 "ms_per_step": ms}
 
     cpu = None
+    accuracy = None
     if rank == 0 and not args.no_cpu_baseline:
         U = torch.empty(g.n, p.k, dtype=torch.float32, device="cuda")
         lam = torch.empty(p.k, dtype=torch.float64, device="cuda")
         ws_f = sk.workspace(g.n, g.nnz, p, sk.SNE_WS_FREIGS)
         sk.sne_freigs(G, p, ws_f, U, lam)
+        sk.check_status(ws_f, "freigs")
+        del ws_f
         from oracle import sketchne_oracle as o
         op = o.Params(k=p.k, d=p.d, q=p.q, T=p.T, h=p.h, l=p.l).resolved()
-        r = oracle_sample_rate(g, op, U.cpu().double().numpy(), lam.cpu().numpy(), args.cpu_seconds)
+        Uh, lh = U.cpu().double().numpy(), lam.cpu().numpy()
+        r = oracle_sample_rate(g, op, Uh, lh, args.cpu_seconds)
         cpu = {"value": r["value"], "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                "sample": f"Eq. 4 (trunc_log(L'R'(:,p))S, FP64) on {r['rows']} random rows, "
                          f"{r['seconds']:.1f} s, factors from this run's freigs"}
+        accuracy = sketch_error_vs_oracle(sk, g, G, p, U, lam, Uh, lh, op,
+                                          ["fp32"] + ([] if args.no_mixed else [args.mixed_precision]))
 
     if rank == 0:
         line = {
@@ -478,6 +509,7 @@ def run_ours(args, rank: int, world: int) -> None:
             "gpu_launches": int(launches),
             "roofline": roofline,
             "mixed": mixed,
+            "error_vs_oracle": accuracy,
             "cpu_baseline": cpu,
             "clocks": clk,
             "kernel_ms_per_step": {k: v[2] / args.steps for k, v in sorted(prof.items(), key=lambda kv: -kv[1][2])},

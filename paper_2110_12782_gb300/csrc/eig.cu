@@ -22,6 +22,7 @@
 // Jacobi on each cluster's block of X^T A X.
 #include <cfloat>
 #include <cmath>
+#include <cstdlib>
 
 #include "sne_internal.cuh"
 
@@ -663,6 +664,222 @@ __global__ void __launch_bounds__(1024) chol_inv_blocked_kernel(const T *__restr
     for (int j = lane; j < n; j += 32) Rinv[(int64_t)i * ldi + j] = j >= i ? at(i, j) : T(0);
 }
 
+// ---------------------------------------------------------------------------
+// FP32 Cholesky and inverse in 32 x 32 blocks (n <= 288), one CTA, for the
+// orthonormalizations inside the power iteration of Alg. 5 (Q = Y R^-1 with
+// Y^T Y = R^T R).  The upper triangle is held as nb (nb + 1) / 2 blocks of
+// 32 x 33 floats (the padding keeps column walks free of bank conflicts);
+// rows and columns past n are those of the identity, so the factor of the
+// padded matrix is diag(R, I).
+//   factor, panel p: one warp factors block (p, p) (column per lane); warp w
+//   solves R_pp^T R_pq = A_pq for q = p + 1 + w (column per lane); all warps
+//   update the trailing blocks A_qr -= R_pq^T R_pr with 4 x 4 register tiles;
+//   three barriers per panel.
+//   inverse, block column j: T_i = sum_{m=i}^{j-1} X_im R_mj for i < j (X = R^-1,
+//   columns < j already done) while one warp inverts R_jj, then
+//   X_ij = -T_i X_jj; two barriers per block column.
+// A non-positive or non-finite pivot records SNE_ERR_NUMERIC and is replaced
+// by 1.
+// ---------------------------------------------------------------------------
+constexpr int kQB = 32;
+constexpr int kQLd = 33;
+constexpr int kQMaxNb = 9;
+
+__device__ __forceinline__ int qblk(int nb, int bi, int bj) {  // bi <= bj
+  return bi * nb - bi * (bi - 1) / 2 + (bj - bi);
+}
+
+size_t chol_quick_smem(int n) {
+  const int nb = (n + kQB - 1) / kQB;
+  return ((size_t)nb * (nb + 1) / 2 * kQB * kQLd + (size_t)nb * kQB * kQB) * sizeof(float);
+}
+
+__global__ void __launch_bounds__(1024) chol_inv_quick_kernel(const float *__restrict__ A, int n,
+                                                              int lda, float *__restrict__ Rinv,
+                                                              int ldi, Ctrl *ctrl) {
+  extern __shared__ __align__(16) float qsm[];
+  const int nb = (n + kQB - 1) / kQB;
+  float *blk = qsm;                                              // triangle of blocks
+  float *tmp = qsm + (size_t)nb * (nb + 1) / 2 * kQB * kQLd;     // nb blocks of 32 x 32
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  auto B = [&](int bi, int bj) { return blk + (size_t)qblk(nb, bi, bj) * kQB * kQLd; };
+  // ---- load (upper triangle; identity past n)
+  for (int bi = 0; bi < nb; ++bi)
+    for (int bj = bi; bj < nb; ++bj) {
+      float *b = B(bi, bj);
+      for (int e = tid; e < kQB * kQB; e += blockDim.x) {
+        const int r = e >> 5, c = e & 31;
+        const int i = bi * kQB + r, j = bj * kQB + c;
+        float v = 0.f;
+        if (i < n && j < n) v = (i <= j) ? A[(int64_t)i * lda + j] : 0.f;
+        else if (i == j) v = 1.f;
+        b[r * kQLd + c] = v;
+      }
+    }
+  __syncthreads();
+  // ---- factorization
+  for (int p = 0; p < nb; ++p) {
+    float *bpp = B(p, p);
+    if (warp == 0) {
+      // lane c owns column c of the diagonal block
+      for (int j = 0; j < kQB; ++j) {
+        float djj = bpp[j * kQLd + j];
+        if (!(djj > 0.f) || !isfinite(djj)) {
+          if (lane == 0) record_error(ctrl, SNE_ERR_NUMERIC, W_CHOL);
+          djj = 1.f;
+        }
+        const float d = sqrtf(djj);
+        __syncwarp();
+        if (lane == j) bpp[j * kQLd + j] = d;
+        else if (lane > j) bpp[j * kQLd + lane] /= d;
+        __syncwarp();
+        const float rjc = bpp[j * kQLd + lane];
+        for (int r = j + 1; r <= lane; ++r) bpp[r * kQLd + lane] -= bpp[j * kQLd + r] * rjc;
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    // R_pq = R_pp^-T A_pq, q > p: warp per block, lane per column (forward substitution)
+    for (int q = p + 1 + warp; q < nb; q += nw) {
+      float *bpq = B(p, q);
+      for (int r = 0; r < kQB; ++r) {
+        float x = bpq[r * kQLd + lane];
+        for (int m = 0; m < r; ++m) x -= bpp[m * kQLd + r] * bpq[m * kQLd + lane];
+        bpq[r * kQLd + lane] = x / bpp[r * kQLd + r];
+      }
+    }
+    __syncthreads();
+    // trailing update A_qr -= R_pq^T R_pr, p < q <= r, in 4 x 4 tiles
+    {
+      const int nrem = nb - p - 1;
+      const int nblocks = nrem * (nrem + 1) / 2;
+      for (int task = tid; task < nblocks * 64; task += blockDim.x) {
+        const int bl = task >> 6, t = task & 63;
+        // decode block bl -> (q, r), q <= r, among the remaining blocks
+        int q = 0, rem = bl, len = nrem;
+        while (rem >= len) {
+          rem -= len;
+          ++q;
+          --len;
+        }
+        const int qq = p + 1 + q, rr = qq + rem;
+        const int a0 = 4 * (t >> 3), b0 = 4 * (t & 7);
+        const float *rq = B(p, qq), *rr_ = B(p, rr);
+        float acc[4][4] = {};
+#pragma unroll 4
+        for (int m = 0; m < kQB; ++m) {
+          float av[4], bv[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            av[u] = rq[m * kQLd + a0 + u];
+            bv[u] = rr_[m * kQLd + b0 + u];
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+        }
+        float *dst = B(qq, rr);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) dst[(a0 + u) * kQLd + b0 + v] -= acc[u][v];
+      }
+    }
+    __syncthreads();
+  }
+  // ---- inverse X = R^-1, block column by block column
+  for (int j = 0; j < nb; ++j) {
+    float *xjj = tmp + (size_t)j * kQB * kQB;  // X_jj, row-major 32 x 32
+    if (warp == nw - 1) {
+      // lane c: column c of R_jj^-1 by back substitution (rows c .. 0)
+      const float *bjj = B(j, j);
+      for (int r = kQB - 1; r >= 0; --r) {
+        float x = 0.f;
+        if (r == lane) {
+          x = 1.f / bjj[r * kQLd + r];
+        } else if (r < lane) {
+          for (int m = r + 1; m <= lane; ++m) x -= bjj[r * kQLd + m] * xjj[m * kQB + lane];
+          x /= bjj[r * kQLd + r];
+        }
+        xjj[r * kQB + lane] = x;
+        __syncwarp();
+      }
+    }
+    // T_i = sum_{m=i}^{j-1} X_im R_mj for i < j (into tmp block i), 4 x 4 tiles
+    const int tw = (nw - 1) * 32;  // the other warps
+    if (tid < tw) {
+      for (int task = tid; task < j * 64; task += tw) {
+        const int i = task >> 6, t = task & 63;
+        const int a0 = 4 * (t >> 3), b0 = 4 * (t & 7);
+        float acc[4][4] = {};
+        for (int m = i; m < j; ++m) {
+          const float *xim = B(i, m), *rmj = B(m, j);
+#pragma unroll 4
+          for (int kk = 0; kk < kQB; ++kk) {
+            float av[4], bv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              av[u] = xim[(a0 + u) * kQLd + kk];
+              bv[u] = rmj[kk * kQLd + b0 + u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+          }
+        }
+        float *ti = tmp + (size_t)i * kQB * kQB;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) ti[(a0 + u) * kQB + b0 + v] = acc[u][v];
+      }
+    }
+    __syncthreads();
+    // X_ij = -T_i X_jj (i < j), X_jj into block (j, j)
+    for (int task = tid; task < (j + 1) * 64; task += blockDim.x) {
+      const int i = task >> 6, t = task & 63;
+      const int a0 = 4 * (t >> 3), b0 = 4 * (t & 7);
+      float *dst = B(i, j);
+      if (i == j) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) dst[(a0 + u) * kQLd + b0 + v] = xjj[(a0 + u) * kQB + b0 + v];
+        continue;
+      }
+      const float *ti = tmp + (size_t)i * kQB * kQB;
+      float acc[4][4] = {};
+#pragma unroll 4
+      for (int kk = 0; kk < kQB; ++kk) {
+        float av[4], bv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          av[u] = ti[(a0 + u) * kQB + kk];
+          bv[u] = xjj[kk * kQB + b0 + u];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) dst[(a0 + u) * kQLd + b0 + v] = -acc[u][v];
+    }
+    __syncthreads();
+  }
+  // ---- write R^-1 (upper triangular, zeros below)
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    const int i = e / n, j = e % n;
+    float v = 0.f;
+    if (j >= i) v = B(i / kQB, j / kQB)[(i % kQB) * kQLd + (j % kQB)];
+    Rinv[(int64_t)i * ldi + j] = v;
+  }
+}
+
 template <typename T>
 size_t chol_blocked_smem(int n) {
   return ((size_t)n * (n + 1) / 2 + n + (size_t)kCB * kCB + (size_t)n * kCB) * sizeof(T);
@@ -674,11 +891,32 @@ size_t chol_inv_smem(int n, bool packed) {
          (size_t)n * sizeof(int);
 }
 
+// The blocked FP32 kernel above, unless SNE_CHOL_QUICK=0 (for comparisons).
+static bool chol_quick_enabled() {
+  static int on = -1;
+  if (on < 0) {
+    const char *v = getenv("SNE_CHOL_QUICK");
+    on = (v && v[0] == '0') ? 0 : 1;
+  }
+  return on == 1;
+}
+
 template <typename T>
 cudaError_t launch_chol_inverse(const T *A, int32_t n, int32_t lda, T *Rinv, int32_t ldi, T *scratch,
                                 Ctrl *ctrl, cudaStream_t st, double tol) {
   if (n <= 0) return cudaSuccess;
   if (n > 1024) return cudaErrorInvalidValue;
+  if (sizeof(T) == 4 && tol < 0.0 && n <= kQB * kQMaxNb && chol_quick_smem(n) <= 226 * 1024 &&
+      chol_quick_enabled()) {
+    const size_t smem = chol_quick_smem(n);
+    cudaError_t e = cudaFuncSetAttribute(chol_inv_quick_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    ProfScope ps_(K_CHOL, st);
+    chol_inv_quick_kernel<<<1, 1024, smem, st>>>(reinterpret_cast<const float *>(A), n, lda,
+                                                 reinterpret_cast<float *>(Rinv), ldi, ctrl);
+    return cudaGetLastError();
+  }
   if (tol < 0.0 && chol_blocked_smem<T>(n) <= 220 * 1024) {
     const size_t smem = chol_blocked_smem<T>(n);
     cudaError_t e = cudaFuncSetAttribute(chol_inv_blocked_kernel<T>,

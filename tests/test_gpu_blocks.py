@@ -256,7 +256,9 @@ def test_chol_inverse(sk, n, dtype, pivot):
     Mh = M.cpu().numpy().astype(np.float64)
     err = np.abs(Mh.T @ A @ Mh - np.eye(n)).max()
     if not pivot:
+        # upper triangular with a positive diagonal and M^T A M = I: M = R^-1
         assert np.allclose(np.tril(Mh, -1), 0)
+        assert np.all(np.diag(Mh) > 0)
     tol = 2e-3 if dtype == torch.float32 else 1e-10
     print(f"chol inverse n={n} {dtype} pivot={pivot}: |M^T A M - I| {err:.1e}")
     assert err < tol

@@ -125,7 +125,11 @@ def test_embedding_matches_oracle(run):
     singular values within 1e-3 on the leading block of singular directions
     separated by a relative gap of at least 1e-2 (only such a block is
     determined, Davis-Kahan), for FP32 and FP16 pairs.  The single-FP16 path
-    is reported."""
+    (one product of 11-bit operands): singular values within its Y bound 5e-3
+    (a singular value moves by at most the norm of the perturbation of the
+    sketched matrix) and the top singular direction, separated from the next
+    by a relative gap of 0.28, within a sine of 1e-2; the directions of the
+    rest of the block, whose gaps are near 1e-2, are reported."""
     ref = run["ref"]
     sp = ref.sp
     G = sp.O.rows_at_p().T @ sp.Q[sp.O.p]
@@ -150,3 +154,6 @@ def test_embedding_matches_oracle(run):
         if prec in TOL_EMBED:
             assert srel.max() < TOL_EMBED[prec], prec
             assert sines[blk] < TOL_EMBED[prec], prec
+        else:
+            assert srel.max() < TOL_SKETCH[prec], prec
+            assert sines[1] < 1e-2, prec
