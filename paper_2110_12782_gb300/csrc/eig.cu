@@ -958,12 +958,32 @@ size_t eig_scratch_bytes(int n) {
          3 * n2 * sizeof(double) + 1024;
 }
 
-cudaError_t launch_sym_eig_fast(float *A, int32_t n, int32_t lda, float *w, float *V, int32_t ldv,
-                                void *scratch, Ctrl *ctrl, cudaStream_t st) {
-  char *base = static_cast<char *>(scratch);
+// The FP32 eigensolver: Householder tridiagonalization, bisection and
+// inverse iteration (tridiag.cu) for n >= 32, cyclic Jacobi for smaller n or
+// when SNE_EIG_JACOBI=1 (for comparisons).  The scratch region of the Jacobi
+// rotations holds the tridiagonal solver's arrays.
+static bool eig_use_tridiag(int n) {
+  static int jac = -1;
+  if (jac < 0) {
+    const char *v = getenv("SNE_EIG_JACOBI");
+    jac = (v && v[0] == '1') ? 1 : 0;
+  }
+  return jac == 0 && n >= 32 && tri_eig_smem(n) <= 227 * 1024 &&
+         tri_eig_scratch_floats(n) * sizeof(float) <= jacobi_rot_capacity(n) * sizeof(Rot);
+}
+
+static cudaError_t eig_f32(const float *A, int32_t n, int32_t lda, float *w, float *V, int32_t ldv,
+                           char *base, Ctrl *ctrl, cudaStream_t st) {
   int *nrounds = reinterpret_cast<int *>(base);
   void *rot = base + 256;
+  if (eig_use_tridiag(n))
+    return launch_sym_eig_tridiag(A, n, lda, w, V, ldv, static_cast<float *>(rot), ctrl, st);
   return launch_jacobi_f32(A, n, lda, w, V, ldv, rot, nrounds, ctrl, st);
+}
+
+cudaError_t launch_sym_eig_fast(float *A, int32_t n, int32_t lda, float *w, float *V, int32_t ldv,
+                                void *scratch, Ctrl *ctrl, cudaStream_t st) {
+  return eig_f32(A, n, lda, w, V, ldv, static_cast<char *>(scratch), ctrl, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -1112,7 +1132,7 @@ cudaError_t launch_sym_eig_fast(double *A, int32_t n, int32_t lda, double *w, do
   if (ldv != n) return cudaErrorInvalidValue;
   cudaError_t e = launch_d2f(A, n, n, lda, A32, n, st);
   if (e != cudaSuccess) return e;
-  e = launch_jacobi_f32(A32, n, n, w32, V32, n, rot, nrounds, ctrl, st);
+  e = eig_f32(A32, n, n, w32, V32, n, base, ctrl, st);
   if (e != cudaSuccess) return e;
   // X = V (FP64), A copied compact into T3's neighbour: use T3 for S
   e = launch_f2d(V32, n, n, n, V, ldv, st);

@@ -181,6 +181,13 @@ cudaError_t launch_sym_eig_fast(float *A, int32_t n, int32_t lda, float *w, floa
 cudaError_t launch_sym_eig_fast(double *A, int32_t n, int32_t lda, double *w, double *V,
                                 int32_t ldv, void *scratch, Ctrl *ctrl, cudaStream_t st);
 constexpr int kFastEigMaxN = 320;
+// tridiag.cu: FP32 symmetric eigendecomposition (Householder tridiagonalization,
+// bisection, inverse iteration); w unordered, column j of V the eigenvector of
+// w[j]; scratch: tri_eig_scratch_floats(n) floats.
+size_t tri_eig_scratch_floats(int n);
+size_t tri_eig_smem(int n);  // shared memory of the tridiagonalization
+cudaError_t launch_sym_eig_tridiag(const float *A, int32_t n, int32_t lda, float *w, float *V,
+                                   int32_t ldv, float *scratch, Ctrl *ctrl, cudaStream_t st);
 
 // M = R^-1 where A = R^T R (Cholesky); scratch: n*n + 2n + 8 T (used only for
 // n too large for shared memory).  tol >= 0 selects diagonal pivoting with a rank
