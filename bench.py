@@ -52,6 +52,16 @@ WORKLOADS = {
                          "kernel captures)"),
     "sbm4096": dict(kind="sbm", n=4096, d=32, k=128, T=10, q=20,
                     label="SBM n=4096 8 blocks p_in=0.01 p_out=0.001, T=10 b=1 k=128 d=32 zeta=8"),
+    "cl10m": dict(kind="chung_lu_device", n=10_000_000, avg=30.0, gamma=2.2, d=128, k=256, T=10,
+                  q=20, precision="bf16",
+                  label="Chung-Lu n=10M avg-degree 30 gamma 2.2 (drawn on the GPU), T=10 b=1 k=256 "
+                        "d=128 zeta=8 h=2d+16 l=d+1000 q=20 alpha=0.5; BF16 reconstruction with "
+                        "FP32 accumulation, FP64 Rayleigh-Ritz/QR/SVD"),
+    "cl50m": dict(kind="chung_lu_device", n=50_000_000, avg=40.0, gamma=2.1, d=128, k=128, T=10,
+                  q=20, precision="fp16",
+                  label="Chung-Lu n=50M avg-degree 40 gamma 2.1 (drawn on the GPU), T=10 b=1 k=128 "
+                        "d=128 zeta=8 h=2d+16 l=d+1000 q=20 alpha=0.5; FP16 reconstruction with "
+                        "FP32 accumulation"),
     "batch64": dict(kind="batch", count=64, d=64, k=64, T=10, q=20,
                     label="64 graphs, n ~ U[2000, 200000], mean degree ~ U[8, 32], even: 8-block "
                           "SBM p_in/p_out = 10, odd: Chung-Lu gamma 2.1, graph g seeded g; "
@@ -59,8 +69,28 @@ WORKLOADS = {
 }
 
 
+class DeviceDrawnGraph:
+    """A graph drawn on the GPU (synth.chung_lu_device): the device CSR, and
+    the host arrays on demand."""
+
+    def __init__(self, n, row_ptr, col_idx):
+        self.n, self.row_ptr_dev, self.col_idx_dev = n, row_ptr, col_idx
+        self.nnz = int(col_idx.numel())
+
+    @property
+    def row_ptr(self):
+        return self.row_ptr_dev.cpu().numpy()
+
+    @property
+    def col_idx(self):
+        return self.col_idx_dev.cpu().numpy()
+
+
 def make_graph(w):
     from paper_2110_12782_gb300 import synth
+    if w["kind"] == "chung_lu_device":
+        rp, ci = synth.chung_lu_device(w["n"], w["avg"], w["gamma"], seed=0)
+        return DeviceDrawnGraph(w["n"], rp, ci)
     if w["kind"] == "batch":
         # the reference arm samples the largest graph of the batch
         return max(synth.batched_mix(w["count"]), key=lambda g: g.n)
@@ -493,6 +523,20 @@ def run_ours(args, rank: int, world: int) -> None:
         accuracy = sketch_error_vs_oracle(sk, g, G, p, U, lam, Uh, lh, op,
                                           ["fp32"] + ([] if args.no_mixed else [args.mixed_precision]))
 
+    # ---- the other workloads of the configuration list, fewer steps each
+    extra = None
+    if not args.no_extra and args.workload == "cl1m":
+        del ws, E, sig, flush
+        torch.cuda.empty_cache()
+        ek, ew = min(args.steps, 3), max(3, min(args.warmup, 3))
+        extra = {}
+        extra["cl10m"] = measure_single(args, "cl10m", ek, ew) if rank == 0 or world > 1 else None
+        bline = measure_batch(args, rank, world, "batch64", "fp16", ek, ew)
+        if bline is not None:
+            extra["batch64"] = {k: bline[k] for k in ("value", "ms_per_step", "steps", "warmup",
+                                                       "config", "e2e", "gpu_launches",
+                                                       "kernel_ms_per_step_summed_over_lanes")
+                                if k in bline}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -510,6 +554,7 @@ def run_ours(args, rank: int, world: int) -> None:
             "roofline": roofline,
             "mixed": mixed,
             "error_vs_oracle": accuracy,
+            "workloads": extra,
             "cpu_baseline": cpu,
             "clocks": clk,
             "kernel_ms_per_step": {k: v[2] / args.steps for k, v in sorted(prof.items(), key=lambda kv: -kv[1][2])},
@@ -517,7 +562,120 @@ def run_ours(args, rank: int, world: int) -> None:
         print(json.dumps(line), flush=True)
 
 
+def measure_single(args, workload: str, steps: int, warmup: int) -> dict:
+    """One graph of a large workload at its configured (mixed) precision and
+    at plain FP32, steps embeddings each after `warmup` untimed ones (L2
+    flushed between steps); with the CPU-baseline leg on, the error of Y on a
+    seeded sample of 100,000 rows against the FP64 oracle from this run's
+    eigenpairs."""
+    import torch
+
+    from paper_2110_12782_gb300 import sketchne as sk
+    w = WORKLOADS[workload]
+    t0 = time.perf_counter()
+    g = make_graph(w)
+    gen_s = time.perf_counter() - t0
+    if isinstance(g, DeviceDrawnGraph):
+        G = sk.DeviceGraph(g.row_ptr_dev, g.col_idx_dev)
+    else:
+        G = sk.DeviceGraph.from_numpy(g.row_ptr, g.col_idx)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = {"workload": w["label"], "n": g.n, "nnz": g.nnz, "steps": steps, "warmup": warmup,
+           "graph_generation_s": gen_s, "l2": "flushed between steps (256 MB write)"}
+    sigmas = {}
+    for prec in (w["precision"], "fp32"):
+        p = sk.sne_params_init(w["d"], w["k"], q=w["q"], T=w["T"], precision=sk.PRECISIONS[prec],
+                               orth=sk.SNE_ORTH_CHOLQR)
+        ws = sk.workspace(g.n, g.nnz, p, sk.SNE_WS_EMBED)
+        E = torch.empty(g.n, p.d, dtype=torch.float32, device="cuda")
+        sig = torch.empty(p.d, dtype=torch.float64, device="cuda")
+        for _ in range(warmup):
+            sk.sne_embed(G, p, ws, E, sig)
+        sk.check_status(ws, f"{workload} {prec}")
+        st = sk.sne_stats_read(ws)
+        entries = g.n * st.v_s + st.v_o * st.v_o
+        times = []
+        for _ in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            sk.sne_embed(G, p, ws, E, sig)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        sk.check_status(ws, f"{workload} {prec} timed")
+        sk.sne_profile_start()
+        flush.zero_()
+        torch.cuda.synchronize()
+        sk.sne_embed(G, p, ws, E, sig)
+        prof = sk.sne_profile_stop()
+        ms = float(np.mean(times))
+        out[prec] = {"ms_per_step": ms, "value": entries / (ms / 1e3), "unit": UNIT,
+                     "entries_per_step": entries,
+                     "kernel_ms_per_step": {k: v[2] for k, v in sorted(prof.items(), key=lambda kv: -kv[1][2])}}
+        sigmas[prec] = sig.cpu().numpy()
+        del ws, E, sig
+        torch.cuda.empty_cache()
+    out["sigma_rel_diff_vs_fp32"] = float(np.max(np.abs(sigmas[w["precision"]] - sigmas["fp32"]) /
+                                                 np.abs(sigmas["fp32"])))
+    if not args.no_cpu_baseline:
+        out["error_vs_oracle"] = large_sample_error(sk, g, G, w, [w["precision"], "fp32"])
+    del G, g, flush
+    torch.cuda.empty_cache()
+    return out
+
+
+def large_sample_error(sk, g, G, w, precisions, rows=100_000) -> dict:
+    """Part of the CPU-baseline leg: Y = trunc_log(L'R'(:, p)) S on a seeded
+    sample of rows, FP64 oracle (factors of Eq. 11 for the sampled rows and
+    the columns p only, the Gram of U summed in row chunks) against the
+    library at each precision, from the same eigenpairs."""
+    import torch
+    from oracle import sketchne_oracle as o
+    p = sk.sne_params_init(w["d"], w["k"], q=w["q"], T=w["T"], orth=sk.SNE_ORTH_CHOLQR)
+    ws = sk.workspace(g.n, g.nnz, p, sk.SNE_WS_FREIGS)
+    U = torch.empty(g.n, p.k, dtype=torch.float32, device="cuda")
+    lam = torch.empty(p.k, dtype=torch.float64, device="cuda")
+    sk.sne_freigs(G, p, ws, U, lam)
+    sk.check_status(ws, "freigs")
+    del ws
+    t0 = time.perf_counter()
+    Uh, lh = U.cpu().numpy(), lam.cpu().numpy()
+    deg = np.diff(g.row_ptr).astype(np.float64)
+    sel = np.sort(np.random.default_rng(1).choice(g.n, size=min(rows, g.n), replace=False))
+    S = o.gen_sparse_sign(g.n, p.h, p.zeta, p.seed, o.STREAM_S)
+    Lr, Rc = o.netmf_factor_rows(Uh, lh, deg, float(deg.sum()), p.alpha, p.T, p.b, sel, S.p)
+    ref = o.sketch_Y_rows_at(Lr, Rc, S)
+    out = {"rows": int(len(sel)), "seed": 1, "metric": "relative Frobenius error of Y rows",
+           "oracle_s": time.perf_counter() - t0}
+    del Uh
+    for prec in precisions:
+        q = sk.sne_params_init(w["d"], w["k"], q=w["q"], T=w["T"], precision=sk.PRECISIONS[prec],
+                               orth=sk.SNE_ORTH_CHOLQR)
+        wss = sk.workspace(g.n, g.nnz, q, sk.SNE_WS_SKETCH)
+        Y = torch.empty(g.n, q.h, dtype=torch.float32, device="cuda")
+        sk.sne_sketch_from_factors(G, q, U, lam, wss, Y=Y)
+        sk.check_status(wss, f"sketch {prec}")
+        got = Y[torch.as_tensor(sel, device="cuda")].cpu().double().numpy()
+        out[prec] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        del wss, Y
+        torch.cuda.empty_cache()
+    del U, lam
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours_batch(args, rank: int, world: int) -> None:
+    """The many-graphs workload as the main line."""
+    line = measure_batch(args, rank, world, args.workload, args.precision, args.steps, args.warmup)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def measure_batch(args, rank: int, world: int, workload: str, precision: str, steps: int,
+                  warmup: int) -> dict:
     """The many-graphs workload: every step embeds the whole batch with one
     sne_embed_batched call, replayed from a CUDA graph."""
     import torch
@@ -529,10 +687,10 @@ def run_ours_batch(args, rank: int, world: int) -> None:
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     build.build()
-    w = WORKLOADS[args.workload]
+    w = WORKLOADS[workload]
     graphs = synth.batched_mix(w["count"])
     orth = {"eigsvd": sk.SNE_ORTH_EIGSVD, "cholqr": sk.SNE_ORTH_CHOLQR}[args.orth]
-    prec = sk.PRECISIONS[args.precision]
+    prec = sk.PRECISIONS[precision]
     p = sk.sne_params_init(w["d"], w["k"], q=w["q"], T=w["T"], precision=prec, orth=orth)
     dev = [sk.DeviceGraph.from_numpy(g.row_ptr, g.col_idx) for g in graphs]
     E = [torch.empty(g.n, p.d, dtype=torch.float32, device="cuda") for g in graphs]
@@ -553,7 +711,7 @@ def run_ours_batch(args, rank: int, world: int) -> None:
     cg = torch.cuda.CUDAGraph()
     with torch.cuda.graph(cg):
         sk.sne_embed_batched(dev, p, ws, E, sig, status=status)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         cg.replay()
     torch.cuda.synchronize()
     if int(status.abs().sum()) != 0:
@@ -567,7 +725,7 @@ def run_ours_batch(args, rank: int, world: int) -> None:
     clocks = ClockSampler(local)
     times = []
     launches0 = sk.sne_kernel_launches()
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.zero_()
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -582,12 +740,12 @@ def run_ours_batch(args, rank: int, world: int) -> None:
     l0 = sk.sne_kernel_launches()
     sk.sne_embed_batched(dev, p, ws, E, sig, status=status)
     torch.cuda.synchronize()
-    launches = (sk.sne_kernel_launches() - l0) * args.steps
+    launches = (sk.sne_kernel_launches() - l0) * steps
     total_ms = max_over_ranks(float(sum(times)), world)
-    value = job_value(entries, world, args.steps, total_ms)
+    value = job_value(entries, world, steps, total_ms)
     # per-class times (eager batched calls; lanes overlap, so shares are of summed kernel time)
     sk.sne_profile_start()
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.zero_()
         torch.cuda.synchronize()
         sk.sne_embed_batched(dev, p, ws, E, sig, status=status)
@@ -602,7 +760,7 @@ def run_ours_batch(args, rank: int, world: int) -> None:
     h_E = [torch.empty(g.n, p.d, dtype=torch.float32).pin_memory() for g in graphs]
     h_s = [torch.empty(p.d, dtype=torch.float64).pin_memory() for g in graphs]
     e2e_t = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.zero_()
         barrier()
         t0 = time.perf_counter()
@@ -619,21 +777,22 @@ def run_ours_batch(args, rank: int, world: int) -> None:
     peaks, peak_kind = measured_peaks()
     dom = max(prof.items(), key=lambda kv: kv[1][2])[0] if prof else None
     prof_total = sum(v[2] for v in prof.values())
+    line = None
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": warmup, "ms_per_step": total_ms / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if prec == sk.SNE_FP32 else args.precision, "data": "synthetic",
+            "dtype": "f32" if prec == sk.SNE_FP32 else precision, "data": "synthetic",
             "config": {"workload": w["label"], "graphs": len(graphs),
                        "sum_n": int(sum(g.n for g in graphs)),
                        "sum_nnz": int(sum(g.nnz for g in graphs)), "entries_per_step": entries,
-                       "precision": args.precision, "orth": args.orth, "cuda_graph": True,
+                       "precision": precision, "orth": args.orth, "cuda_graph": True,
                        "l2": "flushed between steps (256 MB write)",
                        "parallelism": "replicas" if world > 1 else "single GPU, stream lanes"},
-            "e2e": {"value": job_value(entries, world, args.steps, 1e3 * e2e_total), "unit": UNIT,
+            "e2e": {"value": job_value(entries, world, steps, 1e3 * e2e_total), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "ms_per_step": 1e3 * e2e_total / args.steps},
+                    "ms_per_step": 1e3 * e2e_total / steps},
             "gpu_launches": int(launches),
             "roofline": {"kernel": dom, "bound": None, "achieved": None, "peak": None,
                          "unit": None, "frac": None, "traffic": None,
@@ -642,10 +801,12 @@ def run_ours_batch(args, rank: int, world: int) -> None:
             "cpu_baseline": None,
             "clocks": clk,
             "kernel_ms_per_step_summed_over_lanes": {
-                k: v[2] / args.steps for k, v in sorted(prof.items(), key=lambda kv: -kv[1][2])},
+                k: v[2] / steps for k, v in sorted(prof.items(), key=lambda kv: -kv[1][2])},
             "kernel_share": {k: v[2] / prof_total for k, v in prof.items()} if prof_total else None,
         }
-        print(json.dumps(line), flush=True)
+    del ws, E, sig, dev, flush
+    torch.cuda.empty_cache()
+    return line
 
 
 def main():
@@ -670,6 +831,8 @@ def main():
                     help="run one embedding and exit (for ncu)")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the mixed-precision comparison steps")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the n=10M and 64-graph workloads measured after the main line")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

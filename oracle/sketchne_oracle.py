@@ -320,6 +320,39 @@ def netmf_factors(U: np.ndarray, lam: np.ndarray, deg: np.ndarray, vol: float,
     return Factors(Lp=Lp, Rp=Rp, K=K, Csum=Csum)
 
 
+def netmf_factor_rows(U: np.ndarray, lam: np.ndarray, deg: np.ndarray, vol: float, alpha: float,
+                      T: int, b: float, rows: np.ndarray, cols: np.ndarray,
+                      chunk: int = 1 << 20):
+    """Eq. 11 as in ``netmf_factors``, returning only the rows ``rows`` of L'
+    and the columns ``cols`` of R' (for graphs whose n x k factors do not fit
+    in host memory): K = U^T D^(-1+2a) U Lambda is summed over row chunks of
+    U, the rest is the same arithmetic on the selected rows and columns."""
+    k = len(lam)
+    a = degree_power(deg, -1.0 + alpha)
+    w = degree_power(deg, -1.0 + 2.0 * alpha)
+    G = np.zeros((k, k))
+    for r0 in range(0, U.shape[0], chunk):
+        Uc = np.asarray(U[r0:r0 + chunk], dtype=np.float64)
+        G += Uc.T @ (w[r0:r0 + chunk, None] * Uc)
+    Lam = np.diag(lam)
+    K = G @ Lam
+    Csum = np.zeros((k, k))
+    Kpow = np.eye(k)
+    for _ in range(T):
+        Csum += Kpow
+        Kpow = Kpow @ K
+    Lp_rows = (vol / (b * T)) * (a[rows, None] * np.asarray(U[rows], dtype=np.float64))
+    Rp_cols = (Lam @ Csum @ np.asarray(U[cols], dtype=np.float64).T) * a[None, cols]
+    return Lp_rows, Rp_cols
+
+
+def sketch_Y_rows_at(Lp_rows: np.ndarray, Rp_at_p: np.ndarray, S: "SparseSign", f=None):
+    """Rows of Y of Eq. 4 given the rows of L' and the columns R'(:, p) at the
+    unique coordinates p of S."""
+    f = trunc_log if f is None else f
+    return f(Lp_rows @ Rp_at_p) @ S.rows_at_p()
+
+
 # ---------------------------------------------------------------------------
 # Alg. 4: sparse-sign randomized single-pass SVD of f(L R)
 # ---------------------------------------------------------------------------

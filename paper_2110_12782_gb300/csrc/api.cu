@@ -400,7 +400,8 @@ int run_sketch(const sne_csr &g, const sne_params &p, const Dims &D, const Bufs 
   // G = U^T D^(-1+2 alpha) U in FP64 accuracy: most entries of L'R' lie just
   // above the trunc_log threshold, where an error in the core C shifts every
   // one of them, and the Horner sum multiplies the error of G by up to T^2/2
-  CK(launch_gram_accurate(U, k, k, U, k, k, D.n, b.wgt, b.wgt_lo, true, b.partial, b.m64[0], k, st));
+  CK(launch_gram_accurate(U, k, k, U, k, k, D.n, b.wgt, b.wgt_lo, true, b.partial, b.m64[0], k, st,
+                          true));
   { ProfScope ps_(K_MISC, st); scale_cols_kernel<<<grid_for((int64_t)k * k), 256, 0, st>>>(b.m64[0], k, lam, b.m64[1]); }  // K
   { ProfScope ps_(K_MISC, st); eye_kernel<<<grid_for((int64_t)k * k), 256, 0, st>>>(b.m64[2], k); }                        // I
   CK(cudaGetLastError());

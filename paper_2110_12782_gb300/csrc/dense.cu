@@ -198,7 +198,7 @@ __device__ __forceinline__ void two_sum_into(float &hi, float &lo, float x) {
 // FP32 pair carrying the weight to FP64 accuracy): the scaled entry is kept as
 // the pair (fl(w_hi a), fma(w_hi, a, -fl(w_hi a)) + w_lo a), whose second part
 // enters the products' error terms.
-template <bool WEIGHTED>
+template <bool WEIGHTED, bool EXACT>
 __global__ void __launch_bounds__(kDThreads) gram_df_partial_kernel(
     const float *__restrict__ A, int64_t lda, int32_t Ka, const float *__restrict__ B, int64_t ldb,
     int32_t Kb, int64_t n, const float *__restrict__ w, const float *__restrict__ w_lo,
@@ -286,10 +286,41 @@ __global__ void __launch_bounds__(kDThreads) gram_df_partial_kernel(
     }
     __syncthreads();
     if (rs + kGR < r1) fetch(rs + kGR);  // in flight while this stage is summed
-    // every product is split exactly into p + e (p = fl(a b), e = fma(a, b, -p))
-    // and p is added into the pair (hi, lo) by TwoSum, e into lo: no rounding
-    // of a product or of a running sum is lost, only the final rounding of
-    // lo, whose terms are about 2^-24 of the sum's
+    if (!EXACT) {
+      // FP32 FMA sums over groups of 16 rows, each group sum added into the
+      // pair (hi, lo) by TwoSum: relative error about 16 eps32 of the largest
+      // group sum
+#pragma unroll
+      for (int g = 0; g < kGR; g += 16) {
+        float acc[4][8];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+#pragma unroll
+        for (int r = g; r < g + 16; ++r) {
+          const float4 av = *reinterpret_cast<const float4 *>(&As[r][ty * 4]);
+          const float4 b_lo = *reinterpret_cast<const float4 *>(&Bs[r][tx * 8]);
+          const float4 b_hi = *reinterpret_cast<const float4 *>(&Bs[r][tx * 8 + 4]);
+          const float a4[4] = {av.x, av.y, av.z, av.w};
+          const float b8[8] = {b_lo.x, b_lo.y, b_lo.z, b_lo.w, b_hi.x, b_hi.y, b_hi.z, b_hi.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a4[i], b8[j], acc[i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) two_sum_into(hi[i][j], lo[i][j], acc[i][j]);
+      }
+      __syncthreads();
+      continue;
+    }
+    // EXACT: every product is split exactly into p + e (p = fl(a b),
+    // e = fma(a, b, -p)) and p is added into the pair (hi, lo) by TwoSum, e into
+    // lo: no rounding of a product or of a running sum is lost, only the final
+    // rounding of lo, whose terms are about 2^-24 of the sum's
 #pragma unroll 4
     for (int r = 0; r < kGR; ++r) {
       const float4 av = *reinterpret_cast<const float4 *>(&As[r][ty * 4]);
@@ -349,7 +380,7 @@ __global__ void gram_reduce64_kernel(const double *__restrict__ partial, int32_t
 cudaError_t launch_gram_accurate(const float *A, int64_t lda, int32_t Ka, const float *B,
                                  int64_t ldb, int32_t Kb, int64_t n, const float *w,
                                  const float *w_lo, bool symmetric, float *partial, double *C,
-                                 int32_t ldc, cudaStream_t st) {
+                                 int32_t ldc, cudaStream_t st, bool exact) {
   if (symmetric && (A != B || Ka != Kb || lda != ldb)) return cudaErrorInvalidValue;
   if (n <= 0 || Ka <= 0 || Kb <= 0) return cudaErrorInvalidValue;
   int tiles, chunks;
@@ -359,13 +390,14 @@ cudaError_t launch_gram_accurate(const float *A, int64_t lda, int32_t Ka, const 
   double *p64 = reinterpret_cast<double *>(partial);
   {
     ProfScope ps_(K_GRAM, st, 2);
-    if (w)
-      gram_df_partial_kernel<true><<<dim3(tiles, chunks), kDThreads, 0, st>>>(
-          A, lda, Ka, B, ldb, Kb, n, w, w_lo, symmetric ? 1 : 0, ceil_div(Ka, kGT), rpc, p64);
-    else
-      gram_df_partial_kernel<false><<<dim3(tiles, chunks), kDThreads, 0, st>>>(
-          A, lda, Ka, B, ldb, Kb, n, nullptr, nullptr, symmetric ? 1 : 0, ceil_div(Ka, kGT), rpc,
-          p64);
+#define SNE_GDF(WV, EV)                                                                      \
+  gram_df_partial_kernel<WV, EV><<<dim3(tiles, chunks), kDThreads, 0, st>>>(                  \
+      A, lda, Ka, B, ldb, Kb, n, w, w_lo, symmetric ? 1 : 0, ceil_div(Ka, kGT), rpc, p64)
+    if (w && exact) SNE_GDF(true, true);
+    else if (w) SNE_GDF(true, false);
+    else if (exact) SNE_GDF(false, true);
+    else SNE_GDF(false, false);
+#undef SNE_GDF
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int64_t total = (int64_t)Ka * Kb;

@@ -132,14 +132,16 @@ size_t gram_partial_floats(int64_t n, int32_t Ka, int32_t Kb);
 cudaError_t launch_gram(const float *A, int64_t lda, int32_t Ka, const float *B, int64_t ldb,
                         int32_t Kb, int64_t n, const float *w, bool symmetric, float *partial,
                         double *C, int32_t ldc, cudaStream_t st, Ctrl *ctrl = nullptr);
-// The same Gram with FP64 accuracy (every product split exactly and summed in
-// double-float on the FP32 pipes), for sums whose errors later steps amplify;
-// same scratch.  The weight may be given as an FP32 pair w + w_lo (w_lo NULL:
-// w exact).
+// The same Gram summed in double-float on the FP32 pipes (FP32 sums of 16
+// products added into hi/lo pairs, relative error ~1e-8), or with `exact`
+// every product split exactly and added into the pair by TwoSum (FP64
+// accuracy, about 1e-9 absolute at n = 10^6 for sums of size 1), for sums
+// whose errors later steps amplify; same scratch.  The weight may be given as
+// an FP32 pair w + w_lo (w_lo NULL: w exact).
 cudaError_t launch_gram_accurate(const float *A, int64_t lda, int32_t Ka, const float *B,
                                  int64_t ldb, int32_t Kb, int64_t n, const float *w,
                                  const float *w_lo, bool symmetric, float *partial, double *C,
-                                 int32_t ldc, cudaStream_t st);
+                                 int32_t ldc, cudaStream_t st, bool exact = false);
 // gemm_tc.cu: FP32-accurate (3 x TF32) tensor-core versions, used when
 // tc_gemm_supported(columns) and the operands are 16-byte aligned.
 bool tc_gemm_supported(int ncols);

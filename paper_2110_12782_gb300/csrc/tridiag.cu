@@ -19,8 +19,8 @@
 //     Gram-Schmidt) against the other members of their cluster: eigenvalues of
 //     one block closer than 1e-3 |T_block| (the approach of LAPACK's stein),
 //     with shifts inside a cluster kept at least 10 eps |T| apart.  A warp per
-//     cluster: lane 0 runs the sequential tridiagonal solves, the warp the
-//     dot products.
+//     cluster; its lane 0 runs the factorization, the solves, the
+//     orthogonalization and the normalization (O(size) sequential steps each).
 //  3. tri_backtransform_kernel: V = H_0 H_1 ... H_{n-3} Z, a warp per column.
 #include <cfloat>
 #include <cmath>
@@ -287,11 +287,11 @@ __global__ void __launch_bounds__(1024) tri_eig_kernel(const float *__restrict__
         u1[sz - 1] = 0.f;
         u2[sz - 1] = 0.f;
       }
-      for (int i = lane; i < sz; i += 32) x[i] = hash_unit((uint32_t)m, (uint32_t)i);
-      __syncwarp();
-      for (int iter = 0; iter < 3; ++iter) {
-        if (lane == 0) {
-          // solve L U y = P x: forward (apply the row swaps and multipliers) ...
+      // iterate, orthogonalize and normalize in lane 0 alone (O(sz) per step)
+      if (lane == 0) {
+        for (int i = 0; i < sz; ++i) x[i] = hash_unit((uint32_t)m, (uint32_t)i);
+        for (int iter = 0; iter < 3; ++iter) {
+          // solve L U y = P x: forward (the row swaps and multipliers) ...
           for (int i = 0; i < sz - 1; ++i) {
             if (piv[i] != 0.f) {
               const float t0 = x[i];
@@ -308,35 +308,25 @@ __global__ void __launch_bounds__(1024) tri_eig_kernel(const float *__restrict__
             if (i + 2 < sz) r -= u2[i] * x[i + 2];
             x[i] = r / u0[i];
           }
+          // scale, orthogonalize against the cluster's earlier vectors, normalize
+          float mx = 0.f;
+          for (int i = 0; i < sz; ++i) mx = fmaxf(mx, fabsf(x[i]));
+          const float inv = mx > 0.f ? 1.f / mx : 1.f;
+          for (int i = 0; i < sz; ++i) x[i] *= inv;
+          for (int q = m0; q < m; ++q) {
+            const float *zq = Z + (int64_t)s * ldz + q;
+            float dot = 0.f;
+            for (int i = 0; i < sz; ++i) dot += zq[(int64_t)i * ldz] * x[i];
+            for (int i = 0; i < sz; ++i) x[i] -= dot * zq[(int64_t)i * ldz];
+          }
+          float nrm = 0.f;
+          for (int i = 0; i < sz; ++i) nrm += x[i] * x[i];
+          if (!(nrm > 0.f)) record_error(ctrl, SNE_ERR_NUMERIC, W_EIG);
+          const float rn = nrm > 0.f ? 1.0f / sqrtf(nrm) : 0.f;
+          for (int i = 0; i < sz; ++i) x[i] *= rn;
         }
-        __syncwarp();
-        // scale, then orthogonalize against the cluster's earlier vectors
-        float mx = 0.f;
-        for (int i = lane; i < sz; i += 32) mx = fmaxf(mx, fabsf(x[i]));
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        const float inv = mx > 0.f ? 1.f / mx : 1.f;
-        for (int i = lane; i < sz; i += 32) x[i] *= inv;
-        __syncwarp();
-        for (int q = m0; q < m; ++q) {
-          float dot = 0.f;
-          for (int i = lane; i < sz; i += 32) dot += Z[(int64_t)(s + i) * ldz + q] * x[i];
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-          for (int i = lane; i < sz; i += 32) x[i] -= dot * Z[(int64_t)(s + i) * ldz + q];
-          __syncwarp();
-        }
-        float nrm = 0.f;
-        for (int i = lane; i < sz; i += 32) nrm += x[i] * x[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
-        const float rn = nrm > 0.f ? rsqrtf(nrm) : 0.f;
-        if (!(nrm > 0.f) && lane == 0) record_error(ctrl, SNE_ERR_NUMERIC, W_EIG);
-        for (int i = lane; i < sz; i += 32) x[i] *= rn;
-        __syncwarp();
+        for (int i = 0; i < n; ++i) Z[(int64_t)i * ldz + m] = (i >= s && i <= t) ? x[i - s] : 0.f;
       }
-      for (int i = lane; i < n; i += 32)
-        Z[(int64_t)i * ldz + m] = (i >= s && i <= t) ? x[i - s] : 0.f;
       __syncwarp();
     }
   }

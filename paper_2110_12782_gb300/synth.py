@@ -151,18 +151,9 @@ def sbm(n: int, blocks: int, p_in: float, p_out: float, seed: int = 0) -> Graph:
 def chung_lu(n: int, avg_degree: float, gamma: float, seed: int = 0, i0: float = 1.0,
              chunk: int = 1 << 24) -> Graph:
     rng = np.random.Generator(np.random.PCG64(seed))
-    base = (np.arange(n, dtype=np.float64) + i0) ** (-1.0 / (gamma - 1.0))
     target = n * avg_degree
-    # scale so that sum(min(s * base, sqrt(sum))) = n * avg_degree (the cap keeps p_ij <= 1)
-    cap = np.sqrt(target)
-    lo_s, hi_s = 0.0, target / base.sum() * 1e3
-    for _ in range(100):
-        mid = 0.5 * (lo_s + hi_s)
-        if np.minimum(base * mid, cap).sum() < target:
-            lo_s = mid
-        else:
-            hi_s = mid
-    w = np.minimum(base * hi_s, cap)
+    # scaled so that sum(min(s * base, sqrt(sum))) = n * avg_degree (the cap keeps p_ij <= 1)
+    w = chung_lu_weights(n, avg_degree, gamma, i0)
     cdf = np.cumsum(w / w.sum())
     cdf[-1] = 1.0
     want = int(round(target / 2.0))  # distinct undirected edges
@@ -180,6 +171,70 @@ def chung_lu(n: int, avg_degree: float, gamma: float, seed: int = 0, i0: float =
         key = np.unique(np.concatenate([key, *parts]))
         draw = int((want - key.size) * 1.3) + 1024
     return _csr_from_unique_keys(n, key, name=f"chung_lu(n={n},avg={avg_degree},gamma={gamma},seed={seed})")
+
+
+def chung_lu_weights(n: int, avg_degree: float, gamma: float, i0: float = 1.0) -> np.ndarray:
+    """The vertex weights of ``chung_lu`` (power law, capped at sqrt(n avg))."""
+    base = (np.arange(n, dtype=np.float64) + i0) ** (-1.0 / (gamma - 1.0))
+    target = n * avg_degree
+    cap = np.sqrt(target)
+    lo_s, hi_s = 0.0, target / base.sum() * 1e3
+    for _ in range(100):
+        mid = 0.5 * (lo_s + hi_s)
+        if np.minimum(base * mid, cap).sum() < target:
+            lo_s = mid
+        else:
+            hi_s = mid
+    return np.minimum(base * hi_s, cap)
+
+
+def chung_lu_device(n: int, avg_degree: float, gamma: float, seed: int = 0, device="cuda",
+                    chunk: int = 1 << 27):
+    """The Chung-Lu recipe of ``chung_lu`` drawn on a GPU with torch's
+    generator (seeded; a different stream of random numbers than the NumPy
+    version, so a different graph from the same distribution), for graphs
+    whose NumPy generation would take many minutes (n = 5 * 10^7, about
+    2 * 10^9 stored entries).  Returns (row_ptr int64 [n+1], col_idx int32
+    [nnz]) as device tensors, columns sorted within each row."""
+    import torch
+    w = torch.as_tensor(chung_lu_weights(n, avg_degree, gamma), dtype=torch.float64, device=device)
+    cdf = torch.cumsum(w / w.sum(), 0)
+    cdf[-1] = 1.0
+    del w
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    want = int(round(n * avg_degree / 2.0))
+    key = torch.zeros(0, dtype=torch.int64, device=device)
+    draw = want
+    while key.numel() < want:
+        parts = [key]
+        for c0 in range(0, draw, chunk):
+            c = min(chunk, draw - c0)
+            a = torch.searchsorted(cdf, torch.rand(c, generator=gen, device=device, dtype=torch.float64),
+                                   right=True).clamp_(max=n - 1)
+            b = torch.searchsorted(cdf, torch.rand(c, generator=gen, device=device, dtype=torch.float64),
+                                   right=True).clamp_(max=n - 1)
+            keep = a != b
+            a, b = a[keep], b[keep]
+            parts.append(torch.minimum(a, b) * n + torch.maximum(a, b))
+            del a, b, keep
+        key = torch.unique(torch.cat(parts))
+        del parts
+        draw = int((want - key.numel()) * 1.3) + 1024
+    lo = key // n
+    hi = key - lo * n
+    del key
+    both = torch.cat([lo * n + hi, hi * n + lo])
+    del lo, hi
+    both, _ = torch.sort(both)
+    src = both // n
+    col = (both - src * n).to(torch.int32)
+    del both
+    counts = torch.bincount(src, minlength=n)
+    del src
+    row_ptr = torch.zeros(n + 1, dtype=torch.int64, device=device)
+    torch.cumsum(counts, 0, out=row_ptr[1:])
+    return row_ptr, col
 
 
 def batched_mix(count: int = 64, n_lo: int = 2000, n_hi: int = 200000, deg_lo: float = 8.0,

@@ -433,3 +433,23 @@ def test_lemire_rejection_leaves_exactly_one_preimage(monkeypatch):
                     assert val == v
                     accepted += 1
             assert accepted == 1, (n, v, lo_x, hi_x)
+
+
+def test_factor_rows_equal_full_factors():
+    """netmf_factor_rows (chunked Gram, selected rows and columns) is the same
+    arithmetic as netmf_factors; with chunks smaller than n it agrees to
+    rounding on the selected rows and columns, and sketch_Y_rows_at gives the
+    same rows of Y as sketch_Y."""
+    g = synth.sbm(600, 3, 0.05, 0.005, seed=9)
+    A = o.adjacency(g.row_ptr, g.col_idx, g.n)
+    deg = o.degrees(A)
+    X = o.normalized_operator(A, 0.4)
+    U, lam = o.freigs(X, 24, q=6, s=8, seed=2)
+    fac = o.netmf_factors(U, lam, deg, o.volume(A), 0.4, 10, 1.0)
+    S = o.gen_sparse_sign(g.n, 40, 8, 0, o.STREAM_S)
+    rows = np.array([0, 7, 123, 599])
+    Lr, Rc = o.netmf_factor_rows(U, lam, deg, o.volume(A), 0.4, 10, 1.0, rows, S.p, chunk=97)
+    assert np.allclose(Lr, fac.Lp[rows], rtol=1e-12, atol=0)
+    assert np.allclose(Rc, fac.Rp[:, S.p], rtol=1e-10, atol=1e-14 * np.abs(fac.Rp).max())
+    Y = o.sketch_Y(fac.Lp, fac.Rp, S)
+    assert np.allclose(o.sketch_Y_rows_at(Lr, Rc, S), Y[rows], rtol=1e-10, atol=1e-12)

@@ -3,6 +3,7 @@ only inputs the oracle and the CUDA path share, so their structure is pinned
 here: symmetric CSR without self-loops or repeats, SBM block densities within
 binomial bounds, the Chung-Lu power-law tail and degree order, the batch mix."""
 import numpy as np
+import pytest
 
 from paper_2110_12782_gb300 import synth
 
@@ -71,3 +72,26 @@ def test_closed_form_graphs():
     check_csr(u)
     assert u.n == 10 and u.nnz == 2 * (2 * 3 + 1 * 4)
     assert list(u.degrees()) == [3, 3, 2, 2, 2, 4, 1, 1, 1, 1]
+
+
+def test_chung_lu_device_recipe_on_cpu():
+    """The torch form of the Chung-Lu recipe (run here on the CPU): a
+    symmetric CSR without self-loops or repeated edges, at least the target
+    number of edges, and the same expected-degree order as the NumPy form."""
+    torch = pytest.importorskip("torch")
+    n, avg = 50_000, 20.0
+    rp, ci = synth.chung_lu_device(n, avg, 2.1, seed=3, device="cpu")
+    rp, ci = rp.numpy(), ci.numpy().astype(np.int64)
+    nnz = int(rp[-1])
+    assert rp[0] == 0 and np.all(np.diff(rp) >= 0) and len(ci) == nnz
+    assert nnz >= n * avg and nnz < 1.02 * n * avg
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    assert np.all(rows != ci)
+    key = rows * n + ci
+    assert np.all(np.diff(key) > 0)                      # sorted, no repeats
+    assert np.array_equal(np.sort(ci * n + rows), key)  # symmetric
+    deg = np.diff(rp)
+    ref = synth.chung_lu(n, avg, 2.1, seed=3).degrees()
+    # same weights: the hubs are the low ids in both, with matching mean degrees
+    assert abs(deg[:100].mean() / ref[:100].mean() - 1.0) < 0.1
+    assert deg.argmax() < 50  # the largest weights are capped alike
