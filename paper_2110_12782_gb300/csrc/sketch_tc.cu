@@ -30,6 +30,8 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
 
 #include "sne_internal.cuh"
 #include "tc_ptx.cuh"
@@ -45,7 +47,8 @@ __global__ void __launch_bounds__(tc::kThreadsSketch, 1) fused_sketch_tc_kernel(
     int64_t nrows_max, const int32_t *__restrict__ nrows_dev, int kblocks, int stages,
     int ncols_eval, int cols_out, const float *__restrict__ rowf,
     const float2 *__restrict__ rowdat, const float4 *__restrict__ coldat, float out_scale,
-    uint32_t idesc, float *__restrict__ out, int64_t ldo, Ctrl *ctrl) {
+    uint32_t idesc, float *__restrict__ out, int64_t ldo, Ctrl *ctrl, int stall,
+    uint64_t wait_ns) {
   using namespace tc;
   constexpr int NPART = SPLIT ? 2 : 1;
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
@@ -108,44 +111,46 @@ __global__ void __launch_bounds__(tc::kThreadsSketch, 1) fused_sketch_tc_kernel(
                       (int)row0);
       }
       int it = 0;
-      int issued = 0;
+      int last_it = -1;  // the ring index of the last copy issued
       bool ok = true;
       for (int j = blockIdx.y; j < ntiles && ok; j += gridDim.y) {
         for (int q = 0; q < steps; ++q, ++it) {
           const int kb = q / NPART, part = q % NPART;
           const int s = it % stages;
           const uint32_t ph = (uint32_t)((it / stages) & 1);
-          if (!mbar_wait(&empty[s], ph ^ 1u, abortv, ctrl)) {
+          if (!mbar_wait(&empty[s], ph ^ 1u, abortv, ctrl, wait_ns)) {
             ok = false;
             break;
           }
+          // fault injection (tests only): the first stage is never loaded,
+          // so the MMA warp's wait on it runs out
+          if (stall && it == 0) continue;
           mbar_expect_tx(&full[s], (uint32_t)kBStageBytes);
           tma_load_2d(sB + (size_t)s * kBStageBytes, part ? &tmB2 : &tmB, &full[s], kb * BK, j * BN);
-          ++issued;
+          last_it = it;
         }
       }
       if (!ok) {
-        // let the copies already issued land before the CTA exits
-        (void)mbar_wait(a_full, 0, abortv, ctrl);
-        const int first = issued > stages ? issued - stages : 0;
-        for (int q = first; q < issued; ++q) {
-          const uint64_t t0 = gtimer();
-          while (!mbar_try_wait(&full[q % stages], (uint32_t)((q / stages) & 1)) &&
-                 gtimer() - t0 < kTimeoutNs) {
-          }
+        // let the copies already issued land before the CTA exits (the
+        // last `stages` of them; the others completed before their stage
+        // was reused)
+        mbar_drain(a_full, 0, wait_ns);
+        for (int q = (last_it - stages + 1 > 0 ? last_it - stages + 1 : 0); q <= last_it; ++q) {
+          if (stall && q == 0) continue;
+          mbar_drain(&full[q % stages], (uint32_t)((q / stages) & 1), wait_ns);
         }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer
-      bool ok = mbar_wait(a_full, 0, abortv, ctrl);
+      bool ok = mbar_wait(a_full, 0, abortv, ctrl, wait_ns);
       int it = 0;
       int jj = 0;  // local tile count (accumulator buffer and phase)
       for (int j = blockIdx.y; j < ntiles && ok; j += gridDim.y, ++jj) {
         const int buf = jj & 1;
         const uint32_t use = (uint32_t)(jj >> 1);
-        if (!mbar_wait(&tempty[buf], (use & 1u) ^ 1u, abortv, ctrl)) {
+        if (!mbar_wait(&tempty[buf], (use & 1u) ^ 1u, abortv, ctrl, wait_ns)) {
           ok = false;
           break;
         }
@@ -154,7 +159,7 @@ __global__ void __launch_bounds__(tc::kThreadsSketch, 1) fused_sketch_tc_kernel(
         for (int q = 0; q < steps; ++q, ++it) {
           const int kb = q / NPART, part = q % NPART;
           const int s = it % stages;
-          if (!mbar_wait(&full[s], (uint32_t)((it / stages) & 1), abortv, ctrl)) {
+          if (!mbar_wait(&full[s], (uint32_t)((it / stages) & 1), abortv, ctrl, wait_ns)) {
             ok = false;
             break;
           }
@@ -185,9 +190,7 @@ __global__ void __launch_bounds__(tc::kThreadsSketch, 1) fused_sketch_tc_kernel(
       }
       // wait for every MMA issued by this thread before TMEM is released
       mma_commit(done);
-      const uint64_t t0 = gtimer();
-      while (!mbar_try_wait(done, 0) && gtimer() - t0 < kTimeoutNs) {
-      }
+      mbar_drain(done, 0, wait_ns);
     }
   } else {
     // ---------------- epilogue warps 2..17: warp w reads TMEM lane quarter
@@ -203,7 +206,7 @@ __global__ void __launch_bounds__(tc::kThreadsSketch, 1) fused_sketch_tc_kernel(
     for (int j = blockIdx.y; j < ntiles; j += gridDim.y, ++jj) {
       const int buf = jj & 1;
       const uint32_t use = (uint32_t)(jj >> 1);
-      if (!mbar_wait(&tfull[buf], use & 1u, abortv, ctrl)) break;
+      if (!mbar_wait(&tfull[buf], use & 1u, abortv, ctrl, wait_ns)) break;
       fence_after();
       const int ebase = j * BN + quarter * 64;
       float v[2][32];
@@ -337,6 +340,17 @@ cudaError_t launch_fused_sketch_tc(bool fp16, bool split, const void *Ahi, const
   const dim3 grid(grid_x, splits);
   const int kblocks = kpad / tc::BK;
   const float out_scale = sv;
+  // SNE_FAULT_INJECT=tc_stall (tests of the failure path only): the kernel
+  // leaves one shared-memory stage unloaded, and every bounded wait runs out
+  // after 20 ms instead of 2 s
+  int stall = 0;
+  uint64_t wait_ns = tc::kTimeoutNs;
+  if (const char *fi = getenv("SNE_FAULT_INJECT")) {
+    if (std::strcmp(fi, "tc_stall") == 0) {
+      stall = 1;
+      wait_ns = 20000000ull;
+    }
+  }
 #define SNE_TC_LAUNCH(FV, ZV, SV)                                                                 \
   do {                                                                                            \
     auto kern = fused_sketch_tc_kernel<FV, ZV, SV>;                                               \
@@ -347,7 +361,7 @@ cudaError_t launch_fused_sketch_tc(bool fp16, bool split, const void *Ahi, const
     kern<<<grid, tc::kThreadsSketch, smem, st>>>(tmA, tmA2, tmB, tmB2, nrows_max, nrows_dev,      \
                                                  kblocks, stages, ncols_eval, cols_out, rowf,     \
                                                  rowdat, coldat, out_scale, idesc, out, ldo,      \
-                                                 ctrl);                                           \
+                                                 ctrl, stall, wait_ns);                           \
   } while (0)
 #define SNE_TC_Z(FV, SV)                        \
   switch (z) {                                  \

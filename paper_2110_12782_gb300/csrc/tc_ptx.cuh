@@ -75,19 +75,27 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait; false on timeout or when another role aborted.
+// Bounded wait; false on timeout (after limit_ns of %globaltimer) or when
+// another role aborted.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
-                                          Ctrl *ctrl) {
+                                          Ctrl *ctrl, uint64_t limit_ns = kTimeoutNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = gtimer();
   for (;;) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort_flag) return false;
-    if (gtimer() - t0 > kTimeoutNs) {
+    if (gtimer() - t0 > limit_ns) {
       *abort_flag = 1;
       record_error(ctrl, SNE_ERR_TIMEOUT, W_TC);
       return false;
     }
+  }
+}
+// Bounded wait that ignores the abort flag: for a CTA that is about to exit
+// and must let its own copies and MMAs land first.
+__device__ __forceinline__ void mbar_drain(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+  const uint64_t t0 = gtimer();
+  while (!mbar_try_wait(bar, parity) && gtimer() - t0 < limit_ns) {
   }
 }
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, uint64_t *bar, int x,

@@ -156,7 +156,9 @@ __device__ __forceinline__ float hash_unit(uint32_t a, uint32_t b) {
   return (float)(z >> 40) * (2.0f / 16777216.0f) - 1.0f;  // [-1, 1)
 }
 
-// scratch per warp: 6 arrays of n floats (LU factors and the iterate)
+// Inverse iteration runs on the first kIIWarps warps; each keeps its LU
+// factors and iterate (6 arrays of n floats) in dynamic shared memory.
+constexpr int kIIWarps = 16;
 __global__ void __launch_bounds__(1024) tri_eig_kernel(const float *__restrict__ dg,
                                                        const float *__restrict__ eg, int n,
                                                        float *__restrict__ w,
@@ -245,10 +247,12 @@ __global__ void __launch_bounds__(1024) tri_eig_kernel(const float *__restrict__
   }
   __syncthreads();
   const int nc = nclu_s;
-  float *ws = scratch + (size_t)warp * 6 * n;
+  extern __shared__ float iism[];
+  float *ws = iism + (size_t)warp * 6 * n;
   float *u0 = ws, *u1 = ws + n, *u2 = ws + 2 * n, *lm = ws + 3 * n, *x = ws + 4 * n, *piv = ws + 5 * n;
+  (void)scratch;
   const float pertol = 10.0f * FLT_EPSILON * tnorm;
-  for (int c = warp; c < nc; c += nw) {
+  for (int c = warp; c < nc && warp < kIIWarps; c += kIIWarps) {
     const int m0 = cstart[c], m1 = cstart[c + 1];
     const int b = blk_of[m0];
     const int s = bstart[b], t = bstart[b + 1] - 1, sz = t - s + 1;
@@ -287,10 +291,13 @@ __global__ void __launch_bounds__(1024) tri_eig_kernel(const float *__restrict__
         u1[sz - 1] = 0.f;
         u2[sz - 1] = 0.f;
       }
-      // iterate, orthogonalize and normalize in lane 0 alone (O(sz) per step)
-      if (lane == 0) {
-        for (int i = 0; i < sz; ++i) x[i] = hash_unit((uint32_t)m, (uint32_t)i);
-        for (int iter = 0; iter < 3; ++iter) {
+      // lane 0 solves; the lanes scale, orthogonalize and normalize the
+      // iterate in shared memory, each on the rows i = lane, lane + 32, ...
+      // (also the rows of Z it wrote itself for the earlier members)
+      for (int i = lane; i < sz; i += 32) x[i] = hash_unit((uint32_t)m, (uint32_t)i);
+      __syncwarp();
+      for (int iter = 0; iter < 3; ++iter) {
+        if (lane == 0) {
           // solve L U y = P x: forward (the row swaps and multipliers) ...
           for (int i = 0; i < sz - 1; ++i) {
             if (piv[i] != 0.f) {
@@ -308,25 +315,34 @@ __global__ void __launch_bounds__(1024) tri_eig_kernel(const float *__restrict__
             if (i + 2 < sz) r -= u2[i] * x[i + 2];
             x[i] = r / u0[i];
           }
-          // scale, orthogonalize against the cluster's earlier vectors, normalize
-          float mx = 0.f;
-          for (int i = 0; i < sz; ++i) mx = fmaxf(mx, fabsf(x[i]));
-          const float inv = mx > 0.f ? 1.f / mx : 1.f;
-          for (int i = 0; i < sz; ++i) x[i] *= inv;
-          for (int q = m0; q < m; ++q) {
-            const float *zq = Z + (int64_t)s * ldz + q;
-            float dot = 0.f;
-            for (int i = 0; i < sz; ++i) dot += zq[(int64_t)i * ldz] * x[i];
-            for (int i = 0; i < sz; ++i) x[i] -= dot * zq[(int64_t)i * ldz];
-          }
-          float nrm = 0.f;
-          for (int i = 0; i < sz; ++i) nrm += x[i] * x[i];
-          if (!(nrm > 0.f)) record_error(ctrl, SNE_ERR_NUMERIC, W_EIG);
-          const float rn = nrm > 0.f ? 1.0f / sqrtf(nrm) : 0.f;
-          for (int i = 0; i < sz; ++i) x[i] *= rn;
         }
-        for (int i = 0; i < n; ++i) Z[(int64_t)i * ldz + m] = (i >= s && i <= t) ? x[i - s] : 0.f;
+        __syncwarp();
+        float mx = 0.f;
+        for (int i = lane; i < sz; i += 32) mx = fmaxf(mx, fabsf(x[i]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const float inv = mx > 0.f ? 1.f / mx : 1.f;
+        for (int i = lane; i < sz; i += 32) x[i] *= inv;
+        for (int q = m0; q < m; ++q) {
+          float dot = 0.f;
+          for (int i = lane; i < sz; i += 32) dot += Z[(int64_t)(s + i) * ldz + q] * x[i];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+          for (int i = lane; i < sz; i += 32) x[i] -= dot * Z[(int64_t)(s + i) * ldz + q];
+        }
+        float nrm = 0.f;
+        for (int i = lane; i < sz; i += 32) nrm += x[i] * x[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+        if (!(nrm > 0.f) && lane == 0) record_error(ctrl, SNE_ERR_NUMERIC, W_EIG);
+        const float rn = nrm > 0.f ? 1.0f / sqrtf(nrm) : 0.f;
+        for (int i = lane; i < sz; i += 32) x[i] *= rn;
+        __syncwarp();
       }
+      // column m of Z: rows s + i written by the lane that owns i
+      for (int i = lane; i < sz; i += 32) Z[(int64_t)(s + i) * ldz + m] = x[i];
+      for (int i = lane; i < n; i += 32)
+        if (i < s || i > t) Z[(int64_t)i * ldz + m] = 0.f;
       __syncwarp();
     }
   }
@@ -404,9 +420,12 @@ cudaError_t launch_sym_eig_tridiag(const float *A, int32_t n, int32_t lda, float
   }
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
+  const size_t iism = (size_t)kIIWarps * 6 * n * sizeof(float);
+  err = cudaFuncSetAttribute(tri_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)iism);
+  if (err != cudaSuccess) return err;
   {
     ProfScope ps_(K_EIG, st);
-    tri_eig_kernel<<<1, 1024, 0, st>>>(d, e, n, w, Z, n, wsc, ctrl);
+    tri_eig_kernel<<<1, 1024, iism, st>>>(d, e, n, w, Z, n, wsc, ctrl);
   }
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
