@@ -2,25 +2,24 @@
 //   TALL  C[i, :] = A[i, :] M            (A n x K row-major, M K x Kc; the
 //                                          operand B is M^T, K-major)
 //   GRAM  P[c]    = sum_{i in chunk c} w_i A[i, :]^T B[i, :]
-//                                        (both operands MN-major, read straight
-//                                          from the row-major tall matrices)
+//                                        (the row-major tall matrices arrive
+//                                          as 32 x 32 boxes and are transposed
+//                                          into K-major tiles in shared memory)
 // used for the eigSVD / Cholesky-QR orthonormalizations and the Rayleigh-Ritz
 // product of Alg. 5, the sketch QR of Alg. 4 and E = Q U_hat.
 //
 // Each operand x is split in shared memory into hi = rna_tf32(x) and
 // lo = x - hi (exact), and the accumulator takes A_hi B_hi + A_hi B_lo +
 // A_lo B_hi, so the product carries about 2^-21 relative error per term
-// (the FP32 result up to the dropped A_lo B_lo term).  The split is done
-// elementwise on the swizzled tiles by the four epilogue warps between the TMA
-// load and the MMA of every stage.
+// (the FP32 result up to the dropped A_lo B_lo term).  Four split warps do
+// this between the TMA load and the MMA of every stage.
 //
-// The tall product uses gemm_tf32x3_kernel<false>; the Gram uses
-// gram_tf32x3_kernel below, which transposes its tiles in shared memory.
-//
-// One CTA computes a 128-row output tile over all Npad <= 288 output columns
-// (TMEM holds the 128 x Npad FP32 accumulator; the columns are issued as MMAs
-// of N = 256 and N = Npad - 256).  Warp 0: TMA; warp 1: TMEM and MMA issue;
-// warps 2-5: operand split, then the epilogue (tcgen05.ld, store).
+// TALL: a persistent CTA per SM walks 128-row output tiles over all
+// Npad <= 288 output columns (TMEM holds the 128 x Npad FP32 accumulator; the
+// columns are issued as MMAs of N = 256 and N = Npad - 256).  Warp 0: TMA;
+// warp 1: TMEM and MMA issue; warps 2-5: operand split; warps 6-9: epilogue
+// (tcgen05.ld, store).
+#include <cuda.h>
 #include <cuda.h>
 
 #include "sne_internal.cuh"
@@ -29,52 +28,50 @@
 namespace sne {
 
 namespace gt {
-constexpr int BM = 128;        // output rows per CTA (MMA M)
+constexpr int BM = 128;        // output rows per tile (MMA M)
 constexpr int BK = 32;         // FP32 elements per k-block (128 bytes)
-constexpr int kMaxN = 288;     // padded output columns per CTA
-constexpr int kThreads = 192;
+constexpr int kMaxN = 288;     // padded output columns
+constexpr int kStages = 2;
+constexpr int kThreads = 320;  // TMA, MMA, 4 split warps, 4 epilogue warps
 constexpr int kABytes = BM * BK * 4;  // 16 KB
 }  // namespace gt
 
-template <bool MN>
-__global__ void __launch_bounds__(gt::kThreads, 1) gemm_tf32x3_kernel(
+// Persistent: CTA b takes the row tiles b, b + gridDim.x, ...  The stage ring
+// and its barrier phases run on across tiles, so the loads and splits of tile
+// t + 1 overlap the epilogue of tile t; only the MMA waits for the epilogue
+// warps to have read the accumulator out of TMEM (accfree).
+__global__ void __launch_bounds__(gt::kThreads, 1) tall_tf32x3_kernel(
     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-    const __grid_constant__ CUtensorMap tmB2, int npad,
-    int nkb, int64_t rows_per_chunk, int64_t nrows_total, const float *__restrict__ w, int mrows,
-    int ncols, float *__restrict__ out, int64_t ldo, int64_t chunk_stride, Ctrl *ctrl) {
+    const __grid_constant__ CUtensorMap tmB2, int npad, int nkb, int64_t ntiles, int64_t nrows,
+    int ncols, float *__restrict__ out, int64_t ldo, int vec4, Ctrl *ctrl) {
   using namespace tc;
   extern __shared__ __align__(1024) unsigned char g_smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(g_smem_raw) + 1023) & ~(uintptr_t)1023);
   const int bbytes = npad * gt::BK * 4;                       // B region of a stage
   const int stage_bytes = 2 * gt::kABytes + 2 * bbytes;        // hi + lo of A and B
-  const int stages = 2;
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)stages * stage_bytes);
-  uint64_t *full = bars;            // [stages] TMA landed
-  uint64_t *split = full + stages;  // [stages] hi/lo ready for the MMA
-  uint64_t *empty = split + stages; // [stages] MMA done with the stage
-  uint64_t *done = empty + stages;  // accumulator complete
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)gt::kStages * stage_bytes);
+  uint64_t *full = bars;                  // [stages] TMA landed
+  uint64_t *split = full + gt::kStages;   // [stages] hi/lo ready for the MMA
+  uint64_t *empty = split + gt::kStages;  // [stages] MMA done with the stage
+  uint64_t *accfull = empty + gt::kStages;  // accumulator of a tile complete
+  uint64_t *accfree = accfull + 1;          // epilogue has read it out
+  uint64_t *done = accfree + 1;             // every MMA issued has completed
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
   int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // tile coordinates
-  const int64_t m0 = (int64_t)blockIdx.x * gt::BM;          // TALL: row i0; GRAM: column a0
-  const int64_t r0 = MN ? (int64_t)blockIdx.y * rows_per_chunk : 0;
-  int kblocks = nkb;
-  if (MN) {
-    const int64_t r1 = min64(nrows_total, r0 + rows_per_chunk);
-    kblocks = r1 > r0 ? (int)((r1 - r0 + gt::BK - 1) / gt::BK) : 0;
-  }
   const int n1 = npad > 256 ? 256 : npad;  // first MMA column block
-  const int n2 = npad - n1;                // second (0, 32 ... 32)
+  const int n2 = npad - n1;                // second (0, 32)
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < stages; ++s) {
+    for (int s = 0; s < gt::kStages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&split[s], 128);
       mbar_init(&empty[s], 1);
     }
+    mbar_init(accfull, 1);
+    mbar_init(accfree, 128);
     mbar_init(done, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -93,167 +90,143 @@ __global__ void __launch_bounds__(gt::kThreads, 1) gemm_tf32x3_kernel(
   volatile int *abortv = abort_flag;
 
   auto stage_ptr = [&](int s) { return smem + (size_t)s * stage_bytes; };
-  // stage layout: A_hi | A_lo | B_hi | B_lo
+  // stage layout: A_hi | A_lo | B_hi | B_lo (K-major, 128-byte swizzle)
   if (warp == 0) {
     if (lane == 0) {
-      int issued = 0;
+      uint32_t it = 0;
       bool ok = true;
-      for (int kb = 0; kb < kblocks; ++kb) {
-        const int s = kb % stages;
-        if (!mbar_wait(&empty[s], (uint32_t)(((kb / stages) & 1) ^ 1), abortv, ctrl)) {
-          ok = false;
-          break;
-        }
-        unsigned char *st = stage_ptr(s);
-        mbar_expect_tx(&full[s], (uint32_t)(gt::kABytes + bbytes));
-        if (!MN) {
-          // K-major: A box {32 k, 128 rows}; B boxes {32 k, n1 rows} and {32 k, n2 rows}
-          tma_load_2d(st, &tmA, &full[s], kb * gt::BK, (int)m0);
+      for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const int m0 = (int)(tile * gt::BM);
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = it % gt::kStages;
+          if (!mbar_wait(&empty[s], ((it / gt::kStages) & 1) ^ 1, abortv, ctrl)) {
+            ok = false;
+            break;
+          }
+          unsigned char *st = stage_ptr(s);
+          mbar_expect_tx(&full[s], (uint32_t)(gt::kABytes + bbytes));
+          // A box {32 k, 128 rows}; B boxes {32 k, n1 rows} and {32 k, n2 rows}
+          tma_load_2d(st, &tmA, &full[s], kb * gt::BK, m0);
           tma_load_2d(st + 2 * gt::kABytes, &tmB, &full[s], kb * gt::BK, 0);
           if (n2 > 0) tma_load_2d(st + 2 * gt::kABytes + n1 * 128, &tmB2, &full[s], kb * gt::BK, n1);
-        } else {
-          // MN-major: boxes {32 columns, 32 rows}; A: 4 boxes, B: npad/32 boxes, 4 KB apart
-          const int y = (int)(r0 + (int64_t)kb * gt::BK);
-          for (int m = 0; m < gt::BM / 32; ++m)
-            tma_load_2d(st + m * 4096, &tmA, &full[s], (int)m0 + 32 * m, y);
-          for (int t = 0; t < npad / 32; ++t)
-            tma_load_2d(st + 2 * gt::kABytes + t * 4096, &tmB, &full[s], 32 * t, y);
         }
-        ++issued;
       }
       if (!ok) {
-        const int first = issued > stages ? issued - stages : 0;
-        for (int q = first; q < issued; ++q) {
-          const uint64_t t0 = gtimer();
-          while (!mbar_try_wait(&full[q % stages], (uint32_t)((q / stages) & 1)) &&
-                 gtimer() - t0 < kTimeoutNs) {
-          }
-        }
+        // let the copies this CTA issued land before it exits
+        const uint32_t first = it > (uint32_t)gt::kStages ? it - gt::kStages : 0;
+        for (uint32_t q = first; q < it; ++q)
+          mbar_drain(&full[q % gt::kStages], (q / gt::kStages) & 1, kTimeoutNs);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      // instruction descriptors: D F32, A/B TF32 (2), major bits, N, M = 128
-      const uint32_t major = MN ? ((1u << 15) | (1u << 16)) : 0u;
-      const uint32_t base = (1u << 4) | (2u << 7) | (2u << 10) | major | ((uint32_t)(gt::BM >> 4) << 24);
+      // instruction descriptors: D F32, A/B TF32 (2), K-major, N, M = 128
+      const uint32_t base = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(gt::BM >> 4) << 24);
       const uint32_t id1 = base | ((uint32_t)(n1 >> 3) << 17);
       const uint32_t id2 = base | ((uint32_t)((n2 > 0 ? n2 : 16) >> 3) << 17);
+      uint32_t it = 0, lt = 0;
       bool ok = true;
-      for (int kb = 0; kb < kblocks; ++kb) {
-        const int s = kb % stages;
-        if (!mbar_wait(&split[s], (uint32_t)((kb / stages) & 1), abortv, ctrl)) {
+      for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++lt) {
+        if (!mbar_wait(accfree, (lt & 1) ^ 1, abortv, ctrl)) break;
+        fence_after();
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = it % gt::kStages;
+          if (!mbar_wait(&split[s], (it / gt::kStages) & 1, abortv, ctrl)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t ahi = smem_u32(stage_ptr(s));
+          const uint32_t alo = ahi + gt::kABytes;
+          const uint32_t bhi = ahi + 2 * gt::kABytes;
+          const uint32_t blo = bhi + bbytes;
+#pragma unroll
+          for (int kk = 0; kk < gt::BK / 8; ++kk) {
+            const uint32_t acc = (kb | kk) ? 1u : 0u;
+            const uint64_t da_hi = sdesc2(ahi + kk * 32, 16, 1024);
+            const uint64_t da_lo = sdesc2(alo + kk * 32, 16, 1024);
+            const uint64_t db1_hi = sdesc2(bhi + kk * 32, 16, 1024);
+            mma_tf32(tmem, da_hi, db1_hi, id1, acc);
+            mma_tf32(tmem, da_hi, sdesc2(blo + kk * 32, 16, 1024), id1, 1u);
+            mma_tf32(tmem, da_lo, db1_hi, id1, 1u);
+            if (n2 > 0) {
+              const uint64_t db2_hi = sdesc2(bhi + n1 * 128 + kk * 32, 16, 1024);
+              mma_tf32(tmem + n1, da_hi, db2_hi, id2, acc);
+              mma_tf32(tmem + n1, da_hi, sdesc2(blo + n1 * 128 + kk * 32, 16, 1024), id2, 1u);
+              mma_tf32(tmem + n1, da_lo, db2_hi, id2, 1u);
+            }
+          }
+          mma_commit(&empty[s]);
+        }
+        if (ok) mma_commit(accfull);
+      }
+      // every issued MMA has completed before TMEM is released
+      mma_commit(done);
+      mbar_drain(done, 0, kTimeoutNs);
+    }
+  } else if (warp < 6) {
+    // ---------------- warps 2..5: operand split (elementwise, in place)
+    const int t = threadIdx.x - 64;  // 0..127
+    uint32_t it = 0;
+    bool ok = true;
+    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      for (int kb = 0; kb < nkb; ++kb, ++it) {
+        const int s = it % gt::kStages;
+        if (!mbar_wait(&full[s], (it / gt::kStages) & 1, abortv, ctrl)) {
           ok = false;
           break;
         }
-        fence_after();
-        const uint32_t ahi = smem_u32(stage_ptr(s));
-        const uint32_t alo = ahi + gt::kABytes;
-        const uint32_t bhi = ahi + 2 * gt::kABytes;
-        const uint32_t blo = bhi + bbytes;
-#pragma unroll
-        for (int kk = 0; kk < gt::BK / 8; ++kk) {
-          const uint32_t acc = (kb | kk) ? 1u : 0u;
-          uint64_t da_hi, da_lo, db1_hi, db1_lo, db2_hi, db2_lo;
-          if (!MN) {
-            da_hi = sdesc2(ahi + kk * 32, 16, 1024);
-            da_lo = sdesc2(alo + kk * 32, 16, 1024);
-            db1_hi = sdesc2(bhi + kk * 32, 16, 1024);
-            db1_lo = sdesc2(blo + kk * 32, 16, 1024);
-            db2_hi = sdesc2(bhi + n1 * 128 + kk * 32, 16, 1024);
-            db2_lo = sdesc2(blo + n1 * 128 + kk * 32, 16, 1024);
-          } else {
-            da_hi = sdesc2(ahi + kk * 1024, 4096, 1024);
-            da_lo = sdesc2(alo + kk * 1024, 4096, 1024);
-            db1_hi = sdesc2(bhi + kk * 1024, 4096, 1024);
-            db1_lo = sdesc2(blo + kk * 1024, 4096, 1024);
-            db2_hi = sdesc2(bhi + (n1 / 32) * 4096 + kk * 1024, 4096, 1024);
-            db2_lo = sdesc2(blo + (n1 / 32) * 4096 + kk * 1024, 4096, 1024);
-          }
-          mma_tf32(tmem, da_hi, db1_hi, id1, acc);
-          mma_tf32(tmem, da_hi, db1_lo, id1, 1u);
-          mma_tf32(tmem, da_lo, db1_hi, id1, 1u);
-          if (n2 > 0) {
-            mma_tf32(tmem + n1, da_hi, db2_hi, id2, acc);
-            mma_tf32(tmem + n1, da_hi, db2_lo, id2, 1u);
-            mma_tf32(tmem + n1, da_lo, db2_hi, id2, 1u);
-          }
+        unsigned char *st = stage_ptr(s);
+        float4 *ahi = reinterpret_cast<float4 *>(st);
+        float4 *alo = reinterpret_cast<float4 *>(st + gt::kABytes);
+#pragma unroll 4
+        for (int q = t; q < gt::kABytes / 16; q += 128) {
+          const float4 x = ahi[q];
+          const float4 h = make_float4(tf32_rna(x.x), tf32_rna(x.y), tf32_rna(x.z), tf32_rna(x.w));
+          ahi[q] = h;
+          alo[q] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
         }
-        mma_commit(&empty[s]);
+        float4 *bhi = reinterpret_cast<float4 *>(st + 2 * gt::kABytes);
+        float4 *blo = reinterpret_cast<float4 *>(st + 2 * gt::kABytes + bbytes);
+        const int nB4 = bbytes / 16;
+#pragma unroll 4
+        for (int q = t; q < nB4; q += 128) {
+          const float4 x = bhi[q];
+          const float4 h = make_float4(tf32_rna(x.x), tf32_rna(x.y), tf32_rna(x.z), tf32_rna(x.w));
+          bhi[q] = h;
+          blo[q] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&split[s]);
       }
-      (void)ok;
-      mma_commit(done);
     }
   } else {
-    // ---------------- warps 2..5: operand split, then epilogue
-    const int t = threadIdx.x - 64;  // 0..127
-    bool ok = true;
-    for (int kb = 0; kb < kblocks; ++kb) {
-      const int s = kb % stages;
-      if (!mbar_wait(&full[s], (uint32_t)((kb / stages) & 1), abortv, ctrl)) {
-        ok = false;
-        break;
-      }
-      unsigned char *st = stage_ptr(s);
-      float4 *ahi = reinterpret_cast<float4 *>(st);
-      float4 *alo = reinterpret_cast<float4 *>(st + gt::kABytes);
-      const int nA4 = gt::kABytes / 16;
-      for (int q = t; q < nA4; q += 128) {
-        float4 x = ahi[q];
-        if (MN && w) {
-          // row (K index) of this 16-byte chunk inside its 32 x 32 box
-          const int64_t i = r0 + (int64_t)kb * gt::BK + ((q % 256) / 8);
-          const float wi = i < nrows_total ? w[i] : 0.0f;
-          x.x *= wi;
-          x.y *= wi;
-          x.z *= wi;
-          x.w *= wi;
-        }
-        const float4 h = make_float4(tf32_rna(x.x), tf32_rna(x.y), tf32_rna(x.z), tf32_rna(x.w));
-        ahi[q] = h;
-        alo[q] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
-      }
-      float4 *bhi = reinterpret_cast<float4 *>(st + 2 * gt::kABytes);
-      float4 *blo = reinterpret_cast<float4 *>(st + 2 * gt::kABytes + bbytes);
-      const int nB4 = bbytes / 16;
-      for (int q = t; q < nB4; q += 128) {
-        const float4 x = bhi[q];
-        const float4 h = make_float4(tf32_rna(x.x), tf32_rna(x.y), tf32_rna(x.z), tf32_rna(x.w));
-        bhi[q] = h;
-        blo[q] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(&split[s]);
-    }
-    // epilogue: the accumulator row of this thread
-    if (ok && kblocks > 0 && mbar_wait(done, 0, abortv, ctrl)) {
+    // ---------------- warps 6..9: epilogue, one accumulator row per thread
+    const int ew = warp & 3;  // TMEM lane quarter of this warp
+    uint32_t lt = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
+      if (!mbar_wait(accfull, lt & 1, abortv, ctrl)) break;
       fence_after();
-      const int ew = warp & 3;
-      const int64_t r = m0 + 32 * ew + lane;  // output row (TALL) or column a (GRAM)
-      float *orow = out + (MN ? (int64_t)blockIdx.y * chunk_stride : 0) + r * ldo;
-      const bool rok = r < mrows;
+      const int64_t r = tile * gt::BM + 32 * ew + lane;
+      float *orow = out + r * ldo;
+      const bool rok = r < nrows;
       for (int c = 0; c < npad; c += 32) {
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(32 * ew) << 16) + (uint32_t)c, v);
         if (rok) {
+          if (vec4 && c + 32 <= ncols) {
 #pragma unroll
-          for (int q = 0; q < 32; ++q)
-            if (c + q < ncols) orow[c + q] = v[q];
+            for (int q = 0; q < 32; q += 4)
+              *reinterpret_cast<float4 *>(orow + c + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+          } else {
+#pragma unroll
+            for (int q = 0; q < 32; ++q)
+              if (c + q < ncols) orow[c + q] = v[q];
+          }
         }
       }
-    } else if (MN && kblocks == 0) {
-      // empty chunk: its partial sums are zero
-      const int ew = warp & 3;
-      const int64_t r = m0 + 32 * ew + lane;
-      if (r < mrows) {
-        float *orow = out + (int64_t)blockIdx.y * chunk_stride + r * ldo;
-        for (int c = 0; c < ncols; ++c) orow[c] = 0.0f;
-      }
-    }
-  }
-  // release TMEM once every MMA has completed
-  if (warp == 1 && lane == 0) {
-    const uint64_t t0 = gtimer();
-    while (!mbar_try_wait(done, 0) && gtimer() - t0 < kTimeoutNs) {
+      fence_before();
+      mbar_arrive(accfree);
     }
   }
   fence_before();
@@ -333,7 +306,10 @@ __global__ void __launch_bounds__(gg::kThreads, 1) gram_tf32x3_kernel(
   const int kblocks = r1 > r0 ? (int)((r1 - r0 + gt::BK - 1) / gt::BK) : 0;
   const int nseg = (kblocks + gg::kSeg - 1) / gg::kSeg;
   const int bbytes = npad * 128;
-  const uint32_t raw_bytes = (uint32_t)(gt::kABytes + bbytes);
+  // a diagonal tile of the unweighted symmetric Gram reads its B columns from
+  // the A tile (with weights, A holds w_i A[i, :] and B must stay unweighted)
+  const bool diag = symmetric && ta == tb && w == nullptr;
+  const uint32_t raw_bytes = (uint32_t)(gt::kABytes + (diag ? 0 : bbytes));
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < 2; ++s) {
@@ -371,8 +347,9 @@ __global__ void __launch_bounds__(gg::kThreads, 1) gram_tf32x3_kernel(
         mbar_expect_tx(&full[s], raw_bytes);
         const int y = (int)(r0 + (int64_t)kb * gt::BK);
         for (int m = 0; m < 4; ++m) tma_load_2d(rb + m * 4096, &tmA, &full[s], a0 + 32 * m, y);
-        for (int t = 0; t < npad / 32; ++t)
-          tma_load_2d(rb + gg::kTileBytes + t * 4096, &tmB, &full[s], b0 + 32 * t, y);
+        if (!diag)
+          for (int t = 0; t < npad / 32; ++t)
+            tma_load_2d(rb + gg::kTileBytes + t * 4096, &tmB, &full[s], b0 + 32 * t, y);
         ++issued;
       }
       const int first = issued > 2 ? issued - 2 : 0;
@@ -407,7 +384,8 @@ __global__ void __launch_bounds__(gg::kThreads, 1) gram_tf32x3_kernel(
         fence_after();
         const uint32_t base = smem_u32(hilo + (size_t)s * 4 * gg::kTileBytes);
         const uint32_t ahi = base, alo = base + gg::kTileBytes;
-        const uint32_t bhi = base + 2 * gg::kTileBytes, blo = base + 3 * gg::kTileBytes;
+        const uint32_t bhi = diag ? ahi : base + 2 * gg::kTileBytes;
+        const uint32_t blo = diag ? alo : base + 3 * gg::kTileBytes;
         const uint32_t dt = tmem + (uint32_t)(buf * gg::BN);
 #pragma unroll
         for (int kk = 0; kk < gt::BK / 8; ++kk) {
@@ -439,39 +417,51 @@ __global__ void __launch_bounds__(gg::kThreads, 1) gram_tf32x3_kernel(
       float *hB = lA + gg::kTileBytes / 4;
       float *lB = hB + gg::kTileBytes / 4;
       const int64_t ibase = r0 + (int64_t)kb * gt::BK;
-      // task (box m, K-chunk ic, output index a): the 4 values A[i][a], i = 4 ic ..
-      // 4 ic + 3, read with conflict-free scalar loads (the 32 lanes of a warp
-      // take the 32 a of one raw row) and written as one 16-byte hi and one lo
-      // store into the K-major swizzled row r = 32 m + a (chunk ic ^ (r % 8))
-      const int ntask = (4 + npad / 32) * 256;
+      // task (box, ic, j): the 4 x 4 block rows i = 4 ic .. 4 ic + 3, columns
+      // 4 j .. 4 j + 3 of a raw box (16-byte chunk j of row i sits at chunk
+      // j ^ (i % 8)), read as four float4, transposed in registers and
+      // written as four hi and four lo float4: K-major row r = 32 m + 4 j + v,
+      // K-chunk ic at chunk ic ^ (r % 8).  The 8 lanes of a quarter-warp take
+      // ic = 0..7 with j = ic ^ g, so both their loads (chunks j ^ 4(ic & 1) ^ u)
+      // and their stores (chunks ic ^ 4(j & 1) ^ v) fall on 8 distinct chunks:
+      // no bank conflicts.
+      const int ntask = (4 + (diag ? 0 : npad / 32)) * 64;
       for (int tau = t; tau < ntask; tau += 128) {
-        const bool isA = tau < 4 * 256;
-        const int tt = isA ? tau : tau - 4 * 256;
-        const int m = tt >> 8, ic = (tt >> 5) & 7, a = tt & 31;
-        const float *box = rawf + (isA ? 0 : gg::kTileBytes / 4) + m * 1024;
-        float x[4];
+        const int box = tau >> 6, g = (tau >> 3) & 7, ic = tau & 7, j = ic ^ g;
+        const bool isA = box < 4;
+        const int m = isA ? box : box - 4;
+        const float *bx = rawf + (isA ? 0 : gg::kTileBytes / 4) + m * 1024;
+        float4 X[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int i = 4 * ic + u;
-          x[u] = box[i * 32 + ((((a >> 2) ^ (i & 7)) << 2) | (a & 3))];
+          X[u] = *reinterpret_cast<const float4 *>(bx + i * 32 + ((j ^ (i & 7)) << 2));
         }
         if (isA && w) {
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const int64_t gi = ibase + 4 * ic + u;
-            x[u] *= gi < nrows_total ? __ldg(w + gi) : 0.0f;
+            const float wi = gi < nrows_total ? __ldg(w + gi) : 0.0f;
+            X[u].x *= wi;
+            X[u].y *= wi;
+            X[u].z *= wi;
+            X[u].w *= wi;
           }
         }
-        float4 h, l;
-        h.x = tf32_rna(x[0]);
-        h.y = tf32_rna(x[1]);
-        h.z = tf32_rna(x[2]);
-        h.w = tf32_rna(x[3]);
-        l = make_float4(x[0] - h.x, x[1] - h.y, x[2] - h.z, x[3] - h.w);
-        const int r = 32 * m + a;
-        const int off = r * 32 + ((ic ^ (r & 7)) << 2);
-        *reinterpret_cast<float4 *>((isA ? hA : hB) + off) = h;
-        *reinterpret_cast<float4 *>((isA ? lA : lB) + off) = l;
+        float *dh = isA ? hA : hB;
+        float *dl = isA ? lA : lB;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const float x0 = v == 0 ? X[0].x : v == 1 ? X[0].y : v == 2 ? X[0].z : X[0].w;
+          const float x1 = v == 0 ? X[1].x : v == 1 ? X[1].y : v == 2 ? X[1].z : X[1].w;
+          const float x2 = v == 0 ? X[2].x : v == 1 ? X[2].y : v == 2 ? X[2].z : X[2].w;
+          const float x3 = v == 0 ? X[3].x : v == 1 ? X[3].y : v == 2 ? X[3].z : X[3].w;
+          const float4 h = make_float4(tf32_rna(x0), tf32_rna(x1), tf32_rna(x2), tf32_rna(x3));
+          const int r = 32 * m + 4 * j + v;
+          const int off = r * 32 + ((ic ^ (r & 7)) << 2);
+          *reinterpret_cast<float4 *>(dh + off) = h;
+          *reinterpret_cast<float4 *>(dl + off) = make_float4(x0 - h.x, x1 - h.y, x2 - h.z, x3 - h.w);
+        }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(&rawfree[s]);
@@ -557,7 +547,7 @@ static bool map_f32(CUtensorMap *tm, const float *ptr, int64_t rows, int64_t col
 
 static size_t gemm_tc_smem(int npad) {
   const size_t stage = 2 * (size_t)gt::kABytes + 2 * (size_t)npad * gt::BK * 4;
-  return 1024 + 2 * stage + 256;
+  return 1024 + gt::kStages * stage + 256;
 }
 
 bool tc_gemm_supported(int ncols) {
@@ -570,7 +560,7 @@ cudaError_t launch_tall_gemm_tc(const float *A, int64_t lda, int64_t n, int K, c
                                 float *C, int64_t ldc, Ctrl *ctrl, cudaStream_t st) {
   if (n <= 0 || Kc <= 0) return cudaSuccess;
   const int npad = (Kc + 31) / 32 * 32;
-  if (!tc_gemm_supported(Kc)) return cudaErrorInvalidValue;
+  if (!tc_gemm_supported(Kc) || n > (int64_t)INT32_MAX - gt::BM) return cudaErrorInvalidValue;
   CUtensorMap tmA, tmB, tmB2;
   const int n1 = npad > 256 ? 256 : npad;
   const int n2 = npad - n1;
@@ -579,13 +569,16 @@ cudaError_t launch_tall_gemm_tc(const float *A, int64_t lda, int64_t n, int K, c
   if (!map_f32(&tmB, Mt, Kc, K, K, gt::BK, n1)) return cudaErrorInvalidValue;
   if (!map_f32(&tmB2, Mt, Kc, K, K, gt::BK, n2 > 0 ? n2 : 32)) return cudaErrorInvalidValue;
   const size_t smem = gemm_tc_smem(npad);
-  auto kern = gemm_tf32x3_kernel<false>;
+  auto kern = tall_tf32x3_kernel;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int nkb = (K + gt::BK - 1) / gt::BK;
+  const int64_t ntiles = (n + gt::BM - 1) / gt::BM;
+  const int grid = (int)min64(ntiles, (int64_t)sm_count());
+  const int vec4 = (ldc % 4 == 0 && (uintptr_t)C % 16 == 0) ? 1 : 0;
   ProfScope ps_(K_TALL_TC, st);
-  kern<<<(unsigned)((n + gt::BM - 1) / gt::BM), gt::kThreads, smem, st>>>(
-      tmA, tmB, tmB2, npad, nkb, 0, n, nullptr, (int)min64(n, (int64_t)INT32_MAX), Kc, C, ldc, 0, ctrl);
+  kern<<<grid, gt::kThreads, smem, st>>>(tmA, tmB, tmB2, npad, nkb, ntiles, n, Kc, C, ldc, vec4,
+                                         ctrl);
   return cudaGetLastError();
 }
 
