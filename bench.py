@@ -62,6 +62,16 @@ WORKLOADS = {
                   label="Chung-Lu n=50M avg-degree 40 gamma 2.1 (drawn on the GPU), T=10 b=1 k=128 "
                         "d=128 zeta=8 h=2d+16 l=d+1000 q=20 alpha=0.5; FP16 reconstruction with "
                         "FP32 accumulation"),
+    "cl1m_a04": dict(kind="chung_lu", n=1_000_000, avg=20.0, gamma=2.1, d=128, k=256, T=10,
+                     q=20, alpha=0.4, precision="fp16x2",
+                     label="Chung-Lu n=1M avg-degree 20 gamma 2.1, T=10 b=1 k=256 d=128 zeta=8 "
+                           "h=2d+16 l=d+1000 q=20 alpha=0.4; FP16 hi/lo pair reconstruction "
+                           "against plain FP32"),
+    "cl50m_s0": dict(kind="chung_lu_device", n=50_000_000, avg=40.0, gamma=2.1, d=32, k=32, T=5,
+                     q=6, alpha=0.45, h=32, precision="fp16x2",
+                     label="Chung-Lu n=50M avg-degree 40 gamma 2.1 (drawn on the GPU), the "
+                           "very-large-graph setting: s1=0 (h=d=32), k=32, T=5, q=6, alpha=0.45, "
+                           "l=d+1000 zeta=8; FP16 hi/lo pair reconstruction against plain FP32"),
     "batch64": dict(kind="batch", count=64, d=64, k=64, T=10, q=20,
                     label="64 graphs, n ~ U[2000, 200000], mean degree ~ U[8, 32], even: 8-block "
                           "SBM p_in/p_out = 10, odd: Chung-Lu gamma 2.1, graph g seeded g; "
@@ -530,7 +540,8 @@ def run_ours(args, rank: int, world: int) -> None:
         torch.cuda.empty_cache()
         ek, ew = min(args.steps, 3), max(3, min(args.warmup, 3))
         extra = {}
-        extra["cl10m"] = measure_single(args, "cl10m", ek, ew) if rank == 0 or world > 1 else None
+        for name in ("cl10m", "cl1m_a04", "cl50m_s0"):
+            extra[name] = measure_single(args, name, ek, ew) if rank == 0 or world > 1 else None
         bline = measure_batch(args, rank, world, "batch64", "fp16", ek, ew)
         if bline is not None:
             extra["batch64"] = {k: bline[k] for k in ("value", "ms_per_step", "steps", "warmup",
@@ -562,6 +573,15 @@ def run_ours(args, rank: int, world: int) -> None:
         print(json.dumps(line), flush=True)
 
 
+def workload_params(sk, w, precision="fp32"):
+    """sne_params of a workload (alpha 0.5 and h = 2d + 16 unless it says otherwise)."""
+    p = sk.sne_params_init(w["d"], w["k"], q=w["q"], T=w["T"], precision=sk.PRECISIONS[precision],
+                           orth=sk.SNE_ORTH_CHOLQR, alpha=w.get("alpha", 0.5))
+    if "h" in w:
+        p.h = w["h"]
+    return p
+
+
 def measure_single(args, workload: str, steps: int, warmup: int) -> dict:
     """One graph of a large workload at its configured (mixed) precision and
     at plain FP32, steps embeddings each after `warmup` untimed ones (L2
@@ -584,8 +604,7 @@ def measure_single(args, workload: str, steps: int, warmup: int) -> dict:
            "graph_generation_s": gen_s, "l2": "flushed between steps (256 MB write)"}
     sigmas = {}
     for prec in (w["precision"], "fp32"):
-        p = sk.sne_params_init(w["d"], w["k"], q=w["q"], T=w["T"], precision=sk.PRECISIONS[prec],
-                               orth=sk.SNE_ORTH_CHOLQR)
+        p = workload_params(sk, w, prec)
         ws = sk.workspace(g.n, g.nnz, p, sk.SNE_WS_EMBED)
         E = torch.empty(g.n, p.d, dtype=torch.float32, device="cuda")
         sig = torch.empty(p.d, dtype=torch.float64, device="cuda")
@@ -634,7 +653,7 @@ def large_sample_error(sk, g, G, w, precisions, rows=100_000) -> dict:
     library at each precision, from the same eigenpairs."""
     import torch
     from oracle import sketchne_oracle as o
-    p = sk.sne_params_init(w["d"], w["k"], q=w["q"], T=w["T"], orth=sk.SNE_ORTH_CHOLQR)
+    p = workload_params(sk, w)
     ws = sk.workspace(g.n, g.nnz, p, sk.SNE_WS_FREIGS)
     U = torch.empty(g.n, p.k, dtype=torch.float32, device="cuda")
     lam = torch.empty(p.k, dtype=torch.float64, device="cuda")
@@ -652,8 +671,7 @@ def large_sample_error(sk, g, G, w, precisions, rows=100_000) -> dict:
            "oracle_s": time.perf_counter() - t0}
     del Uh
     for prec in precisions:
-        q = sk.sne_params_init(w["d"], w["k"], q=w["q"], T=w["T"], precision=sk.PRECISIONS[prec],
-                               orth=sk.SNE_ORTH_CHOLQR)
+        q = workload_params(sk, w, prec)
         wss = sk.workspace(g.n, g.nnz, q, sk.SNE_WS_SKETCH)
         Y = torch.empty(g.n, q.h, dtype=torch.float32, device="cuda")
         sk.sne_sketch_from_factors(G, q, U, lam, wss, Y=Y)

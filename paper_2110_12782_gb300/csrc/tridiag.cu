@@ -15,12 +15,13 @@
 //     Sturm count (the number of negative pivots of the LDL^T factorization
 //     of T - x I, Sylvester's law of inertia); eigenvectors by inverse
 //     iteration with T - lambda I factored by Gaussian elimination with
-//     partial pivoting, from a pseudo-random start, re-orthogonalized (modified
-//     Gram-Schmidt) against the other members of their cluster: eigenvalues of
-//     one block closer than 1e-3 |T_block| (the approach of LAPACK's stein),
-//     with shifts inside a cluster kept at least 10 eps |T| apart.  A warp per
-//     cluster; its lane 0 runs the factorization, the solves, the
-//     orthogonalization and the normalization (O(size) sequential steps each).
+//     partial pivoting, from a pseudo-random start, one thread per vector
+//     (O(size) sequential steps per factorization or solve, all vectors at
+//     once).  Members of a cluster (eigenvalues of one block closer than
+//     1e-3 |T_block|, the grouping of LAPACK's stein, with shifts kept at least
+//     10 eps |T| apart) are re-orthogonalized by modified Gram-Schmidt by the
+//     whole CTA: two solves, the cluster pass, a third solve, the cluster pass
+//     again.
 //  3. tri_backtransform_kernel: V = H_0 H_1 ... H_{n-3} Z, a warp per column.
 #include <cfloat>
 #include <cmath>
@@ -156,21 +157,128 @@ __device__ __forceinline__ float hash_unit(uint32_t a, uint32_t b) {
   return (float)(z >> 40) * (2.0f / 16777216.0f) - 1.0f;  // [-1, 1)
 }
 
-// Inverse iteration runs on the first kIIWarps warps; each keeps its LU
-// factors and iterate (6 arrays of n floats) in dynamic shared memory.
-constexpr int kIIWarps = 16;
+// Inverse iteration: one thread per eigenvector.  The factors of
+// T_b - shift_m I and the iterate of vector m live in global scratch at
+// [i * n + m], so that the 32 threads of a warp, which run their sequential
+// loops in lockstep over the same row i, touch 32 consecutive words.
+struct TriLU {
+  float *r0, *u1, *u2, *lm, *pv;  // 1/U(i,i), U(i,i+1), U(i,i+2), multiplier, swap flag
+};
+
+// LU of T_b - shift I with partial pivoting for the column m (rows s .. t).
+__device__ void tri_lu(const float *d, const float *e, int s, int sz, float shift, float pertol,
+                       const TriLU &f, int n, int m) {
+  float a = d[s] - shift, bnext = e[s];
+  for (int i = 0; i < sz - 1; ++i) {
+    const float sub = e[s + i];             // T(i+1, i)
+    const float dn = d[s + i + 1] - shift;  // T(i+1, i+1)
+    const float sup2 = (i + 2 < sz) ? e[s + i + 1] : 0.f;
+    float u0, u1, u2, l, pv;
+    if (fabsf(a) >= fabsf(sub)) {
+      l = (a != 0.f) ? sub / a : 0.f;
+      u0 = a; u1 = bnext; u2 = 0.f; pv = 0.f;
+      a = dn - l * bnext;
+      bnext = sup2;
+    } else {
+      l = a / sub;
+      u0 = sub; u1 = dn; u2 = sup2; pv = 1.f;
+      a = bnext - l * dn;
+      bnext = -l * sup2;
+    }
+    if (fabsf(u0) < pertol) u0 = copysignf(pertol, u0 == 0.f ? 1.f : u0);
+    const int64_t q = (int64_t)i * n + m;
+    f.r0[q] = 1.0f / u0; f.u1[q] = u1; f.u2[q] = u2; f.lm[q] = l; f.pv[q] = pv;
+  }
+  const float u0 = (fabsf(a) < pertol) ? copysignf(pertol, a == 0.f ? 1.f : a) : a;
+  const int64_t q = (int64_t)(sz - 1) * n + m;
+  f.r0[q] = 1.0f / u0; f.u1[q] = 0.f; f.u2[q] = 0.f; f.lm[q] = 0.f; f.pv[q] = 0.f;
+}
+
+// x <- (T_b - shift I)^-1 x (x = column m of X, rows s ..), then scaled to
+// max |x_i| = 1.
+__device__ void tri_solve(const TriLU &f, float *X, int s, int sz, int n, int m) {
+  float *x = X + (int64_t)s * n + m;
+  // forward: the row swaps and multipliers
+  float cur = x[0];
+  for (int i = 0; i < sz - 1; ++i) {
+    const int64_t q = (int64_t)i * n + m;
+    const float nxt = x[(int64_t)(i + 1) * n];
+    const float l = f.lm[q];
+    if (f.pv[q] != 0.f) {
+      x[(int64_t)i * n] = nxt;
+      cur = cur - l * nxt;
+    } else {
+      x[(int64_t)i * n] = cur;
+      cur = nxt - l * cur;
+    }
+  }
+  x[(int64_t)(sz - 1) * n] = cur;
+  // back substitution with U
+  float x1 = 0.f, x2 = 0.f, mx = 0.f;
+  for (int i = sz - 1; i >= 0; --i) {
+    const int64_t q = (int64_t)i * n + m;
+    const float r = (x[(int64_t)i * n] - f.u1[q] * x1 - f.u2[q] * x2) * f.r0[q];
+    x[(int64_t)i * n] = r;
+    x2 = x1;
+    x1 = r;
+    mx = fmaxf(mx, fabsf(r));
+  }
+  const float inv = mx > 0.f ? 1.f / mx : 1.f;
+  for (int i = 0; i < sz; ++i) x[(int64_t)i * n] *= inv;
+}
+
+// Modified Gram-Schmidt inside every cluster of two or more members, by the
+// whole CTA: member j is normalized, then its component is removed from the
+// later members (a warp per member).  Clusters in order, members in order.
+__device__ void tri_cluster_mgs(float *X, int n, const int *cstart, int nc, const int *blk_of,
+                                const int *bstart, float *red, Ctrl *ctrl) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int c = 0; c < nc; ++c) {
+    const int m0 = cstart[c], m1 = cstart[c + 1];
+    if (m1 - m0 < 2) continue;
+    const int b = blk_of[m0];
+    const int s = bstart[b], sz = bstart[b + 1] - s;
+    for (int j = m0; j < m1; ++j) {
+      float part = 0.f;
+      for (int i = tid; i < sz; i += blockDim.x) {
+        const float v = X[(int64_t)(s + i) * n + j];
+        part += v * v;
+      }
+      const float nrm = block_sum(part, red);
+      if (!(nrm > 0.f)) {
+        if (tid == 0) record_error(ctrl, SNE_ERR_NUMERIC, W_EIG);
+      }
+      const float rn = nrm > 0.f ? 1.0f / sqrtf(nrm) : 0.f;
+      for (int i = tid; i < sz; i += blockDim.x) X[(int64_t)(s + i) * n + j] *= rn;
+      __syncthreads();
+      for (int q = j + 1 + warp; q < m1; q += nw) {
+        float dot = 0.f;
+        for (int i = lane; i < sz; i += 32)
+          dot += X[(int64_t)(s + i) * n + j] * X[(int64_t)(s + i) * n + q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+        for (int i = lane; i < sz; i += 32)
+          X[(int64_t)(s + i) * n + q] -= dot * X[(int64_t)(s + i) * n + j];
+      }
+      __syncthreads();
+    }
+  }
+}
+
 __global__ void __launch_bounds__(1024) tri_eig_kernel(const float *__restrict__ dg,
                                                        const float *__restrict__ eg, int n,
                                                        float *__restrict__ w,
-                                                       float *__restrict__ Z, int ldz,
+                                                       float *__restrict__ Z,
                                                        float *__restrict__ scratch,
                                                        Ctrl *ctrl) {
-  __shared__ float d[kTriMaxN], e[kTriMaxN], e2[kTriMaxN], lam[kTriMaxN];
+  __shared__ float d[kTriMaxN], e[kTriMaxN], e2[kTriMaxN], lam[kTriMaxN], shift[kTriMaxN];
   __shared__ int bstart[kTriMaxN + 1], blk_of[kTriMaxN], cstart[kTriMaxN + 1];
   __shared__ float bnorm[kTriMaxN];
+  __shared__ int csz[kTriMaxN];  // size of the cluster of eigenvalue m
+  __shared__ float red[32];
   __shared__ int nblk_s, nclu_s;
   __shared__ float tnorm_s;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int tid = threadIdx.x;
   for (int i = tid; i < n; i += blockDim.x) {
     d[i] = dg[i];
     e[i] = i + 1 < n ? eg[i] : 0.f;
@@ -233,7 +341,9 @@ __global__ void __launch_bounds__(1024) tri_eig_kernel(const float *__restrict__
     w[m] = lam[m];
   }
   __syncthreads();
-  // clusters: consecutive eigenvalues of one block closer than 1e-3 |T_block|
+  // clusters: consecutive eigenvalues of one block closer than 1e-3 |T_block|;
+  // the shifts inside a cluster kept at least 10 eps |T| apart
+  const float pertol = 10.0f * FLT_EPSILON * tnorm;
   if (tid == 0) {
     int nc = 0;
     for (int m = 0; m < n; ++m) {
@@ -241,110 +351,55 @@ __global__ void __launch_bounds__(1024) tri_eig_kernel(const float *__restrict__
       bool newc = (m == 0) || (blk_of[m - 1] != b);
       if (!newc) newc = (lam[m] - lam[m - 1]) > 1e-3f * bnorm[b];
       if (newc) cstart[nc++] = m;
+      shift[m] = (!newc && lam[m] - shift[m - 1] < pertol) ? shift[m - 1] + pertol : lam[m];
     }
     cstart[nc] = n;
     nclu_s = nc;
   }
   __syncthreads();
   const int nc = nclu_s;
-  extern __shared__ float iism[];
-  float *ws = iism + (size_t)warp * 6 * n;
-  float *u0 = ws, *u1 = ws + n, *u2 = ws + 2 * n, *lm = ws + 3 * n, *x = ws + 4 * n, *piv = ws + 5 * n;
-  (void)scratch;
-  const float pertol = 10.0f * FLT_EPSILON * tnorm;
-  for (int c = warp; c < nc && warp < kIIWarps; c += kIIWarps) {
-    const int m0 = cstart[c], m1 = cstart[c + 1];
-    const int b = blk_of[m0];
-    const int s = bstart[b], t = bstart[b + 1] - 1, sz = t - s + 1;
-    float shift_prev = -FLT_MAX;
-    for (int m = m0; m < m1; ++m) {
-      float shift = lam[m];
-      if (m > m0 && shift - shift_prev < pertol) shift = shift_prev + pertol;
-      shift_prev = shift;
-      if (sz == 1) {
-        for (int i = lane; i < n; i += 32) Z[(int64_t)i * ldz + m] = (i == s) ? 1.f : 0.f;
-        continue;
-      }
-      // LU of T_b - shift I with partial pivoting (lane 0): row i of U holds
-      // u0[i] (diagonal), u1[i], u2[i] (the next two columns); lm[i] the
-      // multiplier of step i, piv[i] = 1 if rows i and i+1 were swapped
-      if (lane == 0) {
-        float a = d[s] - shift, bnext = e[s];
-        for (int i = 0; i < sz - 1; ++i) {
-          const float sub = e[s + i];             // T(i+1, i)
-          const float dn = d[s + i + 1] - shift;  // T(i+1, i+1)
-          const float sup2 = (i + 2 < sz) ? e[s + i + 1] : 0.f;  // T(i+1, i+2)
-          if (fabsf(a) >= fabsf(sub)) {
-            const float l = (a != 0.f) ? sub / a : 0.f;
-            u0[i] = a; u1[i] = bnext; u2[i] = 0.f; lm[i] = l; piv[i] = 0.f;
-            a = dn - l * bnext;
-            bnext = sup2;
-          } else {
-            const float l = a / sub;
-            u0[i] = sub; u1[i] = dn; u2[i] = sup2; lm[i] = l; piv[i] = 1.f;
-            a = bnext - l * dn;
-            bnext = -l * sup2;
-          }
-          if (fabsf(u0[i]) < pertol) u0[i] = copysignf(pertol, u0[i] == 0.f ? 1.f : u0[i]);
-        }
-        u0[sz - 1] = (fabsf(a) < pertol) ? copysignf(pertol, a == 0.f ? 1.f : a) : a;
-        u1[sz - 1] = 0.f;
-        u2[sz - 1] = 0.f;
-      }
-      // lane 0 solves; the lanes scale, orthogonalize and normalize the
-      // iterate in shared memory, each on the rows i = lane, lane + 32, ...
-      // (also the rows of Z it wrote itself for the earlier members)
-      for (int i = lane; i < sz; i += 32) x[i] = hash_unit((uint32_t)m, (uint32_t)i);
-      __syncwarp();
-      for (int iter = 0; iter < 3; ++iter) {
-        if (lane == 0) {
-          // solve L U y = P x: forward (the row swaps and multipliers) ...
-          for (int i = 0; i < sz - 1; ++i) {
-            if (piv[i] != 0.f) {
-              const float t0 = x[i];
-              x[i] = x[i + 1];
-              x[i + 1] = t0 - lm[i] * x[i];
-            } else {
-              x[i + 1] -= lm[i] * x[i];
-            }
-          }
-          // ... and back substitution with U
-          for (int i = sz - 1; i >= 0; --i) {
-            float r = x[i];
-            if (i + 1 < sz) r -= u1[i] * x[i + 1];
-            if (i + 2 < sz) r -= u2[i] * x[i + 2];
-            x[i] = r / u0[i];
-          }
-        }
-        __syncwarp();
-        float mx = 0.f;
-        for (int i = lane; i < sz; i += 32) mx = fmaxf(mx, fabsf(x[i]));
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        const float inv = mx > 0.f ? 1.f / mx : 1.f;
-        for (int i = lane; i < sz; i += 32) x[i] *= inv;
-        for (int q = m0; q < m; ++q) {
-          float dot = 0.f;
-          for (int i = lane; i < sz; i += 32) dot += Z[(int64_t)(s + i) * ldz + q] * x[i];
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-          for (int i = lane; i < sz; i += 32) x[i] -= dot * Z[(int64_t)(s + i) * ldz + q];
-        }
-        float nrm = 0.f;
-        for (int i = lane; i < sz; i += 32) nrm += x[i] * x[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
-        if (!(nrm > 0.f) && lane == 0) record_error(ctrl, SNE_ERR_NUMERIC, W_EIG);
-        const float rn = nrm > 0.f ? 1.0f / sqrtf(nrm) : 0.f;
-        for (int i = lane; i < sz; i += 32) x[i] *= rn;
-        __syncwarp();
-      }
-      // column m of Z: rows s + i written by the lane that owns i
-      for (int i = lane; i < sz; i += 32) Z[(int64_t)(s + i) * ldz + m] = x[i];
-      for (int i = lane; i < n; i += 32)
-        if (i < s || i > t) Z[(int64_t)i * ldz + m] = 0.f;
-      __syncwarp();
+  for (int c = tid; c < nc; c += blockDim.x)
+    for (int m = cstart[c]; m < cstart[c + 1]; ++m) csz[m] = cstart[c + 1] - cstart[c];
+  __syncthreads();
+  const int64_t n2 = (int64_t)n * n;
+  TriLU f{scratch, scratch + n2, scratch + 2 * n2, scratch + 3 * n2, scratch + 4 * n2};
+  // two inverse-iteration solves per vector from a pseudo-random start
+  for (int m = tid; m < n; m += blockDim.x) {
+    const int b = blk_of[m];
+    const int s = bstart[b], sz = bstart[b + 1] - s;
+    for (int i = 0; i < n; ++i) Z[(int64_t)i * n + m] = 0.f;
+    if (sz == 1) {
+      Z[(int64_t)s * n + m] = 1.f;
+      continue;
     }
+    tri_lu(d, e, s, sz, shift[m], pertol, f, n, m);
+    for (int i = 0; i < sz; ++i) Z[(int64_t)(s + i) * n + m] = hash_unit((uint32_t)m, (uint32_t)i);
+    tri_solve(f, Z, s, sz, n, m);
+    tri_solve(f, Z, s, sz, n, m);
+  }
+  __syncthreads();
+  tri_cluster_mgs(Z, n, cstart, nc, blk_of, bstart, red, ctrl);
+  // a third solve, then orthonormal again (clusters) or normalized (the rest)
+  for (int m = tid; m < n; m += blockDim.x) {
+    const int b = blk_of[m];
+    const int s = bstart[b], sz = bstart[b + 1] - s;
+    if (sz > 1) tri_solve(f, Z, s, sz, n, m);
+  }
+  __syncthreads();
+  tri_cluster_mgs(Z, n, cstart, nc, blk_of, bstart, red, ctrl);
+  for (int m = tid; m < n; m += blockDim.x) {
+    const int b = blk_of[m];
+    const int s = bstart[b], sz = bstart[b + 1] - s;
+    // members of clusters are orthonormal after the cluster pass
+    if (csz[m] > 1 || sz == 1) continue;
+    float nrm = 0.f;
+    for (int i = 0; i < sz; ++i) {
+      const float v = Z[(int64_t)(s + i) * n + m];
+      nrm += v * v;
+    }
+    if (!(nrm > 0.f)) record_error(ctrl, SNE_ERR_NUMERIC, W_EIG);
+    const float rn = nrm > 0.f ? 1.0f / sqrtf(nrm) : 0.f;
+    for (int i = 0; i < sz; ++i) Z[(int64_t)(s + i) * n + m] *= rn;
   }
 }
 
@@ -394,8 +449,9 @@ __global__ void __launch_bounds__(256) tri_backtransform_kernel(const float *__r
 }  // namespace
 
 size_t tri_eig_scratch_floats(int n) {
-  // Hv (n-1 x n-1 rounded to n x n), Z (n x n), d, e, beta, per-warp solve scratch
-  return 2 * (size_t)n * n + 3 * (size_t)n + 32 * 6 * (size_t)n + 64;
+  // Hv (n-1 x n-1 rounded to n x n), Z (n x n), d, e, beta, the LU factors of
+  // every inverse iteration (5 n x n)
+  return 7 * (size_t)n * n + 3 * (size_t)n + 64;
 }
 
 size_t tri_eig_smem(int n) { return ((size_t)n * (n + 1) / 2 + 2 * (size_t)n + 32) * sizeof(float); }
@@ -420,12 +476,9 @@ cudaError_t launch_sym_eig_tridiag(const float *A, int32_t n, int32_t lda, float
   }
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  const size_t iism = (size_t)kIIWarps * 6 * n * sizeof(float);
-  err = cudaFuncSetAttribute(tri_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)iism);
-  if (err != cudaSuccess) return err;
   {
     ProfScope ps_(K_EIG, st);
-    tri_eig_kernel<<<1, 1024, iism, st>>>(d, e, n, w, Z, n, wsc, ctrl);
+    tri_eig_kernel<<<1, 1024, 0, st>>>(d, e, n, w, Z, wsc, ctrl);
   }
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
