@@ -474,6 +474,54 @@ def embed(row_ptr, col_idx, n, params: Params, val=None, U_k=None, lam=None) -> 
 
 
 # ---------------------------------------------------------------------------
+# Alg. 6 line 6: spectral propagation
+# ---------------------------------------------------------------------------
+def propagation_coefficients(steps: int, theta: float) -> np.ndarray:
+    """c_0 .. c_steps of exp(-theta/2 [(lam - mu)^2 - 1]) as a Chebyshev series
+    in x = (lam - mu)^2 / 2 - 1: the filter is exp(-theta/2) exp(-theta x), and
+    exp(-theta x) = I_0(theta) + 2 sum_{r>=1} (-1)^r I_r(theta) T_r(x) on
+    [-1, 1] (the generating function of the modified Bessel functions of the
+    first kind I_r).  Reading of the coefficients the paper leaves to ProNE
+    (Zhang et al., IJCAI 2019: band-pass filter g, Chebyshev expansion with
+    Bessel coefficients)."""
+    import scipy.special
+    r = np.arange(steps + 1)
+    c = 2.0 * (-1.0) ** r * scipy.special.iv(r, theta)
+    c[0] = scipy.special.iv(0, theta)
+    return math.exp(-0.5 * theta) * c
+
+
+def spectral_propagation(A: sp.csr_matrix, E: np.ndarray, steps: int = 10, theta: float = 0.5,
+                         mu: float = 0.2) -> np.ndarray:
+    """Alg. 6 line 6: E <- sum_{r=0..steps} c_r T_r(X) E, the Chebyshev series
+    of g(L) = exp(-theta/2 [(L - mu I)^2 - I]) for the normalized Laplacian
+    L = I - D^-1 A (Sec. 4.3), in the variable X = (L - mu I)^2 / 2 - I, whose
+    spectrum lies in [-1, 1] when 0 <= mu <= 2 (that of L lies in [0, 2]).
+    T_0 = E, T_1 = X E, T_{r+1} = 2 X T_r - T_{r-1}.  Defaults p = 10,
+    theta = 0.5, mu = 0.2 (Sec. 5.2).  Isolated vertices: D^-1 A has a zero
+    row, so their rows are scaled by g(1)."""
+    deg = degrees(A)
+    P = (sp.diags(degree_power(deg, -1.0)) @ A).tocsr()  # D^-1 A
+
+    def M(V):  # (L - mu I) V
+        return (1.0 - mu) * V - P @ V
+
+    def X(V):
+        return 0.5 * M(M(V)) - V
+
+    c = propagation_coefficients(steps, theta)
+    E = np.asarray(E, dtype=np.float64)
+    F = c[0] * E
+    if steps >= 1:
+        T_prev, T_cur = E, X(E)
+        F = F + c[1] * T_cur
+        for r in range(2, steps + 1):
+            T_prev, T_cur = T_cur, 2.0 * X(T_cur) - T_prev
+            F = F + c[r] * T_cur
+    return F
+
+
+# ---------------------------------------------------------------------------
 # Dense references for tiny graphs
 # ---------------------------------------------------------------------------
 def netmf_matrix_dense(A_dense: np.ndarray, T: int, b: float) -> np.ndarray:

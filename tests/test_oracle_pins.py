@@ -453,3 +453,54 @@ def test_factor_rows_equal_full_factors():
     assert np.allclose(Rc, fac.Rp[:, S.p], rtol=1e-10, atol=1e-14 * np.abs(fac.Rp).max())
     Y = o.sketch_Y(fac.Lp, fac.Rp, S)
     assert np.allclose(o.sketch_Y_rows_at(Lr, Rc, S), Y[rows], rtol=1e-10, atol=1e-12)
+
+
+# ---------------------------------------------------------------- spectral propagation (Alg. 6 line 6)
+@pytest.mark.parametrize("steps,theta", [(10, 0.5), (24, 2.0)])
+def test_propagation_coefficients_sum_to_the_exponential(steps, theta):
+    """sum_r c_r T_r(x) = exp(-theta/2) exp(-theta x) on [-1, 1]: the Bessel
+    generating function, truncated where its terms are below rounding."""
+    c = o.propagation_coefficients(steps, theta)
+    x = np.linspace(-1.0, 1.0, 201)
+    got = np.polynomial.chebyshev.chebval(x, c)
+    want = np.exp(-0.5 * theta) * np.exp(-theta * x)
+    assert np.max(np.abs(got - want)) < 1e-12 * want.max()
+
+
+def _filter_dense(A_dense, E, theta, mu):
+    """g(L) E through the spectrum: L = I - D^-1 A = D^-1/2 L_sym D^1/2 with
+    L_sym = I - D^-1/2 A D^-1/2 = V diag(lam) V^T, g applied to lam."""
+    deg = A_dense.sum(axis=1)
+    s = 1.0 / np.sqrt(deg)
+    Ls = np.eye(len(deg)) - s[:, None] * A_dense * s[None, :]
+    lam, V = np.linalg.eigh(Ls)
+    g = np.exp(-0.5 * theta * ((lam - mu) ** 2 - 1.0))
+    return (s[:, None] * V) @ (g[:, None] * (V.T @ (np.sqrt(deg)[:, None] * E)))
+
+
+@pytest.mark.parametrize("theta,mu", [(0.5, 0.2), (1.0, 1.0)])
+def test_spectral_propagation_equals_the_filter_through_the_spectrum(theta, mu):
+    g = synth.sbm(240, 4, 0.1, 0.02, seed=5)
+    A = o.adjacency(g.row_ptr, g.col_idx, g.n)
+    assert np.all(o.degrees(A) > 0)
+    E = np.random.default_rng(0).standard_normal((g.n, 7))
+    want = _filter_dense(A.toarray(), E, theta, mu)
+    got = o.spectral_propagation(A, E, steps=10, theta=theta, mu=mu)
+    assert np.max(np.abs(got - want)) < 1e-10 * np.max(np.abs(want))
+    # no propagation steps: the constant term only
+    got0 = o.spectral_propagation(A, E, steps=0, theta=theta, mu=mu)
+    assert np.allclose(got0, o.propagation_coefficients(0, theta)[0] * E, rtol=0, atol=1e-15)
+
+
+def test_spectral_propagation_isolated_rows_scale_by_g_of_one():
+    """A vertex without edges is an eigenvector of L with eigenvalue 1."""
+    n = 60
+    edges = [(i, (i + 1) % 50) for i in range(50)] + [(i, (i + 7) % 50) for i in range(50)]
+    g = synth.from_edges(n, edges)  # vertices 50..59 isolated
+    A = o.adjacency(g.row_ptr, g.col_idx, g.n)
+    E = np.random.default_rng(1).standard_normal((n, 3))
+    got = o.spectral_propagation(A, E)
+    g1 = math.exp(-0.25 * ((1.0 - 0.2) ** 2 - 1.0))
+    assert np.allclose(got[50:], g1 * E[50:], rtol=1e-13, atol=0)
+    want = _filter_dense(A.toarray()[:50, :50], E[:50], 0.5, 0.2)
+    assert np.max(np.abs(got[:50] - want)) < 1e-10 * np.max(np.abs(want))
