@@ -514,6 +514,12 @@ def run_ours(args, rank: int, world: int) -> None:
                 "peak_source": f"{peak_kind} bf16 dense sustained (FP16 has the same tensor rate)",
                 "ms_per_step": ms}
 
+    # ---- spectral propagation (Alg. 6 line 6) of this run's embedding
+    propagation = None
+    if not args.no_extra:
+        propagation = measure_propagation(sk, G, E, g.n, g.nnz, args.steps, args.warmup, flush,
+                                          peaks, peak_kind)
+
     cpu = None
     accuracy = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -564,6 +570,7 @@ def run_ours(args, rank: int, world: int) -> None:
             "gpu_launches": int(launches),
             "roofline": roofline,
             "mixed": mixed,
+            "propagation": propagation,
             "error_vs_oracle": accuracy,
             "workloads": extra,
             "cpu_baseline": cpu,
@@ -571,6 +578,43 @@ def run_ours(args, rank: int, world: int) -> None:
             "kernel_ms_per_step": {k: v[2] / args.steps for k, v in sorted(prof.items(), key=lambda kv: -kv[1][2])},
         }
         print(json.dumps(line), flush=True)
+
+
+def measure_propagation(sk, G, E, n, nnz, steps, warmup, flush, peaks, peak_kind,
+                        p_steps=10, theta=0.5, mu=0.2) -> dict:
+    """sne_spectral_propagate (p = 10, theta = 0.5, mu = 0.2) of the embedding E,
+    L2 flushed before each call.  Algorithmic bytes of one Chebyshev step (two
+    passes): the CSR arrays and 1/d twice, and 4 n d bytes for each of the
+    operand read and result write of the first pass and the operand read, the
+    two earlier terms, the result write and the read and write of the running
+    sum of the second."""
+    import torch
+    d = E.shape[1]
+    wsp = sk.propagate_workspace(n, d)
+    Ep = torch.empty_like(E)
+    times = []
+    for it in range(warmup + steps):
+        Ep.copy_(E)
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sk.sne_spectral_propagate(G, Ep, wsp, steps=p_steps, theta=theta, mu=mu)
+        e1.record()
+        torch.cuda.synchronize()
+        if it >= warmup:
+            times.append(e0.elapsed_time(e1))
+    sk.check_status(wsp, "propagate")
+    ms = float(np.mean(times))
+    per_step = 2 * (8 * (n + 1) + 4 * nnz + 4 * n) + 8 * 4 * n * d
+    work = p_steps * per_step + 2 * 4 * n * d
+    ach = work / (ms / 1e3) / 1e9
+    peak = float(peaks["hbm_gbs"])
+    del wsp, Ep
+    return {"ms": ms, "steps": p_steps, "theta": theta, "mu": mu, "d": d, "calls_timed": steps,
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                         "frac": ach / peak, "algorithmic_bytes": work, "peak_source": peak_kind}}
 
 
 def workload_params(sk, w, precision="fp32"):

@@ -191,6 +191,36 @@ int sne_spmm_weights(const sne_csr *g, const float *dpow, float *w_nz, sne_strea
 int sne_spmm(const sne_csr *g, const float *dpow, const float *w_nz, const float *B, int32_t ncols,
              float *Y, sne_stream_t stream);
 
+/* Spectral propagation, Alg. 6 line 6 (Sec. 4.3): E <- sum_{r=0..steps}
+ * c_r T_r(X) E with L = I - D^-1 A (the normalized graph Laplacian of
+ * Sec. 4.3) and X = (L - mu I)^2 / 2 - I.  The paper names c_r "coefficients
+ * of Chebyshev polynomials" and takes p = 10, theta = 0.5, mu = 0.2 (Sec. 5.2)
+ * from ProNE without printing them; here they are those of ProNE's band-pass
+ * filter g(lambda) = exp(-theta/2 [(lambda - mu)^2 - 1]):
+ * c_0 = e^(-theta/2) I_0(theta), c_r = 2 e^(-theta/2) (-1)^r I_r(theta), with
+ * I_r the modified Bessel functions of the first kind (the Chebyshev series
+ * of exp(-theta x) on [-1, 1]).
+ *
+ * sne_propagation_coefficients: host only; writes c_0 .. c_steps (steps + 1
+ * doubles) to c.  SNE_ERR_ARG for c == NULL, steps outside [0, 1000], theta
+ * negative or not finite.
+ *
+ * sne_spectral_propagate: E (device, n x d FP32, row-major, leading dimension
+ * lde >= d, caller-owned) is replaced by the propagated embedding.  Each step
+ * is two SpMMs by D^-1 A at width d (a vertex without edges is scaled by
+ * g(1)); FP32 arithmetic.  The workspace (device, 256-byte aligned, at least
+ * sne_spectral_propagate_workspace_bytes bytes, caller-owned) holds the status
+ * word, 1/d and four n x d buffers.  Errors: SNE_ERR_ARG (graph or pointer
+ * missing, d outside [1, 1024], lde < d, steps outside [0, 1000], theta < 0,
+ * mu outside [0, 2]), SNE_ERR_SIZE (n above the int32 range),
+ * SNE_ERR_WORKSPACE, SNE_ERR_CUDA (a launch or copy failed).  Stream-ordered;
+ * nothing is synchronized. */
+int sne_propagation_coefficients(int32_t steps, double theta, double *c);
+int sne_spectral_propagate_workspace_bytes(int64_t n, int32_t d, size_t *bytes);
+int sne_spectral_propagate(const sne_csr *g, int32_t steps, double theta, double mu, float *E,
+                           int64_t lde, int32_t d, void *workspace, size_t ws_bytes,
+                           sne_stream_t stream);
+
 /* Checks the CSR on the device (monotone row_ptr, indices in range, symmetric
  * pattern and weights) and records SNE_ERR_GRAPH in the workspace status word
  * (any workspace of at least 256 bytes).  Read the result with sne_status(). */

@@ -204,6 +204,9 @@ size_t carve(const Dims &D, int mode, void *base, Bufs *b) {
     if (e__ != cudaSuccess) return SNE_ERR_CUDA; \
   } while (0)
 
+constexpr int kMaxPropagationSteps = 1000;
+constexpr int kMaxPropagationWidth = 1024;
+
 int check_graph(const sne_csr *g) {
   if (!g || g->n <= 0 || g->nnz < 0 || !g->row_ptr || (g->nnz > 0 && !g->col_idx))
     return SNE_ERR_ARG;
@@ -656,6 +659,32 @@ int sne_validate_csr(const sne_csr *g, void *ws, size_t ws_bytes, sne_stream_t s
   return launch_validate(*g, reinterpret_cast<Ctrl *>(ws), (cudaStream_t)stream) == cudaSuccess
              ? SNE_OK
              : SNE_ERR_CUDA;
+}
+
+int sne_propagation_coefficients(int32_t steps, double theta, double *c) {
+  if (!c || steps < 0 || steps > kMaxPropagationSteps || !(theta >= 0.0) || !std::isfinite(theta))
+    return SNE_ERR_ARG;
+  propagation_coefficients(steps, theta, c);
+  return SNE_OK;
+}
+
+int sne_spectral_propagate_workspace_bytes(int64_t n, int32_t d, size_t *bytes) {
+  if (!bytes || n <= 0 || d <= 0 || d > kMaxPropagationWidth) return SNE_ERR_ARG;
+  *bytes = propagate_workspace_bytes(n, d);
+  return SNE_OK;
+}
+
+int sne_spectral_propagate(const sne_csr *g, int32_t steps, double theta, double mu, float *E,
+                           int64_t lde, int32_t d, void *ws, size_t ws_bytes, sne_stream_t stream) {
+  int rc = check_graph(g);
+  if (rc) return rc;
+  if (!E || d <= 0 || d > kMaxPropagationWidth || lde < d || steps < 0 ||
+      steps > kMaxPropagationSteps || !(theta >= 0.0) || !std::isfinite(theta) || !(mu >= 0.0) ||
+      !(mu <= 2.0))
+    return SNE_ERR_ARG;
+  rc = check_ws(ws, ws_bytes, propagate_workspace_bytes(g->n, d));
+  if (rc) return rc;
+  return run_propagate(*g, steps, theta, mu, E, lde, d, ws, (cudaStream_t)stream);
 }
 
 int sne_freigs(const sne_csr *g, const sne_params *p, void *ws, size_t ws_bytes, float *U,

@@ -38,7 +38,7 @@ cudaEvent_t take_event() {
 const char *kClassNames[K_COUNT] = {"spmm",   "gram",  "tall_gemm", "small_gemm", "sym_eig",
                                     "cholesky", "triu_inverse", "fused_sketch", "gather",
                                     "rng", "unique", "misc", "fused_sketch_tc", "gram_tc",
-                                    "tall_gemm_tc"};
+                                    "tall_gemm_tc", "propagate"};
 }  // namespace
 
 int sm_count() {

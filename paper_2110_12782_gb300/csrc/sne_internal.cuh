@@ -55,7 +55,7 @@ __device__ __forceinline__ void record_error(Ctrl *c, int32_t code, int32_t wher
 // ---------------------------------------------------------------------------
 enum KClass : int {
   K_SPMM = 0, K_GRAM, K_TALL_GEMM, K_SMALL_GEMM, K_EIG, K_CHOL, K_TRIINV, K_FUSED, K_GATHER, K_RNG,
-  K_UNIQUE, K_MISC, K_FUSED_TC, K_GRAM_TC, K_TALL_TC, K_COUNT
+  K_UNIQUE, K_MISC, K_FUSED_TC, K_GRAM_TC, K_TALL_TC, K_PROP, K_COUNT
 };
 class ProfScope {
  public:
@@ -268,5 +268,14 @@ cudaError_t launch_signed_gather_sum64(const float *In, int64_t ldi, int32_t wid
 cudaError_t launch_signed_gather_sum(const float *In, int64_t ldi, int32_t width, const int32_t *idx,
                                      const int8_t *sign, int32_t cols, int32_t z, float sv,
                                      float *out, int64_t ldo, cudaStream_t st);
+
+// Spectral propagation (propagate.cu): c_0 .. c_steps of the filter's
+// Chebyshev series, the workspace of run_propagate, and the run itself (E in
+// place, n x d with leading dimension lde).
+double bessel_i(int r, double theta);
+void propagation_coefficients(int steps, double theta, double *c);
+size_t propagate_workspace_bytes(int64_t n, int32_t d);
+int run_propagate(const sne_csr &g, int steps, double theta, double mu, float *E, int64_t lde, int d,
+                  void *ws, cudaStream_t st);
 
 }  // namespace sne

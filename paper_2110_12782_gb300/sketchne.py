@@ -14,6 +14,7 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
 import torch
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -43,7 +44,8 @@ EXPORTS = [
     "sne_profile_stop", "sne_freigs_static", "sne_gram_workspace_bytes", "sne_gram",
     "sne_tall_gemm_workspace_bytes", "sne_tall_gemm", "sne_sym_eig_workspace_bytes", "sne_sym_eig",
     "sne_embed_batched_workspace_bytes", "sne_embed_batched", "sne_chol_inverse_workspace_bytes",
-    "sne_chol_inverse",
+    "sne_chol_inverse", "sne_propagation_coefficients", "sne_spectral_propagate_workspace_bytes",
+    "sne_spectral_propagate",
 ]
 
 
@@ -122,6 +124,10 @@ def lib() -> ctypes.CDLL:
             "sne_sym_eig": [i32, vp, i32, vp, vp, i32, vp, ctypes.c_size_t, vp],
             "sne_chol_inverse_workspace_bytes": [i32, i32, P(ctypes.c_size_t)],
             "sne_chol_inverse": [i32, vp, i32, vp, i32, i32, dbl, vp, ctypes.c_size_t, vp],
+            "sne_propagation_coefficients": [i32, dbl, vp],
+            "sne_spectral_propagate_workspace_bytes": [i64, i32, P(ctypes.c_size_t)],
+            "sne_spectral_propagate": [P(sne_csr), i32, dbl, dbl, vp, i64, i32, vp,
+                                       ctypes.c_size_t, vp],
             "sne_embed_batched_workspace_bytes": [i32, P(sne_csr), P(sne_params), i32,
                                                   P(ctypes.c_size_t)],
             "sne_embed_batched": [i32, P(sne_csr), P(sne_params), i32, vp, ctypes.c_size_t,
@@ -272,6 +278,31 @@ def sne_spmm(g: DeviceGraph, dpow: torch.Tensor, B: torch.Tensor, Y: torch.Tenso
     _check(lib().sne_spmm(ctypes.byref(g.csr), _ptr(dpow, torch.float32, "dpow"),
                           _ptr(w_nz, torch.float32, "w_nz", True), _ptr(B, torch.float32, "B"),
                           B.shape[1], _ptr(Y, torch.float32, "Y"), _stream(stream)), "sne_spmm")
+
+
+def sne_propagation_coefficients(steps: int = 10, theta: float = 0.5) -> np.ndarray:
+    """c_0 .. c_steps of the spectral-propagation filter (host only)."""
+    c = np.zeros(steps + 1, dtype=np.float64)
+    _check(lib().sne_propagation_coefficients(steps, theta, c.ctypes.data), "sne_propagation_coefficients")
+    return c
+
+
+def propagate_workspace(n: int, d: int, device="cuda") -> torch.Tensor:
+    nb = ctypes.c_size_t(0)
+    _check(lib().sne_spectral_propagate_workspace_bytes(n, d, ctypes.byref(nb)),
+           "sne_spectral_propagate_workspace_bytes")
+    return _aligned_bytes(nb.value, device)
+
+
+def sne_spectral_propagate(g: DeviceGraph, E: torch.Tensor, ws: torch.Tensor, steps: int = 10,
+                           theta: float = 0.5, mu: float = 0.2, stream=None) -> None:
+    """Alg. 6 line 6 on the CUDA FP32 row-major E (n x d), in place."""
+    if E.dim() != 2 or E.stride(1) != 1:
+        raise ValueError("E must be a row-major matrix")
+    _check(lib().sne_spectral_propagate(ctypes.byref(g.csr), steps, theta, mu,
+                                        _ptr(E, torch.float32, "E"), E.stride(0), E.shape[1],
+                                        _ptr(ws, torch.uint8, "workspace"), ws.numel(),
+                                        _stream(stream)), "sne_spectral_propagate")
 
 
 def sne_validate_csr(g: DeviceGraph, ws: torch.Tensor, stream=None) -> None:

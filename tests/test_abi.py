@@ -196,3 +196,44 @@ def test_pair_precision_rejects_k_beyond_the_resident_tile(L):
             with pytest.raises(sk.SketchNEError) as e:
                 sk.sne_workspace_bytes(100_000, 1_000_000, q, sk.SNE_WS_SKETCH)
             assert e.value.code == sk.SNE_ERR_SIZE
+
+
+def test_propagation_coefficients_match_the_oracle_on_the_host(L):
+    """The library's host-side Bessel series (Alg. 6 line 6 coefficients)
+    against the oracle's, which calls SciPy's modified Bessel functions."""
+    import numpy as np
+    from oracle import sketchne_oracle as o
+    for steps, theta in ((10, 0.5), (0, 0.5), (30, 4.0), (5, 0.0)):
+        got = sk.sne_propagation_coefficients(steps, theta)
+        want = o.propagation_coefficients(steps, theta)
+        assert np.allclose(got, want, rtol=1e-14, atol=1e-300), (steps, theta)
+    c = (ctypes.c_double * 4)()
+    ARG = sk.SNE_ERR_ARG
+    assert L.sne_propagation_coefficients(-1, 0.5, c) == ARG
+    assert L.sne_propagation_coefficients(1001, 0.5, c) == ARG
+    assert L.sne_propagation_coefficients(3, -0.1, c) == ARG
+    assert L.sne_propagation_coefficients(3, float("nan"), c) == ARG
+    assert L.sne_propagation_coefficients(3, 0.5, None) == ARG
+
+
+def test_spectral_propagate_argument_errors_on_the_host(L):
+    ARG, WS = sk.SNE_ERR_ARG, sk.SNE_ERR_WORKSPACE
+    nb = ctypes.c_size_t(0)
+    assert L.sne_spectral_propagate_workspace_bytes(1000, 32, ctypes.byref(nb)) == 0
+    assert L.sne_spectral_propagate_workspace_bytes(1000, 1025, ctypes.byref(nb)) == ARG
+    assert L.sne_spectral_propagate_workspace_bytes(1000, 32, ctypes.byref(nb)) == 0
+    need = nb.value
+    g = sk.sne_csr(1000, 10, 1 << 20, 1 << 21, None)
+    E = 1 << 22
+    call = lambda steps=10, theta=0.5, mu=0.2, e=E, lde=32, d=32, ws=256, nbytes=need: \
+        L.sne_spectral_propagate(ctypes.byref(g), steps, theta, mu, e, lde, d, ws, nbytes, None)
+    assert call(steps=-1) == ARG
+    assert call(steps=1001) == ARG
+    assert call(theta=-1.0) == ARG
+    assert call(mu=2.5) == ARG
+    assert call(mu=-0.1) == ARG
+    assert call(lde=31) == ARG
+    assert call(e=None) == ARG
+    assert call(ws=None) == WS
+    assert call(ws=257) == WS
+    assert call(nbytes=need - 1) == WS
