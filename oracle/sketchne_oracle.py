@@ -40,7 +40,8 @@ starts at s is mix64(s + i * 0x9E3779B97F4A7C15).  Bounded integers use
 Lemire's multiply-shift with rejection ("Fast random integer generation in an
 interval", ACM TOMACS 2019); Gaussians use the Box-Muller transform on 24-bit
 uniforms.  Stream ids: 1 = Omega (Alg. 5), 2 = S (Alg. 4 line 3),
-3 = O (Alg. 4 line 6).
+3 = O (Alg. 4 line 6), 4 = C and 5 = H (the general single-pass SVD of
+Eqs. 5-10).
 """
 from __future__ import annotations
 
@@ -61,6 +62,8 @@ MIX2 = 0x94D049BB133111EB
 STREAM_OMEGA = 1
 STREAM_S = 2
 STREAM_O = 3
+STREAM_C = 4
+STREAM_H = 5
 
 
 def mix64(z: int) -> int:
@@ -414,6 +417,45 @@ def single_pass_svd(Lp: np.ndarray, Rp: np.ndarray, d: int, h: int, l: int, zeta
     W = Wt.T
     Uh, sig, _ = np.linalg.svd(W)
     return SinglePassResult(U=Q @ Uh[:, :d], sigma=sig[:d], Y=Y, Q=Q, Z=Z, W=W, S=S, O=O)
+
+
+@dataclasses.dataclass
+class GeneralSinglePassResult:
+    U: np.ndarray      # n x d, left singular vectors
+    sigma: np.ndarray  # d
+    V: np.ndarray      # m x d, right singular vectors
+    Y: np.ndarray
+    K: np.ndarray
+    Z: np.ndarray
+    W: np.ndarray
+
+
+def single_pass_svd_general(L: np.ndarray, Rt: np.ndarray, d: int, h: int, l: int, zeta: int,
+                            seed: int, f=trunc_log) -> GeneralSinglePassResult:
+    """Eqs. 5-10 (Sec. 4.1) for a general, not necessarily symmetric or square,
+    f(L R) with L n x k and R = Rt^T k x m: sparse-sign C (n x h), S (m x h),
+    H (n x l), O (m x l) (Alg. 3; random streams 4, 2, 5, 3);
+    K = f(LR)^T C, Y = f(LR) S, Z = H^T f(LR) O (Eq. 5); P = orth(K),
+    Q = orth(Y) (Eq. 6); W = (H^T Q)^+ Z (P^T O)^+ (Eq. 9), taken as two
+    least-squares solves; svd(W) = U_w Sigma V_w^T, f(LR) ~ (Q U_w) Sigma
+    (P V_w)^T (Eq. 10), the leading d triplets."""
+    n, m = L.shape[0], Rt.shape[0]
+    C = gen_sparse_sign(n, h, zeta, seed, STREAM_C)
+    S = gen_sparse_sign(m, h, zeta, seed, STREAM_S)
+    H = gen_sparse_sign(n, l, zeta, seed, STREAM_H)
+    O = gen_sparse_sign(m, l, zeta, seed, STREAM_O)
+    Y = f(L @ Rt[S.p].T) @ S.rows_at_p()
+    K = f(Rt @ L[C.p].T) @ C.rows_at_p()
+    Z = H.rows_at_p().T @ f(L[H.p] @ Rt[O.p].T) @ O.rows_at_p()
+    P, _ = np.linalg.qr(K)
+    Q, _ = np.linalg.qr(Y)
+    HQ = H.rows_at_p().T @ Q[H.p]     # H^T Q, l x h
+    OP = O.rows_at_p().T @ P[O.p]     # O^T P = (P^T O)^T, l x h
+    Tm = np.linalg.lstsq(HQ, Z, rcond=None)[0]          # (H^T Q) T = Z
+    W = np.linalg.lstsq(OP, Tm.T, rcond=None)[0].T      # W (P^T O) = T
+    Uw, sig, Vwt = np.linalg.svd(W)
+    return GeneralSinglePassResult(U=Q @ Uw[:, :d], sigma=sig[:d], V=P @ Vwt.T[:, :d], Y=Y, K=K, Z=Z,
+                                   W=W)
 
 
 # ---------------------------------------------------------------------------

@@ -504,3 +504,42 @@ def test_spectral_propagation_isolated_rows_scale_by_g_of_one():
     assert np.allclose(got[50:], g1 * E[50:], rtol=1e-13, atol=0)
     want = _filter_dense(A.toarray()[:50, :50], E[:50], 0.5, 0.2)
     assert np.max(np.abs(got[:50] - want)) < 1e-10 * np.max(np.abs(want))
+
+
+# ---------------------------------------------------------------- general single-pass SVD (Eqs. 5-10)
+@pytest.mark.parametrize("n,m,k", [(400, 300, 12), (250, 250, 20)])
+def test_general_single_pass_recovers_a_low_rank_product_exactly(n, m, k):
+    """With f the identity and rank(LR) = k <= h, the sketches span the row
+    and column spaces, and Eq. 10 reproduces LR and its SVD (to rounding)."""
+    rng = np.random.default_rng(n + k)
+    L = rng.standard_normal((n, k))
+    Rt = rng.standard_normal((m, k)) * np.linspace(1.0, 0.05, k)[None, :]
+    M = L @ Rt.T
+    r = o.single_pass_svd_general(L, Rt, d=k, h=k + 6, l=k + 40, zeta=8, seed=3, f=o.identity)
+    ref = np.linalg.svd(M, compute_uv=False)[:k]
+    assert np.allclose(r.sigma, ref, rtol=1e-9)
+    assert np.allclose((r.U * r.sigma) @ r.V.T, M, atol=1e-9 * np.abs(M).max())
+    assert np.allclose(r.U.T @ r.U, np.eye(k), atol=1e-10)
+    assert np.allclose(r.V.T @ r.V, np.eye(k), atol=1e-10)
+
+
+def test_general_single_pass_trunc_log_against_dense_svd():
+    """f = trunc_log of a rectangular product whose result has a decaying
+    spectrum: the leading singular values within the randomized-sketch error
+    of the dense SVD, and the sketches equal their definitions (Eq. 5) with
+    dense sparse-sign matrices."""
+    rng = np.random.default_rng(9)
+    n, m, k = 300, 200, 6
+    L = np.abs(rng.standard_normal((n, k))) * 1.5
+    Rt = np.abs(rng.standard_normal((m, k)))
+    F = o.trunc_log(L @ Rt.T)
+    r = o.single_pass_svd_general(L, Rt, d=4, h=40, l=160, zeta=8, seed=1, f=o.trunc_log)
+    ref = np.linalg.svd(F, compute_uv=False)
+    assert np.allclose(r.sigma, ref[:4], rtol=2e-2)
+    C = o.gen_sparse_sign(n, 40, 8, 1, o.STREAM_C).dense()
+    S = o.gen_sparse_sign(m, 40, 8, 1, o.STREAM_S).dense()
+    H = o.gen_sparse_sign(n, 160, 8, 1, o.STREAM_H).dense()
+    O = o.gen_sparse_sign(m, 160, 8, 1, o.STREAM_O).dense()
+    assert np.allclose(r.Y, F @ S)
+    assert np.allclose(r.K, F.T @ C)
+    assert np.allclose(r.Z, H.T @ F @ O)
