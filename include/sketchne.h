@@ -191,6 +191,29 @@ int sne_spmm_weights(const sne_csr *g, const float *dpow, float *w_nz, sne_strea
 int sne_spmm(const sne_csr *g, const float *dpow, const float *w_nz, const float *B, int32_t ncols,
              float *Y, sne_stream_t stream);
 
+/* The general randomized single-pass SVD of Eqs. 5-10 (Sec. 4.1) for a
+ * rectangular f(L R), not necessarily symmetric: L n x k and Rt = R^T m x k
+ * (device, FP32, row-major, leading dimensions ldl, ldr >= k, caller-owned),
+ * f = p->f (trunc_log or the identity).  With sparse-sign C (n x h),
+ * S (m x h), H (n x l), O (m x l) drawn by Alg. 3 from p->seed (streams 4, 2,
+ * 5, 3): K = f(LR)^T C, Y = f(LR) S, Z = H^T f(LR) O (Eq. 5); P = orth(K),
+ * Q = orth(Y) (Eq. 6); W = (H^T Q)^+ Z (P^T O)^+ (Eq. 9); svd(W) =
+ * U_w Sigma V_w^T and f(LR) ~ (Q U_w) Sigma (P V_w)^T (Eq. 10).  Writes the
+ * leading d = p->d triplets: U (n x d, ldu), sigma (d, FP64, descending),
+ * V (m x d, ldv), all device and caller-owned; U or V may be NULL.  Uses
+ * p->d, h, l, zeta, seed and f only (the sketch sizes need d <= h <= l,
+ * h <= min(n, m), h <= 320).  FP32 sketches, FP64 small solves.  The
+ * workspace (device, 256-byte aligned, sne_single_pass_svd_workspace_bytes)
+ * is caller-owned; the unique rows of H are counted in the stats' v_o.
+ * Errors: SNE_ERR_ARG, SNE_ERR_SIZE, SNE_ERR_WORKSPACE, SNE_ERR_CUDA on the
+ * host; numerical failures in the workspace status word. */
+int sne_single_pass_svd_workspace_bytes(int64_t n, int64_t m, int32_t k, const sne_params *p,
+                                        size_t *bytes);
+int sne_single_pass_svd(int64_t n, int64_t m, int32_t k, const float *L, int64_t ldl,
+                        const float *Rt, int64_t ldr, const sne_params *p, void *workspace,
+                        size_t ws_bytes, float *U, int64_t ldu, double *sigma, float *V,
+                        int64_t ldv, sne_stream_t stream);
+
 /* Spectral propagation, Alg. 6 line 6 (Sec. 4.3): E <- sum_{r=0..steps}
  * c_r T_r(X) E with L = I - D^-1 A (the normalized graph Laplacian of
  * Sec. 4.3) and X = (L - mu I)^2 / 2 - I.  The paper names c_r "coefficients

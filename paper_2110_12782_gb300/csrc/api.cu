@@ -661,6 +661,41 @@ int sne_validate_csr(const sne_csr *g, void *ws, size_t ws_bytes, sne_stream_t s
              : SNE_ERR_CUDA;
 }
 
+static int general_check(int64_t n, int64_t m, int32_t k, const sne_params *p) {
+  if (!p || n <= 0 || m <= 0 || k <= 0 || p->d <= 0 || p->h <= 0 || p->l <= 0 || p->zeta <= 0)
+    return SNE_ERR_ARG;
+  if (p->f != SNE_F_TRUNC_LOG && p->f != SNE_F_IDENTITY) return SNE_ERR_ARG;
+  if (n > (int64_t)INT32_MAX - 1 || m > (int64_t)INT32_MAX - 1 || k > 4096) return SNE_ERR_SIZE;
+  const int64_t zn = std::min<int64_t>(n, p->zeta), zm = std::min<int64_t>(m, p->zeta);
+  if (zn > 64 || zm > 64) return SNE_ERR_SIZE;
+  if (p->d > p->h || p->h > p->l || p->h > std::min(n, m) || p->h > kFastEigMaxN) return SNE_ERR_SIZE;
+  if ((int64_t)p->l * zn > kUniqueMax || (int64_t)p->l * zm > kUniqueMax) return SNE_ERR_SIZE;
+  return SNE_OK;
+}
+
+int sne_single_pass_svd_workspace_bytes(int64_t n, int64_t m, int32_t k, const sne_params *p,
+                                        size_t *bytes) {
+  if (!bytes) return SNE_ERR_ARG;
+  const int rc = general_check(n, m, k, p);
+  if (rc) return rc;
+  *bytes = general_workspace_bytes(n, m, k, p->d, p->h, p->l, p->zeta);
+  return SNE_OK;
+}
+
+int sne_single_pass_svd(int64_t n, int64_t m, int32_t k, const float *L, int64_t ldl,
+                        const float *Rt, int64_t ldr, const sne_params *p, void *ws,
+                        size_t ws_bytes, float *U, int64_t ldu, double *sigma, float *V,
+                        int64_t ldv, sne_stream_t stream) {
+  int rc = general_check(n, m, k, p);
+  if (rc) return rc;
+  if (!L || !Rt || !sigma || ldl < k || ldr < k || (U && ldu < p->d) || (V && ldv < p->d))
+    return SNE_ERR_ARG;
+  rc = check_ws(ws, ws_bytes, general_workspace_bytes(n, m, k, p->d, p->h, p->l, p->zeta));
+  if (rc) return rc;
+  return run_general_svd(n, m, k, L, ldl, Rt, ldr, *p, ws, U, ldu, sigma, V, ldv,
+                         (cudaStream_t)stream);
+}
+
 int sne_propagation_coefficients(int32_t steps, double theta, double *c) {
   if (!c || steps < 0 || steps > kMaxPropagationSteps || !(theta >= 0.0) || !std::isfinite(theta))
     return SNE_ERR_ARG;

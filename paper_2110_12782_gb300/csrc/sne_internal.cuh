@@ -278,4 +278,13 @@ size_t propagate_workspace_bytes(int64_t n, int32_t d);
 int run_propagate(const sne_csr &g, int steps, double theta, double mu, float *E, int64_t lde, int d,
                   void *ws, cudaStream_t st);
 
+// The general single-pass SVD of Eqs. 5-10 (general.cu): workspace bytes and
+// the run (L n x k, Rt = R^T m x k, outputs U n x d, sigma d (FP64), V m x d;
+// U or V may be NULL).
+size_t general_workspace_bytes(int64_t n, int64_t m, int32_t k, int32_t d, int32_t h, int32_t l,
+                               int32_t zeta);
+int run_general_svd(int64_t n, int64_t m, int32_t k, const float *L, int64_t ldl, const float *Rt,
+                    int64_t ldr, const sne_params &p, void *ws, float *U, int64_t ldu, double *sigma,
+                    float *V, int64_t ldv, cudaStream_t st);
+
 }  // namespace sne

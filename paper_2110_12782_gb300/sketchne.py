@@ -45,7 +45,7 @@ EXPORTS = [
     "sne_tall_gemm_workspace_bytes", "sne_tall_gemm", "sne_sym_eig_workspace_bytes", "sne_sym_eig",
     "sne_embed_batched_workspace_bytes", "sne_embed_batched", "sne_chol_inverse_workspace_bytes",
     "sne_chol_inverse", "sne_propagation_coefficients", "sne_spectral_propagate_workspace_bytes",
-    "sne_spectral_propagate",
+    "sne_spectral_propagate", "sne_single_pass_svd_workspace_bytes", "sne_single_pass_svd",
 ]
 
 
@@ -124,6 +124,10 @@ def lib() -> ctypes.CDLL:
             "sne_sym_eig": [i32, vp, i32, vp, vp, i32, vp, ctypes.c_size_t, vp],
             "sne_chol_inverse_workspace_bytes": [i32, i32, P(ctypes.c_size_t)],
             "sne_chol_inverse": [i32, vp, i32, vp, i32, i32, dbl, vp, ctypes.c_size_t, vp],
+            "sne_single_pass_svd_workspace_bytes": [i64, i64, i32, P(sne_params),
+                                                    P(ctypes.c_size_t)],
+            "sne_single_pass_svd": [i64, i64, i32, vp, i64, vp, i64, P(sne_params), vp,
+                                    ctypes.c_size_t, vp, i64, vp, vp, i64, vp],
             "sne_propagation_coefficients": [i32, dbl, vp],
             "sne_spectral_propagate_workspace_bytes": [i64, i32, P(ctypes.c_size_t)],
             "sne_spectral_propagate": [P(sne_csr), i32, dbl, dbl, vp, i64, i32, vp,
@@ -278,6 +282,31 @@ def sne_spmm(g: DeviceGraph, dpow: torch.Tensor, B: torch.Tensor, Y: torch.Tenso
     _check(lib().sne_spmm(ctypes.byref(g.csr), _ptr(dpow, torch.float32, "dpow"),
                           _ptr(w_nz, torch.float32, "w_nz", True), _ptr(B, torch.float32, "B"),
                           B.shape[1], _ptr(Y, torch.float32, "Y"), _stream(stream)), "sne_spmm")
+
+
+def single_pass_svd_workspace(n: int, m: int, k: int, p: sne_params, device="cuda") -> torch.Tensor:
+    nb = ctypes.c_size_t(0)
+    _check(lib().sne_single_pass_svd_workspace_bytes(n, m, k, ctypes.byref(p), ctypes.byref(nb)),
+           "sne_single_pass_svd_workspace_bytes")
+    return _aligned_bytes(nb.value, device)
+
+
+def sne_single_pass_svd(L: torch.Tensor, Rt: torch.Tensor, p: sne_params, ws: torch.Tensor,
+                        U: torch.Tensor | None, sigma: torch.Tensor, V: torch.Tensor | None,
+                        stream=None) -> None:
+    """Eqs. 5-10 for f(L Rt^T): L (n x k), Rt (m x k) row-major CUDA float32;
+    U (n x d), V (m x d) float32 or None, sigma (d) float64."""
+    for t, nm in ((L, "L"), (Rt, "Rt")):
+        if t.dim() != 2 or t.stride(1) != 1:
+            raise ValueError(f"{nm} must be a row-major matrix")
+    if L.shape[1] != Rt.shape[1]:
+        raise ValueError("L and Rt need the same number of columns")
+    _check(lib().sne_single_pass_svd(
+        L.shape[0], Rt.shape[0], L.shape[1], _ptr(L, torch.float32, "L"), L.stride(0),
+        _ptr(Rt, torch.float32, "Rt"), Rt.stride(0), ctypes.byref(p), _ptr(ws, torch.uint8, "workspace"),
+        ws.numel(), _ptr(U, torch.float32, "U", True), U.stride(0) if U is not None else 0,
+        _ptr(sigma, torch.float64, "sigma"), _ptr(V, torch.float32, "V", True),
+        V.stride(0) if V is not None else 0, _stream(stream)), "sne_single_pass_svd")
 
 
 def sne_propagation_coefficients(steps: int = 10, theta: float = 0.5) -> np.ndarray:

@@ -237,3 +237,29 @@ def test_spectral_propagate_argument_errors_on_the_host(L):
     assert call(ws=None) == WS
     assert call(ws=257) == WS
     assert call(nbytes=need - 1) == WS
+
+
+def test_single_pass_svd_argument_errors_on_the_host(L):
+    ARG, SIZE, WS = sk.SNE_ERR_ARG, sk.SNE_ERR_SIZE, sk.SNE_ERR_WORKSPACE
+    p = sk.sne_params_init(16, 32)
+    p.h, p.l = 24, 200
+    nb = ctypes.c_size_t(0)
+    assert L.sne_single_pass_svd_workspace_bytes(5000, 3000, 32, ctypes.byref(p), ctypes.byref(nb)) == 0
+    need = nb.value
+    assert L.sne_single_pass_svd_workspace_bytes(0, 3000, 32, ctypes.byref(p), ctypes.byref(nb)) == ARG
+    q = sk.sne_params_init(16, 32)
+    q.h, q.l = 12, 200                              # d > h
+    assert L.sne_single_pass_svd_workspace_bytes(5000, 3000, 32, ctypes.byref(q), ctypes.byref(nb)) == SIZE
+    q.h, q.l = 24, 20                               # h > l
+    assert L.sne_single_pass_svd_workspace_bytes(5000, 3000, 32, ctypes.byref(q), ctypes.byref(nb)) == SIZE
+    q.h, q.l = 400, 1000                            # h beyond the small eigensolver
+    assert L.sne_single_pass_svd_workspace_bytes(5000, 3000, 32, ctypes.byref(q), ctypes.byref(nb)) == SIZE
+    A, B, U, S, V = 1 << 20, 1 << 21, 1 << 22, 1 << 23, 1 << 24
+    call = lambda ldl=32, ldr=32, ldu=16, ldv=16, s=S, ws=256, nbytes=need: L.sne_single_pass_svd(
+        5000, 3000, 32, A, ldl, B, ldr, ctypes.byref(p), ws, nbytes, U, ldu, s, V, ldv, None)
+    assert call(ldl=31) == ARG
+    assert call(ldr=31) == ARG
+    assert call(ldu=15) == ARG
+    assert call(s=None) == ARG
+    assert call(ws=None) == WS
+    assert call(nbytes=need - 1) == WS
