@@ -354,7 +354,7 @@ int run_freigs(const sne_csr &g, const sne_params &p, const Dims &D, const Bufs 
   float *Q = b.A, *T1 = b.B, *T2 = b.C;
   CK(launch_degree_power(b.deg, D.n, -p.alpha, b.dpow, 1.0f, st));
   CK(launch_spmm_weights(g, b.dpow, b.wnz, st));                  // d_j^-alpha a_ij per nonzero
-  CK(launch_spmm_hot_threshold(b.dpow, D.n, (int64_t)K * 4, b.ctrl, st));  // rows kept in L2
+  CK(launch_spmm_hot_threshold(b.dpow, D.n, spmm_row_bytes(D.n, K), b.ctrl, st));  // rows kept in L2
   const uint32_t *hot = &b.ctrl->hot_bits;
   CK(launch_gaussian(D.n, K, p.seed, 1, T1, ld, st));              // Omega
   CK(launch_spmm(g, b.dpow, b.wnz, T1, ld, K, T2, K, st, hot));   // Y = X Omega

@@ -186,64 +186,92 @@ __global__ void __launch_bounds__(256, 2) spmm_vec4_kernel(
   }
 }
 
-// Column-blocked SpMM for operands larger than L2: Y[:, cb] = X B[:, cb] for
-// column blocks of CB = 4 * LPN columns, one block after the other
-// (blockIdx.y; the hardware dispatches the CTAs of one block before the next),
-// so that the gathered rows of one column block (n * CB * 4 bytes, 64 MB at
-// n = 10^6 and CB = 16) stay in L2 while the CSR arrays and the outputs stream
-// past evict-first.  Every row of B is then read from DRAM once per SpMM
-// instead of once per L2 miss of its deg(j) gathers.  One warp per row: the 32
-// lanes form 32 / LPN groups, each gathering the CB-column segment of a
-// different nonzero as LPN float4 (two nonzeros per group in flight), and the
-// groups' partial sums are added by shuffles at the end of the row.
-template <int LPN>
-__global__ void __launch_bounds__(256) spmm_colblock_kernel(
+// Column-panel SpMM for operands larger than L2: Y[:, panel] = X B[:, panel]
+// for P panels of nqp float4 columns each, one panel after the other
+// (blockIdx.y; the hardware dispatches the CTAs of one panel before the next),
+// so that the L2 holds P times as many rows of the panel as of whole rows:
+// a row j of B is gathered deg(j) times, and on power-law graphs the share of
+// those gathers that land on the rows L2 keeps grows with the number of rows
+// it keeps.  The CSR arrays are read once per panel.  One warp per row; the 32
+// lanes form G = 32 / L groups of L lanes, each group gathering the panel
+// segment of a different nonzero (V float4 per lane, two nonzeros per group in
+// flight); the groups' partial sums are added by shuffles at the end of the
+// row.
+template <int L, int V>
+__global__ void __launch_bounds__(256) spmm_panel_kernel(
     int64_t n, const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
     const float *__restrict__ val, const float *__restrict__ dpow, const float *__restrict__ wnz,
-    const float *__restrict__ B, int64_t ldb, float *__restrict__ Y, int64_t ldy) {
-  constexpr int NG = 32 / LPN;  // nonzero groups per warp
+    const float *__restrict__ B, int64_t ldb, int nq, int nqp, float *__restrict__ Y, int64_t ldy,
+    const uint32_t *__restrict__ hot) {
+  constexpr int G = 32 / L;
   const int lane = threadIdx.x & 31;
-  const int grp = lane / LPN, sub = lane % LPN;
+  const int grp = lane / L, sub = lane % L;
   const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (row >= n) return;
   const uint64_t pol_keep = l2_policy_normal(), pol_stream = l2_policy_first();
-  const int64_t c0 = (int64_t)blockIdx.y * (4 * LPN);  // first column of the block
-  const float *Bc = B + c0 + 4 * sub;
-  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  const uint32_t thr = hot ? *hot : 0xffffffffu;
+  const int q0 = blockIdx.y * nqp;
+  const int qn = min(nqp, nq - q0);
+  const float4 *Bp = reinterpret_cast<const float4 *>(B) + q0;  // row j at Bp + j * ldb / 4
+  const int64_t ldb4 = ldb / 4;
+  float4 acc[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
   const int64_t beg = row_ptr[row], end = row_ptr[row + 1];
-  int64_t p = beg + grp;
-  for (; p + NG < end; p += 2 * NG) {
-    const int32_t ca = ld_nc_s32(col + p, pol_stream);
-    const int32_t cb = ld_nc_s32(col + p + NG, pol_stream);
-    const float wa = wnz ? ld_nc_f32(wnz + p, pol_stream) : dpow[ca] * (val ? val[p] : 1.0f);
-    const float wb = wnz ? ld_nc_f32(wnz + p + NG, pol_stream) : dpow[cb] * (val ? val[p + NG] : 1.0f);
-    const float4 xa = ld_nc_f4(reinterpret_cast<const float4 *>(Bc + (int64_t)ca * ldb), pol_keep);
-    const float4 xb = ld_nc_f4(reinterpret_cast<const float4 *>(Bc + (int64_t)cb * ldb), pol_keep);
-    acc.x += wa * xa.x + wb * xb.x;
-    acc.y += wa * xa.y + wb * xb.y;
-    acc.z += wa * xa.z + wb * xb.z;
-    acc.w += wa * xa.w + wb * xb.w;
-  }
-  if (p < end) {
-    const int32_t ca = ld_nc_s32(col + p, pol_stream);
-    const float wa = wnz ? ld_nc_f32(wnz + p, pol_stream) : dpow[ca] * (val ? val[p] : 1.0f);
-    const float4 xa = ld_nc_f4(reinterpret_cast<const float4 *>(Bc + (int64_t)ca * ldb), pol_keep);
-    acc.x += wa * xa.x;
-    acc.y += wa * xa.y;
-    acc.z += wa * xa.z;
-    acc.w += wa * xa.w;
+  for (int64_t p0 = beg; p0 < end; p0 += 32) {
+    const int64_t p = p0 + lane;
+    int32_t c = 0;
+    float w = 0.f;
+    if (p < end) {
+      c = ld_nc_s32(col + p, pol_stream);
+      w = wnz ? ld_nc_f32(wnz + p, pol_stream) : dpow[c] * (val ? val[p] : 1.0f);
+    }
+    const int cnt = (int)min64(32, end - p0);
+    for (int t = 0; t < cnt; t += 2 * G) {
+      const int ta = t + grp, tb = t + G + grp;  // both < 32
+      const int32_t ca = __shfl_sync(0xffffffffu, c, ta);
+      const int32_t cb = __shfl_sync(0xffffffffu, c, tb);
+      const float wa = __shfl_sync(0xffffffffu, w, ta);
+      const float wb = __shfl_sync(0xffffffffu, w, tb);
+      const bool va = ta < cnt, vb = tb < cnt;
+      const uint64_t pa = __float_as_uint(wa) < thr ? pol_keep : pol_stream;
+      const uint64_t pb = __float_as_uint(wb) < thr ? pol_keep : pol_stream;
+      const float4 *ra = Bp + (int64_t)ca * ldb4;
+      const float4 *rb = Bp + (int64_t)cb * ldb4;
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const int q = sub + L * v;
+        if (q < qn) {
+          const float4 xa = va ? ld_nc_f4(ra + q, pa) : make_float4(0.f, 0.f, 0.f, 0.f);
+          const float4 xb = vb ? ld_nc_f4(rb + q, pb) : make_float4(0.f, 0.f, 0.f, 0.f);
+          acc[v].x += wa * xa.x + wb * xb.x;
+          acc[v].y += wa * xa.y + wb * xb.y;
+          acc[v].z += wa * xa.z + wb * xb.z;
+          acc[v].w += wa * xa.w + wb * xb.w;
+        }
+      }
+    }
   }
 #pragma unroll
-  for (int o = LPN; o < 32; o <<= 1) {
-    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-    acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
-    acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
+  for (int v = 0; v < V; ++v) {
+#pragma unroll
+    for (int o = L; o < 32; o <<= 1) {
+      acc[v].x += __shfl_xor_sync(0xffffffffu, acc[v].x, o);
+      acc[v].y += __shfl_xor_sync(0xffffffffu, acc[v].y, o);
+      acc[v].z += __shfl_xor_sync(0xffffffffu, acc[v].z, o);
+      acc[v].w += __shfl_xor_sync(0xffffffffu, acc[v].w, o);
+    }
   }
   if (grp == 0) {
     const float si = dpow[row];
-    st_f4(reinterpret_cast<float4 *>(Y + row * ldy + c0 + 4 * sub),
-          make_float4(si * acc.x, si * acc.y, si * acc.z, si * acc.w), pol_stream);
+    float4 *yr = reinterpret_cast<float4 *>(Y + row * ldy) + q0;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const int q = sub + L * v;
+      if (q < qn)
+        st_f4(yr + q, make_float4(si * acc[v].x, si * acc[v].y, si * acc[v].z, si * acc[v].w),
+              pol_stream);
+    }
   }
 }
 
@@ -349,19 +377,28 @@ cudaError_t launch_spmm_hot_threshold(const float *dpow, int64_t n, int64_t row_
   return cudaGetLastError();
 }
 
-// Column-block width of the SpMM for operands beyond L2: 0 (the row-at-once
-// kernel) unless SNE_SPMM_CB=16 or 8 selects the column-blocked kernel, which
-// measured slower (CTA dispatch of one CTA per 8 rows and column block).
-constexpr double kSpmmBlockFromBytes = 256.0 * 1024 * 1024;
-static int spmm_col_block() {
-  static int cb = -1;
-  if (cb < 0) {
-    const char *v = getenv("SNE_SPMM_CB");
-    cb = 0;
-    if (v && v[0] == '8' && v[1] == 0) cb = 8;
-    if (v && v[0] == '1' && v[1] == '6' && v[2] == 0) cb = 16;
+// Number of column panels of the SpMM (1: whole rows at once).  Operands of
+// at most kSpmmPanelFromBytes use one panel; above, SNE_SPMM_PANELS (1, 2, 4
+// or 8) when set, else kSpmmPanelsDefault.
+constexpr double kSpmmPanelFromBytes = 256.0 * 1024 * 1024;
+constexpr int kSpmmPanelsDefault = 1;
+int spmm_panels(int64_t n, int32_t ncols) {
+  if ((double)n * ncols * 4.0 <= kSpmmPanelFromBytes) return 1;
+  static int env = -1;
+  if (env < 0) {
+    const char *v = getenv("SNE_SPMM_PANELS");
+    env = 0;
+    if (v && (v[0] == '1' || v[0] == '2' || v[0] == '4' || v[0] == '8') && v[1] == 0) env = v[0] - '0';
   }
-  return cb;
+  return env > 0 ? env : kSpmmPanelsDefault;
+}
+
+// Bytes of one gathered row segment when the SpMM runs with spmm_panels():
+// the row size the L2 keep bound is computed for.
+int64_t spmm_row_bytes(int64_t n, int32_t ncols) {
+  const int P = spmm_panels(n, ncols);
+  const int nq = (ncols + 3) / 4;
+  return (int64_t)16 * ((nq + P - 1) / P);
 }
 
 cudaError_t launch_spmm(const sne_csr &g, const float *dpow, const float *wnz, const float *B,
@@ -374,16 +411,26 @@ cudaError_t launch_spmm(const sne_csr &g, const float *dpow, const float *wnz, c
   const bool vec = (ncols % 4 == 0) && (ldb % 4 == 0) && (ldy % 4 == 0) &&
                    ((uintptr_t)B % 16 == 0) && ((uintptr_t)Y % 16 == 0);
   const int nvec = ncols / 4;
-  // operands well beyond L2 (129 MB): column blocks of 16 that fit in it
-  const int cb = spmm_col_block();
-  if (vec && cb > 0 && ncols % cb == 0 && (double)g.n * ncols * 4.0 > kSpmmBlockFromBytes) {
-    const dim3 grid(blocks, (unsigned)(ncols / cb));
-    if (cb == 16)
-      spmm_colblock_kernel<4><<<grid, 256, 0, st>>>(g.n, g.row_ptr, g.col_idx, g.val, dpow, wnz, B,
-                                                    ldb, Y, ldy);
-    else
-      spmm_colblock_kernel<2><<<grid, 256, 0, st>>>(g.n, g.row_ptr, g.col_idx, g.val, dpow, wnz, B,
-                                                    ldb, Y, ldy);
+  // operands beyond L2: column panels (lanes per nonzero L and float4 per lane
+  // V chosen for the panel width, at most 4 float4 per lane)
+  const int P = vec ? spmm_panels(g.n, ncols) : 1;
+  if (P > 1) {
+    const int nqp = (nvec + P - 1) / P;
+    const int L = nqp <= 32 ? 8 : (nqp <= 64 ? 16 : 32);
+    const int V = (nqp + L - 1) / L;
+    const dim3 grid(blocks, (unsigned)((nvec + nqp - 1) / nqp));
+#define SNE_PANEL(LV, VV)                                                                    \
+  spmm_panel_kernel<LV, VV><<<grid, 256, 0, st>>>(g.n, g.row_ptr, g.col_idx, g.val, dpow, wnz, B, \
+                                                  ldb, nvec, nqp, Y, ldy, hot)
+    if (V > 4) return cudaErrorInvalidValue;
+    if (L == 8) {
+      if (V == 1) SNE_PANEL(8, 1); else if (V == 2) SNE_PANEL(8, 2); else if (V == 3) SNE_PANEL(8, 3); else SNE_PANEL(8, 4);
+    } else if (L == 16) {
+      if (V == 1) SNE_PANEL(16, 1); else if (V == 2) SNE_PANEL(16, 2); else if (V == 3) SNE_PANEL(16, 3); else SNE_PANEL(16, 4);
+    } else {
+      if (V == 1) SNE_PANEL(32, 1); else if (V == 2) SNE_PANEL(32, 2); else if (V == 3) SNE_PANEL(32, 3); else SNE_PANEL(32, 4);
+    }
+#undef SNE_PANEL
     return cudaGetLastError();
   }
   if (vec && nvec <= 32 * 12) {

@@ -117,6 +117,10 @@ cudaError_t launch_spmm_weights(const sne_csr &g, const float *dpow, float *wnz,
 // `row_bytes` a row; writes the bit pattern bound to ctrl->hot_bits.
 cudaError_t launch_spmm_hot_threshold(const float *dpow, int64_t n, int64_t row_bytes, Ctrl *ctrl,
                                       cudaStream_t st);
+// Column panels launch_spmm uses for an n x ncols operand, and the bytes of the
+// row segment one panel gathers (the row size for the keep bound).
+int spmm_panels(int64_t n, int32_t ncols);
+int64_t spmm_row_bytes(int64_t n, int32_t ncols);
 // hot: that bound (a gathered row whose weight bits are below it is loaded with
 // the normal L2 priority, every other row and the CSR streams evict-first), or
 // NULL to load every row with the normal priority.

@@ -155,7 +155,9 @@ def _stream(stream) -> int:
     return int(stream)
 
 
-def _ptr(t, dtype=None, name="tensor", allow_none=False) -> int | None:
+def _ptr(t, dtype=None, name="tensor", allow_none=False, row_major=False) -> int | None:
+    """Device pointer of t; with row_major a 2-D view with unit column stride
+    (a leading dimension passed separately) is accepted as well."""
     if t is None:
         if allow_none:
             return None
@@ -164,7 +166,10 @@ def _ptr(t, dtype=None, name="tensor", allow_none=False) -> int | None:
         raise ValueError(f"{name} must be a CUDA tensor")
     if dtype is not None and t.dtype != dtype:
         raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
-    if not t.is_contiguous():
+    if row_major:
+        if t.dim() != 2 or t.stride(1) != 1:
+            raise ValueError(f"{name} must be a row-major matrix")
+    elif not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
     return t.data_ptr()
 
@@ -296,16 +301,14 @@ def sne_single_pass_svd(L: torch.Tensor, Rt: torch.Tensor, p: sne_params, ws: to
                         stream=None) -> None:
     """Eqs. 5-10 for f(L Rt^T): L (n x k), Rt (m x k) row-major CUDA float32;
     U (n x d), V (m x d) float32 or None, sigma (d) float64."""
-    for t, nm in ((L, "L"), (Rt, "Rt")):
-        if t.dim() != 2 or t.stride(1) != 1:
-            raise ValueError(f"{nm} must be a row-major matrix")
     if L.shape[1] != Rt.shape[1]:
         raise ValueError("L and Rt need the same number of columns")
     _check(lib().sne_single_pass_svd(
-        L.shape[0], Rt.shape[0], L.shape[1], _ptr(L, torch.float32, "L"), L.stride(0),
-        _ptr(Rt, torch.float32, "Rt"), Rt.stride(0), ctypes.byref(p), _ptr(ws, torch.uint8, "workspace"),
-        ws.numel(), _ptr(U, torch.float32, "U", True), U.stride(0) if U is not None else 0,
-        _ptr(sigma, torch.float64, "sigma"), _ptr(V, torch.float32, "V", True),
+        L.shape[0], Rt.shape[0], L.shape[1], _ptr(L, torch.float32, "L", row_major=True), L.stride(0),
+        _ptr(Rt, torch.float32, "Rt", row_major=True), Rt.stride(0), ctypes.byref(p),
+        _ptr(ws, torch.uint8, "workspace"), ws.numel(),
+        _ptr(U, torch.float32, "U", True, row_major=True), U.stride(0) if U is not None else 0,
+        _ptr(sigma, torch.float64, "sigma"), _ptr(V, torch.float32, "V", True, row_major=True),
         V.stride(0) if V is not None else 0, _stream(stream)), "sne_single_pass_svd")
 
 
@@ -326,10 +329,9 @@ def propagate_workspace(n: int, d: int, device="cuda") -> torch.Tensor:
 def sne_spectral_propagate(g: DeviceGraph, E: torch.Tensor, ws: torch.Tensor, steps: int = 10,
                            theta: float = 0.5, mu: float = 0.2, stream=None) -> None:
     """Alg. 6 line 6 on the CUDA FP32 row-major E (n x d), in place."""
-    if E.dim() != 2 or E.stride(1) != 1:
-        raise ValueError("E must be a row-major matrix")
     _check(lib().sne_spectral_propagate(ctypes.byref(g.csr), steps, theta, mu,
-                                        _ptr(E, torch.float32, "E"), E.stride(0), E.shape[1],
+                                        _ptr(E, torch.float32, "E", row_major=True), E.stride(0),
+                                        E.shape[1],
                                         _ptr(ws, torch.uint8, "workspace"), ws.numel(),
                                         _stream(stream)), "sne_spectral_propagate")
 
