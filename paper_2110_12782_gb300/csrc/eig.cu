@@ -28,7 +28,6 @@
 
 namespace sne {
 
-constexpr int kJacobiMaxN = 320;
 constexpr int kJacobiMaxSweeps = 30;
 constexpr int kRefineSteps = 6;
 constexpr double kClusterFloor = 1e-4;  // eigenvalue gaps below this x max|lambda| form clusters
@@ -671,13 +670,14 @@ __global__ void __launch_bounds__(1024) chol_inv_blocked_kernel(const T *__restr
 // 32 x 33 floats (the padding keeps column walks free of bank conflicts);
 // rows and columns past n are those of the identity, so the factor of the
 // padded matrix is diag(R, I).
-//   factor, panel p: one warp factors block (p, p) (column per lane); warp w
-//   solves R_pp^T R_pq = A_pq for q = p + 1 + w (column per lane); all warps
-//   update the trailing blocks A_qr -= R_pq^T R_pr with 4 x 4 register tiles;
-//   three barriers per panel.
+//   factor, panel p: one warp factors block (p, p) and inverts it,
+//   X_pp = R_pp^-1 (column per lane, by back substitution; kept for the
+//   inverse); all warps form R_pq = X_pp^T A_pq for q > p and update the
+//   trailing blocks A_qr -= R_pq^T R_pr with 4 x 4 register tiles; four
+//   barriers per panel and no sequential solve outside the diagonal block.
 //   inverse, block column j: T_i = sum_{m=i}^{j-1} X_im R_mj for i < j (X = R^-1,
-//   columns < j already done) while one warp inverts R_jj, then
-//   X_ij = -T_i X_jj; two barriers per block column.
+//   columns < j already done), then X_ij = -T_i X_jj; two barriers per block
+//   column.
 // A non-positive or non-finite pivot records SNE_ERR_NUMERIC and is replaced
 // by 1.
 // ---------------------------------------------------------------------------
@@ -701,7 +701,7 @@ __global__ void __launch_bounds__(1024) chol_inv_quick_kernel(const float *__res
   const int nb = (n + kQB - 1) / kQB;
   float *blk = qsm;                                              // triangle of blocks
   float *tmp = qsm + (size_t)nb * (nb + 1) / 2 * kQB * kQLd;     // nb blocks of 32 x 32
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   auto B = [&](int bi, int bj) { return blk + (size_t)qblk(nb, bi, bj) * kQB * kQLd; };
   // ---- load (upper triangle; identity past n)
   for (int bi = 0; bi < nb; ++bi)
@@ -737,15 +737,55 @@ __global__ void __launch_bounds__(1024) chol_inv_quick_kernel(const float *__res
         for (int r = j + 1; r <= lane; ++r) bpp[r * kQLd + lane] -= bpp[j * kQLd + r] * rjc;
         __syncwarp();
       }
+      // X_pp = R_pp^-1 into tmp block p: lane c, column c, rows c .. 0
+      float *xpp = tmp + (size_t)p * kQB * kQB;
+      for (int r = kQB - 1; r >= 0; --r) {
+        float x = 0.f;
+        if (r == lane) {
+          x = 1.f / bpp[r * kQLd + r];
+        } else if (r < lane) {
+          for (int m = r + 1; m <= lane; ++m) x -= bpp[r * kQLd + m] * xpp[m * kQB + lane];
+          x /= bpp[r * kQLd + r];
+        }
+        xpp[r * kQB + lane] = x;
+        __syncwarp();
+      }
     }
     __syncthreads();
-    // R_pq = R_pp^-T A_pq, q > p: warp per block, lane per column (forward substitution)
-    for (int q = p + 1 + warp; q < nb; q += nw) {
-      float *bpq = B(p, q);
-      for (int r = 0; r < kQB; ++r) {
-        float x = bpq[r * kQLd + lane];
-        for (int m = 0; m < r; ++m) x -= bpp[m * kQLd + r] * bpq[m * kQLd + lane];
-        bpq[r * kQLd + lane] = x / bpp[r * kQLd + r];
+    // R_pq = X_pp^T A_pq, q > p, in 4 x 4 tiles (at most 8 blocks x 64 tiles,
+    // one tile per thread): products first, then the blocks are overwritten
+    {
+      const float *xpp = tmp + (size_t)p * kQB * kQB;
+      const int ntask = (nb - p - 1) * 64;
+      float acc[4][4] = {};
+      int q = 0, a0 = 0, b0 = 0;
+      if (tid < ntask) {
+        q = p + 1 + (tid >> 6);
+        const int t = tid & 63;
+        a0 = 4 * (t >> 3);
+        b0 = 4 * (t & 7);
+        const float *apq = B(p, q);
+        // X_pp[m][a] = 0 for m > a: m runs to a0 + 3
+        for (int m = 0; m < a0 + 4; ++m) {
+          float av[4], bv[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            av[u] = xpp[m * kQB + a0 + u];
+            bv[u] = apq[m * kQLd + b0 + u];
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+        }
+      }
+      __syncthreads();
+      if (tid < ntask) {
+        float *dst = B(p, q);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) dst[(a0 + u) * kQLd + b0 + v] = acc[u][v];
       }
     }
     __syncthreads();
@@ -790,26 +830,10 @@ __global__ void __launch_bounds__(1024) chol_inv_quick_kernel(const float *__res
   }
   // ---- inverse X = R^-1, block column by block column
   for (int j = 0; j < nb; ++j) {
-    float *xjj = tmp + (size_t)j * kQB * kQB;  // X_jj, row-major 32 x 32
-    if (warp == nw - 1) {
-      // lane c: column c of R_jj^-1 by back substitution (rows c .. 0)
-      const float *bjj = B(j, j);
-      for (int r = kQB - 1; r >= 0; --r) {
-        float x = 0.f;
-        if (r == lane) {
-          x = 1.f / bjj[r * kQLd + r];
-        } else if (r < lane) {
-          for (int m = r + 1; m <= lane; ++m) x -= bjj[r * kQLd + m] * xjj[m * kQB + lane];
-          x /= bjj[r * kQLd + r];
-        }
-        xjj[r * kQB + lane] = x;
-        __syncwarp();
-      }
-    }
+    const float *xjj = tmp + (size_t)j * kQB * kQB;  // X_jj from the factorization
     // T_i = sum_{m=i}^{j-1} X_im R_mj for i < j (into tmp block i), 4 x 4 tiles
-    const int tw = (nw - 1) * 32;  // the other warps
-    if (tid < tw) {
-      for (int task = tid; task < j * 64; task += tw) {
+    {
+      for (int task = tid; task < j * 64; task += blockDim.x) {
         const int i = task >> 6, t = task & 63;
         const int a0 = 4 * (t >> 3), b0 = 4 * (t & 7);
         float acc[4][4] = {};
