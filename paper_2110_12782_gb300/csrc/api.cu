@@ -140,7 +140,7 @@ size_t carve(const Dims &D, int mode, void *base, Bufs *b) {
   for (auto &m : x.m64) m = bp.take<double>(S2);
   x.eigscr = bp.take<char>(std::max(eig_scratch_bytes(D.Sm), (S2 + 4 * (size_t)D.Sm) * 8 + 1024));
   for (auto &m : x.m32) m = bp.take<float>(S2);
-  x.mT = bp.take<float>(S2);
+  x.mT = bp.take<float>(tall_tc_scratch_floats(D.Sm, D.Sm));
   x.w64 = bp.take<double>(D.Sm);
   x.lam = bp.take<double>(D.Sm);
   x.w32 = bp.take<float>(D.Sm);

@@ -75,7 +75,7 @@ int sne_gram(int64_t n, int32_t ka, int32_t kb, const float *A, int64_t lda, con
 
 int sne_tall_gemm_workspace_bytes(int32_t ka, int32_t kc, size_t *bytes) {
   if (!bytes || ka <= 0 || kc <= 0) return SNE_ERR_ARG;
-  *bytes = align256(sizeof(Ctrl)) + align256((size_t)ka * kc * sizeof(float));
+  *bytes = align256(sizeof(Ctrl)) + align256(tall_tc_scratch_floats(ka, kc) * sizeof(float));
   return SNE_OK;
 }
 
@@ -85,7 +85,8 @@ int sne_tall_gemm(int64_t n, int32_t ka, int32_t kc, const float *A, int64_t lda
   if (n <= 0 || ka <= 0 || kc <= 0 || !A || !M || !C || lda < ka || ldm < kc || ldc < kc)
     return SNE_ERR_ARG;
   const int rc = check_ws_(ws, ws_bytes,
-                           align256(sizeof(Ctrl)) + align256((size_t)ka * kc * sizeof(float)));
+                           align256(sizeof(Ctrl)) +
+                               align256(tall_tc_scratch_floats(ka, kc) * sizeof(float)));
   if (rc) return rc;
   Ctrl *ctrl = reinterpret_cast<Ctrl *>(ws);
   if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), (cudaStream_t)stream) != cudaSuccess) return SNE_ERR_CUDA;

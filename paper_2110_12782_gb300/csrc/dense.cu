@@ -499,27 +499,12 @@ __global__ void __launch_bounds__(256) tall_gemm_kernel(
   }
 }
 
-__global__ void transpose_kernel(const float *M, int rows, int cols, int ldm, float *Mt) {
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < rows * cols; q += gridDim.x * blockDim.x) {
-    const int r = q / cols, c = q % cols;
-    Mt[(int64_t)c * rows + r] = M[(int64_t)r * ldm + c];
-  }
-}
-
 cudaError_t launch_tall_gemm_auto(const float *A, int64_t lda, int64_t n, int32_t Ka, const float *M,
                                   int32_t ldm, int32_t Kc, float *C, int64_t ldc, float *Mt,
                                   Ctrl *ctrl, cudaStream_t st) {
   if (tc_gemm_enabled() && tc_gemm_supported(Kc) && Mt && lda % 4 == 0 && ldc % 4 == 0 &&
-      Ka % 4 == 0 && (uintptr_t)A % 16 == 0 && n >= 256) {
-    {
-      ProfScope ps_(K_MISC, st);
-      transpose_kernel<<<(unsigned)min64(1024, ((int64_t)Ka * Kc + 255) / 256), 256, 0, st>>>(
-          M, Ka, Kc, ldm, Mt);
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    return launch_tall_gemm_tc(A, lda, n, Ka, Mt, Kc, C, ldc, ctrl, st);
-  }
+      Ka % 4 == 0 && (uintptr_t)A % 16 == 0 && (uintptr_t)Mt % 16 == 0 && n >= 256)
+    return launch_tall_gemm_tc(A, lda, n, Ka, M, ldm, Kc, C, ldc, Mt, ctrl, st);
   return launch_tall_gemm(A, lda, nullptr, n, Ka, M, ldm, Kc, nullptr, C, ldc, st);
 }
 

@@ -8,17 +8,18 @@
 // used for the eigSVD / Cholesky-QR orthonormalizations and the Rayleigh-Ritz
 // product of Alg. 5, the sketch QR of Alg. 4 and E = Q U_hat.
 //
-// Each operand x is split in shared memory into hi = rna_tf32(x) and
-// lo = x - hi (exact), and the accumulator takes A_hi B_hi + A_hi B_lo +
-// A_lo B_hi, so the product carries about 2^-21 relative error per term
-// (the FP32 result up to the dropped A_lo B_lo term).  Four split warps do
-// this between the TMA load and the MMA of every stage.
+// Each operand x is split into hi = rna_tf32(x) and lo = x - hi (exact), and
+// the accumulator takes A_hi B_hi + A_hi B_lo + A_lo B_hi, so the product
+// carries about 2^-21 relative error per term (the FP32 result up to the
+// dropped A_lo B_lo term).  Four split warps do this in shared memory between
+// the TMA load and the MMA of every stage, for the tall operands.
 //
-// TALL: a persistent CTA per SM walks 128-row output tiles over all
-// Npad <= 288 output columns (TMEM holds the 128 x Npad FP32 accumulator; the
-// columns are issued as MMAs of N = 256 and N = Npad - 256).  Warp 0: TMA;
-// warp 1: TMEM and MMA issue; warps 2-5: operand split; warps 6-9: epilogue
-// (tcgen05.ld, store).
+// TALL: a persistent CTA per SM walks (128-row tile, column half) work items
+// over Npad <= 288 output columns (halves of at most 160 columns, one MMA of
+// N = half width per k-step and product); the small operand M^T is split into
+// TF32 hi/lo once per call and loaded by TMA, so only A is split in shared
+// memory.  Warp 0: TMA; warp 1: TMEM and MMA issue; warps 2-5: split of A;
+// warps 6-9: epilogue (tcgen05.ld, store) from two alternating accumulators.
 #include <cuda.h>
 #include <cuda.h>
 
@@ -31,38 +32,58 @@ namespace gt {
 constexpr int BM = 128;        // output rows per tile (MMA M)
 constexpr int BK = 32;         // FP32 elements per k-block (128 bytes)
 constexpr int kMaxN = 288;     // padded output columns
-constexpr int kStages = 2;
+constexpr int kHalfFrom = 160; // wider outputs go in two column halves
+constexpr int kStages = 3;
 constexpr int kThreads = 320;  // TMA, MMA, 4 split warps, 4 epilogue warps
 constexpr int kABytes = BM * BK * 4;  // 16 KB
 }  // namespace gt
 
-// Persistent: CTA b takes the row tiles b, b + gridDim.x, ...  The stage ring
-// and its barrier phases run on across tiles, so the loads and splits of tile
-// t + 1 overlap the epilogue of tile t; only the MMA waits for the epilogue
-// warps to have read the accumulator out of TMEM (accfree).
+// Column halves of an npad-column output: N0 (the wider, a multiple of 32) and
+// N1 (0 for one pass).
+__host__ __device__ inline void tall_halves(int npad, int *N0, int *N1) {
+  if (npad <= gt::kHalfFrom) {
+    *N0 = npad;
+    *N1 = 0;
+  } else {
+    *N0 = ((npad / 2) + 31) / 32 * 32;
+    *N1 = npad - *N0;
+  }
+}
+
+// Persistent: CTA b takes the work items b, b + gridDim.x, ... of the list
+// (row tile, column half); the second half of a tile re-reads the tile's A
+// rows, from L2.  The operand B = M^T arrives already split (rows 0 .. npad
+// hi, rows npad .. 2 npad lo; split once per call), so the split warps only
+// split A, and with halves of at most 160 columns a stage (A hi, A lo, B hi,
+// B lo) is at most 72 KB: three stages.  The two TMEM accumulators (columns
+// 0 and 256) alternate between work items, so that the epilogue of one
+// overlaps the MMAs of the next; the stage ring and the barrier phases run on
+// across work items.
 __global__ void __launch_bounds__(gt::kThreads, 1) tall_tf32x3_kernel(
-    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-    const __grid_constant__ CUtensorMap tmB2, int npad, int nkb, int64_t ntiles, int64_t nrows,
+    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB0,
+    const __grid_constant__ CUtensorMap tmB1, int npad, int nkb, int64_t ntiles, int64_t nrows,
     int ncols, float *__restrict__ out, int64_t ldo, int vec4, Ctrl *ctrl) {
   using namespace tc;
   extern __shared__ __align__(1024) unsigned char g_smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(g_smem_raw) + 1023) & ~(uintptr_t)1023);
-  const int bbytes = npad * gt::BK * 4;                       // B region of a stage
-  const int stage_bytes = 2 * gt::kABytes + 2 * bbytes;        // hi + lo of A and B
+  int N0, N1;
+  tall_halves(npad, &N0, &N1);
+  const int nhalf = N1 > 0 ? 2 : 1;
+  const int bmax = N0 * gt::BK * 4;                    // B bytes (hi or lo) of the wider half
+  const int stage_bytes = 2 * gt::kABytes + 2 * bmax;  // A hi | A lo | B hi | B lo
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)gt::kStages * stage_bytes);
-  uint64_t *full = bars;                  // [stages] TMA landed
-  uint64_t *split = full + gt::kStages;   // [stages] hi/lo ready for the MMA
-  uint64_t *empty = split + gt::kStages;  // [stages] MMA done with the stage
-  uint64_t *accfull = empty + gt::kStages;  // accumulator of a tile complete
-  uint64_t *accfree = accfull + 1;          // epilogue has read it out
-  uint64_t *done = accfree + 1;             // every MMA issued has completed
+  uint64_t *full = bars;                    // [stages] TMA landed
+  uint64_t *split = full + gt::kStages;     // [stages] A split
+  uint64_t *empty = split + gt::kStages;    // [stages] MMA done with the stage
+  uint64_t *accfull = empty + gt::kStages;  // [2] accumulator of a work item complete
+  uint64_t *accfree = accfull + 2;          // [2] the epilogue has read it out
+  uint64_t *done = accfree + 2;             // every MMA issued has completed
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
   int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n1 = npad > 256 ? 256 : npad;  // first MMA column block
-  const int n2 = npad - n1;                // second (0, 32)
+  const int64_t nitems = ntiles * nhalf;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < gt::kStages; ++s) {
@@ -70,8 +91,10 @@ __global__ void __launch_bounds__(gt::kThreads, 1) tall_tf32x3_kernel(
       mbar_init(&split[s], 128);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(accfull, 1);
-    mbar_init(accfree, 128);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accfull[b], 1);
+      mbar_init(&accfree[b], 128);
+    }
     mbar_init(done, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -90,12 +113,16 @@ __global__ void __launch_bounds__(gt::kThreads, 1) tall_tf32x3_kernel(
   volatile int *abortv = abort_flag;
 
   auto stage_ptr = [&](int s) { return smem + (size_t)s * stage_bytes; };
-  // stage layout: A_hi | A_lo | B_hi | B_lo (K-major, 128-byte swizzle)
   if (warp == 0) {
     if (lane == 0) {
+      // ---------------- TMA producer
       uint32_t it = 0;
       bool ok = true;
-      for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      for (int64_t w = blockIdx.x; w < nitems && ok; w += gridDim.x) {
+        const int64_t tile = w / nhalf;
+        const int half = (int)(w - tile * nhalf);
+        const int N = half ? N1 : N0, c0 = half ? N0 : 0;
+        const CUtensorMap *tmB = half ? &tmB1 : &tmB0;
         const int m0 = (int)(tile * gt::BM);
         for (int kb = 0; kb < nkb; ++kb, ++it) {
           const int s = it % gt::kStages;
@@ -104,11 +131,12 @@ __global__ void __launch_bounds__(gt::kThreads, 1) tall_tf32x3_kernel(
             break;
           }
           unsigned char *st = stage_ptr(s);
-          mbar_expect_tx(&full[s], (uint32_t)(gt::kABytes + bbytes));
-          // A box {32 k, 128 rows}; B boxes {32 k, n1 rows} and {32 k, n2 rows}
+          mbar_expect_tx(&full[s], (uint32_t)(gt::kABytes + 2 * N * gt::BK * 4));
+          // A box {32 k, 128 rows}; B boxes {32 k, N rows}: hi rows c0 ..,
+          // lo rows npad + c0 ..
           tma_load_2d(st, &tmA, &full[s], kb * gt::BK, m0);
-          tma_load_2d(st + 2 * gt::kABytes, &tmB, &full[s], kb * gt::BK, 0);
-          if (n2 > 0) tma_load_2d(st + 2 * gt::kABytes + n1 * 128, &tmB2, &full[s], kb * gt::BK, n1);
+          tma_load_2d(st + 2 * gt::kABytes, tmB, &full[s], kb * gt::BK, c0);
+          tma_load_2d(st + 2 * gt::kABytes + bmax, tmB, &full[s], kb * gt::BK, npad + c0);
         }
       }
       if (!ok) {
@@ -120,15 +148,20 @@ __global__ void __launch_bounds__(gt::kThreads, 1) tall_tf32x3_kernel(
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      // instruction descriptors: D F32, A/B TF32 (2), K-major, N, M = 128
+      // ---------------- MMA issuer.  Instruction descriptor: D F32, A/B TF32
+      // (2), K-major, N, M = 128
       const uint32_t base = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(gt::BM >> 4) << 24);
-      const uint32_t id1 = base | ((uint32_t)(n1 >> 3) << 17);
-      const uint32_t id2 = base | ((uint32_t)((n2 > 0 ? n2 : 16) >> 3) << 17);
-      uint32_t it = 0, lt = 0;
+      uint32_t it = 0, u = 0;
       bool ok = true;
-      for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++lt) {
-        if (!mbar_wait(accfree, (lt & 1) ^ 1, abortv, ctrl)) break;
+      for (int64_t w = blockIdx.x; w < nitems && ok; w += gridDim.x, ++u) {
+        const int64_t tile = w / nhalf;
+        const int half = (int)(w - tile * nhalf);
+        const int N = half ? N1 : N0;
+        const uint32_t idesc = base | ((uint32_t)(N >> 3) << 17);
+        const int buf = u & 1;
+        if (!mbar_wait(&accfree[buf], ((u >> 1) & 1) ^ 1, abortv, ctrl)) break;
         fence_after();
+        const uint32_t dt = tmem + (uint32_t)(buf * 256);
         for (int kb = 0; kb < nkb; ++kb, ++it) {
           const int s = it % gt::kStages;
           if (!mbar_wait(&split[s], (it / gt::kStages) & 1, abortv, ctrl)) {
@@ -139,37 +172,30 @@ __global__ void __launch_bounds__(gt::kThreads, 1) tall_tf32x3_kernel(
           const uint32_t ahi = smem_u32(stage_ptr(s));
           const uint32_t alo = ahi + gt::kABytes;
           const uint32_t bhi = ahi + 2 * gt::kABytes;
-          const uint32_t blo = bhi + bbytes;
+          const uint32_t blo = bhi + bmax;
 #pragma unroll
           for (int kk = 0; kk < gt::BK / 8; ++kk) {
             const uint32_t acc = (kb | kk) ? 1u : 0u;
             const uint64_t da_hi = sdesc2(ahi + kk * 32, 16, 1024);
-            const uint64_t da_lo = sdesc2(alo + kk * 32, 16, 1024);
-            const uint64_t db1_hi = sdesc2(bhi + kk * 32, 16, 1024);
-            mma_tf32(tmem, da_hi, db1_hi, id1, acc);
-            mma_tf32(tmem, da_hi, sdesc2(blo + kk * 32, 16, 1024), id1, 1u);
-            mma_tf32(tmem, da_lo, db1_hi, id1, 1u);
-            if (n2 > 0) {
-              const uint64_t db2_hi = sdesc2(bhi + n1 * 128 + kk * 32, 16, 1024);
-              mma_tf32(tmem + n1, da_hi, db2_hi, id2, acc);
-              mma_tf32(tmem + n1, da_hi, sdesc2(blo + n1 * 128 + kk * 32, 16, 1024), id2, 1u);
-              mma_tf32(tmem + n1, da_lo, db2_hi, id2, 1u);
-            }
+            const uint64_t db_hi = sdesc2(bhi + kk * 32, 16, 1024);
+            mma_tf32(dt, da_hi, db_hi, idesc, acc);
+            mma_tf32(dt, da_hi, sdesc2(blo + kk * 32, 16, 1024), idesc, 1u);
+            mma_tf32(dt, sdesc2(alo + kk * 32, 16, 1024), db_hi, idesc, 1u);
           }
           mma_commit(&empty[s]);
         }
-        if (ok) mma_commit(accfull);
+        if (ok) mma_commit(&accfull[buf]);
       }
       // every issued MMA has completed before TMEM is released
       mma_commit(done);
       mbar_drain(done, 0, kTimeoutNs);
     }
   } else if (warp < 6) {
-    // ---------------- warps 2..5: operand split (elementwise, in place)
+    // ---------------- warps 2..5: split of A (elementwise, in place)
     const int t = threadIdx.x - 64;  // 0..127
     uint32_t it = 0;
     bool ok = true;
-    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    for (int64_t w = blockIdx.x; w < nitems && ok; w += gridDim.x) {
       for (int kb = 0; kb < nkb; ++kb, ++it) {
         const int s = it % gt::kStages;
         if (!mbar_wait(&full[s], (it / gt::kStages) & 1, abortv, ctrl)) {
@@ -186,16 +212,6 @@ __global__ void __launch_bounds__(gt::kThreads, 1) tall_tf32x3_kernel(
           ahi[q] = h;
           alo[q] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
         }
-        float4 *bhi = reinterpret_cast<float4 *>(st + 2 * gt::kABytes);
-        float4 *blo = reinterpret_cast<float4 *>(st + 2 * gt::kABytes + bbytes);
-        const int nB4 = bbytes / 16;
-#pragma unroll 4
-        for (int q = t; q < nB4; q += 128) {
-          const float4 x = bhi[q];
-          const float4 h = make_float4(tf32_rna(x.x), tf32_rna(x.y), tf32_rna(x.z), tf32_rna(x.w));
-          bhi[q] = h;
-          blo[q] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
-        }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&split[s]);
       }
@@ -203,30 +219,34 @@ __global__ void __launch_bounds__(gt::kThreads, 1) tall_tf32x3_kernel(
   } else {
     // ---------------- warps 6..9: epilogue, one accumulator row per thread
     const int ew = warp & 3;  // TMEM lane quarter of this warp
-    uint32_t lt = 0;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
-      if (!mbar_wait(accfull, lt & 1, abortv, ctrl)) break;
+    uint32_t u = 0;
+    for (int64_t w = blockIdx.x; w < nitems; w += gridDim.x, ++u) {
+      const int64_t tile = w / nhalf;
+      const int half = (int)(w - tile * nhalf);
+      const int N = half ? N1 : N0, c0 = half ? N0 : 0;
+      const int buf = u & 1;
+      if (!mbar_wait(&accfull[buf], (u >> 1) & 1, abortv, ctrl)) break;
       fence_after();
       const int64_t r = tile * gt::BM + 32 * ew + lane;
-      float *orow = out + r * ldo;
+      float *orow = out + r * ldo + c0;
       const bool rok = r < nrows;
-      for (int c = 0; c < npad; c += 32) {
+      for (int c = 0; c < N; c += 32) {
         float v[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * ew) << 16) + (uint32_t)c, v);
+        tmem_ld32(tmem + ((uint32_t)(32 * ew) << 16) + (uint32_t)(buf * 256 + c), v);
         if (rok) {
-          if (vec4 && c + 32 <= ncols) {
+          if (vec4 && c0 + c + 32 <= ncols) {
 #pragma unroll
             for (int q = 0; q < 32; q += 4)
               *reinterpret_cast<float4 *>(orow + c + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
           } else {
 #pragma unroll
             for (int q = 0; q < 32; ++q)
-              if (c + q < ncols) orow[c + q] = v[q];
+              if (c0 + c + q < ncols) orow[c + q] = v[q];
           }
         }
       }
       fence_before();
-      mbar_arrive(accfree);
+      mbar_arrive(&accfree[buf]);
     }
   }
   fence_before();
@@ -546,7 +566,9 @@ static bool map_f32(CUtensorMap *tm, const float *ptr, int64_t rows, int64_t col
 }
 
 static size_t gemm_tc_smem(int npad) {
-  const size_t stage = 2 * (size_t)gt::kABytes + 2 * (size_t)npad * gt::BK * 4;
+  int N0, N1;
+  tall_halves(npad, &N0, &N1);
+  const size_t stage = 2 * (size_t)gt::kABytes + 2 * (size_t)N0 * gt::BK * 4;
   return 1024 + gt::kStages * stage + 256;
 }
 
@@ -555,29 +577,58 @@ bool tc_gemm_supported(int ncols) {
   return npad <= gt::kMaxN && gemm_tc_smem(npad) <= 227 * 1024;
 }
 
-// C[i, :Kc] = A[i, :K] M  with Mt = M^T (Kc x K, row-major, ld K).
-cudaError_t launch_tall_gemm_tc(const float *A, int64_t lda, int64_t n, int K, const float *Mt, int Kc,
-                                float *C, int64_t ldc, Ctrl *ctrl, cudaStream_t st) {
+// Mt2 (2 npad x K): rows c < Kc of M^T split into TF32 hi (row c) and lo
+// (row npad + c); rows Kc .. npad of both halves zero.
+__global__ void split_mt_kernel(const float *__restrict__ M, int K, int Kc, int ldm, int npad,
+                                float *__restrict__ Mt2) {
+  const int64_t total = (int64_t)npad * K;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(q / K), a = (int)(q % K);
+    const float x = c < Kc ? M[(int64_t)a * ldm + c] : 0.0f;
+    const float h = tc::tf32_rna(x);
+    Mt2[q] = h;
+    Mt2[(int64_t)npad * K + q] = x - h;
+  }
+}
+
+size_t tall_tc_scratch_floats(int K, int Kc) {
+  const int npad = (Kc + 31) / 32 * 32;
+  return (size_t)2 * npad * K;
+}
+
+// C[i, :Kc] = A[i, :K] M  (M K x Kc, leading dimension ldm); Mt2: scratch of
+// tall_tc_scratch_floats(K, Kc) floats for the split M^T.
+cudaError_t launch_tall_gemm_tc(const float *A, int64_t lda, int64_t n, int K, const float *M,
+                                int ldm, int Kc, float *C, int64_t ldc, float *Mt2, Ctrl *ctrl,
+                                cudaStream_t st) {
   if (n <= 0 || Kc <= 0) return cudaSuccess;
   const int npad = (Kc + 31) / 32 * 32;
   if (!tc_gemm_supported(Kc) || n > (int64_t)INT32_MAX - gt::BM) return cudaErrorInvalidValue;
-  CUtensorMap tmA, tmB, tmB2;
-  const int n1 = npad > 256 ? 256 : npad;
-  const int n2 = npad - n1;
+  {
+    ProfScope ps_(K_MISC, st);
+    split_mt_kernel<<<(unsigned)min64(1024, ((int64_t)npad * K + 255) / 256), 256, 0, st>>>(
+        M, K, Kc, ldm, npad, Mt2);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int N0, N1;
+  tall_halves(npad, &N0, &N1);
+  CUtensorMap tmA, tmB0, tmB1;
   if (!map_f32(&tmA, A, n, K, lda, gt::BK, gt::BM)) return cudaErrorInvalidValue;
-  // B = M^T: rows [0, n1) in one box, rows [n1, npad) in a second box of n2 rows
-  if (!map_f32(&tmB, Mt, Kc, K, K, gt::BK, n1)) return cudaErrorInvalidValue;
-  if (!map_f32(&tmB2, Mt, Kc, K, K, gt::BK, n2 > 0 ? n2 : 32)) return cudaErrorInvalidValue;
+  if (!map_f32(&tmB0, Mt2, 2 * npad, K, K, gt::BK, N0)) return cudaErrorInvalidValue;
+  if (!map_f32(&tmB1, Mt2, 2 * npad, K, K, gt::BK, N1 > 0 ? N1 : 32)) return cudaErrorInvalidValue;
   const size_t smem = gemm_tc_smem(npad);
   auto kern = tall_tf32x3_kernel;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int nkb = (K + gt::BK - 1) / gt::BK;
   const int64_t ntiles = (n + gt::BM - 1) / gt::BM;
-  const int grid = (int)min64(ntiles, (int64_t)sm_count());
+  const int64_t nitems = ntiles * (N1 > 0 ? 2 : 1);
+  const int grid = (int)min64(nitems, (int64_t)sm_count());
   const int vec4 = (ldc % 4 == 0 && (uintptr_t)C % 16 == 0) ? 1 : 0;
   ProfScope ps_(K_TALL_TC, st);
-  kern<<<grid, gt::kThreads, smem, st>>>(tmA, tmB, tmB2, npad, nkb, ntiles, n, Kc, C, ldc, vec4,
+  kern<<<grid, gt::kThreads, smem, st>>>(tmA, tmB0, tmB1, npad, nkb, ntiles, n, Kc, C, ldc, vec4,
                                          ctrl);
   return cudaGetLastError();
 }

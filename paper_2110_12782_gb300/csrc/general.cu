@@ -43,7 +43,7 @@ struct GenBufs {
   float *Yh, *Z;              // rows of f(LR) O on the rows of H (l z_n x l), Z (l x l)
   float *partial;             // Gram scratch
   float *m32;                 // 3 h x h FP32
-  float *Mt;                  // tall-product scratch (h x h)
+  float *Mt;                  // tall-product scratch (the split M^T)
   double *HY, *OK, *G1, *G2;  // l x h FP64
   double *R1, *R2, *RY, *RK;  // h x h FP64
   double *N, *Ni, *NN;        // h x h FP64 (normal equations)
@@ -99,7 +99,7 @@ size_t gen_carve(const GenDims &D, void *base, GenBufs *b) {
   x.partial = static_cast<float *>(
       take(std::max(gram_partial_floats(D.n, D.h, D.h), gram_partial_floats(D.m, D.h, D.h)) * 4));
   x.m32 = static_cast<float *>(take(3 * hh * 4));
-  x.Mt = static_cast<float *>(take(hh * 4));
+  x.Mt = static_cast<float *>(take(tall_tc_scratch_floats(D.h, D.h) * 4));
   x.HY = static_cast<double *>(take(lh * 8));
   x.OK = static_cast<double *>(take(lh * 8));
   x.G1 = static_cast<double *>(take(lh * 8));

@@ -158,10 +158,15 @@ cudaError_t launch_gram_tc(const float *A, int64_t lda, int Ka, const float *B, 
 // (a, b) with a / sym_tile > b / sym_tile are read from (b, a).
 cudaError_t launch_gram_reduce(const float *partial, int Ka, int Kb, int chunks, int sym_tile,
                                double *C, int ldc, cudaStream_t st);
-cudaError_t launch_tall_gemm_tc(const float *A, int64_t lda, int64_t n, int K, const float *Mt, int Kc,
-                                float *C, int64_t ldc, Ctrl *ctrl, cudaStream_t st);
-// C = A M through the tensor-core path when possible (Mt: Ka x Kc scratch for M^T),
-// else the SIMT tall_gemm.
+// C = A M with M (K x Kc, leading dimension ldm); Mt2: scratch of
+// tall_tc_scratch_floats(K, Kc) floats (M^T split into TF32 hi and lo rows).
+size_t tall_tc_scratch_floats(int K, int Kc);
+cudaError_t launch_tall_gemm_tc(const float *A, int64_t lda, int64_t n, int K, const float *M,
+                                int ldm, int Kc, float *C, int64_t ldc, float *Mt2, Ctrl *ctrl,
+                                cudaStream_t st);
+// C = A M through the tensor-core path when possible (Mt: scratch of
+// tall_tc_scratch_floats(Ka, Kc) floats for the split M^T), else the SIMT
+// tall_gemm.
 cudaError_t launch_tall_gemm_auto(const float *A, int64_t lda, int64_t n, int32_t Ka, const float *M,
                                   int32_t ldm, int32_t Kc, float *C, int64_t ldc, float *Mt,
                                   Ctrl *ctrl, cudaStream_t st);

@@ -101,8 +101,8 @@ def test_gram_cross(sk, n, ka, kb, accurate):
     assert err < TOL[accurate]
 
 
-@pytest.mark.parametrize("n,ka,kc", [(500, 40, 24), (4097, 272, 272), (1_000_000, 272, 256),
-                                     (1_000_000, 272, 128)])
+@pytest.mark.parametrize("n,ka,kc", [(500, 40, 24), (4097, 272, 272), (20_000, 272, 200),
+                                     (1_000_000, 272, 256), (1_000_000, 272, 128)])
 def test_tall_gemm(sk, n, ka, kc):
     A = tall_basis(n, ka, seed=5)
     rng = np.random.default_rng(6)
