@@ -267,16 +267,21 @@ __global__ void __launch_bounds__(gt::kThreads, 1) tall_tf32x3_kernel(
 // The tensor-core accumulator does not round like IEEE addition: summing a
 // long chain of small products into a large total drifts.  So each TMEM
 // accumulator takes only kSeg k-blocks (kSeg * 32 rows, 3 * 4 * kSeg MMA
-// updates) before the MMA moves to the other accumulator, and four drain warps
-// add the finished one into FP32 registers with ordinary (round-to-nearest)
-// additions.  Output tile 128 (a) x 128 (b).
-// Warps: 0 TMA, 1 MMA, 2-5 split, 6-9 drain.
+// updates) before the MMA moves to the other accumulator, and eight drain
+// warps (two per TMEM lane quarter, 64 columns each) add the finished one into
+// FP32 registers with ordinary (round-to-nearest) additions.  Output tile
+// 128 (a) x 128 (b).  The transposing split is the costliest part of the
+// kernel (without it a launch takes 58% of the time), so eight warps share it.
+// Warps: 0 TMA, 1 MMA, 2-9 split, 10-17 drain.
 // ---------------------------------------------------------------------------
 namespace gg {
 constexpr int BN = 128;
 constexpr int kSeg = 4;
-constexpr int kThreads = 320;
+constexpr int kSplitThreads = 256;        // warps 2-9
+constexpr int kDrainThreads = 256;        // warps 10-17
+constexpr int kThreads = 64 + kSplitThreads + kDrainThreads;
 constexpr int kTileBytes = 128 * 32 * 4;  // 16 KB: 128 rows x 32 fp32
+constexpr int kRawStages = 3;             // TMA stages of raw boxes
 }  // namespace gg
 
 __global__ void __launch_bounds__(gg::kThreads, 1) gram_tf32x3_kernel(
@@ -287,13 +292,13 @@ __global__ void __launch_bounds__(gg::kThreads, 1) gram_tf32x3_kernel(
   extern __shared__ __align__(1024) unsigned char gg_smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(gg_smem_raw) + 1023) & ~(uintptr_t)1023);
-  // raw[2] = {A 16 KB, B 16 KB}; hilo[2] = {A_hi, A_lo, B_hi, B_lo} 16 KB each
+  // raw[3] = {A 16 KB, B 16 KB}; hilo[2] = {A_hi, A_lo, B_hi, B_lo} 16 KB each
   unsigned char *raw = smem;
-  unsigned char *hilo = smem + 2 * 2 * gg::kTileBytes;
+  unsigned char *hilo = smem + gg::kRawStages * 2 * gg::kTileBytes;
   uint64_t *bars = reinterpret_cast<uint64_t *>(hilo + 2 * 4 * gg::kTileBytes);
-  uint64_t *full = bars;           // [2]
-  uint64_t *rawfree = full + 2;    // [2]
-  uint64_t *ready = rawfree + 2;   // [2]
+  uint64_t *full = bars;                        // [kRawStages]
+  uint64_t *rawfree = full + gg::kRawStages;    // [kRawStages]
+  uint64_t *ready = rawfree + gg::kRawStages;   // [2]
   uint64_t *hfree = ready + 2;     // [2]
   uint64_t *accfull = hfree + 2;   // [2]
   uint64_t *accfree = accfull + 2; // [2]
@@ -332,13 +337,15 @@ __global__ void __launch_bounds__(gg::kThreads, 1) gram_tf32x3_kernel(
   const uint32_t raw_bytes = (uint32_t)(gt::kABytes + (diag ? 0 : bbytes));
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < gg::kRawStages; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&rawfree[s], 128);
-      mbar_init(&ready[s], 128);
+      mbar_init(&rawfree[s], gg::kSplitThreads);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&ready[s], gg::kSplitThreads);
       mbar_init(&hfree[s], 1);
       mbar_init(&accfull[s], 1);
-      mbar_init(&accfree[s], 128);
+      mbar_init(&accfree[s], gg::kDrainThreads);
     }
     mbar_init(done, 1);
     *abort_flag = 0;
@@ -361,8 +368,8 @@ __global__ void __launch_bounds__(gg::kThreads, 1) gram_tf32x3_kernel(
     if (lane == 0) {
       int issued = 0;
       for (int kb = 0; kb < kblocks; ++kb) {
-        const int s = kb & 1;
-        if (!mbar_wait(&rawfree[s], (uint32_t)(((kb >> 1) & 1) ^ 1), abortv, ctrl)) break;
+        const int s = kb % gg::kRawStages;
+        if (!mbar_wait(&rawfree[s], (uint32_t)(((kb / gg::kRawStages) & 1) ^ 1), abortv, ctrl)) break;
         unsigned char *rb = raw + (size_t)s * 2 * gg::kTileBytes;
         mbar_expect_tx(&full[s], raw_bytes);
         const int y = (int)(r0 + (int64_t)kb * gt::BK);
@@ -372,12 +379,9 @@ __global__ void __launch_bounds__(gg::kThreads, 1) gram_tf32x3_kernel(
             tma_load_2d(rb + gg::kTileBytes + t * 4096, &tmB, &full[s], b0 + 32 * t, y);
         ++issued;
       }
-      const int first = issued > 2 ? issued - 2 : 0;
-      for (int q = first; q < issued; ++q) {
-        const uint64_t t0 = gtimer();
-        while (!mbar_try_wait(&full[q & 1], (uint32_t)((q >> 1) & 1)) && gtimer() - t0 < kTimeoutNs) {
-        }
-      }
+      const int first = issued > gg::kRawStages ? issued - gg::kRawStages : 0;
+      for (int q = first; q < issued; ++q)
+        mbar_drain(&full[q % gg::kRawStages], (uint32_t)((q / gg::kRawStages) & 1), kTimeoutNs);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -424,14 +428,14 @@ __global__ void __launch_bounds__(gg::kThreads, 1) gram_tf32x3_kernel(
       while (!mbar_try_wait(done, 0u) && gtimer() - t0 < kTimeoutNs) {
       }
     }
-  } else if (warp < 6) {
+  } else if (warp < 2 + gg::kSplitThreads / 32) {
     // ---------------- split warps: raw (MN boxes) -> transposed hi / lo
     const int t = threadIdx.x - 64;
     for (int kb = 0; kb < kblocks; ++kb) {
-      const int s = kb & 1;
-      if (!mbar_wait(&full[s], (uint32_t)((kb >> 1) & 1), abortv, ctrl)) break;
+      const int s = kb & 1, rs = kb % gg::kRawStages;
+      if (!mbar_wait(&full[rs], (uint32_t)((kb / gg::kRawStages) & 1), abortv, ctrl)) break;
       if (kb >= 2 && !mbar_wait(&hfree[s], (uint32_t)(((kb >> 1) - 1) & 1), abortv, ctrl)) break;
-      const float *rawf = reinterpret_cast<const float *>(raw + (size_t)s * 2 * gg::kTileBytes);
+      const float *rawf = reinterpret_cast<const float *>(raw + (size_t)rs * 2 * gg::kTileBytes);
       float *hA = reinterpret_cast<float *>(hilo + (size_t)s * 4 * gg::kTileBytes);
       float *lA = hA + gg::kTileBytes / 4;
       float *hB = lA + gg::kTileBytes / 4;
@@ -446,7 +450,7 @@ __global__ void __launch_bounds__(gg::kThreads, 1) gram_tf32x3_kernel(
       // and their stores (chunks ic ^ 4(j & 1) ^ v) fall on 8 distinct chunks:
       // no bank conflicts.
       const int ntask = (4 + (diag ? 0 : npad / 32)) * 64;
-      for (int tau = t; tau < ntask; tau += 128) {
+      for (int tau = t; tau < ntask; tau += gg::kSplitThreads) {
         const int box = tau >> 6, g = (tau >> 3) & 7, ic = tau & 7, j = ic ^ g;
         const bool isA = box < 4;
         const int m = isA ? box : box - 4;
@@ -484,16 +488,20 @@ __global__ void __launch_bounds__(gg::kThreads, 1) gram_tf32x3_kernel(
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(&rawfree[s]);
+      mbar_arrive(&rawfree[rs]);
       mbar_arrive(&ready[s]);
     }
   } else {
-    // ---------------- drain warps: finished accumulators -> FP32 registers
+    // ---------------- drain warps: finished accumulators -> FP32 registers;
+    // warp w reads TMEM lane quarter w % 4 and columns 64 h .. 64 h + 63,
+    // h = (w - 10) / 4
+    constexpr int DW = gg::BN / 2;
     const int ew = warp & 3;
+    const int cb = DW * ((warp - 2 - gg::kSplitThreads / 32) >> 2);
     const int64_t r = a0 + 32 * ew + lane;
-    float acc[gg::BN];
+    float acc[DW];
 #pragma unroll
-    for (int c = 0; c < gg::BN; ++c) acc[c] = 0.0f;
+    for (int c = 0; c < DW; ++c) acc[c] = 0.0f;
     bool ok = true;
     for (int seg = 0; seg < nseg; ++seg) {
       const int buf = seg & 1;
@@ -503,10 +511,10 @@ __global__ void __launch_bounds__(gg::kThreads, 1) gram_tf32x3_kernel(
       }
       fence_after();
 #pragma unroll
-      for (int c = 0; c < gg::BN; c += 32) {
-        if (c < npad) {
+      for (int c = 0; c < DW; c += 32) {
+        if (cb + c < npad) {
           float v[32];
-          tmem_ld32(tmem + ((uint32_t)(32 * ew) << 16) + (uint32_t)(buf * gg::BN + c), v);
+          tmem_ld32(tmem + ((uint32_t)(32 * ew) << 16) + (uint32_t)(buf * gg::BN + cb + c), v);
 #pragma unroll
           for (int q = 0; q < 32; ++q) acc[c + q] += v[q];
         }
@@ -515,10 +523,10 @@ __global__ void __launch_bounds__(gg::kThreads, 1) gram_tf32x3_kernel(
       mbar_arrive(&accfree[buf]);
     }
     if (r < mrows) {
-      float *orow = out + (int64_t)blockIdx.y * chunk_stride + r * ldo + b0;
+      float *orow = out + (int64_t)blockIdx.y * chunk_stride + r * ldo + b0 + cb;
 #pragma unroll
-      for (int c = 0; c < gg::BN; ++c)
-        if (b0 + c < ncols && (ok || kblocks == 0)) orow[c] = acc[c];
+      for (int c = 0; c < DW; ++c)
+        if (b0 + cb + c < ncols && (ok || kblocks == 0)) orow[c] = acc[c];
     }
   }
   fence_before();
@@ -667,7 +675,8 @@ cudaError_t launch_gram_tc(const float *A, int64_t lda, int Ka, const float *B, 
   CUtensorMap tmA, tmB;
   if (!map_f32(&tmA, A, n, Ka, lda, 32, gt::BK)) return cudaErrorInvalidValue;
   if (!map_f32(&tmB, B, n, Kb, ldb, 32, gt::BK)) return cudaErrorInvalidValue;
-  const size_t smem = 1024 + (size_t)2 * 2 * gg::kTileBytes + (size_t)2 * 4 * gg::kTileBytes + 256;
+  const size_t smem =
+      1024 + (size_t)gg::kRawStages * 2 * gg::kTileBytes + (size_t)2 * 4 * gg::kTileBytes + 256;
   auto kern = gram_tf32x3_kernel;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
