@@ -59,6 +59,15 @@ __host__ __device__ inline void tall_halves(int npad, int *N0, int *N1) {
 // 0 and 256) alternate between work items, so that the epilogue of one
 // overlaps the MMAs of the next; the stage ring and the barrier phases run on
 // across work items.
+//
+// PAIR: the CTAs run in clusters of two that take the row tiles 2t and 2t + 1
+// of the same work items in lockstep; each CTA loads half of every B stage
+// and multicasts it to both, so that the split M^T (the same for every tile)
+// is read from L2 once per pair instead of once per CTA.  A stage is free
+// again only when the MMAs of both CTAs are done with it (the MMA commits
+// arrive on the empty barriers of both), and the cluster synchronizes after
+// its barriers are initialized and before it exits.
+template <bool PAIR>
 __global__ void __launch_bounds__(gt::kThreads, 1) tall_tf32x3_kernel(
     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB0,
     const __grid_constant__ CUtensorMap tmB1, int npad, int nkb, int64_t ntiles, int64_t nrows,
@@ -83,13 +92,22 @@ __global__ void __launch_bounds__(gt::kThreads, 1) tall_tf32x3_kernel(
   int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t nitems = ntiles * nhalf;
+  // work items (tile pair or tile, half); this CTA's tile of item w
+  const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
+  const int64_t nitems = (PAIR ? (ntiles + 1) / 2 : ntiles) * nhalf;
+  const int64_t first = PAIR ? (int64_t)(blockIdx.x >> 1) : (int64_t)blockIdx.x;
+  const int64_t step = PAIR ? (int64_t)(gridDim.x >> 1) : (int64_t)gridDim.x;
+  auto item = [&](int64_t w, int64_t &tile, int &half) {
+    const int64_t tq = w / nhalf;
+    half = (int)(w - tq * nhalf);
+    tile = PAIR ? 2 * tq + rank : tq;
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < gt::kStages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&split[s], 128);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], PAIR ? 2 : 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&accfull[b], 1);
@@ -109,6 +127,7 @@ __global__ void __launch_bounds__(gt::kThreads, 1) tall_tf32x3_kernel(
   fence_before();
   __syncthreads();
   fence_after();
+  if (PAIR) cluster_sync_all();  // the peer's barriers exist before any multicast
   const uint32_t tmem = *tmem_slot;
   volatile int *abortv = abort_flag;
 
@@ -118,9 +137,10 @@ __global__ void __launch_bounds__(gt::kThreads, 1) tall_tf32x3_kernel(
       // ---------------- TMA producer
       uint32_t it = 0;
       bool ok = true;
-      for (int64_t w = blockIdx.x; w < nitems && ok; w += gridDim.x) {
-        const int64_t tile = w / nhalf;
-        const int half = (int)(w - tile * nhalf);
+      for (int64_t w = first; w < nitems && ok; w += step) {
+        int64_t tile;
+        int half;
+        item(w, tile, half);
         const int N = half ? N1 : N0, c0 = half ? N0 : 0;
         const CUtensorMap *tmB = half ? &tmB1 : &tmB0;
         const int m0 = (int)(tile * gt::BM);
@@ -135,8 +155,17 @@ __global__ void __launch_bounds__(gt::kThreads, 1) tall_tf32x3_kernel(
           // A box {32 k, 128 rows}; B boxes {32 k, N rows}: hi rows c0 ..,
           // lo rows npad + c0 ..
           tma_load_2d(st, &tmA, &full[s], kb * gt::BK, m0);
-          tma_load_2d(st + 2 * gt::kABytes, tmB, &full[s], kb * gt::BK, c0);
-          tma_load_2d(st + 2 * gt::kABytes + bmax, tmB, &full[s], kb * gt::BK, npad + c0);
+          if (PAIR) {
+            // this CTA's half of the B rows, to both CTAs of the pair
+            const int Nh = N / 2, off = (int)rank * Nh;
+            tma_load_2d_mc(st + 2 * gt::kABytes + off * 128, tmB, &full[s], kb * gt::BK, c0 + off,
+                           (uint16_t)3);
+            tma_load_2d_mc(st + 2 * gt::kABytes + bmax + off * 128, tmB, &full[s], kb * gt::BK,
+                           npad + c0 + off, (uint16_t)3);
+          } else {
+            tma_load_2d(st + 2 * gt::kABytes, tmB, &full[s], kb * gt::BK, c0);
+            tma_load_2d(st + 2 * gt::kABytes + bmax, tmB, &full[s], kb * gt::BK, npad + c0);
+          }
         }
       }
       if (!ok) {
@@ -153,9 +182,10 @@ __global__ void __launch_bounds__(gt::kThreads, 1) tall_tf32x3_kernel(
       const uint32_t base = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(gt::BM >> 4) << 24);
       uint32_t it = 0, u = 0;
       bool ok = true;
-      for (int64_t w = blockIdx.x; w < nitems && ok; w += gridDim.x, ++u) {
-        const int64_t tile = w / nhalf;
-        const int half = (int)(w - tile * nhalf);
+      for (int64_t w = first; w < nitems && ok; w += step, ++u) {
+        int64_t tile;
+        int half;
+        item(w, tile, half);
         const int N = half ? N1 : N0;
         const uint32_t idesc = base | ((uint32_t)(N >> 3) << 17);
         const int buf = u & 1;
@@ -182,7 +212,10 @@ __global__ void __launch_bounds__(gt::kThreads, 1) tall_tf32x3_kernel(
             mma_tf32(dt, da_hi, sdesc2(blo + kk * 32, 16, 1024), idesc, 1u);
             mma_tf32(dt, sdesc2(alo + kk * 32, 16, 1024), db_hi, idesc, 1u);
           }
-          mma_commit(&empty[s]);
+          if (PAIR)
+            mma_commit_mc(&empty[s], (uint16_t)3);
+          else
+            mma_commit(&empty[s]);
         }
         if (ok) mma_commit(&accfull[buf]);
       }
@@ -195,7 +228,7 @@ __global__ void __launch_bounds__(gt::kThreads, 1) tall_tf32x3_kernel(
     const int t = threadIdx.x - 64;  // 0..127
     uint32_t it = 0;
     bool ok = true;
-    for (int64_t w = blockIdx.x; w < nitems && ok; w += gridDim.x) {
+    for (int64_t w = first; w < nitems && ok; w += step) {
       for (int kb = 0; kb < nkb; ++kb, ++it) {
         const int s = it % gt::kStages;
         if (!mbar_wait(&full[s], (it / gt::kStages) & 1, abortv, ctrl)) {
@@ -220,9 +253,10 @@ __global__ void __launch_bounds__(gt::kThreads, 1) tall_tf32x3_kernel(
     // ---------------- warps 6..9: epilogue, one accumulator row per thread
     const int ew = warp & 3;  // TMEM lane quarter of this warp
     uint32_t u = 0;
-    for (int64_t w = blockIdx.x; w < nitems; w += gridDim.x, ++u) {
-      const int64_t tile = w / nhalf;
-      const int half = (int)(w - tile * nhalf);
+    for (int64_t w = first; w < nitems; w += step, ++u) {
+      int64_t tile;
+      int half;
+      item(w, tile, half);
       const int N = half ? N1 : N0, c0 = half ? N0 : 0;
       const int buf = u & 1;
       if (!mbar_wait(&accfull[buf], (u >> 1) & 1, abortv, ctrl)) break;
@@ -252,6 +286,8 @@ __global__ void __launch_bounds__(gt::kThreads, 1) tall_tf32x3_kernel(
   fence_before();
   __syncthreads();
   fence_after();
+  // no copy or MMA commit of the peer targets this CTA after this point
+  if (PAIR) cluster_sync_all();
   if (warp == 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
@@ -622,20 +658,48 @@ cudaError_t launch_tall_gemm_tc(const float *A, int64_t lda, int64_t n, int K, c
   if (e != cudaSuccess) return e;
   int N0, N1;
   tall_halves(npad, &N0, &N1);
-  CUtensorMap tmA, tmB0, tmB1;
-  if (!map_f32(&tmA, A, n, K, lda, gt::BK, gt::BM)) return cudaErrorInvalidValue;
-  if (!map_f32(&tmB0, Mt2, 2 * npad, K, K, gt::BK, N0)) return cudaErrorInvalidValue;
-  if (!map_f32(&tmB1, Mt2, 2 * npad, K, K, gt::BK, N1 > 0 ? N1 : 32)) return cudaErrorInvalidValue;
-  const size_t smem = gemm_tc_smem(npad);
-  auto kern = tall_tf32x3_kernel;
-  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   const int nkb = (K + gt::BK - 1) / gt::BK;
   const int64_t ntiles = (n + gt::BM - 1) / gt::BM;
-  const int64_t nitems = ntiles * (N1 > 0 ? 2 : 1);
-  const int grid = (int)min64(nitems, (int64_t)sm_count());
+  const int nhalf = N1 > 0 ? 2 : 1;
   const int vec4 = (ldc % 4 == 0 && (uintptr_t)C % 16 == 0) ? 1 : 0;
+  const size_t smem = gemm_tc_smem(npad);
+  CUtensorMap tmA;
+  if (!map_f32(&tmA, A, n, K, lda, gt::BK, gt::BM)) return cudaErrorInvalidValue;
   ProfScope ps_(K_TALL_TC, st);
+  // pairs of CTAs sharing each B stage, when the tiles are at least two
+  if (ntiles >= 2 && sm_count() >= 2) {
+    CUtensorMap tmB0, tmB1;
+    if (!map_f32(&tmB0, Mt2, 2 * npad, K, K, gt::BK, N0 / 2)) return cudaErrorInvalidValue;
+    if (!map_f32(&tmB1, Mt2, 2 * npad, K, K, gt::BK, N1 > 0 ? N1 / 2 : 16))
+      return cudaErrorInvalidValue;
+    auto kern = tall_tf32x3_kernel<true>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t items = ((ntiles + 1) / 2) * nhalf;
+    const int grid = 2 * (int)min64(items, (int64_t)(sm_count() / 2));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(gt::kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, kern, tmA, tmB0, tmB1, npad, nkb, ntiles, n, Kc, C, ldc, vec4, ctrl);
+    if (e == cudaSuccess) return cudaSuccess;
+    (void)cudaGetLastError();  // clusters unavailable: one CTA per work item below
+  }
+  CUtensorMap tmB0, tmB1;
+  if (!map_f32(&tmB0, Mt2, 2 * npad, K, K, gt::BK, N0)) return cudaErrorInvalidValue;
+  if (!map_f32(&tmB1, Mt2, 2 * npad, K, K, gt::BK, N1 > 0 ? N1 : 32)) return cudaErrorInvalidValue;
+  auto kern = tall_tf32x3_kernel<false>;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid = (int)min64(ntiles * nhalf, (int64_t)sm_count());
   kern<<<grid, gt::kThreads, smem, st>>>(tmA, tmB0, tmB1, npad, nkb, ntiles, n, Kc, C, ldc, vec4,
                                          ctrl);
   return cudaGetLastError();
