@@ -24,6 +24,8 @@
 #include <cmath>
 #include <cstdlib>
 
+#include <algorithm>
+
 #include "sne_internal.cuh"
 
 namespace sne {
@@ -248,28 +250,39 @@ cudaError_t launch_jacobi_f32(const float *A, int32_t n, int32_t lda, float *w, 
 }
 
 // ---------------------------------------------------------------------------
-// Ogita-Aishima refinement step (FP64), single CTA:
-// given T1 = X^T X and S = X^T A X, writes lambda and E (over T1).
+// Ogita-Aishima refinement step (FP64), over many CTAs: given T1 = X^T X and
+// S = X^T A X, oa_stats_kernel forms lambda_i = S_ii / T1_ii and the sums
+// |S - diag(lambda)|_F^2, |A|_F^2, |I - T1|_F^2 and max |lambda| (acc[0..3],
+// zeroed before the launch); oa_apply_kernel writes the correction E over T1
+// and the largest |E| (acc[4], as bits); oa_done_kernel marks the refinement
+// converged when that correction is at rounding level (this step is applied,
+// later ones are skipped).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) oa_update_kernel(double *T1, const double *S, const double *A,
-                                                         int lda, int n, double *lam, int *done) {
-  __shared__ double red[4][32];
-  __shared__ double sdelta;
-  __shared__ unsigned long long emax_bits;
+__device__ __forceinline__ void atomic_max_nonneg(double *addr, double v) {
+  // non-negative doubles order like their bit patterns
+  atomicMax(reinterpret_cast<unsigned long long *>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+__global__ void __launch_bounds__(256) oa_stats_kernel(const double *T1, const double *S,
+                                                       const double *A, int lda, int n,
+                                                       double *lam, double *acc, const int *done) {
+  __shared__ double red[3][8];
+  __shared__ double rmax[8];
   if (*done) return;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid == 0) emax_bits = 0ull;
-  double lmax = 0.0;
-  for (int i = tid; i < n; i += nt) {
-    lam[i] = S[(int64_t)i * n + i] / T1[(int64_t)i * n + i];
-    lmax = fmax(lmax, fabs(lam[i]));
-  }
-  __syncthreads();
-  double so = 0.0, sa = 0.0, sr = 0.0;
-  for (int64_t q = tid; q < (int64_t)n * n; q += nt) {
+  const int tid = threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  double so = 0.0, sa = 0.0, sr = 0.0, lmax = 0.0;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + tid; q < (int64_t)n * n; q += stride) {
     const int i = (int)(q / n), j = (int)(q % n);
-    const double s = S[q] - (i == j ? lam[i] : 0.0);
-    const double r = (i == j ? 1.0 : 0.0) - T1[q];
+    double s = S[q];
+    double r = -T1[q];
+    if (i == j) {
+      const double li = S[q] / T1[q];
+      lam[i] = li;
+      lmax = fmax(lmax, fabs(li));
+      s -= li;
+      r += 1.0;
+    }
     so += s * s;
     const double av = A[(int64_t)i * lda + j];
     sa += av * av;
@@ -285,28 +298,39 @@ __global__ void __launch_bounds__(1024) oa_update_kernel(double *T1, const doubl
     red[0][tid >> 5] = so;
     red[1][tid >> 5] = sa;
     red[2][tid >> 5] = sr;
-    red[3][tid >> 5] = lmax;
+    rmax[tid >> 5] = lmax;
   }
   __syncthreads();
   if (tid == 0) {
-    double a = 0, b = 0, c = 0, lm = 0;
-    for (int wv = 0; wv < (nt >> 5); ++wv) {
-      a += red[0][wv];
-      b += red[1][wv];
-      c += red[2][wv];
-      lm = fmax(lm, red[3][wv]);
+    double a = 0, b = 0, c = 0, m = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a += red[0][w];
+      b += red[1][w];
+      c += red[2][w];
+      m = fmax(m, rmax[w]);
     }
-    // pairs closer than 1e-4 max|lambda| are treated as one cluster (only
-    // re-orthogonalized).  The FP32 start mixes such a pair by an angle of up
-    // to eps_32 |A| / gap, too large for the first-order correction to
-    // converge; left unresolved, the pair's residual stays at the FP32
-    // rounding level and its eigenvalues within the gap.
-    sdelta = fmax(2.0 * (sqrt(a) + sqrt(b) * sqrt(c)), kClusterFloor * lm);
+    atomicAdd(&acc[0], a);
+    atomicAdd(&acc[1], b);
+    atomicAdd(&acc[2], c);
+    atomic_max_nonneg(&acc[3], m);
   }
-  __syncthreads();
-  const double delta = sdelta;
+}
+
+__global__ void __launch_bounds__(256) oa_apply_kernel(double *T1, const double *S, int n,
+                                                       const double *lam, double *acc,
+                                                       const int *done) {
+  __shared__ double rmax[8];
+  if (*done) return;
+  const int tid = threadIdx.x;
+  // pairs closer than 1e-4 max|lambda| are treated as one cluster (only
+  // re-orthogonalized).  The FP32 start mixes such a pair by an angle of up
+  // to eps_32 |A| / gap, too large for the first-order correction to
+  // converge; left unresolved, the pair's residual stays at the FP32
+  // rounding level and its eigenvalues within the gap.
+  const double delta = fmax(2.0 * (sqrt(acc[0]) + sqrt(acc[1]) * sqrt(acc[2])), kClusterFloor * acc[3]);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   double emax = 0.0;
-  for (int64_t q = tid; q < (int64_t)n * n; q += nt) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + tid; q < (int64_t)n * n; q += stride) {
     const int i = (int)(q / n), j = (int)(q % n);
     const double r = (i == j ? 1.0 : 0.0) - T1[q];
     const double gap = lam[j] - lam[i];
@@ -316,11 +340,18 @@ __global__ void __launch_bounds__(1024) oa_update_kernel(double *T1, const doubl
     T1[q] = e;
     emax = fmax(emax, fabs(e));
   }
-  // non-negative doubles order like their bit patterns
-  atomicMax(&emax_bits, (unsigned long long)__double_as_longlong(emax));
+  for (int o = 16; o > 0; o >>= 1) emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+  if ((tid & 31) == 0) rmax[tid >> 5] = emax;
   __syncthreads();
-  // the correction is at rounding level: this step is applied, later ones are skipped
-  if (tid == 0 && __longlong_as_double((long long)emax_bits) < 1e-14) *done = 1;
+  if (tid == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, rmax[w]);
+    atomic_max_nonneg(&acc[4], m);
+  }
+}
+
+__global__ void oa_done_kernel(const double *acc, int *done) {
+  if (*done == 0 && acc[4] < 1e-14) *done = 1;
 }
 
 __global__ void add_inplace_kernel(double *X, const double *Y, int64_t count, const int *skip) {
@@ -670,11 +701,11 @@ __global__ void __launch_bounds__(1024) chol_inv_blocked_kernel(const T *__restr
 // 32 x 33 floats (the padding keeps column walks free of bank conflicts);
 // rows and columns past n are those of the identity, so the factor of the
 // padded matrix is diag(R, I).
-//   factor, panel p: one warp factors block (p, p) and inverts it,
-//   X_pp = R_pp^-1 (column per lane, by back substitution; kept for the
+//   factor, panel p: the 1024 threads factor block (p, p) (thread per entry,
+//   two barriers per column) and invert it, X_pp = R_pp^-1 (warp per column,
+//   back substitution with the sums as warp reductions; kept for the
 //   inverse); all warps form R_pq = X_pp^T A_pq for q > p and update the
-//   trailing blocks A_qr -= R_pq^T R_pr with 4 x 4 register tiles; four
-//   barriers per panel and no sequential solve outside the diagonal block.
+//   trailing blocks A_qr -= R_pq^T R_pr with 4 x 4 register tiles.
 //   inverse, block column j: T_i = sum_{m=i}^{j-1} X_im R_mj for i < j (X = R^-1,
 //   columns < j already done), then X_ij = -T_i X_jj; two barriers per block
 //   column.
@@ -720,9 +751,10 @@ __global__ void __launch_bounds__(1024) chol_inv_quick_kernel(const float *__res
   // ---- factorization
   for (int p = 0; p < nb; ++p) {
     float *bpp = B(p, p);
-    if (warp == 0) {
-      // lane c owns column c of the diagonal block
-      for (int j = 0; j < kQB; ++j) {
+    // the diagonal block by all 1024 threads, thread (r, c) = (warp, lane):
+    // step j scales row j (warp j) and updates the trailing triangle
+    for (int j = 0; j < kQB; ++j) {
+      if (warp == j) {
         float djj = bpp[j * kQLd + j];
         if (!(djj > 0.f) || !isfinite(djj)) {
           if (lane == 0) record_error(ctrl, SNE_ERR_NUMERIC, W_CHOL);
@@ -732,24 +764,25 @@ __global__ void __launch_bounds__(1024) chol_inv_quick_kernel(const float *__res
         __syncwarp();
         if (lane == j) bpp[j * kQLd + j] = d;
         else if (lane > j) bpp[j * kQLd + lane] /= d;
-        __syncwarp();
-        const float rjc = bpp[j * kQLd + lane];
-        for (int r = j + 1; r <= lane; ++r) bpp[r * kQLd + lane] -= bpp[j * kQLd + r] * rjc;
-        __syncwarp();
       }
-      // X_pp = R_pp^-1 into tmp block p: lane c, column c, rows c .. 0
+      __syncthreads();
+      if (warp > j && lane >= warp) bpp[warp * kQLd + lane] -= bpp[j * kQLd + warp] * bpp[j * kQLd + lane];
+      __syncthreads();
+    }
+    // X_pp = R_pp^-1 into tmp block p: warp c takes column c, lane m holds
+    // X[m][c]; row r = c .. 0: X[r][c] = (delta_rc - sum_{m>r} R[r][m] X[m][c]) / R[r][r]
+    {
       float *xpp = tmp + (size_t)p * kQB * kQB;
-      for (int r = kQB - 1; r >= 0; --r) {
-        float x = 0.f;
-        if (r == lane) {
-          x = 1.f / bpp[r * kQLd + r];
-        } else if (r < lane) {
-          for (int m = r + 1; m <= lane; ++m) x -= bpp[r * kQLd + m] * xpp[m * kQB + lane];
-          x /= bpp[r * kQLd + r];
-        }
-        xpp[r * kQB + lane] = x;
-        __syncwarp();
+      const int c = warp;
+      float xm = 0.f;
+      for (int r = c; r >= 0; --r) {
+        float part = (lane > r && lane <= c) ? bpp[r * kQLd + lane] * xm : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        const float xr = ((r == c ? 1.f : 0.f) - part) / bpp[r * kQLd + r];
+        if (lane == r) xm = xr;
       }
+      xpp[lane * kQB + c] = lane <= c ? xm : 0.f;
     }
     __syncthreads();
     // R_pq = X_pp^T A_pq, q > p, in 4 x 4 tiles (at most 8 blocks x 64 tiles,
@@ -1163,6 +1196,7 @@ cudaError_t launch_sym_eig_fast(double *A, int32_t n, int32_t lda, double *w, do
   if (e != cudaSuccess) return e;
   double *Ac = T3;  // S
   int *done = nrounds + 1;  // set once a correction is at rounding level
+  double *oacc = reinterpret_cast<double *>(base + 64);  // refinement sums (8 doubles)
   e = cudaMemsetAsync(done, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   for (int it = 0; it < kRefineSteps; ++it) {
@@ -1173,8 +1207,13 @@ cudaError_t launch_sym_eig_fast(double *A, int32_t n, int32_t lda, double *w, do
     e = launch_small_gemm<double>(true, false, n, n, n, 1.0, V, ldv, T2, n, 0.0, Ac, n, st, done);  // S
     if (e != cudaSuccess) return e;
     {
-      ProfScope ps_(K_EIG, st);
-      oa_update_kernel<<<1, 1024, 0, st>>>(T1, Ac, A, lda, n, w, done);
+      ProfScope ps_(K_EIG, st, 3);
+      e = cudaMemsetAsync(oacc, 0, 8 * sizeof(double), st);
+      if (e != cudaSuccess) return e;
+      const unsigned g = (unsigned)std::min<int64_t>(sm_count() * 2, ((int64_t)n * n + 255) / 256);
+      oa_stats_kernel<<<g, 256, 0, st>>>(T1, Ac, A, lda, n, w, oacc, done);
+      oa_apply_kernel<<<g, 256, 0, st>>>(T1, Ac, n, w, oacc, done);
+      oa_done_kernel<<<1, 1, 0, st>>>(oacc, done);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
