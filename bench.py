@@ -554,6 +554,14 @@ def run_ours(args, rank: int, world: int) -> None:
                                                        "config", "e2e", "gpu_launches",
                                                        "kernel_ms_per_step_summed_over_lanes")
                                 if k in bline}
+            # the same batch in plain FP32 and with FP16 hi/lo pairs
+            for prec_b in ("fp32", "fp16x2"):
+                bl = measure_batch(args, rank, world, "batch64", prec_b, ek, ew)
+                if bl is not None:
+                    extra["batch64"][prec_b] = {k: bl[k] for k in ("value", "ms_per_step")}
+            if rank == 0 and not args.no_cpu_baseline:
+                extra["batch64"]["error_vs_oracle"] = batch_error_vs_oracle(
+                    "batch64", ["fp16", "fp16x2", "fp32"])
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -734,6 +742,48 @@ def run_ours_batch(args, rank: int, world: int) -> None:
     line = measure_batch(args, rank, world, args.workload, args.precision, args.steps, args.warmup)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def batch_error_vs_oracle(workload: str, precisions, count: int = 4) -> dict:
+    """Part of the CPU-baseline leg: the embeddings of the `count` smallest
+    graphs of the batch (sne_embed, the per-graph pipeline the batched call
+    runs on its lanes) against the FP64 oracle's embedding with the same
+    parameters: the largest relative error of the singular values and the
+    largest principal-angle sine over the leading block whose relative gap is
+    at least 1e-2, per precision (maximum over the graphs)."""
+    import torch
+    from oracle import sketchne_oracle as o
+    from paper_2110_12782_gb300 import synth
+    from paper_2110_12782_gb300 import sketchne as sk
+    w = WORKLOADS[workload]
+    graphs = sorted(synth.batched_mix(w["count"]), key=lambda g: g.n)[:count]
+    out = {"graphs": [int(g.n) for g in graphs],
+           "metric": "max over graphs: sigma relative error, principal-angle sine (leading gapped block)"}
+    refs = [o.embed(g.row_ptr, g.col_idx, g.n, o.Params(k=w["k"], d=w["d"], q=w["q"], T=w["T"]))
+            for g in graphs]
+    for prec in precisions:
+        se, ss = 0.0, 0.0
+        for g, ref in zip(graphs, refs):
+            p = sk.sne_params_init(w["d"], w["k"], q=w["q"], T=w["T"], precision=sk.PRECISIONS[prec],
+                                   orth=sk.SNE_ORTH_CHOLQR)
+            G = sk.DeviceGraph.from_numpy(g.row_ptr, g.col_idx)
+            ws = sk.workspace(g.n, g.nnz, p, sk.SNE_WS_EMBED)
+            E = torch.empty(g.n, p.d, dtype=torch.float32, device="cuda")
+            sig = torch.empty(p.d, dtype=torch.float64, device="cuda")
+            sk.sne_embed(G, p, ws, E, sig)
+            sk.check_status(ws, f"batch graph {prec}")
+            s_ = sig.cpu().numpy()
+            blk = 0
+            for j in range(1, min(p.d, len(ref.sigma) - 1) + 1):
+                if (ref.sigma[j - 1] - ref.sigma[j]) / ref.sigma[j - 1] >= 1e-2:
+                    blk = j
+            if blk == 0:
+                continue
+            se = max(se, float(np.max(np.abs(s_[:blk] - ref.sigma[:blk]) / ref.sigma[:blk])))
+            ss = max(ss, float(o.principal_angle_sines(E.cpu().double().numpy()[:, :blk],
+                                                       ref.E[:, :blk]).max()))
+        out[prec] = {"sigma_rel": se, "sine": ss}
+    return out
 
 
 def measure_batch(args, rank: int, world: int, workload: str, precision: str, steps: int,
