@@ -314,14 +314,7 @@ inline unsigned grid_for(int64_t work, int per = 256, int cap = 0) {
 // Q = Y V diag(w)^-1/2) or Cholesky QR (B = R^T R, Q = Y R^-1).  The small
 // factorization runs in FP64 when `fp64` (sketch QR), else in FP32 (the
 // orthonormalizations inside the power iteration of Alg. 5).
-// Cholesky variants of orth_tall: unpivoted FP32 (inside freigs), pivoted
-// FP64 (the sketch QR's first pass, on Y itself), pivoted FP32 (its second
-// pass, on the already orthonormal Q1, whose Gram is I on its rank and zero
-// past it: FP32 suffices, since Q is FP32 and G = O^T Q is formed from the
-// same R^-1).
-enum { CHOL_F32 = 0, CHOL_F64_PIVOTED = 1, CHOL_F32_PIVOTED = 2 };
-
-int orth_tall(const Dims &D, const Bufs &b, int method, int chol, const float *Y, int64_t ldy, int w,
+int orth_tall(const Dims &D, const Bufs &b, int method, bool fp64, const float *Y, int64_t ldy, int w,
               float *Q, int64_t ldq, cudaStream_t st, bool accurate_gram = false) {
   if (accurate_gram)
     CK(launch_gram_accurate(Y, ldy, w, Y, ldy, w, D.n, nullptr, nullptr, true, b.partial, b.m64[0], w,
@@ -334,12 +327,7 @@ int orth_tall(const Dims &D, const Bufs &b, int method, int chol, const float *Y
     { ProfScope ps_(K_MISC, st); inv_sqrt_cols_kernel<<<grid_for((int64_t)w * w), 256, 0, st>>>(b.m32[1], w, w, b.w32, b.m32[2],
                                                                    w, b.ctrl); }
     CK(cudaGetLastError());
-  } else if (chol == CHOL_F32_PIVOTED) {
-    // rank cut far above the FP32 noise of a Gram that is I on its rank
-    CK(launch_d2f(b.m64[0], w, w, w, b.m32[0], w, st));
-    CK(launch_chol_inverse<float>(b.m32[0], w, w, b.m32[2], w, b.m32[1], b.ctrl, st, 1e-5));
-    CK(launch_f2d(b.m32[2], w, w, w, b.m64[1], w, st));
-  } else if (chol == CHOL_F64_PIVOTED) {
+  } else if (fp64) {
     // the sketch QR, in FP64: Y can be ill-conditioned (with half-precision
     // operands its small singular values are rounding noise), and an FP32
     // Cholesky of Y^T Y loses kappa(Y)^2 eps_32.  Pivoted, and cut only at the
@@ -370,12 +358,12 @@ int run_freigs(const sne_csr &g, const sne_params &p, const Dims &D, const Bufs 
   const uint32_t *hot = &b.ctrl->hot_bits;
   CK(launch_gaussian(D.n, K, p.seed, 1, T1, ld, st));              // Omega
   CK(launch_spmm(g, b.dpow, b.wnz, T1, ld, K, T2, K, st, hot));   // Y = X Omega
-  int rc = orth_tall(D, b, p.orth, CHOL_F32, T2, K, K, Q, ld, st);  // Q = eigSVD(Y)
+  int rc = orth_tall(D, b, p.orth, false, T2, K, K, Q, ld, st);    // Q = eigSVD(Y)
   if (rc) return rc;
   for (int it = 0; it < p.q; ++it) {
     CK(launch_spmm(g, b.dpow, b.wnz, Q, ld, K, T1, ld, st, hot));  // X Q
     CK(launch_spmm(g, b.dpow, b.wnz, T1, ld, K, T2, K, st, hot));  // X X Q
-    rc = orth_tall(D, b, p.orth, CHOL_F32, T2, K, K, Q, ld, st);   // Q = eigSVD(X X Q)
+    rc = orth_tall(D, b, p.orth, false, T2, K, K, Q, ld, st);      // Q = eigSVD(X X Q)
     if (rc) return rc;
   }
   // one more FP32 Cholesky-QR pass over the final basis (a no-op in exact
@@ -383,7 +371,7 @@ int run_freigs(const sne_csr &g, const sne_params &p, const Dims &D, const Bufs 
   // Rayleigh-Ritz step assumes Q^T Q = I
   CK(cudaMemcpy2DAsync(T2, K * sizeof(float), Q, ld * sizeof(float), K * sizeof(float), D.n,
                        cudaMemcpyDeviceToDevice, st));
-  rc = orth_tall(D, b, SNE_ORTH_CHOLQR, CHOL_F32, T2, K, K, Q, ld, st);
+  rc = orth_tall(D, b, SNE_ORTH_CHOLQR, false, T2, K, K, Q, ld, st);
   if (rc) return rc;
   // Rayleigh-Ritz: S = Q^T X Q (FP64), eig(S), U = Q U_hat, top k by |lambda|
   CK(launch_spmm(g, b.dpow, b.wnz, Q, ld, K, T1, ld, st, hot));
@@ -491,11 +479,11 @@ int run_sketch(const sne_csr &g, const sne_params &p, const Dims &D, const Bufs 
   // --- Alg. 4 line 5: Q = orth(Y) = Y R^-1 by Cholesky QR, twice (R = R2 R1)
   // the first pass sees Y itself: Cholesky QR loses about kappa(Y)^2 times the
   // Gram's relative error, so this Gram is the FP64-accurate one
-  int rc = orth_tall(D, b, SNE_ORTH_CHOLQR, CHOL_F64_PIVOTED, Y, h, h, b.B, h, st, true);  // Q1 = Y R1^-1
+  int rc = orth_tall(D, b, SNE_ORTH_CHOLQR, true, Y, h, h, b.B, h, st, true);  // Q1 = Y R1^-1
   if (rc) return rc;
   CK(cudaMemcpyAsync(b.m64[3], b.m64[1], (size_t)h * h * sizeof(double), cudaMemcpyDeviceToDevice,
                      st));                                                  // R1^-1
-  rc = orth_tall(D, b, SNE_ORTH_CHOLQR, CHOL_F32_PIVOTED, b.B, h, h, b.A, h, st);  // Q = Q1 R2^-1
+  rc = orth_tall(D, b, SNE_ORTH_CHOLQR, true, b.B, h, h, b.A, h, st);    // Q = Q1 R2^-1
   if (rc) return rc;
   float *Q = b.A;
   CK(launch_small_gemm<double>(false, false, h, h, h, 1.0, b.m64[3], h, b.m64[1], h, 0.0, b.m64[4],
