@@ -140,7 +140,9 @@ __device__ __forceinline__ int sturm_count(const float *d, const float *e2, int 
   if (fabsf(q) < pivmin) q = -pivmin;
   if (q < 0.f) ++c;
   for (int i = s + 1; i <= t; ++i) {
-    q = d[i] - x - e2[i - 1] / q;
+    // the division needs no IEEE rounding: the count only takes signs, and
+    // bisection tolerates an error of a few ulp in q
+    q = d[i] - x - __fdividef(e2[i - 1], q);
     if (fabsf(q) < pivmin) q = -pivmin;
     if (q < 0.f) ++c;
   }
@@ -148,6 +150,9 @@ __device__ __forceinline__ int sturm_count(const float *d, const float *e2, int 
 }
 
 constexpr int kTriMaxN = 1024;
+// threads of tri_eig_kernel: one per eigenvector up to 512 (more per thread
+// beyond), leaving each thread registers for the blocked solves
+constexpr int kTriEigThreads = 512;
 
 __device__ __forceinline__ float hash_unit(uint32_t a, uint32_t b) {
   uint64_t z = ((uint64_t)a << 32) ^ (uint64_t)b ^ 0x9E3779B97F4A7C15ull;
@@ -197,34 +202,85 @@ __device__ void tri_lu(const float *d, const float *e, int s, int sz, float shif
 // x <- (T_b - shift I)^-1 x (x = column m of X, rows s ..), then scaled to
 // max |x_i| = 1.
 __device__ void tri_solve(const TriLU &f, float *X, int s, int sz, int n, int m) {
+  // Rows are taken in blocks of kSB: the loads of a block (independent of the
+  // recurrence) are issued together, so that one L2 latency covers kSB steps.
+  constexpr int kSB = 4;
   float *x = X + (int64_t)s * n + m;
-  // forward: the row swaps and multipliers
+  const float *__restrict__ lm = f.lm + m;
+  const float *__restrict__ pv = f.pv + m;
+  const float *__restrict__ u1 = f.u1 + m;
+  const float *__restrict__ u2 = f.u2 + m;
+  const float *__restrict__ r0 = f.r0 + m;
+  // forward: the row swaps and multipliers (step i reads x[i + 1] before step
+  // i + 1 overwrites it)
   float cur = x[0];
-  for (int i = 0; i < sz - 1; ++i) {
-    const int64_t q = (int64_t)i * n + m;
-    const float nxt = x[(int64_t)(i + 1) * n];
-    const float l = f.lm[q];
-    if (f.pv[q] != 0.f) {
-      x[(int64_t)i * n] = nxt;
-      cur = cur - l * nxt;
-    } else {
-      x[(int64_t)i * n] = cur;
-      cur = nxt - l * cur;
+  for (int i0 = 0; i0 < sz - 1; i0 += kSB) {
+    float xn[kSB], lv[kSB], pw[kSB], o[kSB];
+#pragma unroll
+    for (int u = 0; u < kSB; ++u) {
+      const int i = i0 + u;
+      if (i < sz - 1) {
+        xn[u] = x[(int64_t)(i + 1) * n];
+        lv[u] = lm[(int64_t)i * n];
+        pw[u] = pv[(int64_t)i * n];
+      }
     }
+#pragma unroll
+    for (int u = 0; u < kSB; ++u) {
+      if (i0 + u < sz - 1) {
+        if (pw[u] != 0.f) {
+          o[u] = xn[u];
+          cur = cur - lv[u] * xn[u];
+        } else {
+          o[u] = cur;
+          cur = xn[u] - lv[u] * cur;
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kSB; ++u)
+      if (i0 + u < sz - 1) x[(int64_t)(i0 + u) * n] = o[u];
   }
   x[(int64_t)(sz - 1) * n] = cur;
-  // back substitution with U
+  // back substitution with U, rows sz - 1 .. 0
   float x1 = 0.f, x2 = 0.f, mx = 0.f;
-  for (int i = sz - 1; i >= 0; --i) {
-    const int64_t q = (int64_t)i * n + m;
-    const float r = (x[(int64_t)i * n] - f.u1[q] * x1 - f.u2[q] * x2) * f.r0[q];
-    x[(int64_t)i * n] = r;
-    x2 = x1;
-    x1 = r;
-    mx = fmaxf(mx, fabsf(r));
+  for (int i0 = sz - 1; i0 >= 0; i0 -= kSB) {
+    float xv[kSB], a1[kSB], a2[kSB], rr[kSB];
+#pragma unroll
+    for (int u = 0; u < kSB; ++u) {
+      const int i = i0 - u;
+      if (i >= 0) {
+        const int64_t q = (int64_t)i * n;
+        xv[u] = x[q];
+        a1[u] = u1[q];
+        a2[u] = u2[q];
+        rr[u] = r0[q];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kSB; ++u) {
+      if (i0 - u >= 0) {
+        const float r = (xv[u] - a1[u] * x1 - a2[u] * x2) * rr[u];
+        xv[u] = r;
+        x2 = x1;
+        x1 = r;
+        mx = fmaxf(mx, fabsf(r));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kSB; ++u)
+      if (i0 - u >= 0) x[(int64_t)(i0 - u) * n] = xv[u];
   }
   const float inv = mx > 0.f ? 1.f / mx : 1.f;
-  for (int i = 0; i < sz; ++i) x[(int64_t)i * n] *= inv;
+  for (int i0 = 0; i0 < sz; i0 += kSB) {
+    float xv[kSB];
+#pragma unroll
+    for (int u = 0; u < kSB; ++u)
+      if (i0 + u < sz) xv[u] = x[(int64_t)(i0 + u) * n];
+#pragma unroll
+    for (int u = 0; u < kSB; ++u)
+      if (i0 + u < sz) x[(int64_t)(i0 + u) * n] = xv[u] * inv;
+  }
 }
 
 // Modified Gram-Schmidt inside every cluster of two or more members, by the
@@ -265,7 +321,7 @@ __device__ void tri_cluster_mgs(float *X, int n, const int *cstart, int nc, cons
   }
 }
 
-__global__ void __launch_bounds__(1024) tri_eig_kernel(const float *__restrict__ dg,
+__global__ void __launch_bounds__(kTriEigThreads) tri_eig_kernel(const float *__restrict__ dg,
                                                        const float *__restrict__ eg, int n,
                                                        float *__restrict__ w,
                                                        float *__restrict__ Z,
@@ -478,7 +534,7 @@ cudaError_t launch_sym_eig_tridiag(const float *A, int32_t n, int32_t lda, float
   if (err != cudaSuccess) return err;
   {
     ProfScope ps_(K_EIG, st);
-    tri_eig_kernel<<<1, 1024, 0, st>>>(d, e, n, w, Z, wsc, ctrl);
+    tri_eig_kernel<<<1, kTriEigThreads, 0, st>>>(d, e, n, w, Z, wsc, ctrl);
   }
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
