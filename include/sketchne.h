@@ -336,6 +336,14 @@ int sne_sym_eig_workspace_bytes(int32_t n, size_t *bytes);
 int sne_sym_eig(int32_t n, const double *S, int32_t lds, double *lambda, double *V, int32_t ldv,
                 void *workspace, size_t ws_bytes, sne_stream_t stream);
 
+/* trunc_log as the tensor-core sketch epilogue evaluates it (Eq. 4 with
+ * f = trunc_log, f(x) = max(0, log x)): out[i] = log1p(r[i]) for r[i] > 0 and
+ * 0 otherwise, where r = x - 1 is the centred entry.  r and out are device
+ * arrays of n FP32 values (may be the same array).  Relative error below 3e-7
+ * for r > 0.  Errors: SNE_ERR_ARG for n < 0 or a null pointer with n > 0,
+ * SNE_ERR_CUDA for a failed launch. */
+int sne_trunc_log_eval(int64_t n, const float *r, float *out, sne_stream_t stream);
+
 /* Kernel accounting (host only).  sne_kernel_launches returns the number of
  * kernels this library has enqueued since it was loaded.  Between
  * sne_profile_start and sne_profile_stop every launcher brackets its kernels

@@ -6,6 +6,7 @@
 #include <algorithm>
 
 #include "sne_internal.cuh"
+#include "tc_ptx.cuh"
 
 using namespace sne;
 
@@ -27,6 +28,12 @@ size_t eig_ws(int32_t n) {
   const size_t nn = (size_t)n * n;
   return align256(sizeof(Ctrl)) + 2 * align256(nn * sizeof(double)) + align256(n * sizeof(double)) +
          align256(n * sizeof(int32_t)) + align256(eig_scratch_bytes(n));
+}
+
+__global__ void trunc_log_eval_kernel(const float *__restrict__ r, float *out, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    out[i] = tc::fr<SNE_F_TRUNC_LOG>(r[i]);
 }
 
 // Vout[a][j] = V[a][perm[j]], lam[j] = w[perm[j]]
@@ -161,6 +168,14 @@ int sne_chol_inverse(int32_t n, const void *A, int32_t lda, void *M, int32_t ldm
                                         static_cast<float *>(M), ldm,
                                         static_cast<float *>(scratch), ctrl, st, tol);
   return e == cudaSuccess ? SNE_OK : SNE_ERR_CUDA;
+}
+
+int sne_trunc_log_eval(int64_t n, const float *r, float *out, sne_stream_t stream) {
+  if (n < 0 || (n > 0 && (!r || !out))) return SNE_ERR_ARG;
+  if (n == 0) return SNE_OK;
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8);
+  trunc_log_eval_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(r, out, n);
+  return cudaGetLastError() == cudaSuccess ? SNE_OK : SNE_ERR_CUDA;
 }
 
 }  // extern "C"

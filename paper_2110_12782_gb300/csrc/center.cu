@@ -56,14 +56,24 @@ __global__ void __launch_bounds__(kMeanThreads) center_mean_partial_kernel(
     }
     __syncthreads();
     const int rows = (int)min64(64, r1 - t0);
-    for (int r = 0; r < rows; ++r) {
-      const double wv = wsh[r];
-      if (wv == 0.0) continue;
-      const float *row = U + (t0 + r) * ldu;
+    // eight rows per step, their loads issued before the multiply-adds (the
+    // rows past the chunk have weight 0 and load row t0 again)
+    for (int r = 0; r < rows; r += 8) {
+      float x[8][4];
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const int c = threadIdx.x + kMeanThreads * m;
-        if (c < k) acc[m] = fma(wv, (double)row[c], acc[m]);
+      for (int u = 0; u < 8; ++u) {
+        const float *row = U + (t0 + (r + u < rows ? r + u : 0)) * ldu;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int c = threadIdx.x + kMeanThreads * m;
+          x[u][m] = c < k ? row[c] : 0.0f;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const double wv = r + u < rows ? wsh[r + u] : 0.0;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) acc[m] = fma(wv, (double)x[u][m], acc[m]);
       }
     }
   }

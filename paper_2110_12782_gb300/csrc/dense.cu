@@ -519,34 +519,45 @@ cudaError_t launch_tall_gemm(const float *A, int64_t lda, const int32_t *ridx, i
 }
 
 // ---------------------------------------------------------------------------
-// Small GEMM: C = alpha op(A) op(B) + beta C.  32x32 tiles, 256 threads x 4.
+// Small GEMM: C = alpha op(A) op(B) + beta C.  TB x TB output tiles, (TB/2)^2
+// threads with 2 x 2 outputs each, K in slabs of 32 through shared memory.
+// GB300's FP64 rate is low (about 2 FMA per clock and SM), so a double GEMM of
+// a few hundred rows is bound by how many SMs take part: 16 x 16 tiles when
+// 32 x 32 ones would leave SMs idle.
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(256) small_gemm_kernel(int ta, int tb, int M, int N, int K,
-                                                         T alpha, const T *__restrict__ A, int lda,
-                                                         const T *__restrict__ B, int ldb, T beta,
-                                                         T *__restrict__ C, int ldc,
-                                                         const int *__restrict__ skip) {
+template <typename T, int TB>
+__global__ void __launch_bounds__((TB / 2) * (TB / 2)) small_gemm_kernel(
+    int ta, int tb, int M, int N, int K, T alpha, const T *__restrict__ A, int lda,
+    const T *__restrict__ B, int ldb, T beta, T *__restrict__ C, int ldc,
+    const int *__restrict__ skip) {
   if (skip && *skip) return;
-  __shared__ T As[32][33];
-  __shared__ T Bs[32][33];
+  constexpr int NT = (TB / 2) * (TB / 2);
+  __shared__ T As[TB][33];  // As[r][c] = op(A)[m0 + r][k0 + c]
+  __shared__ T Bs[32][TB + 1];  // Bs[r][c] = op(B)[k0 + r][n0 + c]
   const int tid = threadIdx.x;
-  const int ty = tid >> 4, tx = tid & 15;  // 16 x 16 threads, 2 x 2 outputs each
-  const int m0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
+  const int ty = tid / (TB / 2), tx = tid % (TB / 2);
+  const int m0 = blockIdx.y * TB, n0 = blockIdx.x * TB;
   T acc[2][2] = {{0, 0}, {0, 0}};
   for (int k0 = 0; k0 < K; k0 += 32) {
-    for (int e = tid; e < 32 * 32; e += 256) {
-      const int r = e >> 5, c = e & 31;
-      // As[r][c] = op(A)[m0 + r][k0 + c]
-      const int m = m0 + r, k = k0 + c;
-      T av = 0;
-      if (m < M && k < K) av = ta ? A[(int64_t)k * lda + m] : A[(int64_t)m * lda + k];
-      As[r][c] = av;
-      // Bs[r][c] = op(B)[k0 + r][n0 + c]
-      const int kb = k0 + r, nb = n0 + c;
-      T bv = 0;
-      if (kb < K && nb < N) bv = tb ? B[(int64_t)nb * ldb + kb] : B[(int64_t)kb * ldb + nb];
-      Bs[r][c] = bv;
+    for (int e = tid; e < TB * 32; e += NT) {
+      // A slab: TB rows x 32 k; with ta the k index runs fastest in memory
+      // order of A's rows, so walk (k, m) with m fastest for coalescing
+      {
+        int r, c;
+        if (ta) { c = e / TB; r = e % TB; } else { r = e / 32; c = e % 32; }
+        const int m = m0 + r, k = k0 + c;
+        T av = 0;
+        if (m < M && k < K) av = ta ? A[(int64_t)k * lda + m] : A[(int64_t)m * lda + k];
+        As[r][c] = av;
+      }
+      {
+        int r, c;
+        if (tb) { c = e / 32; r = e % 32; } else { r = e / TB; c = e % TB; }
+        const int kb = k0 + r, nb = n0 + c;
+        T bv = 0;
+        if (kb < K && nb < N) bv = tb ? B[(int64_t)nb * ldb + kb] : B[(int64_t)kb * ldb + nb];
+        Bs[r][c] = bv;
+      }
     }
     __syncthreads();
 #pragma unroll 8
@@ -577,10 +588,16 @@ cudaError_t launch_small_gemm(bool ta, bool tb, int32_t M, int32_t N, int32_t K,
                               const T *A, int32_t lda, const T *B, int32_t ldb, T beta, T *C,
                               int32_t ldc, cudaStream_t st, const int *skip) {
   if (M <= 0 || N <= 0) return cudaSuccess;
-  dim3 grid((unsigned)ceil_div(N, 32), (unsigned)ceil_div(M, 32));
   ProfScope ps_(K_SMALL_GEMM, st);
-  small_gemm_kernel<T><<<grid, 256, 0, st>>>(ta ? 1 : 0, tb ? 1 : 0, M, N, K, alpha, A, lda, B, ldb,
-                                             beta, C, ldc, skip);
+  if ((int64_t)ceil_div(N, 32) * ceil_div(M, 32) < 2 * (int64_t)sm_count()) {
+    dim3 grid((unsigned)ceil_div(N, 16), (unsigned)ceil_div(M, 16));
+    small_gemm_kernel<T, 16><<<grid, 64, 0, st>>>(ta ? 1 : 0, tb ? 1 : 0, M, N, K, alpha, A, lda,
+                                                  B, ldb, beta, C, ldc, skip);
+  } else {
+    dim3 grid((unsigned)ceil_div(N, 32), (unsigned)ceil_div(M, 32));
+    small_gemm_kernel<T, 32><<<grid, 256, 0, st>>>(ta ? 1 : 0, tb ? 1 : 0, M, N, K, alpha, A, lda,
+                                                   B, ldb, beta, C, ldc, skip);
+  }
   return cudaGetLastError();
 }
 template cudaError_t launch_small_gemm<float>(bool, bool, int32_t, int32_t, int32_t, float,

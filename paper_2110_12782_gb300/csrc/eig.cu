@@ -21,6 +21,7 @@
 // (pairs closer than the floor) are then resolved exactly by a small FP64
 // Jacobi on each cluster's block of X^T A X.
 #include <cfloat>
+#include <climits>
 #include <cmath>
 #include <cstdlib>
 
@@ -547,6 +548,198 @@ __global__ void __launch_bounds__(1024) chol_inv_kernel(const T *__restrict__ A,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Pivoted FP64 Cholesky over a cluster of kCholCl CTAs (left-looking form of
+// the diagonal pivoting of LAPACK's pstrf).  GB300 executes about two FP64
+// fused multiply-adds per clock and SM, so one CTA cannot factor a 272 x 272
+// matrix in less than a millisecond and a half; here the rows of L (A = L L^T,
+// rows in the original order) are spread cyclically over the cluster's shared
+// memory, row i in CTA i % kCholCl.  Step j:
+//   each CTA proposes its largest remaining diagonal d_i (lowest index on
+//   ties); after a cluster barrier every CTA reads the kCholCl proposals
+//   through distributed shared memory and takes the same pivot p (stopping
+//   at the numerical rank: d_p <= tol max_i A_ii, or not finite);
+//   L(p, j) = sqrt(d_p); every CTA copies L(p, 0..j-1) from p's CTA and, for
+//   its rows i not yet pivots, L(i, j) = (A(i, p) - sum_{k<j} L(i, k) L(p, k))
+//   / L(p, j) and d_i -= L(i, j)^2 (a warp per row).
+// In exact arithmetic the pivots and the factor are those of the right-looking
+// kernel above.  The result goes to the same global scratch layout (R = L^T in
+// pivot order, 1 / R_jj, the pivot order and the rank), for chol_backsub_kernel.
+// The waits are the cluster barriers, whose CTAs are co-scheduled.
+// ---------------------------------------------------------------------------
+constexpr int kCholCl = 8;
+constexpr int kCholClThreads = 512;
+
+__device__ __forceinline__ uint32_t cl_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cl_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+__device__ __forceinline__ uint32_t cl_map(const void *p, uint32_t cta) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(cta));
+  return r;
+}
+__device__ __forceinline__ double cl_ld_f64(const double *p, uint32_t cta) {
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(cl_map(p, cta)) : "memory");
+  return v;
+}
+__device__ __forceinline__ int cl_ld_s32(const int *p, uint32_t cta) {
+  int v;
+  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(cl_map(p, cta)) : "memory");
+  return v;
+}
+
+// larger value wins, then lower index
+__device__ __forceinline__ void piv_better(double &v, int &i, double ov, int oi) {
+  if (ov > v || (ov == v && oi < i)) {
+    v = ov;
+    i = oi;
+  }
+}
+
+size_t chol_piv_cluster_smem(int n) {
+  const int nloc = (n + kCholCl - 1) / kCholCl;
+  return ((size_t)nloc * n + n + nloc + 2) * sizeof(double) + (2 + 2 * (size_t)n) * sizeof(int) +
+         (size_t)n + 16;
+}
+
+__global__ void __launch_bounds__(kCholClThreads) chol_piv_cluster_kernel(
+    const double *__restrict__ A, int n, int lda, double *__restrict__ scratch, double tol) {
+  extern __shared__ __align__(16) unsigned char ccm[];
+  constexpr int C = kCholCl;
+  const int nloc = (n + C - 1) / C;
+  double *L = reinterpret_cast<double *>(ccm);  // nloc x n: L[t n + k] = L(me + C t, k)
+  double *rp = L + (size_t)nloc * n;            // n: L(p, k), k < j
+  double *dloc = rp + n;                        // nloc: remaining diagonal of the local rows
+  double *cval = dloc + nloc;                   // 2 slots (step parity): proposed d
+  int *cidx = reinterpret_cast<int *>(cval + 2);  // 2 slots: proposed row
+  int *perm = cidx + 2;                         // n: pivot order (replicated in every CTA)
+  int *pos = perm + n;                          // n: position of each row in perm
+  unsigned char *chosen = reinterpret_cast<unsigned char *>(pos + n);  // n (replicated)
+  __shared__ double s_v;
+  __shared__ int s_p;
+  const uint32_t me = cl_rank();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int t = tid; t < nloc; t += blockDim.x) {
+    const int i = (int)me + C * t;
+    dloc[t] = i < n ? A[(int64_t)i * lda + i] : 0.0;
+  }
+  for (int i = tid; i < n; i += blockDim.x) chosen[i] = 0;
+  if (warp == 0) {  // max_i A_ii, the same in every CTA
+    double m = 0.0;
+    for (int i = lane; i < n; i += 32) m = fmax(m, A[(int64_t)i * lda + i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) s_v = m;
+  }
+  __syncthreads();
+  const double cut = tol * s_v;
+  int r = n;
+  for (int j = 0; j < n; ++j) {
+    const int slot = j & 1;
+    if (warp == 0) {
+      double v = -INFINITY;
+      int ix = INT_MAX;
+      for (int t = lane; t < nloc; t += 32) {
+        const int i = (int)me + C * t;
+        if (i < n && !chosen[i]) piv_better(v, ix, dloc[t], i);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+        piv_better(v, ix, __shfl_xor_sync(0xffffffffu, v, o), __shfl_xor_sync(0xffffffffu, ix, o));
+      if (lane == 0) {
+        cval[slot] = v;
+        cidx[slot] = ix;
+      }
+    }
+    cl_sync();  // the proposals of step j are visible cluster-wide
+    if (warp == 0) {
+      double v = -INFINITY;
+      int ix = INT_MAX;
+      if (lane < C) {
+        v = cl_ld_f64(&cval[slot], (uint32_t)lane);
+        ix = cl_ld_s32(&cidx[slot], (uint32_t)lane);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+        piv_better(v, ix, __shfl_xor_sync(0xffffffffu, v, o), __shfl_xor_sync(0xffffffffu, ix, o));
+      if (lane == 0) {
+        s_v = v;
+        s_p = ix;
+      }
+    }
+    __syncthreads();
+    const double dmax = s_v;
+    const int p = s_p;
+    if (!(dmax > cut) || !isfinite(dmax) || p < 0 || p >= n) {  // the same in every CTA
+      r = j;
+      break;
+    }
+    const double ljj = sqrt(dmax);
+    const double inv = 1.0 / ljj;
+    const uint32_t owner = (uint32_t)(p % C);
+    const int tp = p / C;
+    for (int k = tid; k < j; k += blockDim.x)
+      rp[k] = owner == me ? L[(size_t)tp * n + k] : cl_ld_f64(&L[(size_t)tp * n + k], owner);
+    if (tid == 0) {
+      chosen[p] = 1;
+      perm[j] = p;
+      if (owner == me) L[(size_t)tp * n + j] = ljj;
+    }
+    __syncthreads();
+    for (int t = warp; t < nloc; t += nw) {
+      const int i = (int)me + C * t;
+      if (i >= n || chosen[i]) continue;  // uniform for the warp
+      const double *li = L + (size_t)t * n;
+      double acc = 0.0;
+      for (int k = lane; k < j; k += 32) acc = fma(li[k], rp[k], acc);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) {
+        const double lij = (A[(int64_t)i * lda + p] - acc) * inv;
+        L[(size_t)t * n + j] = lij;
+        dloc[t] -= lij * lij;
+      }
+    }
+    __syncthreads();
+  }
+  // positions r .. n-1: the rows never pivoted, in increasing order
+  if (tid == 0) {
+    int q = r;
+    for (int i = 0; i < n; ++i)
+      if (!chosen[i]) perm[q++] = i;
+  }
+  __syncthreads();
+  for (int c = tid; c < n; c += blockDim.x) pos[perm[c]] = c;
+  __syncthreads();
+  double *R = scratch;  // R[k][c] = L(perm[c], k), k <= c < r
+  double *dinv = scratch + (size_t)n * n;
+  int *gperm = reinterpret_cast<int *>(dinv + n);
+  for (int t = warp; t < nloc; t += nw) {
+    const int i = (int)me + C * t;
+    if (i >= n) continue;
+    const int c = pos[i];
+    if (c >= r) continue;
+    for (int k = lane; k <= c; k += 32) R[(size_t)k * n + c] = L[(size_t)t * n + k];
+    if (lane == 0) dinv[c] = 1.0 / L[(size_t)t * n + c];
+  }
+  if (me == 0) {
+    for (int c = tid; c < n; c += blockDim.x) {
+      gperm[c] = perm[c];
+      if (c >= r) dinv[c] = 0.0;
+    }
+    if (tid == 0) gperm[n] = r;
+  }
+  cl_sync();  // no CTA leaves while another may still read its shared memory
+}
+
 // Back substitution for the factor left in global scratch by chol_inv_kernel
 // (dense n x n R, then dinv[n], then perm[n] and the rank): one warp per
 // column of M = P [R11^-1 0; 0 0], eight columns per CTA.
@@ -948,6 +1141,17 @@ size_t chol_inv_smem(int n, bool packed) {
          (size_t)n * sizeof(int);
 }
 
+// The cluster kernel for pivoted FP64 factors, unless SNE_CHOL_CLUSTER=0 (for
+// comparisons: the one-CTA kernel).
+static bool chol_cluster_enabled() {
+  static int on = -1;
+  if (on < 0) {
+    const char *v = getenv("SNE_CHOL_CLUSTER");
+    on = (v && v[0] == '0') ? 0 : 1;
+  }
+  return on == 1;
+}
+
 // The blocked FP32 kernel above, unless SNE_CHOL_QUICK=0 (for comparisons).
 static bool chol_quick_enabled() {
   static int on = -1;
@@ -985,6 +1189,38 @@ cudaError_t launch_chol_inverse(const T *A, int32_t n, int32_t lda, T *Rinv, int
   }
   const bool packed = chol_inv_smem<T>(n, true) <= 220 * 1024;
   if (!packed && !scratch) return cudaErrorInvalidValue;
+  if (sizeof(T) == 8 && tol >= 0.0 && scratch && chol_piv_cluster_smem(n) <= 220 * 1024 &&
+      chol_cluster_enabled()) {
+    // pivoted FP64: the cluster kernel, then the multi-CTA back substitution
+    const size_t csm = chol_piv_cluster_smem(n);
+    cudaError_t e = cudaFuncSetAttribute(chol_piv_cluster_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kCholCl, 1, 1);
+    cfg.blockDim = dim3(kCholClThreads, 1, 1);
+    cfg.dynamicSmemBytes = csm;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kCholCl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    {
+      ProfScope ps_(K_CHOL, st);
+      e = cudaLaunchKernelEx(&cfg, chol_piv_cluster_kernel, reinterpret_cast<const double *>(A), n,
+                             lda, reinterpret_cast<double *>(scratch), tol);
+      if (e != cudaSuccess) return e;
+      const size_t bsmem = (size_t)8 * n * sizeof(T);
+      e = cudaFuncSetAttribute(chol_backsub_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)bsmem);
+      if (e != cudaSuccess) return e;
+      chol_backsub_kernel<T><<<(n + 7) / 8, 256, bsmem, st>>>(scratch, n, Rinv, ldi);
+    }
+    return cudaGetLastError();
+  }
   const size_t smem = chol_inv_smem<T>(n, packed);
   auto kern = packed ? chol_inv_kernel<T, true> : chol_inv_kernel<T, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -17,10 +17,11 @@
 //            shared-memory stages (128-byte swizzle);
 //   warp 1   allocates 512 TMEM columns (two 128 x 256 FP32 accumulators)
 //            and issues tcgen05.mma (M 128, N 256, K 16) from one thread;
-//   warps 2-17 epilogue: tcgen05.ld of the accumulator rows, r = x - c0,
-//            f(r), sign, and the z-column segmented sums in registers, then
-//            the Y (or Y') row segment is stored.  Warp w reads TMEM lane
-//            quarter w % 4 and 64 of the 256 columns.
+//   warps 2.. epilogue (kSketchEpiWarps of them): tcgen05.ld of the
+//            accumulator rows, r = x - c0, f(r), sign, and the z-column
+//            segmented sums in registers, then the Y (or Y') row segment is
+//            stored.  Warp w reads TMEM lane quarter w % 4 and 256 /
+//            (kSketchEpiWarps / 4) of the 256 columns.
 // Double-buffered accumulators let the epilogue of tile j overlap the MMAs
 // of tile j+1.  When the rows are few (the Z core: v_O rows, thousands of
 // columns) blockIdx.y splits a row tile's column tiles over several CTAs.
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(tc::kThreadsSketch, 1) fused_sketch_tc_kernel(
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 512);
+      mbar_init(&tempty[b], 32 * kSketchEpiWarps);
     }
     mbar_init(done, 1);
     *abort_flag = 0;
@@ -156,6 +157,11 @@ __global__ void __launch_bounds__(tc::kThreadsSketch, 1) fused_sketch_tc_kernel(
         }
         fence_after();
         const uint32_t dt = tmem + (uint32_t)(buf * BN);
+        // a last column tile at most half full runs at N = 128: the columns
+        // past it are neither multiplied nor read by the epilogue
+        const uint32_t id = (ncols_eval - j * BN <= BN / 2)
+                                ? ((idesc & ~(0x3fu << 17)) | ((uint32_t)(BN / 2 >> 3) << 17))
+                                : idesc;
         for (int q = 0; q < steps; ++q, ++it) {
           const int kb = q / NPART, part = q % NPART;
           const int s = it % stages;
@@ -170,18 +176,18 @@ __global__ void __launch_bounds__(tc::kThreadsSketch, 1) fused_sketch_tc_kernel(
             // A_hi B_hi (the first product of the tile starts the accumulator)
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk)
-              mma_f16(dt, sdesc(ahi + kk * 32), sdesc(b0 + kk * 32), idesc, (kb | kk) ? 1u : 0u);
+              mma_f16(dt, sdesc(ahi + kk * 32), sdesc(b0 + kk * 32), id, (kb | kk) ? 1u : 0u);
             if (SPLIT) {
               const uint32_t alo = smem_u32(sA + (size_t)(kblocks + kb) * kABlockBytes);
 #pragma unroll
               for (int kk = 0; kk < BK / 16; ++kk)
-                mma_f16(dt, sdesc(alo + kk * 32), sdesc(b0 + kk * 32), idesc, 1u);
+                mma_f16(dt, sdesc(alo + kk * 32), sdesc(b0 + kk * 32), id, 1u);
             }
           } else {
             // A_hi B_lo
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk)
-              mma_f16(dt, sdesc(ahi + kk * 32), sdesc(b0 + kk * 32), idesc, 1u);
+              mma_f16(dt, sdesc(ahi + kk * 32), sdesc(b0 + kk * 32), id, 1u);
           }
           mma_commit(&empty[s]);
         }
@@ -193,8 +199,10 @@ __global__ void __launch_bounds__(tc::kThreadsSketch, 1) fused_sketch_tc_kernel(
       mbar_drain(done, 0, wait_ns);
     }
   } else {
-    // ---------------- epilogue warps 2..17: warp w reads TMEM lane quarter
-    // w % 4 (rows 32(w%4) .. +32) and quarter (w - 2) / 4 of the 256 columns
+    // ---------------- epilogue warps: warp w reads TMEM lane quarter w % 4
+    // (rows 32(w%4) .. +32) and column slice (w - 2) / 4 of the 256 columns
+    constexpr int CPW = BN / (kSketchEpiWarps / 4);  // columns per warp and tile
+    static_assert(kSketchEpiWarps % 4 == 0 && CPW % 32 == 0, "epilogue warp split");
     const int ew = warp & 3;
     const int quarter = (warp - 2) >> 2;
     const int64_t row = row0 + 32 * ew + lane;
@@ -208,26 +216,41 @@ __global__ void __launch_bounds__(tc::kThreadsSketch, 1) fused_sketch_tc_kernel(
       const uint32_t use = (uint32_t)(jj >> 1);
       if (!mbar_wait(&tfull[buf], use & 1u, abortv, ctrl, wait_ns)) break;
       fence_after();
-      const int ebase = j * BN + quarter * 64;
-      float v[2][32];
-      const uint32_t taddr = tmem + ((uint32_t)(32 * ew) << 16) + (uint32_t)(buf * BN + quarter * 64);
-      tmem_ld32_nw(taddr, v[0]);
-      tmem_ld32_nw(taddr + 32, v[1]);
-      tmem_wait_ld();
-      // the accumulator is in registers: release it to the MMA warp early
-      fence_before();
-      mbar_arrive(&tempty[buf]);
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const float4 *cd4 = coldat + ebase + c * 32;
+      const int ebase = j * BN + quarter * CPW;
+      const uint32_t taddr = tmem + ((uint32_t)(32 * ew) << 16) + (uint32_t)(buf * BN + quarter * CPW);
+      // the warp's columns in chunks of 32; the accumulator goes back to the
+      // MMA warp once the last chunk is in registers
+#pragma unroll 1
+      for (int c = 0; c < CPW / 32; ++c) {
+        if (ebase + 32 * c >= ncols_eval) {
+          // past the evaluated columns (a partial last tile): nothing to read
+          if (c == CPW / 32 - 1) {
+            fence_before();
+            mbar_arrive(&tempty[buf]);
+          }
+          continue;
+        }
+        float vc[32];
+        tmem_ld32_nw(taddr + 32 * c, vc);
+        tmem_wait_ld();
+        if (c == CPW / 32 - 1) {
+          fence_before();
+          mbar_arrive(&tempty[buf]);
+        }
+        // the chunk's column data, lane t holding column t, broadcast by
+        // shuffles (32 uniform loads per chunk, hoisted by the compiler to
+        // the top of the loop, would spill)
+        const float4 cdl = __ldg(coldat + ebase + c * 32 + lane);
         float acc[G];
 #pragma unroll
         for (int g = 0; g < G; ++g) acc[g] = 0.0f;
 #pragma unroll
         for (int t = 0; t < 32; ++t) {
-          const float4 cd = __ldg(cd4 + t);  // (colf, kappa, sgn, 0), the same for the warp
-          const float r = fmaf(v[c][t], rf * cd.x, fmaf(rd.y, cd.y, rd.x));
-          acc[t / Z] = fmaf(cd.z, tc::fr<F>(r), acc[t / Z]);
+          const float colf = __shfl_sync(0xffffffffu, cdl.x, t);
+          const float kappa = __shfl_sync(0xffffffffu, cdl.y, t);
+          const float sgn = __shfl_sync(0xffffffffu, cdl.z, t);
+          const float r = fmaf(vc[t], rf * colf, fmaf(rd.y, kappa, rd.x));
+          acc[t / Z] = fmaf(sgn, tc::fr<F>(r), acc[t / Z]);
         }
         // G consecutive outputs of this row: columns (ebase + 32 c) / Z ..
         const int oc0 = (ebase + 32 * c) / Z;

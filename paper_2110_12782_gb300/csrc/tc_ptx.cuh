@@ -15,7 +15,16 @@ constexpr int BK = 64;                        // elements per k-block (128 bytes
 constexpr int kABlockBytes = BM * BK * 2;     // 16 KB
 constexpr int kBStageBytes = BN * BK * 2;     // 32 KB
 constexpr int kThreads = 192;
-constexpr int kThreadsSketch = 576;  // TMA warp, MMA warp, 16 epilogue warps
+#ifndef SNE_SKETCH_EPI_WARPS
+#define SNE_SKETCH_EPI_WARPS 16
+#endif
+// Fused sketch: TMA warp, MMA warp and kSketchEpiWarps epilogue warps (a
+// multiple of 4: one TMEM lane quarter each, the columns of a tile split
+// between the warps of a quarter).  With 18 warps a thread gets at most 96
+// registers (the column data are broadcast by shuffles so that the epilogue
+// fits); 8 epilogue warps (168 registers) hide less latency and run slower.
+constexpr int kSketchEpiWarps = SNE_SKETCH_EPI_WARPS;
+constexpr int kThreadsSketch = 64 + 32 * kSketchEpiWarps;
 constexpr unsigned long long kTimeoutNs = 2000000000ull;
 
 // Shared-memory descriptor with explicit byte offsets (128-byte swizzle).
@@ -201,21 +210,39 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// p(t), t = r - 1/2, by Horner (coefficients c_8 .. c_0 of fit_log1p.py)
+__device__ __forceinline__ float log1p_poly(float t) {
+  float p = 5.232623778e-03f;
+  p = fmaf(p, t, -8.574461564e-03f);
+  p = fmaf(p, t, 1.158651151e-02f);
+  p = fmaf(p, t, -2.022824623e-02f);
+  p = fmaf(p, t, 3.663385287e-02f);
+  p = fmaf(p, t, -6.771145016e-02f);
+  p = fmaf(p, t, 1.326090842e-01f);
+  p = fmaf(p, t, -2.885266542e-01f);
+  return fmaf(p, t, 8.109301925e-01f);
+}
+
 // f of r = x - c0: trunc_log(x) = log1p(r) for r > 0, else 0; the identity r.
-// u = fl(1 + r) carries the rounding error e = r - (u - 1), which is exact
-// (u - 1 is exact and within a factor of two of r), and
-// log1p(r) = log(u) + log1p(e/u) ~ log(u) + e with |e/u| <= 2^-24 (the 1/u
-// factor matters only where u is far from 1, where e is below 2^-24 of log u).
-// The full-accuracy logf keeps its relative accuracy near u = 1, where
-// lg2.approx has an absolute error of about 1e-7 (so a relative error that
-// grows without bound as r -> 0): measured on sm_103a, logf(u) + e is within
-// 1.3e-7 relative of log1p(r) for r in [2^-26, 4].
+// For 0 <= r < 1, log1p(r) = r p(r - 1/2) with p the degree-8 polynomial
+// fitted to log1p(r)/r on [0, 1] (fit_log1p.py: minimax relative error by
+// iteratively reweighted least squares), which keeps the relative accuracy as
+// r -> 0 and stays within 2e-7 relative in FP32 (Horner with fused
+// multiply-adds); r <= 0 enters the polynomial as 0 and gives 0.  For r >= 1,
+// log(1 + r) = ln 2 log2(1 + r) with the special function unit's base-2
+// logarithm (lg2.approx), whose absolute error of about 2^-22 is below 2e-7 of
+// log(1 + r) >= ln 2; the rounding of 1 + r moves log(1 + r) by at most 2^-24.
+// Both sides are evaluated and selected (no divergence within a warp): about
+// sixteen instructions, half of a full-range logf with its argument
+// correction, and the base-2 logarithm runs on the otherwise idle MUFU pipe.
 template <int F>
 __device__ __forceinline__ float fr(float r) {
   if (F == SNE_F_TRUNC_LOG) {
-    const float u = __fadd_rn(1.0f, r);
-    const float e = __fsub_rn(r, __fsub_rn(u, 1.0f));
-    return r > 0.0f ? __fadd_rn(logf(u), e) : 0.0f;
+    const float rs = fminf(fmaxf(r, 0.0f), 1.0f);
+    const float small = log1p_poly(rs - 0.5f) * rs;
+    float l2;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l2) : "f"(1.0f + r));
+    return r < 1.0f ? small : l2 * 0.693147182f;
   }
   return r;
 }

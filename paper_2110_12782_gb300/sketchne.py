@@ -46,6 +46,7 @@ EXPORTS = [
     "sne_embed_batched_workspace_bytes", "sne_embed_batched", "sne_chol_inverse_workspace_bytes",
     "sne_chol_inverse", "sne_propagation_coefficients", "sne_spectral_propagate_workspace_bytes",
     "sne_spectral_propagate", "sne_single_pass_svd_workspace_bytes", "sne_single_pass_svd",
+    "sne_trunc_log_eval",
 ]
 
 
@@ -124,6 +125,7 @@ def lib() -> ctypes.CDLL:
             "sne_sym_eig": [i32, vp, i32, vp, vp, i32, vp, ctypes.c_size_t, vp],
             "sne_chol_inverse_workspace_bytes": [i32, i32, P(ctypes.c_size_t)],
             "sne_chol_inverse": [i32, vp, i32, vp, i32, i32, dbl, vp, ctypes.c_size_t, vp],
+            "sne_trunc_log_eval": [i64, vp, vp, vp],
             "sne_single_pass_svd_workspace_bytes": [i64, i64, i32, P(sne_params),
                                                     P(ctypes.c_size_t)],
             "sne_single_pass_svd": [i64, i64, i32, vp, i64, vp, i64, P(sne_params), vp,
@@ -514,6 +516,14 @@ def chol_inverse_workspace(n: int, fp64: bool, device="cuda") -> torch.Tensor:
     _check(lib().sne_chol_inverse_workspace_bytes(n, 1 if fp64 else 0, ctypes.byref(nb)),
            "sne_chol_inverse_workspace_bytes")
     return _aligned_bytes(nb.value, device)
+
+
+def sne_trunc_log_eval(r: torch.Tensor, out: torch.Tensor, stream=None) -> None:
+    """out = trunc_log(1 + r) elementwise, as the tensor-core sketch evaluates it."""
+    if r.numel() != out.numel():
+        raise ValueError("r and out must have the same size")
+    _check(lib().sne_trunc_log_eval(r.numel(), _ptr(r, torch.float32, "r"), _ptr(out, torch.float32, "out"),
+                                    _stream(stream)), "sne_trunc_log_eval")
 
 
 def sne_chol_inverse(A: torch.Tensor, M: torch.Tensor, ws: torch.Tensor, tol: float = -1.0,

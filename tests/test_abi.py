@@ -119,6 +119,10 @@ def test_building_block_argument_errors_on_the_host(L):
     assert L.sne_chol_inverse_workspace_bytes(300, 1, ctypes.byref(nb)) == 0
     assert L.sne_chol_inverse(300, A, 300, C, 299, 1, -1.0, 256, nb.value, None) == ARG
     assert L.sne_chol_inverse(300, A, 300, C, 300, 1, -1.0, 256, nb.value - 1, None) == WS
+    assert L.sne_trunc_log_eval(-1, A, C, None) == ARG
+    assert L.sne_trunc_log_eval(10, None, C, None) == ARG
+    assert L.sne_trunc_log_eval(10, A, None, None) == ARG
+    assert L.sne_trunc_log_eval(0, None, None, None) == 0  # nothing to do
 
 
 def test_batched_argument_errors_on_the_host(L):
