@@ -336,6 +336,29 @@ int sne_sym_eig_workspace_bytes(int32_t n, size_t *bytes);
 int sne_sym_eig(int32_t n, const double *S, int32_t lds, double *lambda, double *V, int32_t ldv,
                 void *workspace, size_t ws_bytes, sne_stream_t stream);
 
+/* Autotuner of the fused tensor-core sketch (Eq. 4 and the Z core of Alg. 4
+ * with the half-precision reconstructions; the FP32 path has nothing to
+ * tune): prepares the sketch operands of graph graphs[0] (G = 1, workspace of
+ * sne_workspace_bytes(SNE_WS_EMBED)) or of the whole batch (G > 1, workspace
+ * of sne_embed_batched_workspace_bytes with the same lanes), then times the
+ * persistent sketch launch for every candidate shape: column tile width 128
+ * or 256, every number of B stages that fits shared memory, and the column
+ * split of the Z core (aiming at 1, 2 or 4 work items per SM).  The fastest
+ * shape is kept for this kind of sketch (k, precision, z and log2 of the
+ * rows) and used by later sne_embed / sne_embed_batched calls in this process.
+ * No shape changes a result.  Synchronizes the stream; out receives the
+ * choice and the launch times with it and with the default shape.  Errors:
+ * SNE_ERR_ARG (FP32 precision, graphs of different z), SNE_ERR_WORKSPACE,
+ * the errors of sne_embed. */
+typedef struct sne_tune_result {
+  int32_t tn, stages, split_mult; /* chosen launch shape */
+  int32_t candidates;             /* shapes timed */
+  float best_ms, default_ms;      /* one sketch launch: chosen and default shape */
+} sne_tune_result;
+int sne_autotune_sketch(int32_t G, const sne_csr *graphs, const sne_params *p, int32_t lanes,
+                        void *workspace, size_t ws_bytes, sne_tune_result *out,
+                        sne_stream_t stream);
+
 /* trunc_log as the tensor-core sketch epilogue evaluates it (Eq. 4 with
  * f = trunc_log, f(x) = max(0, log x)): out[i] = log1p(r[i]) for r[i] > 0 and
  * 0 otherwise, where r = x - 1 is the centred entry.  r and out are device

@@ -80,6 +80,15 @@ struct Bump {
     off += count * sizeof(T);
     return ptr;
   }
+  // rows of row_bytes starting at a multiple of row_bytes from the base (the
+  // tensor-core sketch reads its operands as rows of one arena)
+  template <class T>
+  T *take_rows(size_t rows, size_t row_bytes) {
+    off = (off + row_bytes - 1) / row_bytes * row_bytes;
+    T *ptr = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off += rows * row_bytes;
+    return ptr;
+  }
 };
 
 struct Bufs {
@@ -105,11 +114,15 @@ struct Bufs {
   float *ws_hi, *ws_lo;        // s w as an FP32 pair
   float2 *rowdat, *rowdatO;    // (rho, mask) per row of L~ and of L~(p_O, :)
   float4 *coldatS, *coldatO;   // (scale, kappa, sign, 0) per evaluated column
+  char *arena;        // the workspace: base of the tensor-core operand rows
+  size_t arena_bytes;
   int64_t *h_rowptr;  // device staging of a host graph (SNE_WS_EMBED_HOST)
   int32_t *h_col;
   float *h_val, *h_E;
   double *h_sigma;
 };
+
+inline int64_t pad256(int64_t x) { return (x + 255) / 256 * 256; }
 
 size_t carve(const Dims &D, int mode, void *base, Bufs *b) {
   Bump bp{static_cast<char *>(base)};
@@ -173,15 +186,17 @@ size_t carve(const Dims &D, int mode, void *base, Bufs *b) {
     x.coldatS = bp.take<float4>(D.nS + 256);
     x.coldatO = bp.take<float4>(D.nO + 256);
     if (D.half) {
-      x.Ah = bp.take<uint16_t>((size_t)n * D.kpad);
-      x.AhO = bp.take<uint16_t>((size_t)vmax * D.kpad);
-      x.BhS = bp.take<uint16_t>((size_t)D.nS * D.kpad);
-      x.BhO = bp.take<uint16_t>((size_t)D.nO * D.kpad);
+      // operand rows of the arena; B zero padded to whole 256-column tiles
+      const size_t rb = (size_t)D.kpad * 2;
+      x.Ah = bp.take_rows<uint16_t>(n, rb);
+      x.AhO = bp.take_rows<uint16_t>(vmax, rb);
+      x.BhS = bp.take_rows<uint16_t>(pad256(D.nS), rb);
+      x.BhO = bp.take_rows<uint16_t>(pad256(D.nO), rb);
       if (D.split) {
-        x.Al = bp.take<uint16_t>((size_t)n * D.kpad);
-        x.AlO = bp.take<uint16_t>((size_t)vmax * D.kpad);
-        x.BlS = bp.take<uint16_t>((size_t)D.nS * D.kpad);
-        x.BlO = bp.take<uint16_t>((size_t)D.nO * D.kpad);
+        x.Al = bp.take_rows<uint16_t>(n, rb);
+        x.AlO = bp.take_rows<uint16_t>(vmax, rb);
+        x.BlS = bp.take_rows<uint16_t>(pad256(D.nS), rb);
+        x.BlO = bp.take_rows<uint16_t>(pad256(D.nO), rb);
       }
       x.rowfA = bp.take<float>(n);
       x.rowfO = bp.take<float>(vmax);
@@ -194,8 +209,11 @@ size_t carve(const Dims &D, int mode, void *base, Bufs *b) {
     x.h_E = bp.take<float>((size_t)D.n * D.d);
     x.h_sigma = bp.take<double>(D.d);
   }
+  const size_t total = (bp.off + 255) & ~(size_t)255;
+  x.arena = static_cast<char *>(base);
+  x.arena_bytes = total;
   if (b) *b = x;
-  return (bp.off + 255) & ~(size_t)255;
+  return total;
 }
 
 #define CK(call)                               \
@@ -387,11 +405,33 @@ int run_freigs(const sne_csr &g, const sne_params &p, const Dims &D, const Bufs 
 }
 
 // Eq. 11 + Alg. 4 from U_k (ld k), lambda.  Optional outputs Y, Z, E, sigma.
+// The two tensor-core sketches of one graph: Y = f(L'R'(:, p_S)) S(p_S, :)
+// (Alg. 4 line 4) and the Z core's Y' = f(L'(p_O, :) R'(:, p_O)) O(p_O, :)
+// (Alg. 4 line 7), on the rows p_O (device count v_o).
+void tc_jobs(const Dims &D, const Bufs &b, float *Y, int h, int l, TcSketchJobDesc *jobs) {
+  const int64_t vmax = min64(D.n, D.nO);
+  jobs[0] = TcSketchJobDesc{b.Ah, b.Al, b.BhS, b.BlS, D.n, nullptr, (int32_t)D.nS, h,
+                            b.rowfA, b.rowdat, b.coldatS, Y, h, b.ctrl};
+  jobs[1] = TcSketchJobDesc{b.AhO, b.AlO, b.BhO, b.BlO, vmax, &b.ctrl->v_o, (int32_t)D.nO, l,
+                            b.rowfO, b.rowdatO, b.coldatO, b.Yo, l, b.ctrl};
+}
+
+TcTune tc_tune_for(const Dims &D) {
+  return tc_tune_lookup(D.kpad, D.split, D.fp16, D.z, D.n);
+}
+
+// phase 0: all of it.  Phase 1 (half-precision reconstructions only): up to
+// the tensor-core sketch, whose two jobs go to jobs_out instead of being
+// launched (a batch runs the sketches of all its graphs in one launch).
+// Phase 2: from the sketch results on.
 int run_sketch(const sne_csr &g, const sne_params &p, const Dims &D, const Bufs &b, const float *U,
                const double *lam, float *Yout, float *Zout, float *E, double *sigma,
-               cudaStream_t st) {
+               cudaStream_t st, int phase = 0, TcSketchJobDesc *jobs_out = nullptr) {
   const int k = D.k, h = D.h, l = D.l, z = D.z;
   const float sv = 1.0f / sqrtf((float)z);
+  float *Y = Yout ? Yout : b.A;
+  if (phase == 1 && (!D.half || !jobs_out)) return SNE_ERR_ARG;
+  if (phase != 2) {
   // --- Eq. 11 factors
   // d^(-1+2alpha) in FP64, as the FP32 pair (wgt, wgt_lo)
   { ProfScope ps_(K_MISC, st); rowscale_kernel<<<grid_for(D.n), 256, 0, st>>>(b.deg, D.n, -1.0 + 2.0 * p.alpha, nullptr,
@@ -439,7 +479,6 @@ int run_sketch(const sne_csr &g, const sne_params &p, const Dims &D, const Bufs 
                         b.signO, b.RpO, b.coldatO, st));
   // --- Alg. 4 line 4: Y = f(L' R'(:, p)) S(p, :)
   // --- Alg. 4 line 7: Y' = f(L'(p,:) R'(:,p)) O(p,:) on the rows p = p_O
-  float *Y = Yout ? Yout : b.A;
   const int64_t vmax = min64(D.n, D.nO);
   if (!D.half) {
     // centred rows L~ = s (W - w) (FP32) in the free tall buffer
@@ -464,12 +503,30 @@ int run_sketch(const sne_csr &g, const sne_params &p, const Dims &D, const Bufs 
                          reinterpret_cast<float *>(b.coldatS), 4, st));
     CK(launch_split_rows(D.fp16, D.split, b.RpO, k, D.nO, k, D.kpad, b.BhO, b.BlO,
                          reinterpret_cast<float *>(b.coldatO), 4, st));
-    CK(launch_fused_sketch_tc(D.fp16, D.split, b.Ah, b.Al, D.n, nullptr, D.kpad, b.BhS, b.BlS,
-                              D.nS, h, z, b.rowfA, b.rowdat, b.coldatS, sv, p.f, Y, h, b.ctrl, st));
-    CK(launch_fused_sketch_tc(D.fp16, D.split, b.AhO, b.AlO, vmax, &b.ctrl->v_o, D.kpad, b.BhO,
-                              b.BlO, D.nO, l, z, b.rowfO, b.rowdatO, b.coldatO, sv, p.f, b.Yo, l,
-                              b.ctrl, st));
+    // zero rows past the evaluated columns up to the 256-row tile boundary
+    const size_t rb = (size_t)D.kpad * 2;
+    CK(cudaMemsetAsync(static_cast<char *>(b.BhS) + (size_t)D.nS * rb, 0,
+                       (size_t)(pad256(D.nS) - D.nS) * rb, st));
+    CK(cudaMemsetAsync(static_cast<char *>(b.BhO) + (size_t)D.nO * rb, 0,
+                       (size_t)(pad256(D.nO) - D.nO) * rb, st));
+    if (D.split) {
+      CK(cudaMemsetAsync(static_cast<char *>(b.BlS) + (size_t)D.nS * rb, 0,
+                         (size_t)(pad256(D.nS) - D.nS) * rb, st));
+      CK(cudaMemsetAsync(static_cast<char *>(b.BlO) + (size_t)D.nO * rb, 0,
+                         (size_t)(pad256(D.nO) - D.nO) * rb, st));
+    }
+    // Y and the Z core's Y' in one persistent launch
+    TcSketchJobDesc jobs[2];
+    tc_jobs(D, b, Y, h, l, jobs);
+    if (phase == 1) {
+      jobs_out[0] = jobs[0];
+      jobs_out[1] = jobs[1];
+      return SNE_OK;
+    }
+    CK(launch_fused_sketch_tc_jobs(D.fp16, D.split, b.arena, b.arena_bytes, D.kpad, z, sv, p.f, jobs,
+                                   2, tc_tune_for(D), b.ctrl, st));
   }
+  }  // phase != 2
   // --- Z = O(p,:)^T Y'  (Alg. 4 line 7)
   float *Z = Zout ? Zout : b.Zf;
   CK(launch_signed_gather_sum(b.Yo, l, l, b.posO, b.signO, l, z, sv, Z, l, st));
@@ -876,3 +933,51 @@ extern "C" int sne_freigs_static(const sne_csr *g, const sne_params *p, float *U
     CK(cudaMemcpyAsync(status, &b.ctrl->status, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
   return SNE_OK;
 }
+
+namespace sne {
+
+bool embed_tc_shape(const sne_csr *g, const sne_params *p, TcShape *out) {
+  Dims D;
+  if (!g || make_dims(g->n, g->nnz, p, SNE_WS_EMBED, &D) != SNE_OK || !D.half) return false;
+  out->kpad = D.kpad;
+  out->fp16 = D.fp16;
+  out->split = D.split;
+  out->z = D.z;
+  out->f = p->f;
+  return true;
+}
+
+size_t tc_row_bytes(const sne_params *p) {
+  Dims D;
+  if (make_dims(1 << 20, 1 << 20, p, SNE_WS_EMBED, &D) != SNE_OK) return 256;
+  return D.half ? (size_t)D.kpad * 2 : 256;
+}
+
+int embed_phase(const sne_csr *g, const sne_params *p, void *ws, size_t ws_bytes, float *E,
+                double *sigma, int phase, TcSketchJobDesc *jobs, cudaStream_t st) {
+  int rc = check_graph(g);
+  if (rc) return rc;
+  rc = check_has_edges(g);
+  if (rc) return rc;
+  Dims D;
+  rc = make_dims(g->n, g->nnz, p, SNE_WS_EMBED, &D);
+  if (rc) return rc;
+  if (!D.half || (phase != 1 && phase != 2)) return SNE_ERR_ARG;
+  rc = check_ws(ws, ws_bytes, carve(D, SNE_WS_EMBED, nullptr, nullptr));
+  if (rc) return rc;
+  if (!E || !sigma) return SNE_ERR_ARG;
+  Bufs b;
+  carve(D, SNE_WS_EMBED, ws, &b);
+  float *Uk = b.C;
+  double *lam = b.lam;
+  if (phase == 1) {
+    CK(cudaMemsetAsync(b.ctrl, 0, sizeof(Ctrl), st));
+    CK(launch_degrees(*g, b.deg, &b.ctrl->vol, st));
+    rc = run_freigs(*g, *p, D, b, Uk, lam, st);
+    if (rc) return rc;
+    return run_sketch(*g, *p, D, b, Uk, lam, nullptr, nullptr, E, sigma, st, 1, jobs);
+  }
+  return run_sketch(*g, *p, D, b, Uk, lam, nullptr, nullptr, E, sigma, st, 2, nullptr);
+}
+
+}  // namespace sne

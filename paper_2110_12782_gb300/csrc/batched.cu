@@ -8,11 +8,14 @@
 // runs.  The single-graph path never waits on the host, so a whole batch can
 // be captured into a CUDA graph and replayed.
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 #include <numeric>
 #include <vector>
 
 #include "sne_internal.cuh"
+
+using namespace sne;
 
 namespace {
 
@@ -62,10 +65,11 @@ double graph_cost(const sne_csr &g, const sne_params &p) {
 
 struct Plan {
   int lanes = 0;
+  bool lockstep = false;       // tensor-core sketch: one launch for the whole batch
   std::vector<int> order;      // graphs, largest first
   std::vector<int> lane_of;    // lane of each graph
-  std::vector<size_t> bytes;   // workspace of each lane
-  std::vector<size_t> offset;  // byte offset of each lane's slice
+  std::vector<size_t> bytes;   // workspace of each lane (lockstep: of each graph)
+  std::vector<size_t> offset;  // byte offset of each lane's (graph's) slice
   size_t total = 0;
 };
 
@@ -96,19 +100,214 @@ int make_plan(int32_t G, const sne_csr *graphs, const sne_params *p, int32_t lan
     load[l] += cost[i];
     plan->bytes[l] = std::max(plan->bytes[l], wsb[i]);
   }
-  plan->offset.assign(L, 0);
+  TcShape shp;
+  plan->lockstep = G > 1 && embed_tc_shape(&graphs[0], p, &shp);
+  if (!plan->lockstep) {
+    plan->offset.assign(L, 0);
+    size_t off = 0;
+    for (int l = 0; l < L; ++l) {
+      plan->offset[l] = off;
+      off += (plan->bytes[l] + 255) & ~(size_t)255;
+    }
+    plan->total = off;
+    return SNE_OK;
+  }
+  // every graph keeps its own slice from its first half to its second; the
+  // slices start on operand-row boundaries of the one arena the batched
+  // sketch reads
+  const size_t rb = tc_row_bytes(p);
+  const size_t al = std::lcm((size_t)256, rb);
+  plan->bytes = wsb;
+  plan->offset.assign(G, 0);
   size_t off = 0;
-  for (int l = 0; l < L; ++l) {
-    plan->offset[l] = off;
-    off += (plan->bytes[l] + 255) & ~(size_t)255;
+  for (int i = 0; i < G; ++i) {
+    plan->offset[i] = off;
+    off += (wsb[i] + al - 1) / al * al;
   }
   plan->total = off;
   return SNE_OK;
 }
 
+// The lockstep form: the first halves of all embeddings on the lanes, one
+// persistent tensor-core launch for the sketches of all of them (grouped by
+// z, which is min(n, zeta)), the second halves on the lanes.
+int run_lockstep(const Plan &plan, int32_t G, const sne_csr *graphs, const sne_params *p, void *ws,
+                 float *const *E, double *const *sigma, int32_t *status, LanePool *pool,
+                 cudaStream_t st) {
+  std::vector<TcSketchJobDesc> jobs((size_t)2 * G);
+  std::vector<TcShape> shape(G);
+  for (int i = 0; i < G; ++i)
+    if (!embed_tc_shape(&graphs[i], p, &shape[i])) return SNE_ERR_ARG;
+  int first_error = SNE_OK;
+  for (int i : plan.order) {
+    const int l = plan.lane_of[i];
+    char *slice = static_cast<char *>(ws) + plan.offset[i];
+    const int r = embed_phase(&graphs[i], p, slice, plan.bytes[i], E[i], sigma[i], 1,
+                              &jobs[(size_t)2 * i], pool->stream[l]);
+    if (r != SNE_OK) {
+      first_error = r;
+      break;
+    }
+  }
+  for (int l = 0; l < plan.lanes; ++l) {
+    if (cudaEventRecord(pool->join[l], pool->stream[l]) != cudaSuccess) return SNE_ERR_CUDA;
+    if (cudaStreamWaitEvent(st, pool->join[l], 0) != cudaSuccess) return SNE_ERR_CUDA;
+  }
+  if (first_error) return first_error;
+  std::vector<int> zs;
+  for (int i = 0; i < G; ++i)
+    if (std::find(zs.begin(), zs.end(), shape[i].z) == zs.end()) zs.push_back(shape[i].z);
+  for (int z : zs) {
+    std::vector<TcSketchJobDesc> grp;
+    int64_t rows = 0;
+    for (int i = 0; i < G; ++i)
+      if (shape[i].z == z) {
+        grp.push_back(jobs[(size_t)2 * i]);
+        grp.push_back(jobs[(size_t)2 * i + 1]);
+        rows += jobs[(size_t)2 * i].nrows_max + jobs[(size_t)2 * i + 1].nrows_max;
+      }
+    const TcShape &s0 = shape[0];
+    const TcTune tune = tc_tune_lookup(s0.kpad, s0.split, s0.fp16, z, rows);
+    if (launch_fused_sketch_tc_jobs(s0.fp16, s0.split, ws, plan.total, s0.kpad, z,
+                                    1.0f / sqrtf((float)z), s0.f, grp.data(), (int)grp.size(),
+                                    tune, grp[0].ctrl, st) != cudaSuccess)
+      return SNE_ERR_CUDA;
+  }
+  if (cudaEventRecord(pool->fork, st) != cudaSuccess) return SNE_ERR_CUDA;
+  for (int l = 0; l < plan.lanes; ++l)
+    if (cudaStreamWaitEvent(pool->stream[l], pool->fork, 0) != cudaSuccess) return SNE_ERR_CUDA;
+  for (int i : plan.order) {
+    const int l = plan.lane_of[i];
+    char *slice = static_cast<char *>(ws) + plan.offset[i];
+    const int r = embed_phase(&graphs[i], p, slice, plan.bytes[i], E[i], sigma[i], 2, nullptr,
+                              pool->stream[l]);
+    if (r != SNE_OK) {
+      first_error = r;
+      break;
+    }
+    if (status && cudaMemcpyAsync(status + i, slice, sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                                  pool->stream[l]) != cudaSuccess) {
+      first_error = SNE_ERR_CUDA;
+      break;
+    }
+  }
+  return first_error;
+}
+
+// One timed launch of the batch's sketches with launch shape t (ms).
+float time_sketch(const std::vector<TcSketchJobDesc> &jobs, const TcShape &s0, void *arena,
+                  size_t arena_bytes, const TcTune &t, cudaStream_t st, int reps) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return -1.f;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return -1.f;
+  }
+  float best = -1.f;
+  for (int r = 0; r < reps; ++r) {
+    cudaEventRecord(e0, st);
+    const cudaError_t e = launch_fused_sketch_tc_jobs(
+        s0.fp16, s0.split, arena, arena_bytes, s0.kpad, s0.z, 1.0f / sqrtf((float)s0.z), s0.f,
+        jobs.data(), (int)jobs.size(), t, jobs[0].ctrl, st);
+    cudaEventRecord(e1, st);
+    if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+      best = -1.f;
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (best < 0.f || ms < best) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
+}
+
 }  // namespace
 
 extern "C" {
+
+int sne_autotune_sketch(int32_t G, const sne_csr *graphs, const sne_params *p, int32_t lanes,
+                        void *ws, size_t ws_bytes, sne_tune_result *out, sne_stream_t stream) {
+  if (G <= 0 || !graphs || !p || !out) return SNE_ERR_ARG;
+  TcShape s0;
+  if (!embed_tc_shape(&graphs[0], p, &s0)) return SNE_ERR_ARG;  // FP32 path: nothing to tune
+  for (int i = 1; i < G; ++i) {
+    TcShape si;
+    if (!embed_tc_shape(&graphs[i], p, &si) || si.z != s0.z) return SNE_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<TcSketchJobDesc> jobs((size_t)2 * G);
+  // the sketch operands of every graph, as the embedding prepares them (the
+  // outputs E and sigma are not written by the first half)
+  size_t arena_bytes = ws_bytes;
+  int64_t rows = 0;
+  if (G == 1) {
+    size_t need = 0;
+    int rc = sne_workspace_bytes(graphs[0].n, graphs[0].nnz, p, SNE_WS_EMBED, &need);
+    if (rc) return rc;
+    if (!ws || ((uintptr_t)ws % 256) != 0 || ws_bytes < need) return SNE_ERR_WORKSPACE;
+    float dummyE = 0.f;
+    double dummyS = 0.0;
+    rc = embed_phase(&graphs[0], p, ws, ws_bytes, &dummyE, &dummyS, 1, jobs.data(), st);
+    if (rc) return rc;
+    arena_bytes = need;
+    rows = graphs[0].n;
+  } else {
+    Plan plan;
+    int rc = make_plan(G, graphs, p, lanes, &plan);
+    if (rc) return rc;
+    if (!plan.lockstep) return SNE_ERR_ARG;
+    if (!ws || ((uintptr_t)ws % 256) != 0 || ws_bytes < plan.total) return SNE_ERR_WORKSPACE;
+    float dummyE = 0.f;
+    double dummyS = 0.0;
+    for (int i = 0; i < G; ++i) {
+      char *slice = static_cast<char *>(ws) + plan.offset[i];
+      rc = embed_phase(&graphs[i], p, slice, plan.bytes[i], &dummyE, &dummyS, 1, &jobs[(size_t)2 * i],
+                       st);
+      if (rc) return rc;
+      rows += jobs[(size_t)2 * i].nrows_max + jobs[(size_t)2 * i + 1].nrows_max;
+    }
+    arena_bytes = plan.total;
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) return SNE_ERR_CUDA;
+  // candidates: column tile 256 or 128, every stage count that fits from 2,
+  // Z-core column split aiming at 1, 2 or 4 items per SM
+  std::vector<TcTune> cand;
+  for (int tn : {256, 128}) {
+    const int smax = tc_max_stages(s0.kpad, s0.split, tn);
+    for (int stg = 2; stg <= smax; ++stg)
+      for (int sm : {1, 2, 4}) {
+        TcTune t;
+        t.tn = tn;
+        t.stages = stg;
+        t.split_mult = sm;
+        cand.push_back(t);
+      }
+  }
+  const TcTune dflt;
+  const float dms = time_sketch(jobs, s0, ws, arena_bytes, dflt, st, 3);
+  if (dms < 0.f) return SNE_ERR_CUDA;
+  TcTune best = dflt;
+  float bms = dms;
+  for (const TcTune &t : cand) {
+    const float ms = time_sketch(jobs, s0, ws, arena_bytes, t, st, 3);
+    if (ms < 0.f) return SNE_ERR_CUDA;
+    if (ms < bms) {
+      bms = ms;
+      best = t;
+    }
+  }
+  tc_tune_store(s0.kpad, s0.split, s0.fp16, s0.z, rows, best);
+  out->tn = best.tn;
+  out->stages = best.stages > 0 ? best.stages : tc_max_stages(s0.kpad, s0.split, best.tn);
+  out->split_mult = best.split_mult;
+  out->candidates = (int32_t)cand.size() + 1;
+  out->best_ms = bms;
+  out->default_ms = dms;
+  return SNE_OK;
+}
+
 
 int sne_embed_batched_workspace_bytes(int32_t G, const sne_csr *graphs, const sne_params *p,
                                       int32_t lanes, size_t *bytes) {
@@ -139,6 +338,9 @@ int sne_embed_batched(int32_t G, const sne_csr *graphs, const sne_params *p, int
   for (int l = 0; l < plan.lanes; ++l)
     if (cudaStreamWaitEvent(pool->stream[l], pool->fork, 0) != cudaSuccess) return SNE_ERR_CUDA;
   int first_error = SNE_OK;
+  if (plan.lockstep) {
+    first_error = run_lockstep(plan, G, graphs, p, ws, E, sigma, status, pool, st);
+  } else {
   for (int i : plan.order) {
     const int l = plan.lane_of[i];
     char *slice = static_cast<char *>(ws) + plan.offset[l];
@@ -153,6 +355,7 @@ int sne_embed_batched(int32_t G, const sne_csr *graphs, const sne_params *p, int
       first_error = SNE_ERR_CUDA;
       break;
     }
+  }
   }
   // the caller's stream waits for every lane, also after an error, so that
   // nothing enqueued above outlives the call's stream order

@@ -549,14 +549,15 @@ __global__ void __launch_bounds__(1024) chol_inv_kernel(const T *__restrict__ A,
 }
 
 // ---------------------------------------------------------------------------
-// Pivoted FP64 Cholesky over a cluster of kCholCl CTAs (left-looking form of
+// Pivoted FP64 Cholesky over a cluster of C CTAs (16 where the device allows
+// clusters of that size, else 8; left-looking form of
 // the diagonal pivoting of LAPACK's pstrf).  GB300 executes about two FP64
 // fused multiply-adds per clock and SM, so one CTA cannot factor a 272 x 272
 // matrix in less than a millisecond and a half; here the rows of L (A = L L^T,
 // rows in the original order) are spread cyclically over the cluster's shared
-// memory, row i in CTA i % kCholCl.  Step j:
+// memory, row i in CTA i % C.  Step j:
 //   each CTA proposes its largest remaining diagonal d_i (lowest index on
-//   ties); after a cluster barrier every CTA reads the kCholCl proposals
+//   ties); after a cluster barrier every CTA reads the C proposals
 //   through distributed shared memory and takes the same pivot p (stopping
 //   at the numerical rank: d_p <= tol max_i A_ii, or not finite);
 //   L(p, j) = sqrt(d_p); every CTA copies L(p, 0..j-1) from p's CTA and, for
@@ -567,7 +568,6 @@ __global__ void __launch_bounds__(1024) chol_inv_kernel(const T *__restrict__ A,
 // pivot order, 1 / R_jj, the pivot order and the rank), for chol_backsub_kernel.
 // The waits are the cluster barriers, whose CTAs are co-scheduled.
 // ---------------------------------------------------------------------------
-constexpr int kCholCl = 8;
 constexpr int kCholClThreads = 512;
 
 __device__ __forceinline__ uint32_t cl_rank() {
@@ -604,16 +604,16 @@ __device__ __forceinline__ void piv_better(double &v, int &i, double ov, int oi)
   }
 }
 
-size_t chol_piv_cluster_smem(int n) {
-  const int nloc = (n + kCholCl - 1) / kCholCl;
+size_t chol_piv_cluster_smem(int n, int C) {
+  const int nloc = (n + C - 1) / C;
   return ((size_t)nloc * n + n + nloc + 2) * sizeof(double) + (2 + 2 * (size_t)n) * sizeof(int) +
          (size_t)n + 16;
 }
 
+template <int C>
 __global__ void __launch_bounds__(kCholClThreads) chol_piv_cluster_kernel(
     const double *__restrict__ A, int n, int lda, double *__restrict__ scratch, double tol) {
   extern __shared__ __align__(16) unsigned char ccm[];
-  constexpr int C = kCholCl;
   const int nloc = (n + C - 1) / C;
   double *L = reinterpret_cast<double *>(ccm);  // nloc x n: L[t n + k] = L(me + C t, k)
   double *rp = L + (size_t)nloc * n;            // n: L(p, k), k < j
@@ -1189,37 +1189,60 @@ cudaError_t launch_chol_inverse(const T *A, int32_t n, int32_t lda, T *Rinv, int
   }
   const bool packed = chol_inv_smem<T>(n, true) <= 220 * 1024;
   if (!packed && !scratch) return cudaErrorInvalidValue;
-  if (sizeof(T) == 8 && tol >= 0.0 && scratch && chol_piv_cluster_smem(n) <= 220 * 1024 &&
-      chol_cluster_enabled()) {
-    // pivoted FP64: the cluster kernel, then the multi-CTA back substitution
-    const size_t csm = chol_piv_cluster_smem(n);
-    cudaError_t e = cudaFuncSetAttribute(chol_piv_cluster_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
-    if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(kCholCl, 1, 1);
-    cfg.blockDim = dim3(kCholClThreads, 1, 1);
-    cfg.dynamicSmemBytes = csm;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = kCholCl;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    {
-      ProfScope ps_(K_CHOL, st);
-      e = cudaLaunchKernelEx(&cfg, chol_piv_cluster_kernel, reinterpret_cast<const double *>(A), n,
-                             lda, reinterpret_cast<double *>(scratch), tol);
+  if (sizeof(T) == 8 && tol >= 0.0 && scratch && chol_cluster_enabled()) {
+    // pivoted FP64: the cluster kernel (16 CTAs, else 8), then the multi-CTA
+    // back substitution
+    cudaError_t e = cudaErrorInvalidValue;
+    bool launched = false;
+    for (int C : {16, 8}) {
+      const size_t csm = chol_piv_cluster_smem(n, C);
+      if (csm > 220 * 1024) continue;
+      auto kern = C == 16 ? chol_piv_cluster_kernel<16> : chol_piv_cluster_kernel<8>;
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
       if (e != cudaSuccess) return e;
+      if (C > 8) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+            cudaSuccess) {
+          (void)cudaGetLastError();
+          continue;
+        }
+      }
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(C, 1, 1);
+      cfg.blockDim = dim3(kCholClThreads, 1, 1);
+      cfg.dynamicSmemBytes = csm;
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = C;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      if (C > 8) {
+        // a cluster of 16 must fit the device (one GPC's SMs): ask first
+        int ncl = 0;
+        if (cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg) != cudaSuccess || ncl < 1) {
+          (void)cudaGetLastError();
+          continue;
+        }
+      }
+      ProfScope ps_(K_CHOL, st);
+      e = cudaLaunchKernelEx(&cfg, kern, reinterpret_cast<const double *>(A), n, lda,
+                             reinterpret_cast<double *>(scratch), tol);
+      if (e != cudaSuccess) return e;
+      launched = true;
+      break;
+    }
+    if (launched) {
+      ProfScope ps_(K_CHOL, st);
       const size_t bsmem = (size_t)8 * n * sizeof(T);
       e = cudaFuncSetAttribute(chol_backsub_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)bsmem);
       if (e != cudaSuccess) return e;
       chol_backsub_kernel<T><<<(n + 7) / 8, 256, bsmem, st>>>(scratch, n, Rinv, ldi);
+      return cudaGetLastError();
     }
-    return cudaGetLastError();
   }
   const size_t smem = chol_inv_smem<T>(n, packed);
   auto kern = packed ? chol_inv_kernel<T, true> : chol_inv_kernel<T, false>;

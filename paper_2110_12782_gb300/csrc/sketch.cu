@@ -15,7 +15,6 @@
 // (rho_i, mask_i), coldat[e] = (scale, kappa_e, sgn_e, 0); trunc_log(x) is
 // log1p(x - 1) for x - 1 > 0 (c0 = 1) and the identity is x itself (c0 = 0).
 #include "sne_internal.cuh"
-#include "tc_ptx.cuh"
 
 namespace sne {
 
@@ -23,12 +22,13 @@ constexpr int kFM = 64;    // rows per CTA
 constexpr int kFN = 128;   // evaluated columns per CTA
 constexpr int kFK = 16;    // k step
 
-// f from r = x - c0: the evaluation of the tensor-core kernels (tc_ptx.cuh:
-// log1p by a fitted polynomial below r = 1 and the hardware base-2 logarithm
-// above, relative error below 2e-7), so that both paths apply the same f
+// f from r = x - c0 (CUDA's log1pf: in this kernel, bound by the FP32
+// products of k terms per entry, the polynomial form of the tensor-core
+// epilogue measured slower)
 template <int F>
 __device__ __forceinline__ float apply_f(float r) {
-  return tc::fr<F>(r);
+  if (F == SNE_F_TRUNC_LOG) return r > 0.0f ? log1pf(r) : 0.0f;
+  return r;
 }
 
 template <int F>

@@ -260,14 +260,54 @@ cudaError_t launch_rtilde_rows(const float *U, int32_t k, const int32_t *idx, in
                                cudaStream_t st);
 // sketch_tc.cu: the same sums with half-precision operands (BF16 or FP16,
 // optionally hi/lo pairs) on tcgen05 with FP32 accumulation; A rows scaled by
-// rowf, B rows by coldat[e].x; kpad = k rounded up to 64; coldat readable
+// rowf, B rows by coldat[e].x; kpad = k rounded up to 64.  One persistent
+// launch runs any number of such sketches (jobs).  Every operand lies in the
+// arena [arena, arena + arena_bytes) at a byte offset that is a multiple of
+// 2 kpad (one row), B zero padded to a multiple of 256 rows; coldat readable
 // (zero padded) up to a multiple of 256 entries.
-cudaError_t launch_fused_sketch_tc(bool fp16, bool split, const void *Ahi, const void *Alo,
-                                   int64_t nrows_max, const int32_t *nrows_dev, int kpad,
-                                   const void *Bhi, const void *Blo, int ncols_eval, int cols_out,
-                                   int z, const float *rowf, const float2 *rowdat,
-                                   const float4 *coldat, float sv, int f, float *out, int64_t ldo,
-                                   Ctrl *ctrl, cudaStream_t st);
+struct TcSketchJobDesc {
+  const void *Ahi, *Alo, *Bhi, *Blo;  // Alo, Blo: split precisions only
+  int64_t nrows_max;                  // rows of A
+  const int32_t *nrows_dev;           // if set: the rows used (device count)
+  int32_t ncols_eval, cols_out;
+  const float *rowf;
+  const float2 *rowdat;
+  const float4 *coldat;
+  float *out;
+  int64_t ldo;
+  Ctrl *ctrl;                         // status word (timeouts); null: the launch's
+};
+// Launch shape of the fused tensor-core sketch: column tile width (128 or
+// 256), B stages (0: as many as fit), and the column split of jobs with few
+// row tiles (items per SM to aim for).  None of them changes a result.
+struct TcTune {
+  int tn = 256;
+  int stages = 0;
+  int split_mult = 2;
+};
+int tc_max_stages(int kpad, bool split, int tn);
+// The launch shape for a sketch of this kind: the autotuner's choice for the
+// key (kpad, split, fp16, z, log2 of the rows) if it has tuned one, else the
+// default; SNE_TC_TN, SNE_TC_STAGES and SNE_TC_SPLIT override it (for
+// comparisons).
+TcTune tc_tune_lookup(int kpad, bool split, bool fp16, int z, int64_t rows);
+// api.cu: the shape of a graph's tensor-core sketch (false for the FP32 path),
+// the operand row bytes for the parameters, and an embedding in two halves
+// around that sketch (phase 1: up to the sketch, its two jobs returned instead
+// of launched; phase 2: from the sketch results on; the same workspace).
+struct TcShape {
+  int kpad, z, f;
+  bool fp16, split;
+};
+bool embed_tc_shape(const sne_csr *g, const sne_params *p, TcShape *out);
+size_t tc_row_bytes(const sne_params *p);
+int embed_phase(const sne_csr *g, const sne_params *p, void *ws, size_t ws_bytes, float *E,
+                double *sigma, int phase, TcSketchJobDesc *jobs, cudaStream_t st);
+void tc_tune_store(int kpad, bool split, bool fp16, int z, int64_t rows, const TcTune &t);
+cudaError_t launch_fused_sketch_tc_jobs(bool fp16, bool split, const void *arena,
+                                        size_t arena_bytes, int kpad, int z, float sv, int f,
+                                        const TcSketchJobDesc *jobs, int njobs, const TcTune &tune,
+                                        Ctrl *ctrl, cudaStream_t st);
 // The same sum of FP32 rows accumulated and written in FP64.
 cudaError_t launch_signed_gather_sum64(const float *In, int64_t ldi, int32_t width,
                                        const int32_t *idx, const int8_t *sign, int32_t cols,

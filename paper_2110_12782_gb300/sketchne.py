@@ -46,7 +46,7 @@ EXPORTS = [
     "sne_embed_batched_workspace_bytes", "sne_embed_batched", "sne_chol_inverse_workspace_bytes",
     "sne_chol_inverse", "sne_propagation_coefficients", "sne_spectral_propagate_workspace_bytes",
     "sne_spectral_propagate", "sne_single_pass_svd_workspace_bytes", "sne_single_pass_svd",
-    "sne_trunc_log_eval",
+    "sne_trunc_log_eval", "sne_autotune_sketch",
 ]
 
 
@@ -59,6 +59,12 @@ class SketchNEError(RuntimeError):
 class sne_csr(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("row_ptr", ctypes.c_void_p),
                 ("col_idx", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class sne_tune_result(ctypes.Structure):
+    _fields_ = [("tn", ctypes.c_int32), ("stages", ctypes.c_int32), ("split_mult", ctypes.c_int32),
+                ("candidates", ctypes.c_int32), ("best_ms", ctypes.c_float),
+                ("default_ms", ctypes.c_float)]
 
 
 class sne_params(ctypes.Structure):
@@ -126,6 +132,8 @@ def lib() -> ctypes.CDLL:
             "sne_chol_inverse_workspace_bytes": [i32, i32, P(ctypes.c_size_t)],
             "sne_chol_inverse": [i32, vp, i32, vp, i32, i32, dbl, vp, ctypes.c_size_t, vp],
             "sne_trunc_log_eval": [i64, vp, vp, vp],
+            "sne_autotune_sketch": [i32, vp, P(sne_params), i32, vp, ctypes.c_size_t,
+                                    P(sne_tune_result), vp],
             "sne_single_pass_svd_workspace_bytes": [i64, i64, i32, P(sne_params),
                                                     P(ctypes.c_size_t)],
             "sne_single_pass_svd": [i64, i64, i32, vp, i64, vp, i64, P(sne_params), vp,
@@ -509,6 +517,21 @@ def sne_embed_batched(graphs, p: sne_params, ws: torch.Tensor, E, sigma, status:
                                    _ptr(ws, torch.uint8, "workspace"), ws.numel(), e_ptrs, s_ptrs,
                                    _ptr(status, torch.int32, "status", True), _stream(stream)),
            "sne_embed_batched")
+
+
+def sne_autotune_sketch(graphs, p: sne_params, ws: torch.Tensor, lanes: int = 0, stream=None) -> dict:
+    """Time the fused tensor-core sketch over its launch shapes for one graph
+    (workspace of ``workspace(..., SNE_WS_EMBED)``) or a batch (workspace of
+    ``batched_workspace(graphs, p, lanes)``); the fastest shape is used from
+    then on.  Returns the choice and the launch times."""
+    if isinstance(graphs, DeviceGraph):
+        graphs = [graphs]
+    res = sne_tune_result()
+    _check(lib().sne_autotune_sketch(len(graphs), _csr_array(graphs), ctypes.byref(p), lanes,
+                                     _ptr(ws, torch.uint8, "workspace"), ws.numel(),
+                                     ctypes.byref(res), _stream(stream)), "sne_autotune_sketch")
+    return {"tn": res.tn, "stages": res.stages, "split_mult": res.split_mult,
+            "candidates": res.candidates, "best_ms": res.best_ms, "default_ms": res.default_ms}
 
 
 def chol_inverse_workspace(n: int, fp64: bool, device="cuda") -> torch.Tensor:

@@ -138,3 +138,73 @@ def test_batched_cuda_graph_replay(sk, batch):
     torch.cuda.synchronize()
     for a, b in zip(E, ref_E):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("precision", ["fp16x2", "fp16"])
+def test_lockstep_batch_equals_single(sk, batch, precision):
+    """Half-precision reconstructions run the batch in lockstep: the first
+    halves of all embeddings on the lanes, one persistent tensor-core launch
+    for the sketches of every graph, the second halves on the lanes.  Each
+    entry of every sketch is computed by the same arithmetic as in a single
+    sne_embed, so the embeddings are the same bit for bit, also under a CUDA
+    graph."""
+    graphs, dev, _ = batch
+    p = sk.sne_params_init(D, K, orth=sk.SNE_ORTH_CHOLQR, precision=sk.PRECISIONS[precision])
+    E1, s1 = run_single(sk, graphs, dev, p)
+    E, s = outputs(graphs)
+    ws = sk.batched_workspace(dev, p, 3)
+    status = torch.full((len(graphs),), -99, dtype=torch.int32, device="cuda")
+    sk.sne_embed_batched(dev, p, ws, E, s, status=status, lanes=3)
+    torch.cuda.synchronize()
+    assert status.cpu().tolist() == [0] * len(graphs)
+    for a, b, sa, sb in zip(E, E1, s, s1):
+        assert torch.equal(a, b) and torch.equal(sa, sb)
+    for e in E:
+        e.zero_()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        sk.sne_embed_batched(dev, p, ws, E, s, lanes=3)
+    graph.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(E, E1):
+        assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("tn,stages,split", [(128, 2, 1), (128, 0, 4), (256, 2, 1), (256, 3, 8)])
+def test_tc_launch_shape_leaves_results_unchanged(sk, batch, monkeypatch, tn, stages, split):
+    """The launch shapes the autotuner chooses between (column tile width,
+    B stages, column split of the Z core) give the same embedding bit for bit."""
+    graphs, dev, _ = batch
+    g, G = graphs[1], dev[1]
+    p = sk.sne_params_init(D, K, orth=sk.SNE_ORTH_CHOLQR, precision=sk.SNE_FP16X2)
+    E0, s0 = run_single(sk, [g], [G], p)
+    monkeypatch.setenv("SNE_TC_TN", str(tn))
+    monkeypatch.setenv("SNE_TC_STAGES", str(stages))
+    monkeypatch.setenv("SNE_TC_SPLIT", str(split))
+    E1, s1 = run_single(sk, [g], [G], p)
+    assert torch.equal(E0[0], E1[0]) and torch.equal(s0[0], s1[0])
+
+
+def test_autotune_sketch(sk, batch):
+    """The autotuner times the candidate launch shapes of the fused
+    tensor-core sketch for one graph and for the batch, keeps the fastest, and
+    the embeddings computed afterwards (with the tuned shape) are the ones
+    computed before, bit for bit."""
+    graphs, dev, _ = batch
+    p = sk.sne_params_init(D, K, orth=sk.SNE_ORTH_CHOLQR, precision=sk.SNE_FP16X2)
+    E0, s0 = run_single(sk, graphs[:1], dev[:1], p)
+    ws = sk.workspace(graphs[0].n, graphs[0].nnz, p, sk.SNE_WS_EMBED)
+    r = sk.sne_autotune_sketch(dev[0], p, ws)
+    print(f"autotune one graph: {r}")
+    assert r["tn"] in (128, 256) and r["stages"] >= 2 and r["split_mult"] in (1, 2, 4)
+    assert r["candidates"] > 4 and 0 < r["best_ms"] <= r["default_ms"]
+    E1, s1 = run_single(sk, graphs[:1], dev[:1], p)
+    assert torch.equal(E0[0], E1[0]) and torch.equal(s0[0], s1[0])
+    wsb = sk.batched_workspace(dev, p, 3)
+    rb = sk.sne_autotune_sketch(dev, p, wsb, lanes=3)
+    print(f"autotune batch of {len(dev)}: {rb}")
+    assert 0 < rb["best_ms"] <= rb["default_ms"]
+    E, s = outputs(graphs)
+    sk.sne_embed_batched(dev, p, wsb, E, s, lanes=3)
+    torch.cuda.synchronize()
+    assert torch.equal(E[0], E0[0])
