@@ -823,7 +823,7 @@ def measure_batch(args, rank: int, world: int, workload: str, precision: str, st
         del wsg
     # half-precision reconstructions: the batch's sketches run as one
     # persistent launch, its shape timed over the candidates first
-    tune = sk.sne_autotune_sketch(dev, p, ws) if prec != sk.SNE_FP32 else None
+    tune = sk.sne_autotune_sketch(dev, p, ws, E=E, sigma=sig) if prec != sk.SNE_FP32 else None
     sk.sne_embed_batched(dev, p, ws, E, sig, status=status)  # creates the lanes
     torch.cuda.synchronize()
     cg = torch.cuda.CUDAGraph()

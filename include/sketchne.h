@@ -346,18 +346,24 @@ int sne_sym_eig(int32_t n, const double *S, int32_t lds, double *lambda, double 
  * split of the Z core (aiming at 1, 2 or 4 work items per SM).  The fastest
  * shape is kept for this kind of sketch (k, precision, z and log2 of the
  * rows) and used by later sne_embed / sne_embed_batched calls in this process.
- * No shape changes a result.  Synchronizes the stream; out receives the
- * choice and the launch times with it and with the default shape.  Errors:
+ * For a batch with lanes <= 0 and output arrays E, sigma (as sne_embed_batched
+ * takes them; null: skipped) the number of stream lanes (4, 8, 12 or 16) is
+ * then timed over whole batched embeddings and kept for batches of this kind
+ * (G, log2 of the total vertices, k, precision): sne_embed_batched with
+ * lanes = 0 uses it.  No shape and no lane count changes a result.
+ * Synchronizes the stream; out receives the choices and the times.  Errors:
  * SNE_ERR_ARG (FP32 precision, graphs of different z), SNE_ERR_WORKSPACE,
  * the errors of sne_embed. */
 typedef struct sne_tune_result {
   int32_t tn, stages, split_mult; /* chosen launch shape */
   int32_t candidates;             /* shapes timed */
   float best_ms, default_ms;      /* one sketch launch: chosen and default shape */
+  int32_t lanes;                  /* chosen lanes of a batch (0: not tuned) */
+  float batch_ms;                 /* one batched embedding with them */
 } sne_tune_result;
 int sne_autotune_sketch(int32_t G, const sne_csr *graphs, const sne_params *p, int32_t lanes,
-                        void *workspace, size_t ws_bytes, sne_tune_result *out,
-                        sne_stream_t stream);
+                        void *workspace, size_t ws_bytes, float *const *E, double *const *sigma,
+                        sne_tune_result *out, sne_stream_t stream);
 
 /* trunc_log as the tensor-core sketch epilogue evaluates it (Eq. 4 with
  * f = trunc_log, f(x) = max(0, log x)): out[i] = log1p(r[i]) for r[i] > 0 and

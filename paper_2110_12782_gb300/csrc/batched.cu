@@ -21,6 +21,32 @@ namespace {
 
 constexpr int kMaxLanes = 16;
 constexpr int kDefaultLanes = 8;
+
+// Lane counts chosen by the autotuner for lockstep batches, by (number of
+// graphs, log2 of their total vertices, k, precision); lanes = 0 in
+// sne_embed_batched looks here first.
+struct LaneKey {
+  int G, lg, k, prec;
+  bool operator==(const LaneKey &o) const {
+    return G == o.G && lg == o.lg && k == o.k && prec == o.prec;
+  }
+};
+std::mutex g_lane_mu;
+std::vector<std::pair<LaneKey, int>> g_lanes;
+LaneKey lane_key(int32_t G, const sne_csr *graphs, const sne_params *p) {
+  int64_t sum = 0;
+  for (int i = 0; i < G; ++i) sum += graphs[i].n;
+  int lg = 0;
+  while (lg < 62 && ((int64_t)1 << (lg + 1)) <= sum) ++lg;
+  return LaneKey{G, lg, p->k, p->precision};
+}
+int tuned_lanes(int32_t G, const sne_csr *graphs, const sne_params *p) {
+  const LaneKey k = lane_key(G, graphs, p);
+  std::lock_guard<std::mutex> lk(g_lane_mu);
+  for (const auto &e : g_lanes)
+    if (e.first == k) return e.second;
+  return kDefaultLanes;
+}
 constexpr int kMaxDevices = 64;
 
 struct LanePool {
@@ -85,7 +111,7 @@ int make_plan(int32_t G, const sne_csr *graphs, const sne_params *p, int32_t lan
     if (rc) return rc;
     cost[i] = graph_cost(g, *p);
   }
-  const int L = std::min<int>(G, lanes > 0 ? lanes : kDefaultLanes);
+  const int L = std::min<int>(G, lanes > 0 ? lanes : tuned_lanes(G, graphs, p));
   plan->lanes = L;
   plan->order.resize(G);
   std::iota(plan->order.begin(), plan->order.end(), 0);
@@ -228,7 +254,8 @@ float time_sketch(const std::vector<TcSketchJobDesc> &jobs, const TcShape &s0, v
 extern "C" {
 
 int sne_autotune_sketch(int32_t G, const sne_csr *graphs, const sne_params *p, int32_t lanes,
-                        void *ws, size_t ws_bytes, sne_tune_result *out, sne_stream_t stream) {
+                        void *ws, size_t ws_bytes, float *const *E, double *const *sigma,
+                        sne_tune_result *out, sne_stream_t stream) {
   if (G <= 0 || !graphs || !p || !out) return SNE_ERR_ARG;
   TcShape s0;
   if (!embed_tc_shape(&graphs[0], p, &s0)) return SNE_ERR_ARG;  // FP32 path: nothing to tune
@@ -299,6 +326,59 @@ int sne_autotune_sketch(int32_t G, const sne_csr *graphs, const sne_params *p, i
     }
   }
   tc_tune_store(s0.kpad, s0.split, s0.fp16, s0.z, rows, best);
+  // a batch: the number of stream lanes, timed over whole lockstep batches
+  // (the workspace of a lockstep batch does not depend on it)
+  out->lanes = 0;
+  out->batch_ms = 0.f;
+  if (G > 1 && lanes <= 0) {
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return SNE_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+      cudaEventDestroy(e0);
+      return SNE_ERR_CUDA;
+    }
+    if (E && sigma) {
+      int bestL = 0;
+      float bestB = -1.f;
+      for (int L : {4, 8, 12, 16}) {
+        if (L > G) continue;
+        float tb = -1.f;
+        for (int r = 0; r < 2; ++r) {
+          cudaEventRecord(e0, st);
+          const int rc = sne_embed_batched(G, graphs, p, L, ws, arena_bytes, E, sigma, nullptr,
+                                           stream);
+          cudaEventRecord(e1, st);
+          if (rc != SNE_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return rc != SNE_OK ? rc : SNE_ERR_CUDA;
+          }
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (tb < 0.f || ms < tb) tb = ms;
+        }
+        if (bestB < 0.f || tb < bestB) {
+          bestB = tb;
+          bestL = L;
+        }
+      }
+      if (bestL > 0) {
+        const LaneKey key = lane_key(G, graphs, p);
+        std::lock_guard<std::mutex> lk(g_lane_mu);
+        bool found = false;
+        for (auto &e : g_lanes)
+          if (e.first == key) {
+            e.second = bestL;
+            found = true;
+          }
+        if (!found) g_lanes.emplace_back(key, bestL);
+        out->lanes = bestL;
+        out->batch_ms = bestB;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
   out->tn = best.tn;
   out->stages = best.stages > 0 ? best.stages : tc_max_stages(s0.kpad, s0.split, best.tn);
   out->split_mult = best.split_mult;

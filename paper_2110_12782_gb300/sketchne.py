@@ -64,7 +64,8 @@ class sne_csr(ctypes.Structure):
 class sne_tune_result(ctypes.Structure):
     _fields_ = [("tn", ctypes.c_int32), ("stages", ctypes.c_int32), ("split_mult", ctypes.c_int32),
                 ("candidates", ctypes.c_int32), ("best_ms", ctypes.c_float),
-                ("default_ms", ctypes.c_float)]
+                ("default_ms", ctypes.c_float), ("lanes", ctypes.c_int32),
+                ("batch_ms", ctypes.c_float)]
 
 
 class sne_params(ctypes.Structure):
@@ -132,7 +133,7 @@ def lib() -> ctypes.CDLL:
             "sne_chol_inverse_workspace_bytes": [i32, i32, P(ctypes.c_size_t)],
             "sne_chol_inverse": [i32, vp, i32, vp, i32, i32, dbl, vp, ctypes.c_size_t, vp],
             "sne_trunc_log_eval": [i64, vp, vp, vp],
-            "sne_autotune_sketch": [i32, vp, P(sne_params), i32, vp, ctypes.c_size_t,
+            "sne_autotune_sketch": [i32, vp, P(sne_params), i32, vp, ctypes.c_size_t, vp, vp,
                                     P(sne_tune_result), vp],
             "sne_single_pass_svd_workspace_bytes": [i64, i64, i32, P(sne_params),
                                                     P(ctypes.c_size_t)],
@@ -519,19 +520,29 @@ def sne_embed_batched(graphs, p: sne_params, ws: torch.Tensor, E, sigma, status:
            "sne_embed_batched")
 
 
-def sne_autotune_sketch(graphs, p: sne_params, ws: torch.Tensor, lanes: int = 0, stream=None) -> dict:
+def sne_autotune_sketch(graphs, p: sne_params, ws: torch.Tensor, lanes: int = 0, E=None, sigma=None,
+                        stream=None) -> dict:
     """Time the fused tensor-core sketch over its launch shapes for one graph
     (workspace of ``workspace(..., SNE_WS_EMBED)``) or a batch (workspace of
     ``batched_workspace(graphs, p, lanes)``); the fastest shape is used from
-    then on.  Returns the choice and the launch times."""
+    then on.  For a batch with outputs E, sigma (one per graph) and lanes 0,
+    also the number of stream lanes.  Returns the choices and the times."""
     if isinstance(graphs, DeviceGraph):
         graphs = [graphs]
+    G = len(graphs)
+    e_ptrs = s_ptrs = None
+    if E is not None and sigma is not None:
+        if len(E) != G or len(sigma) != G:
+            raise ValueError("one E and one sigma per graph")
+        e_ptrs = (ctypes.c_void_p * G)(*[_ptr(e, torch.float32, "E") for e in E])
+        s_ptrs = (ctypes.c_void_p * G)(*[_ptr(s_, torch.float64, "sigma") for s_ in sigma])
     res = sne_tune_result()
-    _check(lib().sne_autotune_sketch(len(graphs), _csr_array(graphs), ctypes.byref(p), lanes,
-                                     _ptr(ws, torch.uint8, "workspace"), ws.numel(),
+    _check(lib().sne_autotune_sketch(G, _csr_array(graphs), ctypes.byref(p), lanes,
+                                     _ptr(ws, torch.uint8, "workspace"), ws.numel(), e_ptrs, s_ptrs,
                                      ctypes.byref(res), _stream(stream)), "sne_autotune_sketch")
     return {"tn": res.tn, "stages": res.stages, "split_mult": res.split_mult,
-            "candidates": res.candidates, "best_ms": res.best_ms, "default_ms": res.default_ms}
+            "candidates": res.candidates, "best_ms": res.best_ms, "default_ms": res.default_ms,
+            "lanes": res.lanes, "batch_ms": res.batch_ms}
 
 
 def chol_inverse_workspace(n: int, fp64: bool, device="cuda") -> torch.Tensor:

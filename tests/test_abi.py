@@ -127,10 +127,10 @@ def test_building_block_argument_errors_on_the_host(L):
     p32 = sk.sne_params_init(16, 32)
     g1 = (sk.sne_csr * 1)()
     g1[0] = sk.sne_csr(1000, 2000, 256, 256, None)
-    assert L.sne_autotune_sketch(0, g1, ctypes.byref(p32), 0, 256, 1 << 20, ctypes.byref(res), None) == ARG
-    assert L.sne_autotune_sketch(1, g1, ctypes.byref(p32), 0, 256, 1 << 20, None, None) == ARG
+    assert L.sne_autotune_sketch(0, g1, ctypes.byref(p32), 0, 256, 1 << 20, None, None, ctypes.byref(res), None) == ARG
+    assert L.sne_autotune_sketch(1, g1, ctypes.byref(p32), 0, 256, 1 << 20, None, None, None, None) == ARG
     # the FP32 path has no tensor-core sketch to tune
-    assert L.sne_autotune_sketch(1, g1, ctypes.byref(p32), 0, 256, 1 << 20, ctypes.byref(res), None) == ARG
+    assert L.sne_autotune_sketch(1, g1, ctypes.byref(p32), 0, 256, 1 << 20, None, None, ctypes.byref(res), None) == ARG
 
 
 def test_batched_argument_errors_on_the_host(L):

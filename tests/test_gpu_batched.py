@@ -201,10 +201,13 @@ def test_autotune_sketch(sk, batch):
     E1, s1 = run_single(sk, graphs[:1], dev[:1], p)
     assert torch.equal(E0[0], E1[0]) and torch.equal(s0[0], s1[0])
     wsb = sk.batched_workspace(dev, p, 3)
-    rb = sk.sne_autotune_sketch(dev, p, wsb, lanes=3)
+    E, s = outputs(graphs)
+    rb = sk.sne_autotune_sketch(dev, p, wsb, lanes=0, E=E, sigma=s)
     print(f"autotune batch of {len(dev)}: {rb}")
     assert 0 < rb["best_ms"] <= rb["default_ms"]
-    E, s = outputs(graphs)
-    sk.sne_embed_batched(dev, p, wsb, E, s, lanes=3)
+    assert rb["lanes"] in (4, 8, 12, 16) and rb["batch_ms"] > 0
+    for e in E:
+        e.zero_()
+    sk.sne_embed_batched(dev, p, wsb, E, s)  # lanes = 0: the tuned count
     torch.cuda.synchronize()
     assert torch.equal(E[0], E0[0])
