@@ -554,14 +554,15 @@ def run_ours(args, rank: int, world: int) -> None:
         bline = measure_batch(args, rank, world, "batch64", "fp16", ek, ew)
         if bline is not None:
             extra["batch64"] = {k: bline[k] for k in ("value", "ms_per_step", "steps", "warmup",
-                                                       "config", "e2e", "gpu_launches",
+                                                       "config", "e2e", "gpu_launches", "autotune",
                                                        "kernel_ms_per_step_summed_over_lanes")
                                 if k in bline}
             # the same batch in plain FP32 and with FP16 hi/lo pairs
             for prec_b in ("fp32", "fp16x2"):
                 bl = measure_batch(args, rank, world, "batch64", prec_b, ek, ew)
                 if bl is not None:
-                    extra["batch64"][prec_b] = {k: bl[k] for k in ("value", "ms_per_step")}
+                    extra["batch64"][prec_b] = {k: bl[k] for k in ("value", "ms_per_step", "autotune")
+                                                if k in bl}
             if rank == 0 and not args.no_cpu_baseline:
                 extra["batch64"]["error_vs_oracle"] = batch_error_vs_oracle(
                     "batch64", ["fp16", "fp16x2", "fp32"])

@@ -18,9 +18,9 @@
 // x - 1 directly.  c0 = 1 for trunc_log and 0 for f = identity.
 //
 // Kernels here:
-//  * center_mean_partial_kernel / center_finish_kernel: w (FP64, fixed-order
-//    two-stage sum), p = C w^T, q = w C, gamma = s w C w^T - c0, s w as an
-//    FP32 hi/lo pair;
+//  * center_mean_partial_kernel / center_finish_kernel: w (FP32 sums of
+//    64-row groups added in FP64, fixed-order two-stage sum), p = C w^T,
+//    q = w C, gamma = s w C w^T - c0, s w as an FP32 hi/lo pair;
 //  * center_rows_kernel: L~_i = s (W_i - w) in double-float, rounded once
 //    (FP32 rows, or FP16/BF16 rows scaled by a power of two and split into a
 //    hi part and a lo part), and (rho_i, mask_i);
@@ -36,28 +36,35 @@ namespace {
 
 constexpr int kMeanThreads = 256;
 
+// Partial sums of d_i W_i = d_i^a U_i over row chunks.  The reference row w
+// only has to remove the component the entries share: the centred form is an
+// identity for any w, and rho and kappa are computed from the w this gives.
+// So the weights are FP32 powers, each group of 64 rows is summed in FP32
+// (loads of eight rows issued before their multiply-adds) and only the group
+// sums are added in FP64: GB300's FP64 rate would make a per-row FP64 sum the
+// bound of this kernel.
 __global__ void __launch_bounds__(kMeanThreads) center_mean_partial_kernel(
     const float *__restrict__ U, int64_t ldu, int k, int64_t n, const float *__restrict__ deg,
     double alpha, int64_t rows_per_chunk, double *__restrict__ partial) {
-  __shared__ double wsh[64];
+  __shared__ float wsh[64];
   const int64_t r0 = (int64_t)blockIdx.x * rows_per_chunk;
   const int64_t r1 = min64(n, r0 + rows_per_chunk);
+  const float af = (float)alpha;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};  // columns tid + 256 m, k <= 1024
   for (int64_t t0 = r0; t0 < r1; t0 += 64) {
     __syncthreads();
     if (threadIdx.x < 64) {
       const int64_t i = t0 + threadIdx.x;
-      double wv = 0.0;
+      float wv = 0.f;
       if (i < r1) {
         const float d = deg[i];
-        wv = d > 0.f ? pow((double)d, alpha) : 0.0;  // d_i W_i = d_i^a U_i
+        wv = d > 0.f ? powf(d, af) : 0.f;
       }
       wsh[threadIdx.x] = wv;
     }
     __syncthreads();
     const int rows = (int)min64(64, r1 - t0);
-    // eight rows per step, their loads issued before the multiply-adds (the
-    // rows past the chunk have weight 0 and load row t0 again)
+    float a32[4] = {0.f, 0.f, 0.f, 0.f};
     for (int r = 0; r < rows; r += 8) {
       float x[8][4];
 #pragma unroll
@@ -71,11 +78,13 @@ __global__ void __launch_bounds__(kMeanThreads) center_mean_partial_kernel(
       }
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        const double wv = r + u < rows ? wsh[r + u] : 0.0;
+        const float wv = r + u < rows ? wsh[r + u] : 0.f;
 #pragma unroll
-        for (int m = 0; m < 4; ++m) acc[m] = fma(wv, (double)x[u][m], acc[m]);
+        for (int m = 0; m < 4; ++m) a32[m] = fmaf(wv, x[u][m], a32[m]);
       }
     }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) acc[m] += (double)a32[m];
   }
 #pragma unroll
   for (int m = 0; m < 4; ++m) {

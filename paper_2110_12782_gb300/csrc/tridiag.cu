@@ -26,6 +26,8 @@
 #include <cfloat>
 #include <cmath>
 
+#include <algorithm>
+
 #include "sne_internal.cuh"
 
 namespace sne {
@@ -286,18 +288,31 @@ __device__ void tri_solve(const TriLU &f, float *X, int s, int sz, int n, int m)
 // Modified Gram-Schmidt inside every cluster of two or more members, by the
 // whole CTA: member j is normalized, then its component is removed from the
 // later members (a warp per member).  Clusters in order, members in order.
+// A cluster whose members fit in the shared buffer `cb` (cap floats) is
+// copied there first (member-major, coalesced loads and stores of Z's rows):
+// the member vectors are columns of Z, strided in global memory.
 __device__ void tri_cluster_mgs(float *X, int n, const int *cstart, int nc, const int *blk_of,
-                                const int *bstart, float *red, Ctrl *ctrl) {
+                                const int *bstart, float *red, Ctrl *ctrl, float *cb, int cap) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   for (int c = 0; c < nc; ++c) {
     const int m0 = cstart[c], m1 = cstart[c + 1];
     if (m1 - m0 < 2) continue;
     const int b = blk_of[m0];
     const int s = bstart[b], sz = bstart[b + 1] - s;
+    const int mc = m1 - m0;
+    const bool shared = (int64_t)mc * sz <= cap;
+    if (shared) {
+      for (int e = tid; e < mc * sz; e += blockDim.x) {
+        const int i = e / mc, q = e % mc;
+        cb[q * sz + i] = X[(int64_t)(s + i) * n + m0 + q];
+      }
+      __syncthreads();
+    }
     for (int j = m0; j < m1; ++j) {
+      float *xj = shared ? cb + (j - m0) * sz : nullptr;
       float part = 0.f;
       for (int i = tid; i < sz; i += blockDim.x) {
-        const float v = X[(int64_t)(s + i) * n + j];
+        const float v = shared ? xj[i] : X[(int64_t)(s + i) * n + j];
         part += v * v;
       }
       const float nrm = block_sum(part, red);
@@ -305,16 +320,38 @@ __device__ void tri_cluster_mgs(float *X, int n, const int *cstart, int nc, cons
         if (tid == 0) record_error(ctrl, SNE_ERR_NUMERIC, W_EIG);
       }
       const float rn = nrm > 0.f ? 1.0f / sqrtf(nrm) : 0.f;
-      for (int i = tid; i < sz; i += blockDim.x) X[(int64_t)(s + i) * n + j] *= rn;
+      for (int i = tid; i < sz; i += blockDim.x) {
+        if (shared)
+          xj[i] *= rn;
+        else
+          X[(int64_t)(s + i) * n + j] *= rn;
+      }
       __syncthreads();
       for (int q = j + 1 + warp; q < m1; q += nw) {
         float dot = 0.f;
-        for (int i = lane; i < sz; i += 32)
-          dot += X[(int64_t)(s + i) * n + j] * X[(int64_t)(s + i) * n + q];
+        if (shared) {
+          const float *xq = cb + (q - m0) * sz;
+          for (int i = lane; i < sz; i += 32) dot += xj[i] * xq[i];
+        } else {
+          for (int i = lane; i < sz; i += 32)
+            dot += X[(int64_t)(s + i) * n + j] * X[(int64_t)(s + i) * n + q];
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-        for (int i = lane; i < sz; i += 32)
-          X[(int64_t)(s + i) * n + q] -= dot * X[(int64_t)(s + i) * n + j];
+        if (shared) {
+          float *xq = cb + (q - m0) * sz;
+          for (int i = lane; i < sz; i += 32) xq[i] -= dot * xj[i];
+        } else {
+          for (int i = lane; i < sz; i += 32)
+            X[(int64_t)(s + i) * n + q] -= dot * X[(int64_t)(s + i) * n + j];
+        }
+      }
+      __syncthreads();
+    }
+    if (shared) {
+      for (int e = tid; e < mc * sz; e += blockDim.x) {
+        const int i = e / mc, q = e % mc;
+        X[(int64_t)(s + i) * n + m0 + q] = cb[q * sz + i];
       }
       __syncthreads();
     }
@@ -326,7 +363,8 @@ __global__ void __launch_bounds__(kTriEigThreads) tri_eig_kernel(const float *__
                                                        float *__restrict__ w,
                                                        float *__restrict__ Z,
                                                        float *__restrict__ scratch,
-                                                       Ctrl *ctrl) {
+                                                       Ctrl *ctrl, int cbuf_cap) {
+  extern __shared__ __align__(16) float cbuf[];  // cbuf_cap floats: a cluster's vectors
   __shared__ float d[kTriMaxN], e[kTriMaxN], e2[kTriMaxN], lam[kTriMaxN], shift[kTriMaxN];
   __shared__ int bstart[kTriMaxN + 1], blk_of[kTriMaxN], cstart[kTriMaxN + 1];
   __shared__ float bnorm[kTriMaxN];
@@ -434,7 +472,7 @@ __global__ void __launch_bounds__(kTriEigThreads) tri_eig_kernel(const float *__
     tri_solve(f, Z, s, sz, n, m);
   }
   __syncthreads();
-  tri_cluster_mgs(Z, n, cstart, nc, blk_of, bstart, red, ctrl);
+  tri_cluster_mgs(Z, n, cstart, nc, blk_of, bstart, red, ctrl, cbuf, cbuf_cap);
   // a third solve, then orthonormal again (clusters) or normalized (the rest)
   for (int m = tid; m < n; m += blockDim.x) {
     const int b = blk_of[m];
@@ -442,7 +480,7 @@ __global__ void __launch_bounds__(kTriEigThreads) tri_eig_kernel(const float *__
     if (sz > 1) tri_solve(f, Z, s, sz, n, m);
   }
   __syncthreads();
-  tri_cluster_mgs(Z, n, cstart, nc, blk_of, bstart, red, ctrl);
+  tri_cluster_mgs(Z, n, cstart, nc, blk_of, bstart, red, ctrl, cbuf, cbuf_cap);
   for (int m = tid; m < n; m += blockDim.x) {
     const int b = blk_of[m];
     const int s = bstart[b], sz = bstart[b + 1] - s;
@@ -534,7 +572,13 @@ cudaError_t launch_sym_eig_tridiag(const float *A, int32_t n, int32_t lda, float
   if (err != cudaSuccess) return err;
   {
     ProfScope ps_(K_EIG, st);
-    tri_eig_kernel<<<1, kTriEigThreads, 0, st>>>(d, e, n, w, Z, wsc, ctrl);
+    // the cluster buffer: as much shared memory as the kernel may take next
+    // to its static arrays (48 KB of them at kTriMaxN = 1024), at most n^2 floats
+    const int cap = (int)std::min<size_t>((size_t)n * n, (size_t)(160 * 1024) / sizeof(float));
+    err = cudaFuncSetAttribute(tri_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(cap * sizeof(float)));
+    if (err != cudaSuccess) return err;
+    tri_eig_kernel<<<1, kTriEigThreads, cap * sizeof(float), st>>>(d, e, n, w, Z, wsc, ctrl, cap);
   }
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
