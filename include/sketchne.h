@@ -134,12 +134,20 @@ int sne_embed_host(const sne_csr *g_host, const sne_params *p, void *workspace, 
  * (0 = the library's choice, at most 16): largest first, each on the lane
  * with the least estimated work, and the caller's stream waits for all of
  * them, so the outputs are complete when `stream` reaches the end of the call.
- * Each graph's results equal those of sne_embed on that graph.  The lanes are
- * created on the first call on a device (make it before any stream capture);
- * after that the call enqueues work only, and a batch can be captured into a
- * CUDA graph.  Workspace: sne_embed_batched_workspace_bytes (same G, graphs,
- * p and lanes); every lane owns a slice sized for its largest graph.  Errors:
- * those of sne_embed, checked for every graph before anything is enqueued. */
+ * Each graph's results equal those of sne_embed on that graph.  With a
+ * half-precision reconstruction (SNE_BF16 .. SNE_FP16X2) the batch runs in
+ * lockstep: the first halves of all embeddings (up to the sketch operands) on
+ * the lanes, ONE persistent tensor-core launch for the sketches Y and Z of
+ * all graphs (one per distinct z = min(n, zeta)), then the second halves on
+ * the lanes.  lanes = 0 takes the count sne_autotune_sketch chose for a batch
+ * of this kind, else 8.  The lanes are created on the first call on a device
+ * (make it before any stream capture); after that the call enqueues work
+ * only, and a batch can be captured into a CUDA graph.  Workspace:
+ * sne_embed_batched_workspace_bytes (same G, graphs, p and lanes): with FP32
+ * reconstruction every lane owns a slice sized for its largest graph; in
+ * lockstep every graph owns one (the sum of the graphs' sne_embed
+ * workspaces, each rounded up to an operand row).  Errors: those of
+ * sne_embed, checked for every graph before anything is enqueued. */
 int sne_embed_batched_workspace_bytes(int32_t G, const sne_csr *graphs, const sne_params *p,
                                       int32_t lanes, size_t *bytes);
 int sne_embed_batched(int32_t G, const sne_csr *graphs, const sne_params *p, int32_t lanes,
