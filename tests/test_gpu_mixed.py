@@ -11,7 +11,7 @@ BF16 2^-8; hi/lo pairs about u^2, i.e. 2^-22 and 2^-16): a product of two
 rounded operands carries at most 2u relative error per term, the k-term sum a
 few times that relative to the sum of |terms|, and trunc_log passes it with
 slope <= 1.  Stated bounds on Y and Z (relative Frobenius): FP16 5e-3,
-BF16 4e-2, FP16 pairs 1e-4 (the FP32 bound of the benchmark spec), BF16 pairs
+BF16 4e-2, FP16 pairs 1e-4 (the sketch bound stated for FP32), BF16 pairs
 1e-3.  The embedding is compared on the leading block of singular directions
 separated by a relative gap >= 1e-2 (Davis-Kahan): principal-angle sine and
 singular values within 1e-3 for the pairs (the FP32 bound), 1e-2 for FP16
