@@ -2,6 +2,7 @@
 include/sketchne.h declares, and rejects bad arguments on the host (calls that
 return before any CUDA work)."""
 import ctypes
+import math
 import os
 import re
 import types
@@ -131,6 +132,36 @@ def test_building_block_argument_errors_on_the_host(L):
     assert L.sne_autotune_sketch(1, g1, ctypes.byref(p32), 0, 256, 1 << 20, None, None, None, None) == ARG
     # the FP32 path has no tensor-core sketch to tune
     assert L.sne_autotune_sketch(1, g1, ctypes.byref(p32), 0, 256, 1 << 20, None, None, ctypes.byref(res), None) == ARG
+
+
+def test_lockstep_batch_workspace_on_the_host(L):
+    """With a half-precision reconstruction the batch runs in lockstep and
+    every graph keeps its own workspace slice: the batch workspace is the sum
+    of the graphs' sne_embed workspaces (each rounded up to a multiple of 256
+    bytes and of an operand row, 2 * kpad bytes) and does not depend on the
+    number of lanes; with FP32 it is the lanes' slices."""
+    p16 = sk.sne_params_init(16, 64, precision=sk.SNE_FP16X2)
+    graphs = (sk.sne_csr * 3)(sk.sne_csr(5000, 40000, 256, 512, None),
+                              sk.sne_csr(3000, 20000, 768, 1024, None),
+                              sk.sne_csr(7000, 50000, 1280, 1536, None))
+    each = []
+    for g in graphs:
+        b = ctypes.c_size_t(0)
+        assert L.sne_workspace_bytes(g.n, g.nnz, ctypes.byref(p16), sk.SNE_WS_EMBED, ctypes.byref(b)) == 0
+        each.append(b.value)
+    row = 2 * 64  # kpad = 64
+    al = 256 * row // math.gcd(256, row)
+    want = sum((b + al - 1) // al * al for b in each)
+    for lanes in (0, 1, 3):
+        nb = ctypes.c_size_t(0)
+        assert L.sne_embed_batched_workspace_bytes(3, graphs, ctypes.byref(p16), lanes, ctypes.byref(nb)) == 0
+        assert nb.value == want, (lanes, nb.value, want)
+    p32 = sk.sne_params_init(16, 64)
+    one = ctypes.c_size_t(0)
+    assert L.sne_embed_batched_workspace_bytes(3, graphs, ctypes.byref(p32), 1, ctypes.byref(one)) == 0
+    b32 = ctypes.c_size_t(0)
+    assert L.sne_workspace_bytes(7000, 50000, ctypes.byref(p32), sk.SNE_WS_EMBED, ctypes.byref(b32)) == 0
+    assert one.value == (b32.value + 255) // 256 * 256  # one lane: the largest graph's slice
 
 
 def test_batched_argument_errors_on_the_host(L):
