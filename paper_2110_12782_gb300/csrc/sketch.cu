@@ -150,6 +150,12 @@ __global__ void __launch_bounds__(256, 2) fused_sketch_f32_tiled_kernel(
   const int e_count = min(CPT, cols_out - c_begin) * Z;
   const int tid = threadIdx.x;
   const int ty = tid >> 4, tx = tid & 15;  // rows ty*8.., columns tx*8..
+  // the two float4 of a thread's 8 columns are read in swapped order by
+  // threads 4..7 of every 8 (sw = 1): the 8 threads of a 128-bit shared load
+  // phase then cover all 32 banks (in order, columns 8 tx + 0 and 8 tx + 32
+  // fall on the same banks: 2-way conflicts that made the loop bound by shared
+  // memory); the accumulator halves are swapped back before the epilogue
+  const int sw = (tx >> 2) & 1;
   // loader: thread t brings row (t >> 1) of A's tile and column (t >> 1) of
   // B's tile, k-part 4 (t & 1) .. +4, as one float4 each
   const int lr = tid >> 1, lk = 4 * (tid & 1);
@@ -184,8 +190,8 @@ __global__ void __launch_bounds__(256, 2) fused_sketch_f32_tiled_kernel(
     for (int kk = 0; kk < kGK; ++kk) {
       const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 8]);
       const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 8 + 4]);
-      const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 8]);
-      const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 8 + 4]);
+      const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 8 + 4 * sw]);
+      const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 8 + 4 * (sw ^ 1)]);
       const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
       const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
@@ -194,6 +200,16 @@ __global__ void __launch_bounds__(256, 2) fused_sketch_f32_tiled_kernel(
         for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
     }
     buf ^= 1;
+  }
+  if (sw) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float t = acc[i][j];
+        acc[i][j] = acc[i][j + 4];
+        acc[i][j + 4] = t;
+      }
   }
   // epilogue: r = acc + rho_i + mask_i kappa_e, f, sign, segmented sums over Z columns
   float sg[8], kp[8];
