@@ -226,6 +226,11 @@ __global__ void __launch_bounds__(kDThreads) gram_df_partial_kernel(
   const int64_t r1 = min64(n, r0 + rows_per_chunk);
   const int tid = threadIdx.x;
   const int ty = tid >> 3, tx = tid & 7;  // 16 x 8 threads: rows ty*4.., cols tx*8..
+  // threads 4..7 of every 8 read the two float4 of their 8 columns in swapped
+  // order (sw = 1), so that the 8 threads of a 128-bit shared load phase fall
+  // on all 32 banks (else columns 8 tx and 8 tx + 32 share banks: 2-way
+  // conflicts); j < 4 of hi, lo then hold columns 8 tx + 4 sw + j
+  const int sw = (tx >> 2) & 1;
   float hi[4][8], lo[4][8];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -300,8 +305,8 @@ __global__ void __launch_bounds__(kDThreads) gram_df_partial_kernel(
 #pragma unroll
         for (int r = g; r < g + 16; ++r) {
           const float4 av = *reinterpret_cast<const float4 *>(&As[r][ty * 4]);
-          const float4 b_lo = *reinterpret_cast<const float4 *>(&Bs[r][tx * 8]);
-          const float4 b_hi = *reinterpret_cast<const float4 *>(&Bs[r][tx * 8 + 4]);
+          const float4 b_lo = *reinterpret_cast<const float4 *>(&Bs[r][tx * 8 + 4 * sw]);
+          const float4 b_hi = *reinterpret_cast<const float4 *>(&Bs[r][tx * 8 + 4 * (sw ^ 1)]);
           const float a4[4] = {av.x, av.y, av.z, av.w};
           const float b8[8] = {b_lo.x, b_lo.y, b_lo.z, b_lo.w, b_hi.x, b_hi.y, b_hi.z, b_hi.w};
 #pragma unroll
@@ -324,8 +329,8 @@ __global__ void __launch_bounds__(kDThreads) gram_df_partial_kernel(
 #pragma unroll 4
     for (int r = 0; r < kGR; ++r) {
       const float4 av = *reinterpret_cast<const float4 *>(&As[r][ty * 4]);
-      const float4 b_lo = *reinterpret_cast<const float4 *>(&Bs[r][tx * 8]);
-      const float4 b_hi = *reinterpret_cast<const float4 *>(&Bs[r][tx * 8 + 4]);
+      const float4 b_lo = *reinterpret_cast<const float4 *>(&Bs[r][tx * 8 + 4 * sw]);
+      const float4 b_hi = *reinterpret_cast<const float4 *>(&Bs[r][tx * 8 + 4 * (sw ^ 1)]);
       const float a4[4] = {av.x, av.y, av.z, av.w};
       const float b8[8] = {b_lo.x, b_lo.y, b_lo.z, b_lo.w, b_hi.x, b_hi.y, b_hi.z, b_hi.w};
       float al4[4] = {0.f, 0.f, 0.f, 0.f};
@@ -353,7 +358,7 @@ __global__ void __launch_bounds__(kDThreads) gram_df_partial_kernel(
     if (a >= Ka) continue;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const int b = b0 + tx * 8 + j;
+      const int b = b0 + tx * 8 + 4 * ((j >> 2) ^ sw) + (j & 3);
       if (b < Kb) P[(size_t)a * Kb + b] = (double)hi[i][j] + (double)lo[i][j];
     }
   }
