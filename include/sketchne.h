@@ -73,11 +73,12 @@ typedef struct sne_csr {
  *  h      sketch size of Y  (h = d + s1, Alg. 4)   l      sketch size of Z (l = d + s2, Alg. 4)
  *  zeta   sparse-sign column density z (Alg. 3); the library uses z = min(n, zeta) <= 64
  *  s_eig  oversampling of Alg. 5 (k + s_eig columns of Omega)
- *  row_block  rows of L' per batch of Eq. 4 (0 = library's choice)
+ *  row_block  rows of L' per batch of Eq. 4 in the paper; the fused kernels never
+ *             store a block of M-hat and work in 128-row tiles whatever it is
  *  precision  SNE_FP32 | SNE_BF16 | SNE_FP16 | SNE_BF16X2 | SNE_FP16X2 (L'R' reconstruction)
  *  f      SNE_F_TRUNC_LOG (NetMF) or SNE_F_IDENTITY (Problem 1 with f = id)
  *  orth   SNE_ORTH_EIGSVD (Alg. 5 as printed) or SNE_ORTH_CHOLQR
- *  alpha  exponent of the modified Laplacian D^-alpha A D^-alpha, in (0, 0.5]
+ *  alpha  exponent of the modified Laplacian D^-alpha A D^-alpha, in (0, 1] (paper: 0.5, 0.4)
  *  b      number of negative samples (Eq. 1)       seed   seed of all random draws */
 typedef struct sne_params {
   int32_t k, q, T, d, h, l, zeta, s_eig, row_block, precision, f, orth;
